@@ -1,0 +1,200 @@
+"""FP64 reference of Anderson acceleration for gradient descent (Sec. 2.1, Sec. 3).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Contents, each following the paper's statement in its own order:
+  aa_alpha         Alg. 1 step 2, eq. AAopt with the l2 norm: constrained
+                   weights alpha (sum alpha = 1) from the KKT system.
+  aa_update_alpha  Alg. 1 step 3, eq. AAupdate0 with damping beta.
+  aa_gamma         eqs. Ak, AAopt2, solveGamma: unconstrained gamma by a
+                   Householder QR of the explicit n x M_k matrix (the oracle
+                   refactors every iteration; a rank-updated QR as in
+                   Sec. 2.1 gives the same factors up to rounding).
+  aa_gd            Alg. 2: l2-AA on the steepest-descent map G(p) = p - eta*grad J(p)
+                   (eq. GD) with the backtracking line search between the AA
+                   point p~ and the plain point p-bar.
+  gmres_full       full-memory GMRES (Sec. 5.1, eqs. Krylov, GMRES), used to
+                   pin AA on a linear problem.
+
+Readings of points the paper leaves open (shared with the CUDA driver):
+  * A_k / f_k are built from the gradients at the last M_k+1 ACCEPTED iterates;
+    with a fixed eta the factor -eta cancels, so gamma = argmin||dG g - G_k||.
+  * Rank safeguard: while min_j|R_jj| < RANK_TOL * max_j|R_jj| drop the oldest
+    column and refactor (the paper is silent).
+  * Line search (Alg. 2 step 4): lambda in (1, 1/2, 1/4, 1/8); accept the first
+    with J(p_lam) <= J(p_k) + c1*min(0, <grad_k, p_lam - p_k>), c1 = 1e-4;
+    otherwise lambda = 0 (the plain gradient step, taken without a test).
+  * Bound constraint: after each update p is clipped elementwise to
+    [lo, hi] (physical velocity bounds mapped to m = 1/c^2), identically in
+    every trial; the Armijo test is applied to the clipped point.
+  * Alg. 2 input step p_1 = G(p_0) is taken without a line search.
+"""
+import numpy as np
+
+RANK_TOL = 1e-6
+LAMBDAS = (1.0, 0.5, 0.25, 0.125)
+ARMIJO_C1 = 1e-4
+
+
+# --------------------------------------------------------------------------
+# Alg. 1 (general form, used as a pin of the gamma form)
+# --------------------------------------------------------------------------
+
+def aa_alpha(F):
+    """alpha = argmin ||F alpha||_2 s.t. sum(alpha) = 1   (eq. AAopt, l2 norm).
+
+    KKT system [[2 F^T F, 1], [1^T, 0]] [alpha; mu] = [0; 1].
+    """
+    F = np.asarray(F, dtype=np.float64)
+    m = F.shape[1]
+    K = np.zeros((m + 1, m + 1))
+    K[:m, :m] = 2.0 * F.T @ F
+    K[:m, m] = 1.0
+    K[m, :m] = 1.0
+    rhs = np.zeros(m + 1)
+    rhs[m] = 1.0
+    return np.linalg.solve(K, rhs)[:m]
+
+
+def aa_update_alpha(P, GP, alpha, beta=1.0):
+    """eq. AAupdate0: (1-beta) sum alpha_i p_i + beta sum alpha_i G(p_i)."""
+    P, GP = np.asarray(P), np.asarray(GP)
+    return (1.0 - beta) * (P @ alpha) + beta * (GP @ alpha)
+
+
+def gamma_to_alpha(gamma):
+    """Inverse of gamma_i = alpha_0 + ... + alpha_i (Sec. 2.1), with sum alpha = 1."""
+    g = np.concatenate([[0.0], np.asarray(gamma, dtype=np.float64), [1.0]])
+    return np.diff(g)
+
+
+# --------------------------------------------------------------------------
+# gamma form (eqs. Ak, AAopt2, solveGamma, AA2_update)
+# --------------------------------------------------------------------------
+
+def aa_gamma(A, f, rank_tol=RANK_TOL):
+    """Least-squares gamma = argmin ||A gamma - f||_2 by Householder QR.
+
+    Columns of A are ordered oldest first.  Returns (gamma, first) where
+    ``first`` is the number of oldest columns dropped by the rank safeguard;
+    gamma has A.shape[1] - first entries and refers to A[:, first:].
+    """
+    A = np.asarray(A, dtype=np.float64)
+    f = np.asarray(f, dtype=np.float64)
+    first = 0
+    while A.shape[1] - first > 0:
+        Q, R = np.linalg.qr(A[:, first:], mode="reduced")
+        d = np.abs(np.diag(R))
+        if d.min() >= rank_tol * d.max() and d.max() > 0.0:
+            gamma = np.linalg.solve(R, Q.T @ f) if R.shape[0] > 1 else (Q.T @ f) / R[0, 0]
+            return np.atleast_1d(gamma), first
+        first += 1
+    return np.zeros(0), first
+
+
+def anderson_point(P, Gr, eta, rank_tol=RANK_TOL):
+    """Alg. 2 steps 1-3 for the history P = [p_{k-Mk}..p_k], Gr = [G_{k-Mk}..G_k].
+
+    Returns (p_bar, p_tilde, gamma, Mk_used).
+      p_bar   = G(p_k) = p_k - eta G_k                         (step 1, eq. GD)
+      gamma   = argmin || [G_{i+1} - G_i] gamma - G_k ||        (step 2; the -eta of
+                 f_k = -eta G_k and A_k = -eta [dG] cancels)
+      p_tilde = G(p_k) - sum_i gamma_i [G(p_{i+1}) - G(p_i)]   (step 3, eq. AA2_update)
+    """
+    shape = np.shape(P[-1])
+    P = [np.asarray(p, dtype=np.float64).ravel() for p in P]
+    Gr = [np.asarray(g, dtype=np.float64).ravel() for g in Gr]
+    gk = Gr[-1]
+    p_bar = P[-1] - eta * gk
+    Mk = len(P) - 1
+    if Mk == 0:
+        return p_bar.reshape(shape), p_bar.reshape(shape).copy(), np.zeros(0), 0
+    dG = np.stack([Gr[i + 1] - Gr[i] for i in range(Mk)], axis=1)
+    gamma, first = aa_gamma(dG, gk, rank_tol)
+    p_tilde = p_bar.copy()
+    for j, gj in enumerate(gamma):
+        i = first + j
+        dGp = (P[i + 1] - eta * Gr[i + 1]) - (P[i] - eta * Gr[i])
+        p_tilde -= gj * dGp
+    return p_bar.reshape(shape), p_tilde.reshape(shape), gamma, Mk - first
+
+
+def aa_gd(grad_fn, p0, M, eta, iters, line_search=True, bounds=None,
+          lambdas=LAMBDAS, c1=ARMIJO_C1, rank_tol=RANK_TOL, misfit_fn=None):
+    """Alg. 2: l2-based AA for gradient descent.
+
+    grad_fn(p) -> (J, grad); misfit_fn(p) -> J (defaults to grad_fn(p)[0]).
+    Iteration k = 0 is the input step p_1 = G(p_0); iterations k >= 1 are
+    Alg. 2 steps 1-5.  Returns a dict with the accepted iterates ``p``, their
+    misfits ``J`` (J[k] = J(p_k), len iters+1), ``lam`` and ``Mk`` per
+    iteration and the number of misfit-only evaluations ``n_trials``.
+    """
+    if misfit_fn is None:
+        misfit_fn = lambda p: grad_fn(p)[0]
+    clip = (lambda p: np.clip(p, bounds[0], bounds[1])) if bounds is not None else (lambda p: p)
+    p = np.asarray(p0, dtype=np.float64).copy()
+    J, g = grad_fn(p)
+    P, Gr = [p], [g]
+    out = {"p": [p], "J": [J], "lam": [], "Mk": [], "gamma": [], "n_trials": 0}
+    for k in range(iters):
+        if k == 0:
+            p_next = clip(p - eta * g)       # Alg. 2 input: p_1 = G(p_0)
+            lam, Mk, gamma = 0.0, 0, np.zeros(0)
+        else:
+            p_bar, p_tilde, gamma, Mk = anderson_point(P, Gr, eta, rank_tol)
+            lam = 0.0
+            if line_search and Mk > 0:
+                for trial in lambdas:
+                    cand = clip(trial * p_tilde + (1.0 - trial) * p_bar)
+                    Jc = misfit_fn(cand)
+                    out["n_trials"] += 1
+                    if Jc <= J + c1 * min(0.0, float(np.vdot(g, cand - p))):
+                        lam = trial
+                        break
+            elif not line_search:
+                lam = 1.0
+            p_next = clip(lam * p_tilde + (1.0 - lam) * p_bar)
+        p = p_next
+        J, g = grad_fn(p)
+        P.append(p)
+        Gr.append(g)
+        if len(P) > M + 1:
+            P.pop(0)
+            Gr.pop(0)
+        out["p"].append(p)
+        out["J"].append(J)
+        out["lam"].append(lam)
+        out["Mk"].append(Mk)
+        out["gamma"].append(gamma)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Full-memory GMRES (Sec. 5.1)
+# --------------------------------------------------------------------------
+
+def gmres_full(A, b, x0, kmax):
+    """Iterates x_1..x_kmax of GMRES on A x = b: x_k = x0 + V_k y_k minimising
+    ||b - A x_k||_2 over the Krylov space K_k(A, r_0) (Arnoldi with modified
+    Gram-Schmidt; the small least-squares problem by a library lstsq)."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    r0 = b - A @ x0
+    beta = np.linalg.norm(r0)
+    V = np.zeros((n, kmax + 1))
+    H = np.zeros((kmax + 1, kmax))
+    V[:, 0] = r0 / beta
+    xs = []
+    for k in range(kmax):
+        w = A @ V[:, k]
+        for i in range(k + 1):
+            H[i, k] = V[:, i] @ w
+            w = w - H[i, k] * V[:, i]
+        H[k + 1, k] = np.linalg.norm(w)
+        if H[k + 1, k] > 0:
+            V[:, k + 1] = w / H[k + 1, k]
+        e1 = np.zeros(k + 2)
+        e1[0] = beta
+        y = np.linalg.lstsq(H[:k + 2, :k + 1], e1, rcond=None)[0]
+        xs.append(x0 + V[:, :k + 1] @ y)
+    return xs

@@ -1,0 +1,150 @@
+"""Pins of the FP64 Anderson-acceleration oracle (oracle/aa.py), CPU only.
+
+Checked against: plain steepest descent (M = 0, Sec. 2.1), the Picard bound
+(Sec. 2.1), the constrained alpha form (eq. AAopt, solved through its KKT
+system), the multi-secant characterisation (Sec. 5.2, eqs. aa_secant_update,
+aaFnorm, multisecant), an SVD least-squares solver, and full-memory GMRES on a
+linear problem (Sec. 5.1; Walker & Ni 2011: x_AA(k+1) = G(x_GMRES(k))).
+"""
+import numpy as np
+import pytest
+
+from oracle import aa
+
+
+def _quadratic(n=30, seed=0, cond=50.0):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(np.linspace(1.0, cond, n)) @ Q.T
+    b = rng.standard_normal(n)
+
+    def grad_fn(x):
+        return 0.5 * x @ A @ x - b @ x, A @ x - b
+    return A, b, grad_fn
+
+
+def test_memory_zero_is_steepest_descent_bitwise():
+    A, b, gf = _quadratic()
+    eta = 1.0 / 50.0
+    x0 = np.zeros(30)
+    out = aa.aa_gd(gf, x0, M=0, eta=eta, iters=15)
+    x = x0.copy()
+    for k in range(15):
+        x = x - eta * (A @ x - b)
+        assert np.array_equal(out["p"][k + 1], x)
+
+
+def test_fixed_point_iff_zero_gradient():
+    A, b, gf = _quadratic()
+    xs = np.linalg.solve(A, b)
+    _, g = gf(xs)
+    assert np.linalg.norm((xs - 0.01 * g) - xs) < 1e-12
+
+
+def test_gamma_equals_alpha_form_and_update():
+    rng = np.random.default_rng(1)
+    n, m = 50, 6
+    F = rng.standard_normal((n, m + 1))          # f_{k-m} .. f_k
+    P = rng.standard_normal((n, m + 1))
+    GP = P + F                                   # G(p_i) = p_i + f_i
+    alpha = aa.aa_alpha(F)
+    assert alpha.sum() == pytest.approx(1.0, abs=1e-14)
+    A = np.diff(F, axis=1)                       # eq. Ak
+    gamma, first = aa.aa_gamma(A, F[:, -1])
+    assert first == 0
+    np.testing.assert_allclose(aa.gamma_to_alpha(gamma), alpha, rtol=1e-10, atol=1e-12)
+    upd_alpha = aa.aa_update_alpha(P, GP, alpha, beta=1.0)
+    upd_gamma = GP[:, -1] - np.diff(GP, axis=1) @ gamma    # eq. AA2_update
+    np.testing.assert_allclose(upd_gamma, upd_alpha, rtol=1e-10, atol=1e-12)
+    # AA is never worse than Picard: ||F alpha|| <= ||f_k||
+    assert np.linalg.norm(F @ alpha) <= np.linalg.norm(F[:, -1]) + 1e-14
+
+
+def test_gamma_matches_svd_least_squares():
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((200, 8))
+    f = rng.standard_normal(200)
+    g, first = aa.aa_gamma(A, f)
+    ref = np.linalg.lstsq(A, f, rcond=None)[0]
+    assert first == 0
+    np.testing.assert_allclose(g, ref, rtol=1e-11, atol=1e-13)
+
+
+def test_rank_safeguard_drops_oldest_column():
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((40, 4))
+    A[:, 0] = A[:, 2] * 3.0 + 1e-9 * rng.standard_normal(40)   # oldest column nearly dependent
+    f = rng.standard_normal(40)
+    g, first = aa.aa_gamma(A, f)
+    assert first == 1 and len(g) == 3
+    np.testing.assert_allclose(g, np.linalg.lstsq(A[:, 1:], f, rcond=None)[0], rtol=1e-10)
+
+
+def test_picard_bound_along_an_aa_run():
+    A, b, gf = _quadratic(seed=4)
+    eta = 1.0 / 50.0
+    out = aa.aa_gd(gf, np.zeros(30), M=4, eta=eta, iters=12, line_search=False)
+    ps = out["p"]
+    for k in range(1, 12):
+        lo = max(0, k - 4)
+        F = np.stack([-eta * gf(p)[1] for p in ps[lo:k + 1]], axis=1)
+        gamma = out["gamma"][k]
+        alpha = aa.gamma_to_alpha(gamma)
+        Fa = F[:, F.shape[1] - len(alpha):] @ alpha
+        assert np.linalg.norm(Fa) <= np.linalg.norm(F[:, -1]) * (1 + 1e-12)
+
+
+def test_multisecant_characterisation():
+    """p_tilde = p_k - S_k f_k with S_k = -I + (P+D) D^+ : S_k D_k = P_k and S_k
+    has the least ||S + I||_F among all solutions (Sec. 5.2)."""
+    A, b, gf = _quadratic(n=25, seed=5)
+    eta = 0.02
+    rng = np.random.default_rng(5)
+    Ps = [rng.standard_normal(25) for _ in range(5)]
+    Gs = [gf(p)[1] for p in Ps]
+    p_bar, p_tilde, gamma, Mk = aa.anderson_point(Ps, Gs, eta)
+    assert Mk == 4
+    fs = [-eta * g for g in Gs]
+    Pm = np.stack([Ps[i + 1] - Ps[i] for i in range(4)], axis=1)
+    Dm = np.stack([fs[i + 1] - fs[i] for i in range(4)], axis=1)
+    S = -np.eye(25) + (Pm + Dm) @ np.linalg.pinv(Dm)
+    np.testing.assert_allclose(S @ Dm, Pm, atol=1e-10)
+    np.testing.assert_allclose(Ps[-1] - S @ fs[-1], p_tilde, rtol=1e-9, atol=1e-11)
+    # any other solution S + E with E D = 0 is farther from -I
+    E = rng.standard_normal((25, 25))
+    E = E - E @ Dm @ np.linalg.pinv(Dm)
+    assert np.linalg.norm(S + E + np.eye(25)) > np.linalg.norm(S + np.eye(25))
+
+
+def test_gmres_oracle_solves_in_n_steps():
+    A, b, _ = _quadratic(n=8, seed=6)
+    xs = aa.gmres_full(A, b, np.zeros(8), 8)
+    res = [np.linalg.norm(A @ x - b) for x in xs]
+    assert all(res[i + 1] <= res[i] * (1 + 1e-12) for i in range(7))
+    assert res[-1] < 1e-10 * np.linalg.norm(b)
+
+
+def test_full_memory_aa_is_gmres_mapped_by_G():
+    """Sec. 2.1 / 5.1: with M = infinity, beta = 1 and no line search, AA on
+    G(x) = x - eta (A x - b) satisfies x_AA(k+1) = G(x_GMRES(k))."""
+    n, K = 30, 10
+    A, b, gf = _quadratic(n=n, seed=7)
+    eta = 1.0 / 50.0
+    x0 = np.zeros(n)
+    out = aa.aa_gd(gf, x0, M=100, eta=eta, iters=K, line_search=False)
+    xg = aa.gmres_full(A, b, x0, K)
+    G = lambda x: x - eta * (A @ x - b)
+    for k in range(1, K):
+        ref = G(xg[k - 1])
+        assert np.linalg.norm(out["p"][k + 1] - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_line_search_keeps_misfit_monotone_and_beats_sd():
+    A, b, gf = _quadratic(seed=8, cond=200.0)
+    eta = 1.0 / 200.0
+    out = aa.aa_gd(gf, np.zeros(30), M=5, eta=eta, iters=30)
+    J = np.array(out["J"])
+    assert (np.diff(J[1:]) <= 1e-12 * np.abs(J[1:-1])).all()
+    sd = aa.aa_gd(gf, np.zeros(30), M=0, eta=eta, iters=30)
+    Jstar = gf(np.linalg.solve(A, b))[0]
+    assert (J[-1] - Jstar) < 1e-3 * (sd["J"][-1] - Jstar)
