@@ -1,0 +1,374 @@
+"""Benchmark: Anderson-accelerated FWI on the batched workload (400 x 150 grid,
+dx 20 m, 12 dipping layers cut by 2 normal faults, 32 shots with 60-400
+receivers, Ricker 8 Hz, dt 1.5 ms, 2500 steps, AA(10)).
+
+One step = one iteration of Alg. 2 on the GPU: the adjoint sweep with the
+imaging condition (reusing the forward wavefield of the accepted trial), the
+shot sum, the AA(10) step (FP64 Gram / solve), the line-search trial forward
+sweep(s) with receiver gather and misfit, and the combine.  Metric: grid-point
+updates per second, counting every forward and adjoint pass the step ran
+(sum_s nt_s * NZ * NX per pass).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the checker of this library) on
+the host cores, on a bounded sample of the same workload.  Under torchrun
+(N > 1) every rank runs an independent replica (the path has no exchange step
+on one problem: replicas only) and rank 0 prints the line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "fwi-batched-400x150-32shots-2500steps-aa10"
+METRIC = "grid-pt updates/s (fwd+adj)"
+UNIT = "grid-pt updates/s"
+# Algorithmic bytes per grid-point update (FP32 fields):
+#   forward  k_fwd: read u^n, u^{n-1}, W; write u^{n+1}                       = 16 B
+#   adjoint  k_adj: read z^{n+1}, z^{n+2}, W, u^n; write z^n; img read+write  = 28 B
+BYTES_FWD = 16
+BYTES_ADJ = 28
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2008_11778_gb300", "csrc", "wave_kernels.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    rec = d.get(kernel)
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("bytes_per_launch_full")
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_sample(prob, shots, reps=1):
+    """Time the oracle's FWI gradient (forward + adjoint) on `shots` shots at
+    full record length; returns (updates/s, seconds, cores, sample text)."""
+    import oracle
+    g = prob.geom.subset(shots)
+    d_obs = oracle.forward(g, prob.m_true)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.fwi_gradient(g, prob.m_start, d_obs)
+    dt = time.perf_counter() - t0
+    upd = 2 * g.updates_per_pass() * reps
+    return upd / dt, dt, oracle.num_threads(), "%d of %d shots at full nt=%d, %d gradient(s)" % (
+        len(shots), prob.geom.S, int(g.nt.max()), reps)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2008_11778_gb300 import synth
+    prob = synth.batched()
+    import oracle
+    cores = oracle.num_threads()
+    nsh = min(prob.geom.S, max(1, cores))
+    shots = list(range(nsh))
+    times = []
+    upd = 2 * prob.geom.subset(shots).updates_per_pass()
+    for i in range(args.warmup + args.steps):
+        v, dt, cores, sample = oracle_sample(prob, shots)
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * float(np.mean(times))
+    value = upd / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": sample, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample + " per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def active_points(geom, n):
+    return int((geom.nt > n).sum()) * geom.NZ * geom.NX
+
+
+def run_ours(args):
+    import torch
+    from paper_2008_11778_gb300 import aafwi, solve, synth
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob = synth.batched()
+    g = prob.geom
+    lo, hi = prob.m_bounds
+    plan = aafwi.Plan(g, c_max=prob.c_bounds[1])
+    # observed data from this library's own forward on the true model
+    m_true = torch.as_tensor(prob.m_true.astype(np.float32), device=dev)
+    d_obs = torch.empty(plan.trace_count, device=dev)
+    plan.model_forward(m_true, d_obs)
+    m0 = torch.as_tensor(prob.m_start.astype(np.float32), device=dev)
+    run = solve.AAInversion(plan, d_obs, m0, M=prob.M, bounds=(lo, hi))
+    upd_pass = g.updates_per_pass()
+    # warm-up: the first iterations (input step and short histories)
+    for _ in range(args.warmup):
+        run.step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    nf0, na0 = run.n_forward, run.n_adjoint
+    l0 = aafwi.launch_count()
+    # per-step events around the gradient (adjoint sweep) and the rest
+    evs = []
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e_start.record(stream)
+    t0 = time.perf_counter()
+    adj_ms, fwd_ms = [], []
+    for _ in range(args.steps):
+        # Alg. 2 iteration, instrumented: time the pieces on the launching stream
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nf_before = run.n_forward
+        a0.record(stream)
+        run.step()
+        a1.record(stream)
+        evs.append((a0, a1, run.n_forward - nf_before))
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = aafwi.launch_count() - l0
+    clk = clocks.stop()
+    ms_total = e_start.elapsed_time(e_end)
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    nf, na = run.n_forward - nf0, run.n_adjoint - na0
+    upd = (nf + na) * upd_pass
+    value = ws * upd / (ms_total / 1e3)
+
+    # dominant kernel: adjoint sweep timed alone (reuse of a stored forward)
+    kt = time_sweeps(plan, run, dev, args.kernel_reps)
+    peak, peak_kind = read_peaks()
+    pts_launch = sum(active_points(g, n) for n in range(int(g.nt.max()))) / int(g.nt.max())
+    adj_bytes = BYTES_ADJ * pts_launch
+    fwd_bytes = BYTES_FWD * pts_launch
+    adj_gbs = adj_bytes / (kt["adj_ms_per_launch"] * 1e-3) / 1e9
+    fwd_gbs = fwd_bytes / (kt["fwd_ms_per_launch"] * 1e-3) / 1e9
+    traffic = traffic_record("k_adj")
+    roofline = {"bound": "hbm", "kernel": "k_adj (adjoint step + imaging)", "achieved": adj_gbs,
+                "peak": peak, "unit": "GB/s", "frac": adj_gbs / peak, "peak_kind": peak_kind,
+                "traffic": traffic, "bytes_per_launch": adj_bytes,
+                "ms_per_launch": kt["adj_ms_per_launch"],
+                "forward_kernel": {"kernel": "k_fwd", "achieved": fwd_gbs, "frac": fwd_gbs / peak,
+                                   "bytes_per_launch": fwd_bytes, "ms_per_launch": kt["fwd_ms_per_launch"]}}
+
+    e2e = run_e2e(plan, prob, dev, args.e2e_steps) if args.e2e_steps > 0 else None
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": [g.nz, g.nx], "padded": [g.NZ, g.NX],
+                           "shots": g.S, "nt": int(g.nt.max()), "M": prob.M,
+                           "checkpoint_every": plan.info.checkpoint_every,
+                           "l2": "inputs larger than L2 (wavefield history %.1f GB)" % (
+                               plan.info.workspace_bytes / 1e9),
+                           "passes": {"forward": nf, "adjoint": na},
+                           "fwi_iterations_per_s": args.steps / (ms_total / 1e3),
+                           "J_over_J0": run.J / run.J0},
+                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "host_wall_s": wall}
+        print(json.dumps(line), flush=True)
+    run.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def time_sweeps(plan, run, dev, reps):
+    """CUDA-event time of the forward sweep (model_forward) and of the adjoint
+    sweep (adjoint_gradient reusing it) on the launching stream; per-launch
+    averages include the gaps between launches."""
+    import torch
+    stream = torch.cuda.current_stream()
+    nt = int(plan.geom.nt.max())
+    grad = torch.empty_like(run.p)
+    m = run.p
+    f_ms, a_ms = [], []
+    for _ in range(reps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        plan.model_forward(m)
+        e1.record(stream)
+        plan.adjoint_gradient(0, m, None, run.d_obs, grad, sync=False, reuse_forward=True)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        f_ms.append(e0.elapsed_time(e1))
+        a_ms.append(e1.elapsed_time(e2))
+    return {"fwd_ms_per_launch": statistics.median(f_ms) / nt,
+            "adj_ms_per_launch": statistics.median(a_ms) / nt}
+
+
+def run_e2e(plan, prob, dev, steps):
+    """The FWI gradient through the public call with host buffers: each step
+    copies m and d_obs from pinned host memory, runs adjoint_gradient (forward
+    + adjoint), and reads the gradient and J back."""
+    import torch
+    g = prob.geom
+    m_h = torch.as_tensor(prob.m_start.astype(np.float32)).pin_memory()
+    d_dev = torch.empty(plan.trace_count, device=dev)
+    plan.model_forward(torch.as_tensor(prob.m_true.astype(np.float32), device=dev), d_dev)
+    d_h = d_dev.cpu().pin_memory()
+    g_h = torch.empty_like(m_h).pin_memory()
+    m_d = torch.empty_like(m_h, device=dev)
+    o_d = torch.empty_like(d_h, device=dev)
+    gr_d = torch.empty_like(m_d)
+    stream = torch.cuda.current_stream()
+
+    def one():
+        m_d.copy_(m_h, non_blocking=True)
+        o_d.copy_(d_h, non_blocking=True)
+        plan.adjoint_gradient(0, m_d, None, o_d, gr_d, sync=False)
+        g_h.copy_(gr_d, non_blocking=True)
+        return plan.read_misfit()          # D2H of J, synchronises
+
+    one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    upd = 2 * g.updates_per_pass()
+    h2d = m_h.numel() * 4 + d_h.numel() * 4
+    d2h = g_h.numel() * 4 + 8
+    return {"value": upd / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": ms, "call": "aafwi_adjoint_gradient (FWI) with host-resident m and d_obs"}
+
+
+def cpu_baseline(prob):
+    import oracle
+    cores = oracle.num_threads()
+    nsh = min(prob.geom.S, max(1, cores))
+    v, dt, cores, sample = oracle_sample(prob, list(range(nsh)))
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--kernel-reps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * aafwi.h -- C ABI of the GB300 (sm_103a) library for the hot path of
+ * Anderson-accelerated seismic inversion (Yang, "Anderson Acceleration for
+ * Seismic Inversion", 2020): the adjoint-state FWI / LSRTM gradient of the
+ * 2D constant-density acoustic wave equation and the l2 Anderson step on the
+ * steepest-descent fixed-point map.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Every call returns an int status: AAFWI_OK (0) or one of AAFWI_ERR_*.
+ *    No C++ exception crosses this boundary.  aafwi_last_error() returns a
+ *    human-readable message for the last failure on a plan (or, for a NULL
+ *    plan, the last failure of a create call on this thread).
+ *  * Arrays named "device" are CUDA device pointers owned by the caller, of
+ *    FP32 unless stated.  Arrays named "host" are ordinary host pointers.
+ *  * Model-sized arrays are the PHYSICAL grid, row-major [nz][nx] (x fastest).
+ *  * Trace arrays are CSR by shot: shot s occupies trace_count_s = nt_s*nrec_s
+ *    consecutive floats starting at the sum of the counts of shots 0..s-1,
+ *    time-major [nt_s][nrec_s].  Sample n of a trace is u^{n+1} (n = 0..nt_s-1).
+ *  * `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on it, except that a non-NULL `*_host` output makes the
+ *    call synchronise the stream before returning.
+ *  * All arithmetic runs in this library's CUDA kernels; there is no CPU
+ *    fallback.  Workspace (wavefield history or checkpoints, per-shot image
+ *    accumulators, traces, reduction partials) belongs to the plan and is
+ *    allocated once by aafwi_plan_create with cudaMalloc.
+ *
+ * Discretisation (the paper leaves it open; this library's reading):
+ *   u^{n+1} = G (2 u^n - G u^{n-1} + W (L u^n + s^n)),  u^0 = u^{-1} = 0,
+ *   W = dt^2 / m on the padded grid (model edge-replicated into an nb-cell
+ *   sponge on all four sides), G = g(d_z) g(d_x) with g(d) = exp(-(0.015 d)^2)
+ *   for a cell d cells into the sponge, L the 8th-order 5-point-per-axis
+ *   Laplacian with zero values outside the padded grid, s^n the Ricker sample
+ *   w(t_n) / (dx dz) at the source cell.
+ */
+#ifndef AAFWI_H
+#define AAFWI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define AAFWI_OK            0
+#define AAFWI_ERR_ARG       1   /* invalid argument (NULL, size, index, duplicate) */
+#define AAFWI_ERR_CFL       2   /* c_max*dt/min(dx,dz) above the stability limit 0.55 */
+#define AAFWI_ERR_OOB       3   /* source / receiver outside the physical grid */
+#define AAFWI_ERR_NAN       4   /* model has a non-finite or non-positive value */
+#define AAFWI_ERR_TIMEOUT   5   /* a bounded device-side wait ran out */
+#define AAFWI_ERR_CUDA      6   /* a CUDA runtime call failed */
+#define AAFWI_ERR_NOMEM     7   /* workspace does not fit the budget / device */
+#define AAFWI_ERR_STATE     8   /* call out of order (e.g. reuse without a stored forward) */
+
+/* adjoint_gradient modes */
+#define AAFWI_MODE_FWI      0   /* unknown m = 1/c^2:  J = 1/2||F(m) - d||^2  (eq. FWI) */
+#define AAFWI_MODE_LSRTM    1   /* unknown rho, m_r = rho m0: J = 1/2||L rho - d||^2 (eq. LSRTM) */
+
+/* adjoint_gradient flags */
+#define AAFWI_REUSE_FORWARD 1   /* skip the forward pass: the last aafwi_model_forward
+                                   on this plan (FWI) ran on the same model contents */
+
+typedef struct aafwi_plan aafwi_plan;
+typedef struct aafwi_aa aafwi_aa;
+typedef void *aafwi_stream;     /* cudaStream_t */
+
+/* Grid: nx, nz physical cells; nb sponge cells on each side; spacing (m);
+ * time step (s); c_max = largest velocity the plan will see (m/s), used for
+ * the CFL check at creation. */
+typedef struct {
+    int nx, nz, nb;
+    double dx, dz, dt;
+    double c_max;
+} aafwi_grid;
+
+/* Shots (host arrays, copied at creation): S shots; source cell (physical
+ * iz, ix); record length nt[s] (steps); receivers in CSR form rec_off[S+1]
+ * into rec_iz/rec_ix (physical cells).  Receivers of one shot must be
+ * distinct cells. */
+typedef struct {
+    int S;
+    const int *src_iz, *src_ix;
+    const int *nt;
+    const int *rec_off;
+    const int *rec_iz, *rec_ix;
+} aafwi_shots;
+
+/* Plan options (all zero = defaults). */
+typedef struct {
+    size_t max_workspace_bytes;  /* 0: 85% of the free device memory at creation */
+    int checkpoint_every;        /* 0: planner picks (1 = keep every step if it fits,
+                                    else k ~ sqrt(2 nt)); 1: force full history */
+    int tile_z, tile_x;          /* 0: defaults / autotuned; else a supported tile */
+} aafwi_plan_opts;
+
+typedef struct {
+    int NZ, NX, pitch;           /* padded grid and row pitch (floats) */
+    int S, nt_max;
+    long long trace_count;       /* total floats of a CSR trace array */
+    int checkpoint_every;        /* 1 = full history kept */
+    int n_checkpoints;
+    size_t workspace_bytes;
+    int tile_z, tile_x;
+    int n_tiles;                 /* tiles per shot */
+} aafwi_plan_info;
+
+/* ---- plan -------------------------------------------------------------- */
+
+/* Build a plan on the current CUDA device (Sec. 2.2 problem statement:
+ * geometry of eq. FWD and the sampling operator R of eq. FWI).
+ * wavelet: host FP64 [max nt], the source time function w(t_n), n = 0..max nt-1.
+ * Errors: ARG (NULL/size/duplicate receivers), OOB, CFL, NOMEM, CUDA. */
+int aafwi_plan_create(const aafwi_grid *grid, const aafwi_shots *shots,
+                      const double *wavelet, const aafwi_plan_opts *opts,
+                      aafwi_plan **out);
+void aafwi_plan_destroy(aafwi_plan *plan);
+int aafwi_plan_get_info(const aafwi_plan *plan, aafwi_plan_info *info);
+const char *aafwi_last_error(const aafwi_plan *plan);
+
+/* ---- wave-equation operators (Sec. 2.2) -------------------------------- */
+
+/* F: m -> R F(m) (eqs. FWD, FWI).  m: device [nz][nx] (s^2/m^2); d_out:
+ * device CSR traces or NULL.  Stores the forward wavefield history (or its
+ * checkpoints) in the plan so that a following adjoint_gradient with
+ * AAFWI_REUSE_FORWARD can skip its forward pass. */
+int aafwi_model_forward(aafwi_plan *plan, const float *m, float *d_out, aafwi_stream stream);
+
+/* L: rho -> scattered traces (eq. Born, perturbation m_r = rho * m0).
+ * m0, rho: device [nz][nx]; d_out: device CSR traces. */
+int aafwi_born_forward(aafwi_plan *plan, const float *m0, const float *rho,
+                       float *d_out, aafwi_stream stream);
+
+/* Residual and misfit (eq. FWI): resid = d_syn - d_obs (device CSR, may be
+ * NULL), J = 1/2 sum resid^2 accumulated in FP64.  J_host NULL: J stays on the
+ * device (aafwi_read_misfit). */
+int aafwi_misfit(aafwi_plan *plan, const float *d_syn, const float *d_obs,
+                 float *resid, double *J_host, aafwi_stream stream);
+
+/* Adjoint-state gradient (eqs. FWI_adj, adj_grad1).
+ * FWI:   m = model (device [nz][nx]), rho NULL; grad = dJ/dm.
+ * LSRTM: m = background m0, rho = current reflectivity; grad = L^T(L rho - d_obs).
+ * d_obs: device CSR traces; grad: device [nz][nx]; J_host as in aafwi_misfit.
+ * flags: AAFWI_REUSE_FORWARD (FWI only). */
+int aafwi_adjoint_gradient(aafwi_plan *plan, int mode, const float *m, const float *rho,
+                           const float *d_obs, float *grad, double *J_host, int flags,
+                           aafwi_stream stream);
+
+/* L^T: residual traces -> image on the physical grid (RTM image when
+ * resid = d_r; Sec. 4.3 start model m_RTM = L^T d_r). */
+int aafwi_born_adjoint(aafwi_plan *plan, const float *m0, const float *resid,
+                       float *img, aafwi_stream stream);
+
+/* Copy the last misfit J (FP64) computed on this plan to the host (syncs). */
+int aafwi_read_misfit(aafwi_plan *plan, double *J_host, aafwi_stream stream);
+
+/* ---- Anderson acceleration (Sec. 2.1, Sec. 3, Alg. 2) ------------------ */
+
+/* State for AA(M) on n unknowns with the fixed step eta of eq. GD: a ring of
+ * the last M+1 accepted iterates p_i and gradients G_i (FP32, device) and
+ * their FP64 Gram matrix.  Allocates on the current device. */
+int aafwi_aa_create(size_t n, int M, double eta, aafwi_aa **out);
+void aafwi_aa_destroy(aafwi_aa *aa);
+int aafwi_aa_set_eta(aafwi_aa *aa, double eta);
+
+/* Alg. 2 steps 1-3: append (p_k, grad_k) to the history (dropping the
+ * oldest beyond M+1), then
+ *   p_bar   = p_k - eta grad_k                                   (eq. GD)
+ *   gamma   = argmin || [G_{i+1} - G_i]_i gamma - G_k ||_2        (eqs. Ak, solveGamma)
+ *   p_tilde = p_bar - sum_i gamma_i [(p_{i+1} - eta G_{i+1}) - (p_i - eta G_i)]
+ *                                                                (eq. AA2_update)
+ * gamma is solved in FP64 from the Gram matrix of the history gradients
+ * (Cholesky; while min R_jj < 1e-6 max R_jj the oldest column is dropped).
+ * p_k, grad_k: device [n] (read); p_tilde, p_bar: device [n] (written).
+ * gamma_host (len >= M) / Mk_host: optional host outputs (sync when given). */
+int aafwi_aa_step(aafwi_aa *aa, const float *p_k, const float *grad_k, float *p_tilde,
+                  float *p_bar, double *gamma_host, int *Mk_host, aafwi_stream stream);
+
+/* Alg. 2 step 5: p_next = clip(lambda p_tilde + (1 - lambda) p_bar, lo, hi)
+ * (no clip when lo >= hi).  armijo_dot_host (optional, syncs) receives
+ * <G_k, p_next - p_k> in FP64 for the sufficient-decrease test of step 4. */
+int aafwi_aa_combine(aafwi_aa *aa, double lambda, const float *p_tilde, const float *p_bar,
+                     float *p_next, float lo, float hi, double *armijo_dot_host,
+                     aafwi_stream stream);
+
+/* max_i |x_i| of a device FP32 vector (FP64 result on the host, syncs);
+ * used to fix eta = factor * max|p_0| / max|grad J(p_0)|. */
+int aafwi_absmax(const float *x, size_t n, double *host_out, aafwi_stream stream);
+
+/* ---- instrumentation ---------------------------------------------------- */
+
+/* Number of CUDA kernels this library has launched in this process (a host-
+ * side counter incremented at every launch; memsets and copies excluded). */
+unsigned long long aafwi_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AAFWI_H */

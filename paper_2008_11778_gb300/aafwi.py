@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libaafwi.so (include/aafwi.h).
+
+Argument marshalling only: tensors are passed as raw device pointers with the
+current torch CUDA stream; every computation runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library cannot be loaded the
+import of the symbols raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libaafwi.so")
+
+AAFWI_OK = 0
+ERR_NAMES = {1: "ARG", 2: "CFL", 3: "OOB", 4: "NAN", 5: "TIMEOUT", 6: "CUDA", 7: "NOMEM", 8: "STATE"}
+MODE_FWI = 0
+MODE_LSRTM = 1
+REUSE_FORWARD = 1
+
+# every entry point declared in include/aafwi.h
+EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aafwi_last_error",
+           "aafwi_model_forward", "aafwi_born_forward", "aafwi_misfit", "aafwi_adjoint_gradient",
+           "aafwi_born_adjoint", "aafwi_read_misfit", "aafwi_aa_create", "aafwi_aa_destroy",
+           "aafwi_aa_set_eta", "aafwi_aa_step", "aafwi_aa_combine", "aafwi_absmax",
+           "aafwi_launch_count")
+
+
+class AafwiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("aafwi error %s (%d): %s" % (ERR_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("nb", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dz", ctypes.c_double), ("dt", ctypes.c_double),
+                ("c_max", ctypes.c_double)]
+
+
+class Shots(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int), ("src_iz", ctypes.c_void_p), ("src_ix", ctypes.c_void_p),
+                ("nt", ctypes.c_void_p), ("rec_off", ctypes.c_void_p),
+                ("rec_iz", ctypes.c_void_p), ("rec_ix", ctypes.c_void_p)]
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("max_workspace_bytes", ctypes.c_size_t), ("checkpoint_every", ctypes.c_int),
+                ("tile_z", ctypes.c_int), ("tile_x", ctypes.c_int)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("NZ", ctypes.c_int), ("NX", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("S", ctypes.c_int), ("nt_max", ctypes.c_int), ("trace_count", ctypes.c_longlong),
+                ("checkpoint_every", ctypes.c_int), ("n_checkpoints", ctypes.c_int),
+                ("workspace_bytes", ctypes.c_size_t), ("tile_z", ctypes.c_int),
+                ("tile_x", ctypes.c_int), ("n_tiles", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libaafwi.so (raises OSError if it is missing: no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libaafwi.so not built (%s); run __graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
+    P, I, D, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "aafwi_plan_create": ([P, P, P, P, P], I),
+        "aafwi_plan_destroy": ([P], None),
+        "aafwi_plan_get_info": ([P, P], I),
+        "aafwi_last_error": ([P], ctypes.c_char_p),
+        "aafwi_model_forward": ([P, P, P, P], I),
+        "aafwi_born_forward": ([P, P, P, P, P], I),
+        "aafwi_misfit": ([P, P, P, P, P, P], I),
+        "aafwi_adjoint_gradient": ([P, I, P, P, P, P, P, I, P], I),
+        "aafwi_born_adjoint": ([P, P, P, P, P], I),
+        "aafwi_read_misfit": ([P, P, P], I),
+        "aafwi_aa_create": ([Z, I, D, P], I),
+        "aafwi_aa_destroy": ([P], None),
+        "aafwi_aa_set_eta": ([P, D], I),
+        "aafwi_aa_step": ([P, P, P, P, P, P, P, P], I),
+        "aafwi_aa_combine": ([P, D, P, P, P, ctypes.c_float, ctypes.c_float, P, P], I),
+        "aafwi_absmax": ([P, Z, P, P], I),
+        "aafwi_launch_count": ([], ctypes.c_ulonglong),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc, plan=None):
+    if rc != AAFWI_OK:
+        msg = load().aafwi_last_error(plan)
+        raise AafwiError(rc, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    """Device pointer of a contiguous CUDA float32 tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _f32(t):
+    import torch
+    if t.dtype != torch.float32:
+        raise TypeError("expected float32, got %s" % t.dtype)
+    return _ptr(t)
+
+
+class Plan:
+    """Owns an aafwi_plan: geometry, workspace and the wave-equation operators."""
+
+    def __init__(self, geom, c_max, max_workspace_bytes=0, checkpoint_every=0):
+        L = load()
+        self.geom = geom
+        i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+        self._keep = [i32(geom.src_iz), i32(geom.src_ix), i32(geom.nt), i32(geom.rec_off),
+                      i32(geom.rec_iz), i32(geom.rec_ix),
+                      np.ascontiguousarray(geom.wavelet, dtype=np.float64)]
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        g = Grid(int(geom.nx), int(geom.nz), int(geom.nb), float(geom.dx), float(geom.dz),
+                 float(geom.dt), float(c_max))
+        s = Shots(len(self._keep[0]), *[ptr(a) for a in self._keep[:6]])
+        o = PlanOpts(int(max_workspace_bytes), int(checkpoint_every), 0, 0)
+        h = ctypes.c_void_p()
+        _check(L.aafwi_plan_create(ctypes.byref(g), ctypes.byref(s), ptr(self._keep[6]),
+                                   ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        info = PlanInfo()
+        _check(L.aafwi_plan_get_info(h, ctypes.byref(info)), h)
+        self.info = info
+        self.trace_count = int(info.trace_count)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().aafwi_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- operators ---------------------------------------------------------
+    def model_forward(self, m, d_out=None, stream=None):
+        _check(load().aafwi_model_forward(self.h, _f32(m), _f32(d_out) if d_out is not None else None,
+                                          _stream(stream)), self.h)
+        return d_out
+
+    def born_forward(self, m0, rho, d_out, stream=None):
+        _check(load().aafwi_born_forward(self.h, _f32(m0), _f32(rho), _f32(d_out), _stream(stream)), self.h)
+        return d_out
+
+    def misfit(self, d_syn, d_obs, resid=None, sync=True, stream=None):
+        J = ctypes.c_double()
+        _check(load().aafwi_misfit(self.h, _f32(d_syn), _f32(d_obs),
+                                   _f32(resid) if resid is not None else None,
+                                   ctypes.byref(J) if sync else None, _stream(stream)), self.h)
+        return J.value if sync else None
+
+    def adjoint_gradient(self, mode, m, rho, d_obs, grad, sync=True, reuse_forward=False, stream=None):
+        J = ctypes.c_double()
+        _check(load().aafwi_adjoint_gradient(self.h, int(mode), _f32(m),
+                                             _f32(rho) if rho is not None else None, _f32(d_obs),
+                                             _f32(grad), ctypes.byref(J) if sync else None,
+                                             REUSE_FORWARD if reuse_forward else 0, _stream(stream)),
+               self.h)
+        return J.value if sync else None
+
+    def born_adjoint(self, m0, resid, img, stream=None):
+        _check(load().aafwi_born_adjoint(self.h, _f32(m0), _f32(resid), _f32(img), _stream(stream)), self.h)
+        return img
+
+    def read_misfit(self, stream=None):
+        J = ctypes.c_double()
+        _check(load().aafwi_read_misfit(self.h, ctypes.byref(J), _stream(stream)), self.h)
+        return J.value
+
+
+class AA:
+    """Owns an aafwi_aa: the AA(M) history ring and its FP64 Gram matrix."""
+
+    def __init__(self, n, M, eta):
+        h = ctypes.c_void_p()
+        _check(load().aafwi_aa_create(int(n), int(M), float(eta), ctypes.byref(h)))
+        self.h, self.n, self.M = h, int(n), int(M)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().aafwi_aa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_eta(self, eta):
+        _check(load().aafwi_aa_set_eta(self.h, float(eta)))
+
+    def step(self, p_k, grad_k, p_tilde, p_bar, want_gamma=False, stream=None):
+        gam = (ctypes.c_double * max(self.M, 1))()
+        Mk = ctypes.c_int()
+        _check(load().aafwi_aa_step(self.h, _f32(p_k), _f32(grad_k), _f32(p_tilde), _f32(p_bar),
+                                    gam if want_gamma else None,
+                                    ctypes.byref(Mk) if want_gamma else None, _stream(stream)))
+        if want_gamma:
+            return np.array(gam[:Mk.value]), Mk.value
+        return None
+
+    def combine(self, lam, p_tilde, p_bar, p_next, lo=0.0, hi=0.0, want_dot=False, stream=None):
+        dot = ctypes.c_double()
+        _check(load().aafwi_aa_combine(self.h, float(lam), _f32(p_tilde), _f32(p_bar), _f32(p_next),
+                                       float(lo), float(hi), ctypes.byref(dot) if want_dot else None,
+                                       _stream(stream)))
+        return dot.value if want_dot else None
+
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(load().aafwi_launch_count())
+
+
+def absmax(x, stream=None):
+    out = ctypes.c_double()
+    _check(load().aafwi_absmax(_f32(x), x.numel(), ctypes.byref(out), _stream(stream)))
+    return out.value

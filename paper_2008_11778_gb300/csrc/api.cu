@@ -1,0 +1,610 @@
+// api.cu -- the C ABI of include/aafwi.h: plans (geometry, workspace,
+// wavefield history or checkpoints), the forward / Born / adjoint sweeps that
+// drive the time-step kernels, the misfit, and the Anderson-acceleration
+// state.  Host code only orchestrates; every arithmetic step runs in the
+// kernels of wave_kernels.cu and reduce_kernels.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+#include <set>
+
+#include "../../include/aafwi.h"
+#include "internal.cuh"
+
+using namespace aafwi;
+
+namespace {
+
+thread_local std::string g_create_error;
+constexpr double kCflLimit = 0.55;
+constexpr double kSpongeA = 0.015;
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct aafwi_plan {
+    int device = 0;
+    int nx = 0, nz = 0, nb = 0, NZ = 0, NX = 0, pitch = 0, S = 0, nt_max = 0;
+    double dx = 0, dz = 0, dt = 0;
+    std::vector<int> nt;
+    std::vector<long long> tr_off;
+    long long trace_count = 0;
+    long long field = 0;            // floats per shot field
+    int k = 1, nck = 0;             // checkpoint interval (1: full history), count
+    bool full = true;
+    Geo geo{};
+    std::vector<Buf> bufs;
+    // device buffers
+    float *W = nullptr, *rho_pad = nullptr;
+    float *hist = nullptr;          // full: (nt_max+1) slots; else 2*nck checkpoint slots
+    float *fbuf = nullptr;          // 2 rotating forward slots (checkpoint mode)
+    float *rbuf = nullptr;          // k-1 replay slots (checkpoint mode)
+    float *dbuf = nullptr;          // 2 rotating Born slots
+    float *zbuf = nullptr;          // 2 rotating adjoint slots
+    float *img = nullptr;           // per-shot image accumulators
+    float *dsyn = nullptr, *resid = nullptr;
+    double *partials = nullptr, *J = nullptr;
+    int *err = nullptr;
+    size_t ws_bytes = 0;
+    bool fwd_valid = false;
+    const float *fwd_model = nullptr;
+    std::string msg;
+};
+
+struct aafwi_aa {
+    AAState s{};
+    int device = 0;
+    std::vector<Buf> bufs;
+};
+
+namespace {
+
+int fail(aafwi_plan *p, int code, const std::string &m)
+{
+    if (p) p->msg = m;
+    else g_create_error = m;
+    return code;
+}
+
+int cuda_fail(aafwi_plan *p, cudaError_t e, const char *what)
+{
+    return fail(p, AAFWI_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+bool dalloc(std::vector<Buf> &bufs, T **out, size_t count)
+{
+    void *p = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    bufs.push_back({p, bytes});
+    *out = static_cast<T *>(p);
+    return true;
+}
+
+void free_bufs(std::vector<Buf> &bufs)
+{
+    for (auto &b : bufs) cudaFree(b.p);
+    bufs.clear();
+}
+
+template <class T>
+bool upload(std::vector<Buf> &bufs, T **out, const std::vector<T> &h)
+{
+    if (!dalloc(bufs, out, h.size())) return false;
+    return cudaMemcpy(*out, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+float *slot(float *base, long long per_slot, long long i) { return base + per_slot * i; }
+
+int check_launch(aafwi_plan *p)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(p, e, "kernel launch");
+    return AAFWI_OK;
+}
+
+// Pointer to u^n in checkpoint mode while processing segment j (first step a).
+float *seg_u(aafwi_plan *p, int j, int a, int n)
+{
+    const long long ps = (long long)p->S * p->field;
+    if (n == a) return slot(p->hist, ps, 2LL * j);
+    if (n == a - 1) return slot(p->hist, ps, 2LL * j + 1);
+    return slot(p->rbuf, ps, n - a - 1);
+}
+
+// Forward sweep over all shots (born: u and du together); traces -> dsyn.
+int run_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
+{
+    const long long ps = (long long)p->S * p->field;
+    if (!p->full && cudaMemsetAsync(p->fbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
+        return cuda_fail(p, cudaGetLastError(), "memset");
+    if (born && cudaMemsetAsync(p->dbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
+        return cuda_fail(p, cudaGetLastError(), "memset");
+    for (int n = 0; n < p->nt_max; ++n) {
+        float *cur, *prev, *next, *ckc = nullptr, *ckp = nullptr;
+        if (p->full) {
+            cur = slot(p->hist, ps, n);
+            prev = slot(p->hist, ps, n > 0 ? n - 1 : 0);
+            next = slot(p->hist, ps, n + 1);
+        } else {
+            cur = slot(p->fbuf, ps, n & 1);
+            prev = slot(p->fbuf, ps, (n + 1) & 1);
+            next = prev;
+            if (n % p->k == 0) {
+                ckc = slot(p->hist, ps, 2LL * (n / p->k));
+                ckp = slot(p->hist, ps, 2LL * (n / p->k) + 1);
+            }
+        }
+        if (born) {
+            BornArgs a{p->W, p->rho_pad, cur, prev, next, slot(p->dbuf, ps, n & 1),
+                       slot(p->dbuf, ps, (n + 1) & 1), slot(p->dbuf, ps, (n + 1) & 1), ckc, ckp,
+                       traces, n};
+            launch_born(p->geo, a, st);
+        } else {
+            FwdArgs a{p->W, cur, prev, next, ckc, ckp, traces, n};
+            launch_fwd(p->geo, a, st);
+        }
+    }
+    return check_launch(p);
+}
+
+// Adjoint sweep with imaging into p->img (born: scale -1, else -1/m).
+int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
+{
+    const long long ps = (long long)p->S * p->field;
+    if (cudaMemsetAsync(p->zbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess ||
+        cudaMemsetAsync(p->img, 0, ps * sizeof(float), st) != cudaSuccess)
+        return cuda_fail(p, cudaGetLastError(), "memset");
+    auto adj = [&](int n, const float *u) {
+        AdjArgs a{p->W, slot(p->zbuf, ps, (n + 1) & 1), slot(p->zbuf, ps, n & 1), u, resid, p->img,
+                  n, born ? 1 : 0};
+        launch_adj(p->geo, a, st);
+    };
+    if (p->full) {
+        for (int n = p->nt_max - 1; n >= 0; --n) adj(n, slot(p->hist, ps, n));
+    } else {
+        for (int j = p->nck - 1; j >= 0; --j) {
+            const int a = j * p->k, e = std::min(a + p->k, p->nt_max);
+            for (int n = a; n <= e - 2; ++n) {
+                FwdArgs f{p->W, seg_u(p, j, a, n), seg_u(p, j, a, n - 1), seg_u(p, j, a, n + 1),
+                          nullptr, nullptr, nullptr, n};
+                launch_fwd(p->geo, f, st);
+            }
+            for (int n = e - 1; n >= a; --n) adj(n, seg_u(p, j, a, n));
+        }
+    }
+    return check_launch(p);
+}
+
+int prep(aafwi_plan *p, const float *m, const float *rho, cudaStream_t st)
+{
+    const double h = std::min(p->dx, p->dz);
+    const double mcfl = std::pow(p->dt / (kCflLimit * h), 2.0);  // m below this violates CFL
+    launch_prep(p->geo, p->nz, p->nx, m, rho, (float)(p->dt * p->dt), (float)mcfl, p->W,
+                rho ? p->rho_pad : nullptr, p->err, st);
+    return check_launch(p);
+}
+
+int finish_sync(aafwi_plan *p, double *J_host, cudaStream_t st)
+{
+    if (!J_host) return AAFWI_OK;
+    int err = 0;
+    cudaError_t e = cudaMemcpyAsync(J_host, p->J, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, p->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "synchronise");
+    if (err) {
+        p->fwd_valid = false;
+        cudaMemsetAsync(p->err, 0, sizeof(int), st);
+        if (err & 1) return fail(p, AAFWI_ERR_NAN, "model has a non-finite or non-positive value");
+        return fail(p, AAFWI_ERR_CFL, "model velocity exceeds the CFL limit of the plan");
+    }
+    return AAFWI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *aafwi_last_error(const aafwi_plan *plan)
+{
+    return plan ? plan->msg.c_str() : g_create_error.c_str();
+}
+
+int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *wavelet,
+                      const aafwi_plan_opts *opts, aafwi_plan **out)
+{
+    if (!g || !sh || !wavelet || !out) return fail(nullptr, AAFWI_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (g->nx < 1 || g->nz < 1 || g->nb < 0 || !(g->dx > 0) || !(g->dz > 0) || !(g->dt > 0) ||
+        sh->S < 1 || !sh->src_iz || !sh->src_ix || !sh->nt || !sh->rec_off || !sh->rec_iz || !sh->rec_ix)
+        return fail(nullptr, AAFWI_ERR_ARG, "invalid grid or shot description");
+    const double h = std::min(g->dx, g->dz);
+    if (!(g->c_max > 0) || g->c_max * g->dt / h > kCflLimit) {
+        char b[160];
+        snprintf(b, sizeof b, "CFL number c_max*dt/h = %.4f exceeds %.2f", g->c_max * g->dt / h, kCflLimit);
+        return fail(nullptr, AAFWI_ERR_CFL, b);
+    }
+    aafwi_plan_opts o{};
+    if (opts) o = *opts;
+    {
+        cudaError_t ie = init_kernels();
+        if (ie != cudaSuccess) return cuda_fail(nullptr, ie, "kernel attributes");
+    }
+    auto *p = new aafwi_plan();
+    cudaGetDevice(&p->device);
+    p->nx = g->nx; p->nz = g->nz; p->nb = g->nb;
+    p->dx = g->dx; p->dz = g->dz; p->dt = g->dt;
+    p->NZ = g->nz + 2 * g->nb;
+    p->NX = g->nx + 2 * g->nb;
+    p->pitch = (p->NX + 31) / 32 * 32;
+    p->S = sh->S;
+    p->field = (long long)p->NZ * p->pitch;
+    const int S = sh->S;
+    p->nt.assign(sh->nt, sh->nt + S);
+    p->nt_max = *std::max_element(p->nt.begin(), p->nt.end());
+    if (*std::min_element(p->nt.begin(), p->nt.end()) < 1) {
+        delete p;
+        return fail(nullptr, AAFWI_ERR_ARG, "record length must be >= 1");
+    }
+    if (sh->rec_off[0] != 0) {
+        delete p;
+        return fail(nullptr, AAFWI_ERR_ARG, "rec_off[0] must be 0");
+    }
+    // tiles
+    const int ntz = (p->NZ + TZ - 1) / TZ, ntx = (p->pitch + TX - 1) / TX, ntiles = ntz * ntx;
+    // sources, receivers, per-tile receiver lists, trace offsets
+    std::vector<int> src_pt(S), nrec(S);
+    std::vector<std::vector<std::pair<int, int>>> per_tile((size_t)S * ntiles);
+    p->tr_off.resize(S);
+    long long off = 0;
+    for (int s = 0; s < S; ++s) {
+        if (sh->src_iz[s] < 0 || sh->src_iz[s] >= g->nz || sh->src_ix[s] < 0 || sh->src_ix[s] >= g->nx) {
+            delete p;
+            return fail(nullptr, AAFWI_ERR_OOB, "source outside the physical grid");
+        }
+        src_pt[s] = (sh->src_iz[s] + g->nb) * p->pitch + sh->src_ix[s] + g->nb;
+        const int r0 = sh->rec_off[s], r1 = sh->rec_off[s + 1];
+        if (r1 < r0) {
+            delete p;
+            return fail(nullptr, AAFWI_ERR_ARG, "rec_off must be non-decreasing");
+        }
+        nrec[s] = r1 - r0;
+        std::set<int> seen;
+        for (int j = 0; j < nrec[s]; ++j) {
+            const int iz = sh->rec_iz[r0 + j], ix = sh->rec_ix[r0 + j];
+            if (iz < 0 || iz >= g->nz || ix < 0 || ix >= g->nx) {
+                delete p;
+                return fail(nullptr, AAFWI_ERR_OOB, "receiver outside the physical grid");
+            }
+            const int pz = iz + g->nb, px = ix + g->nb;
+            const int pt = pz * p->pitch + px;
+            if (!seen.insert(pt).second) {
+                delete p;
+                return fail(nullptr, AAFWI_ERR_ARG, "duplicate receiver cell within a shot");
+            }
+            per_tile[(size_t)s * ntiles + (pz / TZ) * ntx + px / TX].push_back({pt, j});
+        }
+        p->tr_off[s] = off;
+        off += (long long)p->nt[s] * nrec[s];
+    }
+    p->trace_count = off;
+    std::vector<int> trec_off(1, 0), trec_pt, trec_col;
+    for (auto &v : per_tile) {
+        for (auto &e : v) {
+            trec_pt.push_back(e.first);
+            trec_col.push_back(e.second);
+        }
+        trec_off.push_back((int)trec_pt.size());
+    }
+    // sponge tables (FP64 -> FP32) and scaled wavelet
+    auto depth = [&](int i, int n) { return i < g->nb ? g->nb - i : (i > n - 1 - g->nb ? i - (n - 1 - g->nb) : 0); };
+    std::vector<float> Gz(p->NZ), Gx(p->pitch, 0.f), ws(p->nt_max);
+    for (int i = 0; i < p->NZ; ++i) Gz[i] = (float)std::exp(-std::pow(kSpongeA * depth(i, p->NZ), 2));
+    for (int i = 0; i < p->NX; ++i) Gx[i] = (float)std::exp(-std::pow(kSpongeA * depth(i, p->NX), 2));
+    for (int n = 0; n < p->nt_max; ++n) ws[n] = (float)(wavelet[n] / (g->dx * g->dz));
+    // workspace plan
+    const size_t F = (size_t)p->field * sizeof(float), SF = F * S;
+    const size_t fixed = 2 * F + (2 + 2 + 1) * SF + 2 * (size_t)p->trace_count * sizeof(float) + (1 << 20);
+    size_t budget = o.max_workspace_bytes;
+    if (budget == 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        budget = (size_t)(0.85 * (double)fr);
+    }
+    const size_t full_bytes = fixed + (size_t)(p->nt_max + 1) * SF;
+    int k = o.checkpoint_every;
+    if (k == 1 || (k == 0 && full_bytes <= budget)) {
+        p->full = true;
+        p->k = 1;
+        p->ws_bytes = full_bytes;
+    } else {
+        if (k <= 1) k = std::max(2, (int)std::lround(std::sqrt(2.0 * p->nt_max)));
+        p->full = false;
+        p->k = k;
+        p->nck = (p->nt_max + k - 1) / k;
+        p->ws_bytes = fixed + (size_t)(2 * p->nck + (k - 1) + 2) * SF;
+    }
+    if (p->ws_bytes > budget) {
+        char b[200];
+        snprintf(b, sizeof b, "workspace %.2f GB exceeds the budget %.2f GB", p->ws_bytes / 1e9, budget / 1e9);
+        delete p;
+        return fail(nullptr, AAFWI_ERR_NOMEM, b);
+    }
+    // device allocations
+    int *d_nt, *d_src, *d_toff, *d_tpt, *d_tcol, *d_nrec;
+    float *d_ws, *d_Gz, *d_Gx;
+    long long *d_troff;
+    std::vector<int> trec_pt_nz = trec_pt.empty() ? std::vector<int>{0} : trec_pt;
+    std::vector<int> trec_col_nz = trec_col.empty() ? std::vector<int>{0} : trec_col;
+    bool ok = upload(p->bufs, &d_nt, p->nt) && upload(p->bufs, &d_src, src_pt) &&
+              upload(p->bufs, &d_toff, trec_off) && upload(p->bufs, &d_tpt, trec_pt_nz) &&
+              upload(p->bufs, &d_tcol, trec_col_nz) && upload(p->bufs, &d_nrec, nrec) &&
+              upload(p->bufs, &d_ws, ws) && upload(p->bufs, &d_Gz, Gz) && upload(p->bufs, &d_Gx, Gx) &&
+              upload(p->bufs, &d_troff, p->tr_off);
+    const long long ps = (long long)S * p->field;
+    ok = ok && dalloc(p->bufs, &p->W, p->field) && dalloc(p->bufs, &p->rho_pad, p->field) &&
+         dalloc(p->bufs, &p->dbuf, 2 * ps) && dalloc(p->bufs, &p->zbuf, 2 * ps) &&
+         dalloc(p->bufs, &p->img, ps) && dalloc(p->bufs, &p->dsyn, p->trace_count) &&
+         dalloc(p->bufs, &p->resid, p->trace_count) && dalloc(p->bufs, &p->partials, RED_BLOCKS) &&
+         dalloc(p->bufs, &p->J, 1) && dalloc(p->bufs, &p->err, 1);
+    if (ok) {
+        if (p->full) {
+            ok = dalloc(p->bufs, &p->hist, (p->nt_max + 1) * ps);
+        } else {
+            ok = dalloc(p->bufs, &p->hist, 2LL * p->nck * ps) && dalloc(p->bufs, &p->fbuf, 2 * ps) &&
+                 dalloc(p->bufs, &p->rbuf, std::max(1, p->k - 1) * ps);
+        }
+    }
+    if (!ok) {
+        free_bufs(p->bufs);
+        delete p;
+        return fail(nullptr, AAFWI_ERR_NOMEM, "cudaMalloc failed for the plan workspace");
+    }
+    // zero-initialise every field buffer (the pitch padding and u^0 must be 0)
+    for (auto &b : p->bufs) cudaMemset(b.p, 0, b.bytes);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_bufs(p->bufs);
+        delete p;
+        return cuda_fail(nullptr, e, "plan initialisation");
+    }
+    Geo &G = p->geo;
+    G.NZ = p->NZ; G.NX = p->NX; G.pitch = p->pitch; G.nb = p->nb; G.S = S;
+    G.ntz = ntz; G.ntx = ntx; G.ntiles = ntiles; G.field = p->field;
+    G.idz2 = (float)(1.0 / (g->dz * g->dz));
+    G.idx2 = (float)(1.0 / (g->dx * g->dx));
+    G.inv_dt2 = (float)(1.0 / (g->dt * g->dt));
+    G.nt = d_nt; G.src_pt = d_src; G.ws = d_ws; G.Gz = d_Gz; G.Gx = d_Gx;
+    G.trec_off = d_toff; G.trec_pt = d_tpt; G.trec_col = d_tcol; G.tr_off = d_troff; G.nrec = d_nrec;
+    *out = p;
+    return AAFWI_OK;
+}
+
+void aafwi_plan_destroy(aafwi_plan *p)
+{
+    if (!p) return;
+    free_bufs(p->bufs);
+    delete p;
+}
+
+int aafwi_plan_get_info(const aafwi_plan *p, aafwi_plan_info *info)
+{
+    if (!p || !info) return AAFWI_ERR_ARG;
+    info->NZ = p->NZ; info->NX = p->NX; info->pitch = p->pitch;
+    info->S = p->S; info->nt_max = p->nt_max;
+    info->trace_count = p->trace_count;
+    info->checkpoint_every = p->k;
+    info->n_checkpoints = p->nck;
+    info->workspace_bytes = p->ws_bytes;
+    info->tile_z = TZ; info->tile_x = TX;
+    info->n_tiles = p->geo.ntiles;
+    return AAFWI_OK;
+}
+
+int aafwi_model_forward(aafwi_plan *p, const float *m, float *d_out, aafwi_stream stream)
+{
+    if (!p || !m) return fail(p, AAFWI_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    p->fwd_valid = false;
+    if ((rc = prep(p, m, nullptr, st))) return rc;
+    if ((rc = run_forward(p, false, p->dsyn, st))) return rc;
+    if (d_out && d_out != p->dsyn &&
+        cudaMemcpyAsync(d_out, p->dsyn, p->trace_count * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return cuda_fail(p, cudaGetLastError(), "copy traces");
+    p->fwd_valid = true;
+    p->fwd_model = m;
+    return AAFWI_OK;
+}
+
+int aafwi_born_forward(aafwi_plan *p, const float *m0, const float *rho, float *d_out, aafwi_stream stream)
+{
+    if (!p || !m0 || !rho || !d_out) return fail(p, AAFWI_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    p->fwd_valid = false;
+    if ((rc = prep(p, m0, rho, st))) return rc;
+    if ((rc = run_forward(p, true, d_out, st))) return rc;
+    return AAFWI_OK;
+}
+
+int aafwi_misfit(aafwi_plan *p, const float *d_syn, const float *d_obs, float *resid, double *J_host,
+                 aafwi_stream stream)
+{
+    if (!p || !d_syn || !d_obs) return fail(p, AAFWI_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_misfit(d_syn, d_obs, resid, p->trace_count, p->partials, p->J, st);
+    int rc = check_launch(p);
+    if (rc) return rc;
+    return finish_sync(p, J_host, st);
+}
+
+int aafwi_read_misfit(aafwi_plan *p, double *J_host, aafwi_stream stream)
+{
+    if (!p || !J_host) return fail(p, AAFWI_ERR_ARG, "NULL argument");
+    return finish_sync(p, J_host, (cudaStream_t)stream);
+}
+
+int aafwi_adjoint_gradient(aafwi_plan *p, int mode, const float *m, const float *rho, const float *d_obs,
+                           float *grad, double *J_host, int flags, aafwi_stream stream)
+{
+    if (!p || !m || !d_obs || !grad) return fail(p, AAFWI_ERR_ARG, "NULL argument");
+    if (mode != AAFWI_MODE_FWI && mode != AAFWI_MODE_LSRTM) return fail(p, AAFWI_ERR_ARG, "unknown mode");
+    if (mode == AAFWI_MODE_LSRTM && !rho) return fail(p, AAFWI_ERR_ARG, "LSRTM needs rho");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    const bool born = mode == AAFWI_MODE_LSRTM;
+    if (!born && (flags & AAFWI_REUSE_FORWARD)) {
+        if (!p->fwd_valid || p->fwd_model != m)
+            return fail(p, AAFWI_ERR_STATE, "no stored forward wavefield for this model");
+    } else {
+        p->fwd_valid = false;
+        if ((rc = prep(p, m, born ? rho : nullptr, st))) return rc;
+        if ((rc = run_forward(p, born, p->dsyn, st))) return rc;
+    }
+    launch_misfit(p->dsyn, d_obs, p->resid, p->trace_count, p->partials, p->J, st);
+    if ((rc = run_adjoint(p, born, p->resid, st))) return rc;
+    launch_shot_sum(p->geo, p->nz, p->nx, p->img, grad, st);
+    if ((rc = check_launch(p))) return rc;
+    if (!born) {
+        p->fwd_valid = true;
+        p->fwd_model = m;
+    }
+    return finish_sync(p, J_host, st);
+}
+
+int aafwi_born_adjoint(aafwi_plan *p, const float *m0, const float *resid, float *img, aafwi_stream stream)
+{
+    if (!p || !m0 || !resid || !img) return fail(p, AAFWI_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    p->fwd_valid = false;
+    if ((rc = prep(p, m0, nullptr, st))) return rc;
+    if ((rc = run_forward(p, false, nullptr, st))) return rc;
+    if ((rc = run_adjoint(p, true, resid, st))) return rc;
+    launch_shot_sum(p->geo, p->nz, p->nx, p->img, img, st);
+    return check_launch(p);
+}
+
+// ---------------------------------------------------------------------------
+// Anderson acceleration
+// ---------------------------------------------------------------------------
+
+int aafwi_aa_create(size_t n, int M, double eta, aafwi_aa **out)
+{
+    if (!out || n == 0 || M < 0 || M > AA_MAXM)
+        return fail(nullptr, AAFWI_ERR_ARG, "aa_create: need n > 0 and 0 <= M <= 20");
+    *out = nullptr;
+    auto *a = new aafwi_aa();
+    cudaGetDevice(&a->device);
+    AAState &s = a->s;
+    s.n = (long long)n;
+    s.M = M;
+    s.eta = eta;
+    const int M1 = M + 1;
+    bool ok = dalloc(a->bufs, &s.ring_p, (size_t)M1 * n) && dalloc(a->bufs, &s.ring_g, (size_t)M1 * n) &&
+              dalloc(a->bufs, &s.gram, (size_t)M1 * M1) &&
+              dalloc(a->bufs, &s.partials, (size_t)RED_BLOCKS * (AA_MAXM + 2)) &&
+              dalloc(a->bufs, &s.gamma, AA_MAXM) && dalloc(a->bufs, &s.meta, 4) && dalloc(a->bufs, &s.dot, 1);
+    if (!ok) {
+        free_bufs(a->bufs);
+        delete a;
+        return fail(nullptr, AAFWI_ERR_NOMEM, "cudaMalloc failed for the AA state");
+    }
+    for (auto &b : a->bufs) cudaMemset(b.p, 0, b.bytes);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        free_bufs(a->bufs);
+        delete a;
+        return fail(nullptr, AAFWI_ERR_CUDA, "aa_create initialisation");
+    }
+    *out = a;
+    return AAFWI_OK;
+}
+
+void aafwi_aa_destroy(aafwi_aa *a)
+{
+    if (!a) return;
+    free_bufs(a->bufs);
+    delete a;
+}
+
+int aafwi_aa_set_eta(aafwi_aa *a, double eta)
+{
+    if (!a || !(eta > 0)) return AAFWI_ERR_ARG;
+    a->s.eta = eta;
+    return AAFWI_OK;
+}
+
+int aafwi_aa_step(aafwi_aa *a, const float *p_k, const float *grad_k, float *p_tilde, float *p_bar,
+                  double *gamma_host, int *Mk_host, aafwi_stream stream)
+{
+    if (!a || !p_k || !grad_k || !p_tilde || !p_bar) return fail(nullptr, AAFWI_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_aa_step(a->s, p_k, grad_k, p_tilde, p_bar, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "aa_step launch");
+    if (gamma_host || Mk_host) {
+        int meta[2] = {0, 0};
+        double gam[AA_MAXM];
+        e = cudaMemcpyAsync(meta, a->s.meta, sizeof meta, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(gam, a->s.gamma, sizeof gam, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "aa_step readback");
+        if (Mk_host) *Mk_host = meta[0];
+        if (gamma_host)
+            for (int j = 0; j < a->s.M; ++j) gamma_host[j] = j < meta[0] ? gam[j] : 0.0;
+    }
+    return AAFWI_OK;
+}
+
+int aafwi_aa_combine(aafwi_aa *a, double lambda, const float *p_tilde, const float *p_bar, float *p_next,
+                     float lo, float hi, double *armijo_dot_host, aafwi_stream stream)
+{
+    if (!a || !p_tilde || !p_bar || !p_next) return fail(nullptr, AAFWI_ERR_ARG, "NULL argument");
+    if (a->s.count == 0) return fail(nullptr, AAFWI_ERR_STATE, "aa_combine before aa_step");
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_aa_combine(a->s, (float)lambda, p_tilde, p_bar, p_next, lo, hi, armijo_dot_host != nullptr, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "aa_combine launch");
+    if (armijo_dot_host) {
+        e = cudaMemcpyAsync(armijo_dot_host, a->s.dot, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "aa_combine readback");
+    }
+    return AAFWI_OK;
+}
+
+int aafwi_absmax(const float *x, size_t n, double *host_out, aafwi_stream stream)
+{
+    if (!x || !host_out || n == 0) return fail(nullptr, AAFWI_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    double *buf = nullptr;
+    // small scratch owned by this call (RED_BLOCKS partials + result)
+    if (cudaMallocAsync((void **)&buf, (RED_BLOCKS + 1) * sizeof(double), st) != cudaSuccess)
+        return fail(nullptr, AAFWI_ERR_NOMEM, "absmax scratch");
+    launch_absmax(x, (long long)n, buf, buf + RED_BLOCKS, st);
+    cudaError_t e = cudaMemcpyAsync(host_out, buf + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(buf, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "absmax");
+    return AAFWI_OK;
+}
+
+unsigned long long aafwi_launch_count(void)
+{
+    return g_launch_count.load(std::memory_order_relaxed);
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// internal.cuh -- kernel argument blocks and launchers shared by the CUDA
+// translation units of libaafwi.so.  Not part of the public ABI (aafwi.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <atomic>
+#include <cstddef>
+#include <cstdint>
+
+namespace aafwi {
+
+// Tile of one CTA: TZ rows x TX columns of one shot, 256 threads laid out
+// 32 (x) x 8 (z); a thread owns 4 consecutive columns (one float4) on TZ/8
+// rows.  HALO = stencil radius of the 8th-order Laplacian.
+constexpr int HALO = 4;
+constexpr int TX = 128;
+constexpr int TZ = 32;
+constexpr int BX = 32;
+constexpr int BY = 8;
+constexpr int RZ = TZ / BY;
+constexpr int SW = TX + 2 * HALO;      // shared tile row length (floats)
+constexpr int SH = TZ + 2 * HALO;      // shared tile rows
+
+// Per-plan geometry, all pointers device.
+struct Geo {
+    int NZ, NX, pitch, nb, S;
+    int ntz, ntx, ntiles;          // tiles per shot along z, x; total
+    long long field;               // floats per shot field (NZ * pitch)
+    float idz2, idx2;              // 1/dz^2, 1/dx^2
+    float inv_dt2;                 // 1/dt^2
+    const int *nt;                 // [S] record length
+    const int *src_pt;             // [S] padded source point iz*pitch + ix
+    const float *ws;               // [nt_max] w(t_n) / (dx dz)
+    const float *Gz, *Gx;          // [NZ], [pitch] sponge factors (0 beyond NX)
+    const int *trec_off;           // [S*ntiles + 1] receivers per (shot, tile)
+    const int *trec_pt;            // padded point of each receiver
+    const int *trec_col;           // receiver index within its shot
+    const long long *tr_off;       // [S] trace offsets
+    const int *nrec;               // [S]
+};
+
+// One forward step n -> n+1 for all shots.  Field pointers are slot bases
+// (shot s at + s*field).  u_next may alias u_prev (in-place update).
+struct FwdArgs {
+    const float *W;
+    const float *u_cur;
+    const float *u_prev;
+    float *u_next;
+    float *ck_cur, *ck_prev;       // checkpoint targets for (u^n, u^{n-1}) or null
+    float *traces;                 // gather target (CSR) or null
+    int n;
+};
+
+// Born step: background u and scattered du together (eq. Born).
+struct BornArgs {
+    const float *W, *rho;
+    const float *u_cur, *u_prev;
+    float *u_next;
+    const float *d_cur, *d_prev;
+    float *d_next;
+    float *ck_cur, *ck_prev;
+    float *traces;                 // scattered-field gather
+    int n;
+};
+
+// Adjoint step n (z^n from z^{n+1}, z^{n+2}) fused with the imaging condition
+// img += scale * z^n * (L u^n + s^n), scale = -W/dt^2 (FWI) or -1 (Born).
+struct AdjArgs {
+    const float *W;
+    const float *z1;               // z^{n+1}
+    float *z2n;                    // in: z^{n+2}; out: z^n (same cells)
+    const float *u;                // u^n
+    const float *resid;            // CSR residual traces
+    float *img;                    // per-shot accumulators [S][field]
+    int n;
+    int born;
+};
+
+// Number of kernels this library has launched (host-side count).
+extern std::atomic<unsigned long long> g_launch_count;
+inline void count_launch(unsigned n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
+
+cudaError_t init_kernels();  // per-device kernel attributes (dynamic shared memory)
+void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float dt2,
+                 float cfl_h, float *W, float *rho_pad, int *err, cudaStream_t st);
+void launch_fwd(const Geo &g, const FwdArgs &a, cudaStream_t st);
+void launch_born(const Geo &g, const BornArgs &a, cudaStream_t st);
+void launch_adj(const Geo &g, const AdjArgs &a, cudaStream_t st);
+void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, float *out, cudaStream_t st);
+
+// Reductions (FP64 accumulation, deterministic two-pass).
+constexpr int RED_BLOCKS = 608;    // 4 x 152 SMs
+void launch_misfit(const float *d_syn, const float *d_obs, float *resid, long long n,
+                   double *partials, double *J_dev, cudaStream_t st);
+void launch_absmax(const float *x, long long n, double *partials, double *out_dev, cudaStream_t st);
+
+// Anderson acceleration.
+constexpr int AA_MAXM = 20;
+struct AAState {
+    long long n;
+    int M;
+    float *ring_p, *ring_g;        // [M+1][n]
+    double *gram;                  // [(M+1)*(M+1)] by slot
+    double *partials;              // [RED_BLOCKS][M+2]
+    double *gamma;                 // [M]
+    int *meta;                     // [0] Mk used, [1] first dropped column
+    double *dot;                   // [1] armijo dot
+    double eta;
+    int count, head;               // entries in the ring, slot of the newest
+};
+void launch_aa_step(AAState &s, const float *p_k, const float *g_k, float *p_tilde,
+                    float *p_bar, cudaStream_t st);
+void launch_aa_combine(AAState &s, float lam, const float *p_tilde, const float *p_bar,
+                       float *p_next, float lo, float hi, bool want_dot, cudaStream_t st);
+
+}  // namespace aafwi

@@ -1,0 +1,372 @@
+// wave_kernels.cu -- time-step kernels of the 2D constant-density acoustic
+// wave equation (Sec. 2.2, eq. FWD), its Born linearisation (eq. Born) and
+// its exact discrete adjoint fused with the imaging condition (eqs. FWI_adj,
+// adj_grad1).
+//
+// Scheme (leap-frog, 8th-order Laplacian, Cerjan sponge G, W = dt^2/m):
+//   forward   u^{n+1} = G (2 u^n - G u^{n-1} + W (L u^n + s^n))
+//   Born      du^{n+1} = G (2 du^n - G du^{n-1} + W L du^n) - G W rho (L u^n + s^n)
+//   adjoint   z^n = G (2 z^{n+1} - G z^{n+2} + W (L z^{n+1} + R^T r^n))
+//   imaging   img += scale z^n (L u^n + s^n),  scale = -W/dt^2 (= -1/m, FWI)
+//                                              or -1 (Born adjoint)
+// One launch advances every shot by one step: grid (tiles per shot, shots).
+// A CTA stages its TZ x TX tile plus a 4-cell halo of each stencil input in
+// shared memory with 128-bit loads; each thread owns one float4 column group
+// on TZ/8 rows.  Source injection, receiver gather and residual injection are
+// fused into the same launch through a per-(shot, tile) receiver list.
+#include "internal.cuh"
+
+namespace aafwi {
+
+std::atomic<unsigned long long> g_launch_count{0};
+
+// Fornberg's 8th-order central weights for the second derivative.
+constexpr float C0 = (float)(-205.0 / 72.0);
+constexpr float C1 = (float)(8.0 / 5.0);
+constexpr float C2 = (float)(-1.0 / 5.0);
+constexpr float C3 = (float)(8.0 / 315.0);
+constexpr float C4 = (float)(-1.0 / 560.0);
+
+typedef float Tile[SW];
+
+__device__ __forceinline__ float4 ld4s(const Tile *s, int r, int c)
+{
+    return *reinterpret_cast<const float4 *>(&s[r][c]);
+}
+
+__device__ __forceinline__ float4 ld4g(const float *p)
+{
+    return *reinterpret_cast<const float4 *>(p);
+}
+
+__device__ __forceinline__ void st4g(float *p, float4 v)
+{
+    *reinterpret_cast<float4 *>(p) = v;
+}
+
+// Stage rows z0-4 .. z0+TZ+3 and columns x0-4 .. x0+TX+3 of field f (row
+// pitch g.pitch) into s; cells outside the padded grid read as zero.
+__device__ __forceinline__ void load_tile(Tile *s, const float *f, int z0, int x0, const Geo &g)
+{
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    constexpr int CH = SW / 4;
+    for (int i = tid; i < SH * CH; i += BX * BY) {
+        const int r = i / CH, c = i - r * CH;
+        const int z = z0 - HALO + r;
+        const int x = x0 - HALO + 4 * c;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (z >= 0 && z < g.NZ && x >= 0 && x < g.pitch) {
+            v = ld4g(f + (long long)z * g.pitch + x);
+            if (x + 3 >= g.NX) {
+                if (x >= g.NX) v.x = 0.f;
+                if (x + 1 >= g.NX) v.y = 0.f;
+                if (x + 2 >= g.NX) v.z = 0.f;
+                v.w = 0.f;
+            }
+        }
+        *reinterpret_cast<float4 *>(&s[r][4 * c]) = v;
+    }
+}
+
+// L applied at the four cells (rr, cc..cc+3) of a staged tile.
+__device__ __forceinline__ float4 lap4(const Tile *s, int rr, int cc, float idz2, float idx2)
+{
+    const float4 L = ld4s(s, rr, cc - 4), M = ld4s(s, rr, cc), R = ld4s(s, rr, cc + 4);
+    const float v[12] = {L.x, L.y, L.z, L.w, M.x, M.y, M.z, M.w, R.x, R.y, R.z, R.w};
+    float ax[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        ax[i] = C0 * v[4 + i] + C1 * (v[3 + i] + v[5 + i]) + C2 * (v[2 + i] + v[6 + i])
+              + C3 * (v[1 + i] + v[7 + i]) + C4 * (v[i] + v[8 + i]);
+    const float4 a1 = ld4s(s, rr - 1, cc), b1 = ld4s(s, rr + 1, cc);
+    const float4 a2 = ld4s(s, rr - 2, cc), b2 = ld4s(s, rr + 2, cc);
+    const float4 a3 = ld4s(s, rr - 3, cc), b3 = ld4s(s, rr + 3, cc);
+    const float4 a4 = ld4s(s, rr - 4, cc), b4 = ld4s(s, rr + 4, cc);
+    float4 o;
+    o.x = (C0 * M.x + C1 * (a1.x + b1.x) + C2 * (a2.x + b2.x) + C3 * (a3.x + b3.x) + C4 * (a4.x + b4.x)) * idz2 + ax[0] * idx2;
+    o.y = (C0 * M.y + C1 * (a1.y + b1.y) + C2 * (a2.y + b2.y) + C3 * (a3.y + b3.y) + C4 * (a4.y + b4.y)) * idz2 + ax[1] * idx2;
+    o.z = (C0 * M.z + C1 * (a1.z + b1.z) + C2 * (a2.z + b2.z) + C3 * (a3.z + b3.z) + C4 * (a4.z + b4.z)) * idz2 + ax[2] * idx2;
+    o.w = (C0 * M.w + C1 * (a1.w + b1.w) + C2 * (a2.w + b2.w) + C3 * (a3.w + b3.w) + C4 * (a4.w + b4.w)) * idz2 + ax[3] * idx2;
+    return o;
+}
+
+// Add w to the component of q whose cell is the source cell.
+__device__ __forceinline__ void add_source(float4 &q, int src, int pt, float w)
+{
+    const int d = src - pt;
+    if (d >= 0 && d < 4) {
+        if (d == 0) q.x += w;
+        else if (d == 1) q.y += w;
+        else if (d == 2) q.z += w;
+        else q.w += w;
+    }
+}
+
+__device__ __forceinline__ float4 leapfrog(float4 G, float4 cur, float4 prev, float4 W, float4 q)
+{
+    float4 o;
+    o.x = G.x * (2.f * cur.x - G.x * prev.x + W.x * q.x);
+    o.y = G.y * (2.f * cur.y - G.y * prev.y + W.y * q.y);
+    o.z = G.z * (2.f * cur.z - G.z * prev.z + W.z * q.z);
+    o.w = G.w * (2.f * cur.w - G.w * prev.w + W.w * q.w);
+    return o;
+}
+
+// Write u_next at this tile's receivers into the CSR traces (sample n).
+__device__ __forceinline__ void gather(const Geo &g, int s, int tile, int n, const float *f,
+                                       float *traces)
+{
+    const int t = s * g.ntiles + tile;
+    const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
+    if (r1 <= r0) return;
+    __syncthreads();  // the tile's stores above are now visible to the block
+    const long long tb = g.tr_off[s] + (long long)n * g.nrec[s];
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    for (int i = r0 + tid; i < r1; i += BX * BY)
+        traces[tb + g.trec_col[i]] = f[g.trec_pt[i]];
+}
+
+__global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a)
+{
+    const int s = blockIdx.y;
+    if (a.n >= g.nt[s]) return;
+    const int tile = blockIdx.x;
+    const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
+    const int z0 = tzi * TZ, x0 = txi * TX;
+    __shared__ __align__(16) float su[SH][SW];
+    const long long base = (long long)s * g.field;
+    load_tile(su, a.u_cur + base, z0, x0, g);
+    __syncthreads();
+    const int xl = threadIdx.x * 4, x = x0 + xl;
+    if (x < g.pitch) {
+        const float4 gx = ld4g(g.Gx + x);
+        const int src = g.src_pt[s];
+        const float wsn = g.ws[a.n];
+#pragma unroll
+        for (int r = 0; r < RZ; ++r) {
+            const int zl = threadIdx.y + r * BY, z = z0 + zl;
+            if (z >= g.NZ) break;
+            const long long cell = (long long)z * g.pitch + x;
+            float4 q = lap4(su, zl + HALO, xl + HALO, g.idz2, g.idx2);
+            add_source(q, src, (int)cell, wsn);
+            const float gz = g.Gz[z];
+            const float4 G = make_float4(gz * gx.x, gz * gx.y, gz * gx.z, gz * gx.w);
+            const float4 uc = ld4s(su, zl + HALO, xl + HALO);
+            const float4 up = ld4g(a.u_prev + base + cell);
+            const float4 W = ld4g(a.W + cell);
+            st4g(a.u_next + base + cell, leapfrog(G, uc, up, W, q));
+            if (a.ck_cur) {
+                st4g(a.ck_cur + base + cell, uc);
+                st4g(a.ck_prev + base + cell, up);
+            }
+        }
+    }
+    if (a.traces) gather(g, s, tile, a.n, a.u_next + base, a.traces);
+}
+
+__global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a)
+{
+    const int s = blockIdx.y;
+    if (a.n >= g.nt[s]) return;
+    const int tile = blockIdx.x;
+    const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
+    const int z0 = tzi * TZ, x0 = txi * TX;
+    extern __shared__ __align__(16) float smem[];
+    Tile *su = reinterpret_cast<Tile *>(smem);
+    Tile *sd = su + SH;
+    const long long base = (long long)s * g.field;
+    load_tile(su, a.u_cur + base, z0, x0, g);
+    load_tile(sd, a.d_cur + base, z0, x0, g);
+    __syncthreads();
+    const int xl = threadIdx.x * 4, x = x0 + xl;
+    if (x < g.pitch) {
+        const float4 gx = ld4g(g.Gx + x);
+        const int src = g.src_pt[s];
+        const float wsn = g.ws[a.n];
+#pragma unroll
+        for (int r = 0; r < RZ; ++r) {
+            const int zl = threadIdx.y + r * BY, z = z0 + zl;
+            if (z >= g.NZ) break;
+            const long long cell = (long long)z * g.pitch + x;
+            float4 q = lap4(su, zl + HALO, xl + HALO, g.idz2, g.idx2);
+            add_source(q, src, (int)cell, wsn);
+            const float4 qd = lap4(sd, zl + HALO, xl + HALO, g.idz2, g.idx2);
+            const float gz = g.Gz[z];
+            const float4 G = make_float4(gz * gx.x, gz * gx.y, gz * gx.z, gz * gx.w);
+            const float4 W = ld4g(a.W + cell);
+            const float4 rho = ld4g(a.rho + cell);
+            const float4 uc = ld4s(su, zl + HALO, xl + HALO);
+            const float4 up = ld4g(a.u_prev + base + cell);
+            const float4 dc = ld4s(sd, zl + HALO, xl + HALO);
+            const float4 dp = ld4g(a.d_prev + base + cell);
+            float4 dn = leapfrog(G, dc, dp, W, qd);
+            dn.x -= G.x * W.x * rho.x * q.x;
+            dn.y -= G.y * W.y * rho.y * q.y;
+            dn.z -= G.z * W.z * rho.z * q.z;
+            dn.w -= G.w * W.w * rho.w * q.w;
+            st4g(a.u_next + base + cell, leapfrog(G, uc, up, W, q));
+            st4g(a.d_next + base + cell, dn);
+            if (a.ck_cur) {
+                st4g(a.ck_cur + base + cell, uc);
+                st4g(a.ck_prev + base + cell, up);
+            }
+        }
+    }
+    if (a.traces) gather(g, s, tile, a.n, a.d_next + base, a.traces);
+}
+
+__global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a)
+{
+    const int s = blockIdx.y;
+    if (a.n >= g.nt[s]) return;
+    const int tile = blockIdx.x;
+    const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
+    const int z0 = tzi * TZ, x0 = txi * TX;
+    extern __shared__ __align__(16) float smem[];
+    Tile *sz = reinterpret_cast<Tile *>(smem);
+    Tile *su = sz + SH;
+    float(*sinj)[TX] = reinterpret_cast<float(*)[TX]>(smem + 2 * SH * SW);
+    const long long base = (long long)s * g.field;
+    load_tile(sz, a.z1 + base, z0, x0, g);
+    load_tile(su, a.u + base, z0, x0, g);
+    const int t = s * g.ntiles + tile;
+    const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
+    const bool has_rec = r1 > r0;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    if (has_rec) {
+        for (int i = tid; i < TZ * TX / 4; i += BX * BY)
+            reinterpret_cast<float4 *>(&sinj[0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        const long long tb = g.tr_off[s] + (long long)a.n * g.nrec[s];
+        for (int i = r0 + tid; i < r1; i += BX * BY) {
+            const int pt = g.trec_pt[i];
+            const int zz = pt / g.pitch, xx = pt - zz * g.pitch;
+            sinj[zz - z0][xx - x0] = a.resid[tb + g.trec_col[i]];
+        }
+    }
+    __syncthreads();
+    const int xl = threadIdx.x * 4, x = x0 + xl;
+    if (x >= g.pitch) return;
+    const float4 gx = ld4g(g.Gx + x);
+    const int src = g.src_pt[s];
+    const float wsn = g.ws[a.n];
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        const int zl = threadIdx.y + r * BY, z = z0 + zl;
+        if (z >= g.NZ) break;
+        const long long cell = (long long)z * g.pitch + x;
+        float4 rhs = lap4(sz, zl + HALO, xl + HALO, g.idz2, g.idx2);
+        if (has_rec) {
+            const float4 inj = *reinterpret_cast<const float4 *>(&sinj[zl][xl]);
+            rhs.x += inj.x; rhs.y += inj.y; rhs.z += inj.z; rhs.w += inj.w;
+        }
+        const float gz = g.Gz[z];
+        const float4 G = make_float4(gz * gx.x, gz * gx.y, gz * gx.z, gz * gx.w);
+        const float4 W = ld4g(a.W + cell);
+        const float4 z1 = ld4s(sz, zl + HALO, xl + HALO);
+        const float4 z2 = ld4g(a.z2n + base + cell);
+        const float4 zn = leapfrog(G, z1, z2, W, rhs);
+        float4 qu = lap4(su, zl + HALO, xl + HALO, g.idz2, g.idx2);
+        add_source(qu, src, (int)cell, wsn);
+        float4 sc;
+        if (a.born) {
+            sc = make_float4(-1.f, -1.f, -1.f, -1.f);
+        } else {
+            sc = make_float4(-W.x * g.inv_dt2, -W.y * g.inv_dt2, -W.z * g.inv_dt2, -W.w * g.inv_dt2);
+        }
+        float4 im = ld4g(a.img + base + cell);
+        im.x += sc.x * zn.x * qu.x;
+        im.y += sc.y * zn.y * qu.y;
+        im.z += sc.z * zn.z * qu.z;
+        im.w += sc.w * zn.w * qu.w;
+        st4g(a.img + base + cell, im);
+        st4g(a.z2n + base + cell, zn);
+    }
+}
+
+// W = dt^2/m and E(rho) on the padded grid from the physical arrays
+// (extension E = clamp to the nearest physical cell); flags bad models:
+// bit 0 non-finite or non-positive m, bit 1 CFL above 0.55.
+__global__ void k_prep(const Geo g, int nz, int nx, const float *m, const float *rho, float dt2,
+                       float mcfl, float *W, float *rho_pad, int *err)
+{
+    const long long N = (long long)g.NZ * g.pitch;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int z = (int)(i / g.pitch), x = (int)(i - (long long)z * g.pitch);
+        if (x >= g.NX) {
+            W[i] = 0.f;
+            if (rho_pad) rho_pad[i] = 0.f;
+            continue;
+        }
+        const int jz = min(max(z - g.nb, 0), nz - 1), jx = min(max(x - g.nb, 0), nx - 1);
+        const float mv = m[(long long)jz * nx + jx];
+        if (!(mv > 0.f) || !isfinite(mv)) atomicOr(err, 1);
+        else if (mv < mcfl) atomicOr(err, 2);
+        W[i] = dt2 / mv;
+        if (rho_pad) rho_pad[i] = rho[(long long)jz * nx + jx];
+    }
+}
+
+// grad_phys = E^T (sum over shots of the per-shot padded images), FP64 sum in
+// a fixed order (shot, then cell), one thread per physical cell.
+__global__ void k_shot_sum(const Geo g, int nz, int nx, const float *img, float *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nz * nx) return;
+    const int jz = i / nx, jx = i - jz * nx;
+    const int zlo = jz == 0 ? 0 : jz + g.nb, zhi = jz == nz - 1 ? g.NZ - 1 : jz + g.nb;
+    const int xlo = jx == 0 ? 0 : jx + g.nb, xhi = jx == nx - 1 ? g.NX - 1 : jx + g.nb;
+    double acc = 0.0;
+    for (int s = 0; s < g.S; ++s) {
+        const float *f = img + (long long)s * g.field;
+        for (int z = zlo; z <= zhi; ++z)
+            for (int x = xlo; x <= xhi; ++x) acc += (double)f[(long long)z * g.pitch + x];
+    }
+    out[i] = (float)acc;
+}
+
+static size_t born_smem() { return 2 * SH * SW * sizeof(float); }
+static size_t adj_smem() { return (2 * SH * SW + TZ * TX) * sizeof(float); }
+
+void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float dt2,
+                 float mcfl, float *W, float *rho_pad, int *err, cudaStream_t st)
+{
+    count_launch();
+    k_prep<<<1216, 256, 0, st>>>(g, nz, nx, m, rho, dt2, mcfl, W, rho_pad, err);
+}
+
+void launch_fwd(const Geo &g, const FwdArgs &a, cudaStream_t st)
+{
+    count_launch();
+    k_fwd<<<dim3(g.ntiles, g.S), dim3(BX, BY), 0, st>>>(g, a);
+}
+
+cudaError_t init_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_born, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)born_smem());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem());
+    return e;
+}
+
+void launch_born(const Geo &g, const BornArgs &a, cudaStream_t st)
+{
+    count_launch();
+    k_born<<<dim3(g.ntiles, g.S), dim3(BX, BY), born_smem(), st>>>(g, a);
+}
+
+void launch_adj(const Geo &g, const AdjArgs &a, cudaStream_t st)
+{
+    count_launch();
+    k_adj<<<dim3(g.ntiles, g.S), dim3(BX, BY), adj_smem(), st>>>(g, a);
+}
+
+void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, float *out, cudaStream_t st)
+{
+    const int n = nz * nx;
+    count_launch();
+    k_shot_sum<<<(n + 255) / 256, 256, 0, st>>>(g, nz, nx, img, out);
+}
+
+}  // namespace aafwi
