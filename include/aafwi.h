@@ -146,6 +146,13 @@ int aafwi_adjoint_gradient(aafwi_plan *plan, int mode, const float *m, const flo
                            const float *d_obs, float *grad, double *J_host, int flags,
                            aafwi_stream stream);
 
+/* Adjoint-state gradient for an arbitrary adjoint source (the data-space
+ * derivative dJ/df of any misfit, Sec. 2.2 eq. FWI_adj): grad = (dF/dm)^T adj_src.
+ * m: device [nz][nx]; adj_src: device CSR traces; grad: device [nz][nx].
+ * flags: AAFWI_REUSE_FORWARD as in aafwi_adjoint_gradient. */
+int aafwi_fwi_adjoint(aafwi_plan *plan, const float *m, const float *adj_src, float *grad,
+                      int flags, aafwi_stream stream);
+
 /* L^T: residual traces -> image on the physical grid (RTM image when
  * resid = d_r; Sec. 4.3 start model m_RTM = L^T d_r). */
 int aafwi_born_adjoint(aafwi_plan *plan, const float *m0, const float *resid,

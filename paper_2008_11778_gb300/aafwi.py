@@ -22,7 +22,7 @@ REUSE_FORWARD = 1
 # every entry point declared in include/aafwi.h
 EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aafwi_last_error",
            "aafwi_model_forward", "aafwi_born_forward", "aafwi_misfit", "aafwi_adjoint_gradient",
-           "aafwi_born_adjoint", "aafwi_read_misfit", "aafwi_aa_create", "aafwi_aa_destroy",
+           "aafwi_born_adjoint", "aafwi_fwi_adjoint", "aafwi_read_misfit", "aafwi_aa_create", "aafwi_aa_destroy",
            "aafwi_aa_set_eta", "aafwi_aa_step", "aafwi_aa_combine", "aafwi_absmax",
            "aafwi_launch_count")
 
@@ -80,6 +80,7 @@ def load(path=LIB_PATH):
         "aafwi_misfit": ([P, P, P, P, P, P], I),
         "aafwi_adjoint_gradient": ([P, I, P, P, P, P, P, I, P], I),
         "aafwi_born_adjoint": ([P, P, P, P, P], I),
+        "aafwi_fwi_adjoint": ([P, P, P, P, I, P], I),
         "aafwi_read_misfit": ([P, P, P], I),
         "aafwi_aa_create": ([Z, I, D, P], I),
         "aafwi_aa_destroy": ([P], None),
@@ -185,6 +186,11 @@ class Plan:
                                              REUSE_FORWARD if reuse_forward else 0, _stream(stream)),
                self.h)
         return J.value if sync else None
+
+    def fwi_adjoint(self, m, adj_src, grad, reuse_forward=False, stream=None):
+        _check(load().aafwi_fwi_adjoint(self.h, _f32(m), _f32(adj_src), _f32(grad),
+                                        REUSE_FORWARD if reuse_forward else 0, _stream(stream)), self.h)
+        return grad
 
     def born_adjoint(self, m0, resid, img, stream=None):
         _check(load().aafwi_born_adjoint(self.h, _f32(m0), _f32(resid), _f32(img), _stream(stream)), self.h)

@@ -42,7 +42,7 @@ struct aafwi_plan {
     Geo geo{};
     std::vector<Buf> bufs;
     // device buffers
-    float *W = nullptr, *rho_pad = nullptr;
+    float *m_pad = nullptr, *rho_pad = nullptr;
     float *hist = nullptr;          // full: (nt_max+1) slots; else 2*nck checkpoint slots
     float *fbuf = nullptr;          // 2 rotating forward slots (checkpoint mode)
     float *rbuf = nullptr;          // k-1 replay slots (checkpoint mode)
@@ -88,6 +88,7 @@ bool dalloc(std::vector<Buf> &bufs, T **out, size_t count)
         return false;
     }
     bufs.push_back({p, bytes});
+    if (cudaMemset(p, 0, bytes) != cudaSuccess) return false;   // u^0 = 0, zero pitch padding
     *out = static_cast<T *>(p);
     return true;
 }
@@ -147,12 +148,12 @@ int run_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
             }
         }
         if (born) {
-            BornArgs a{p->W, p->rho_pad, cur, prev, next, slot(p->dbuf, ps, n & 1),
+            BornArgs a{p->m_pad, p->rho_pad, cur, prev, next, slot(p->dbuf, ps, n & 1),
                        slot(p->dbuf, ps, (n + 1) & 1), slot(p->dbuf, ps, (n + 1) & 1), ckc, ckp,
                        traces, n};
             launch_born(p->geo, a, st);
         } else {
-            FwdArgs a{p->W, cur, prev, next, ckc, ckp, traces, n};
+            FwdArgs a{p->m_pad, cur, prev, next, ckc, ckp, traces, n};
             launch_fwd(p->geo, a, st);
         }
     }
@@ -167,7 +168,7 @@ int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
         cudaMemsetAsync(p->img, 0, ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
     auto adj = [&](int n, const float *u) {
-        AdjArgs a{p->W, slot(p->zbuf, ps, (n + 1) & 1), slot(p->zbuf, ps, n & 1), u, resid, p->img,
+        AdjArgs a{p->m_pad, slot(p->zbuf, ps, (n + 1) & 1), slot(p->zbuf, ps, n & 1), u, resid, p->img,
                   n, born ? 1 : 0};
         launch_adj(p->geo, a, st);
     };
@@ -177,7 +178,7 @@ int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
         for (int j = p->nck - 1; j >= 0; --j) {
             const int a = j * p->k, e = std::min(a + p->k, p->nt_max);
             for (int n = a; n <= e - 2; ++n) {
-                FwdArgs f{p->W, seg_u(p, j, a, n), seg_u(p, j, a, n - 1), seg_u(p, j, a, n + 1),
+                FwdArgs f{p->m_pad, seg_u(p, j, a, n), seg_u(p, j, a, n - 1), seg_u(p, j, a, n + 1),
                           nullptr, nullptr, nullptr, n};
                 launch_fwd(p->geo, f, st);
             }
@@ -191,8 +192,8 @@ int prep(aafwi_plan *p, const float *m, const float *rho, cudaStream_t st)
 {
     const double h = std::min(p->dx, p->dz);
     const double mcfl = std::pow(p->dt / (kCflLimit * h), 2.0);  // m below this violates CFL
-    launch_prep(p->geo, p->nz, p->nx, m, rho, (float)(p->dt * p->dt), (float)mcfl, p->W,
-                rho ? p->rho_pad : nullptr, p->err, st);
+    launch_prep(p->geo, p->nz, p->nx, m, rho, (float)mcfl, p->m_pad, rho ? p->rho_pad : nullptr,
+                p->err, st);
     return check_launch(p);
 }
 
@@ -308,12 +309,14 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
         }
         trec_off.push_back((int)trec_pt.size());
     }
-    // sponge tables (FP64 -> FP32) and scaled wavelet
+    // sponge tables 1 - g(d) (FP64 -> FP32; 1 beyond NX so that G = 0 in the
+    // pitch padding) and the wavelet in stencil units 5040 dx^2 w(t_n)/(dx dz)
     auto depth = [&](int i, int n) { return i < g->nb ? g->nb - i : (i > n - 1 - g->nb ? i - (n - 1 - g->nb) : 0); };
-    std::vector<float> Gz(p->NZ), Gx(p->pitch, 0.f), ws(p->nt_max);
-    for (int i = 0; i < p->NZ; ++i) Gz[i] = (float)std::exp(-std::pow(kSpongeA * depth(i, p->NZ), 2));
-    for (int i = 0; i < p->NX; ++i) Gx[i] = (float)std::exp(-std::pow(kSpongeA * depth(i, p->NX), 2));
-    for (int n = 0; n < p->nt_max; ++n) ws[n] = (float)(wavelet[n] / (g->dx * g->dz));
+    std::vector<float> dGz(p->NZ), dGx(p->pitch, 1.f), ws(p->nt_max);
+    for (int i = 0; i < p->NZ; ++i) dGz[i] = (float)(1.0 - std::exp(-std::pow(kSpongeA * depth(i, p->NZ), 2)));
+    for (int i = 0; i < p->NX; ++i) dGx[i] = (float)(1.0 - std::exp(-std::pow(kSpongeA * depth(i, p->NX), 2)));
+    const double t5040 = 5040.0 * g->dx * g->dx;
+    for (int n = 0; n < p->nt_max; ++n) ws[n] = (float)(t5040 * wavelet[n] / (g->dx * g->dz));
     // workspace plan
     const size_t F = (size_t)p->field * sizeof(float), SF = F * S;
     const size_t fixed = 2 * F + (2 + 2 + 1) * SF + 2 * (size_t)p->trace_count * sizeof(float) + (1 << 20);
@@ -344,17 +347,17 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     }
     // device allocations
     int *d_nt, *d_src, *d_toff, *d_tpt, *d_tcol, *d_nrec;
-    float *d_ws, *d_Gz, *d_Gx;
+    float *d_ws, *d_Gz, *d_Gx;  // wavelet, 1 - g tables
     long long *d_troff;
     std::vector<int> trec_pt_nz = trec_pt.empty() ? std::vector<int>{0} : trec_pt;
     std::vector<int> trec_col_nz = trec_col.empty() ? std::vector<int>{0} : trec_col;
     bool ok = upload(p->bufs, &d_nt, p->nt) && upload(p->bufs, &d_src, src_pt) &&
               upload(p->bufs, &d_toff, trec_off) && upload(p->bufs, &d_tpt, trec_pt_nz) &&
               upload(p->bufs, &d_tcol, trec_col_nz) && upload(p->bufs, &d_nrec, nrec) &&
-              upload(p->bufs, &d_ws, ws) && upload(p->bufs, &d_Gz, Gz) && upload(p->bufs, &d_Gx, Gx) &&
+              upload(p->bufs, &d_ws, ws) && upload(p->bufs, &d_Gz, dGz) && upload(p->bufs, &d_Gx, dGx) &&
               upload(p->bufs, &d_troff, p->tr_off);
     const long long ps = (long long)S * p->field;
-    ok = ok && dalloc(p->bufs, &p->W, p->field) && dalloc(p->bufs, &p->rho_pad, p->field) &&
+    ok = ok && dalloc(p->bufs, &p->m_pad, p->field) && dalloc(p->bufs, &p->rho_pad, p->field) &&
          dalloc(p->bufs, &p->dbuf, 2 * ps) && dalloc(p->bufs, &p->zbuf, 2 * ps) &&
          dalloc(p->bufs, &p->img, ps) && dalloc(p->bufs, &p->dsyn, p->trace_count) &&
          dalloc(p->bufs, &p->resid, p->trace_count) && dalloc(p->bufs, &p->partials, RED_BLOCKS) &&
@@ -372,8 +375,6 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
         delete p;
         return fail(nullptr, AAFWI_ERR_NOMEM, "cudaMalloc failed for the plan workspace");
     }
-    // zero-initialise every field buffer (the pitch padding and u^0 must be 0)
-    for (auto &b : p->bufs) cudaMemset(b.p, 0, b.bytes);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_bufs(p->bufs);
@@ -383,10 +384,15 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     Geo &G = p->geo;
     G.NZ = p->NZ; G.NX = p->NX; G.pitch = p->pitch; G.nb = p->nb; G.S = S;
     G.ntz = ntz; G.ntx = ntx; G.ntiles = ntiles; G.field = p->field;
-    G.idz2 = (float)(1.0 / (g->dz * g->dz));
-    G.idx2 = (float)(1.0 / (g->dx * g->dx));
-    G.inv_dt2 = (float)(1.0 / (g->dt * g->dt));
-    G.nt = d_nt; G.src_pt = d_src; G.ws = d_ws; G.Gz = d_Gz; G.Gx = d_Gx;
+    G.rz = (float)((g->dx * g->dx) / (g->dz * g->dz));
+    {
+        const double K = g->dt * g->dt / t5040;
+        G.Khi = (float)K;
+        G.Klo = (float)(K - (double)G.Khi);
+    }
+    G.tscale = (float)(1.0 / t5040);
+    G.inj_scale = (float)t5040;
+    G.nt = d_nt; G.src_pt = d_src; G.ws = d_ws; G.dGz = d_Gz; G.dGx = d_Gx;
     G.trec_off = d_toff; G.trec_pt = d_tpt; G.trec_col = d_tcol; G.tr_off = d_troff; G.nrec = d_nrec;
     *out = p;
     return AAFWI_OK;
@@ -485,6 +491,28 @@ int aafwi_adjoint_gradient(aafwi_plan *p, int mode, const float *m, const float 
     return finish_sync(p, J_host, st);
 }
 
+int aafwi_fwi_adjoint(aafwi_plan *p, const float *m, const float *adj_src, float *grad, int flags,
+                      aafwi_stream stream)
+{
+    if (!p || !m || !adj_src || !grad) return fail(p, AAFWI_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if (flags & AAFWI_REUSE_FORWARD) {
+        if (!p->fwd_valid || p->fwd_model != m)
+            return fail(p, AAFWI_ERR_STATE, "no stored forward wavefield for this model");
+    } else {
+        p->fwd_valid = false;
+        if ((rc = prep(p, m, nullptr, st))) return rc;
+        if ((rc = run_forward(p, false, p->dsyn, st))) return rc;
+    }
+    if ((rc = run_adjoint(p, false, adj_src, st))) return rc;
+    launch_shot_sum(p->geo, p->nz, p->nx, p->img, grad, st);
+    if ((rc = check_launch(p))) return rc;
+    p->fwd_valid = true;
+    p->fwd_model = m;
+    return AAFWI_OK;
+}
+
 int aafwi_born_adjoint(aafwi_plan *p, const float *m0, const float *resid, float *img, aafwi_stream stream)
 {
     if (!p || !m0 || !resid || !img) return fail(p, AAFWI_ERR_ARG, "NULL argument");
@@ -523,7 +551,6 @@ int aafwi_aa_create(size_t n, int M, double eta, aafwi_aa **out)
         delete a;
         return fail(nullptr, AAFWI_ERR_NOMEM, "cudaMalloc failed for the AA state");
     }
-    for (auto &b : a->bufs) cudaMemset(b.p, 0, b.bytes);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         free_bufs(a->bufs);
         delete a;

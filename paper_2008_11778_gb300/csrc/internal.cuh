@@ -25,12 +25,17 @@ struct Geo {
     int NZ, NX, pitch, nb, S;
     int ntz, ntx, ntiles;          // tiles per shot along z, x; total
     long long field;               // floats per shot field (NZ * pitch)
-    float idz2, idx2;              // 1/dz^2, 1/dx^2
-    float inv_dt2;                 // 1/dt^2
+    // The Laplacian is evaluated as T = rz*S_z + S_x with integer weights
+    // (5040 x the 8th-order weights), so that L u = T / (5040 dx^2) and
+    // W (L u + s) = K T / m with K = dt^2 / (5040 dx^2) split in hi + lo.
+    float rz;                      // dx^2 / dz^2
+    float Khi, Klo;                // K = Khi + Klo
+    float tscale;                  // 1 / (5040 dx^2): T -> L u + s
+    float inj_scale;               // 5040 dx^2: residual r -> its T units
     const int *nt;                 // [S] record length
     const int *src_pt;             // [S] padded source point iz*pitch + ix
-    const float *ws;               // [nt_max] w(t_n) / (dx dz)
-    const float *Gz, *Gx;          // [NZ], [pitch] sponge factors (0 beyond NX)
+    const float *ws;               // [nt_max] 5040 dx^2 w(t_n) / (dx dz)
+    const float *dGz, *dGx;        // [NZ], [pitch] 1 - g(d) of the sponge (1 beyond NX)
     const int *trec_off;           // [S*ntiles + 1] receivers per (shot, tile)
     const int *trec_pt;            // padded point of each receiver
     const int *trec_col;           // receiver index within its shot
@@ -41,7 +46,7 @@ struct Geo {
 // One forward step n -> n+1 for all shots.  Field pointers are slot bases
 // (shot s at + s*field).  u_next may alias u_prev (in-place update).
 struct FwdArgs {
-    const float *W;
+    const float *m;                // padded model m = 1/c^2 (extension E applied)
     const float *u_cur;
     const float *u_prev;
     float *u_next;
@@ -52,7 +57,7 @@ struct FwdArgs {
 
 // Born step: background u and scattered du together (eq. Born).
 struct BornArgs {
-    const float *W, *rho;
+    const float *m, *rho;
     const float *u_cur, *u_prev;
     float *u_next;
     const float *d_cur, *d_prev;
@@ -63,9 +68,9 @@ struct BornArgs {
 };
 
 // Adjoint step n (z^n from z^{n+1}, z^{n+2}) fused with the imaging condition
-// img += scale * z^n * (L u^n + s^n), scale = -W/dt^2 (FWI) or -1 (Born).
+// img += scale * z^n * (L u^n + s^n), scale = -1/m (FWI) or -1 (Born).
 struct AdjArgs {
-    const float *W;
+    const float *m;
     const float *z1;               // z^{n+1}
     float *z2n;                    // in: z^{n+2}; out: z^n (same cells)
     const float *u;                // u^n
@@ -80,8 +85,8 @@ extern std::atomic<unsigned long long> g_launch_count;
 inline void count_launch(unsigned n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
 
 cudaError_t init_kernels();  // per-device kernel attributes (dynamic shared memory)
-void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float dt2,
-                 float cfl_h, float *W, float *rho_pad, int *err, cudaStream_t st);
+void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float mcfl,
+                 float *m_pad, float *rho_pad, int *err, cudaStream_t st);
 void launch_fwd(const Geo &g, const FwdArgs &a, cudaStream_t st);
 void launch_born(const Geo &g, const BornArgs &a, cudaStream_t st);
 void launch_adj(const Geo &g, const AdjArgs &a, cudaStream_t st);

@@ -3,12 +3,23 @@
 // its exact discrete adjoint fused with the imaging condition (eqs. FWI_adj,
 // adj_grad1).
 //
-// Scheme (leap-frog, 8th-order Laplacian, Cerjan sponge G, W = dt^2/m):
+// Scheme (leap-frog, 8th-order Laplacian L, Cerjan sponge G, W = dt^2/m):
 //   forward   u^{n+1} = G (2 u^n - G u^{n-1} + W (L u^n + s^n))
 //   Born      du^{n+1} = G (2 du^n - G du^{n-1} + W L du^n) - G W rho (L u^n + s^n)
 //   adjoint   z^n = G (2 z^{n+1} - G z^{n+2} + W (L z^{n+1} + R^T r^n))
-//   imaging   img += scale z^n (L u^n + s^n),  scale = -W/dt^2 (= -1/m, FWI)
-//                                              or -1 (Born adjoint)
+//   imaging   img += scale z^n (L u^n + s^n),  scale = -1/m (FWI) or -1 (Born)
+//
+// FP32 evaluation chosen to keep the rounding error of long runs small
+// (the residual of an inversion is often < 1 % of the data, so trace errors
+// are amplified in the misfit and the gradient):
+//   * L is evaluated as differences to the centre cell with the integer
+//     weights 5040 x (8/5, -1/5, 8/315, -1/560) = (8064, -1008, 128, -9):
+//     T = sum_k a_k [(u_{+k} - u) + (u_{-k} - u)]  (the centre weight is
+//     -2 sum a_k exactly), so no weight carries a rounding error and the
+//     large-magnitude cancellation of c0 u against the neighbours is avoided;
+//   * W (L u + s) = K T / m with K = dt^2/(5040 dx^2) applied as hi + lo;
+//   * G x is applied as x - (1 - G) x with 1 - G tabulated, which is exact
+//     (G = 1) in the interior and accurate to |1-G| eps in the sponge.
 // One launch advances every shot by one step: grid (tiles per shot, shots).
 // A CTA stages its TZ x TX tile plus a 4-cell halo of each stencil input in
 // shared memory with 128-bit loads; each thread owns one float4 column group
@@ -20,12 +31,12 @@ namespace aafwi {
 
 std::atomic<unsigned long long> g_launch_count{0};
 
-// Fornberg's 8th-order central weights for the second derivative.
-constexpr float C0 = (float)(-205.0 / 72.0);
-constexpr float C1 = (float)(8.0 / 5.0);
-constexpr float C2 = (float)(-1.0 / 5.0);
-constexpr float C3 = (float)(8.0 / 315.0);
-constexpr float C4 = (float)(-1.0 / 560.0);
+// 5040 x Fornberg's 8th-order central weights for the second derivative at
+// offsets 1..4 (the centre weight is -2 x their sum).
+constexpr float A1 = 8064.f;
+constexpr float A2 = -1008.f;
+constexpr float A3 = 128.f;
+constexpr float A4 = -9.f;
 
 typedef float Tile[SW];
 
@@ -68,25 +79,30 @@ __device__ __forceinline__ void load_tile(Tile *s, const float *f, int z0, int x
     }
 }
 
-// L applied at the four cells (rr, cc..cc+3) of a staged tile.
-__device__ __forceinline__ float4 lap4(const Tile *s, int rr, int cc, float idz2, float idx2)
+__device__ __forceinline__ float d2(float c, float a, float b) { return (a - c) + (b - c); }
+
+// T = rz * S_z + S_x at the four cells (rr, cc..cc+3) of a staged tile, where
+// S is the integer-weight second difference along each axis (L = T/(5040 dx^2)).
+__device__ __forceinline__ float4 stencil4(const Tile *s, int rr, int cc, float rz)
 {
     const float4 L = ld4s(s, rr, cc - 4), M = ld4s(s, rr, cc), R = ld4s(s, rr, cc + 4);
     const float v[12] = {L.x, L.y, L.z, L.w, M.x, M.y, M.z, M.w, R.x, R.y, R.z, R.w};
-    float ax[4];
+    float sx[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-        ax[i] = C0 * v[4 + i] + C1 * (v[3 + i] + v[5 + i]) + C2 * (v[2 + i] + v[6 + i])
-              + C3 * (v[1 + i] + v[7 + i]) + C4 * (v[i] + v[8 + i]);
+    for (int i = 0; i < 4; ++i) {
+        const float c = v[4 + i];
+        sx[i] = A1 * d2(c, v[3 + i], v[5 + i]) + A2 * d2(c, v[2 + i], v[6 + i])
+              + A3 * d2(c, v[1 + i], v[7 + i]) + A4 * d2(c, v[i], v[8 + i]);
+    }
     const float4 a1 = ld4s(s, rr - 1, cc), b1 = ld4s(s, rr + 1, cc);
     const float4 a2 = ld4s(s, rr - 2, cc), b2 = ld4s(s, rr + 2, cc);
     const float4 a3 = ld4s(s, rr - 3, cc), b3 = ld4s(s, rr + 3, cc);
     const float4 a4 = ld4s(s, rr - 4, cc), b4 = ld4s(s, rr + 4, cc);
     float4 o;
-    o.x = (C0 * M.x + C1 * (a1.x + b1.x) + C2 * (a2.x + b2.x) + C3 * (a3.x + b3.x) + C4 * (a4.x + b4.x)) * idz2 + ax[0] * idx2;
-    o.y = (C0 * M.y + C1 * (a1.y + b1.y) + C2 * (a2.y + b2.y) + C3 * (a3.y + b3.y) + C4 * (a4.y + b4.y)) * idz2 + ax[1] * idx2;
-    o.z = (C0 * M.z + C1 * (a1.z + b1.z) + C2 * (a2.z + b2.z) + C3 * (a3.z + b3.z) + C4 * (a4.z + b4.z)) * idz2 + ax[2] * idx2;
-    o.w = (C0 * M.w + C1 * (a1.w + b1.w) + C2 * (a2.w + b2.w) + C3 * (a3.w + b3.w) + C4 * (a4.w + b4.w)) * idz2 + ax[3] * idx2;
+    o.x = rz * (A1 * d2(M.x, a1.x, b1.x) + A2 * d2(M.x, a2.x, b2.x) + A3 * d2(M.x, a3.x, b3.x) + A4 * d2(M.x, a4.x, b4.x)) + sx[0];
+    o.y = rz * (A1 * d2(M.y, a1.y, b1.y) + A2 * d2(M.y, a2.y, b2.y) + A3 * d2(M.y, a3.y, b3.y) + A4 * d2(M.y, a4.y, b4.y)) + sx[1];
+    o.z = rz * (A1 * d2(M.z, a1.z, b1.z) + A2 * d2(M.z, a2.z, b2.z) + A3 * d2(M.z, a3.z, b3.z) + A4 * d2(M.z, a4.z, b4.z)) + sx[2];
+    o.w = rz * (A1 * d2(M.w, a1.w, b1.w) + A2 * d2(M.w, a2.w, b2.w) + A3 * d2(M.w, a3.w, b3.w) + A4 * d2(M.w, a4.w, b4.w)) + sx[3];
     return o;
 }
 
@@ -102,17 +118,34 @@ __device__ __forceinline__ void add_source(float4 &q, int src, int pt, float w)
     }
 }
 
-__device__ __forceinline__ float4 leapfrog(float4 G, float4 cur, float4 prev, float4 W, float4 q)
+// G (2 cur - G prev + K T / m) with G x = x - dG x.
+__device__ __forceinline__ float step1(float dG, float cur, float prev, float T, float m, float Khi,
+                                       float Klo)
 {
-    float4 o;
-    o.x = G.x * (2.f * cur.x - G.x * prev.x + W.x * q.x);
-    o.y = G.y * (2.f * cur.y - G.y * prev.y + W.y * q.y);
-    o.z = G.z * (2.f * cur.z - G.z * prev.z + W.z * q.z);
-    o.w = G.w * (2.f * cur.w - G.w * prev.w + W.w * q.w);
-    return o;
+    const float y = T / m;
+    const float wq = fmaf(Khi, y, Klo * y);
+    const float gp = prev - dG * prev;
+    const float t = ((cur - gp) + cur) + wq;
+    return t - dG * t;
 }
 
-// Write u_next at this tile's receivers into the CSR traces (sample n).
+__device__ __forceinline__ float4 leapfrog(float4 dG, float4 cur, float4 prev, float4 T, float4 m,
+                                           const Geo &g)
+{
+    return make_float4(step1(dG.x, cur.x, prev.x, T.x, m.x, g.Khi, g.Klo),
+                       step1(dG.y, cur.y, prev.y, T.y, m.y, g.Khi, g.Klo),
+                       step1(dG.z, cur.z, prev.z, T.z, m.z, g.Khi, g.Klo),
+                       step1(dG.w, cur.w, prev.w, T.w, m.w, g.Khi, g.Klo));
+}
+
+// 1 - G(z, x) = dz + dx - dz dx for the four cells of a float4 group.
+__device__ __forceinline__ float4 sponge4(float dz, float4 dx)
+{
+    return make_float4(dz + dx.x - dz * dx.x, dz + dx.y - dz * dx.y, dz + dx.z - dz * dx.z,
+                       dz + dx.w - dz * dx.w);
+}
+
+// Write f at this tile's receivers into the CSR traces (sample n).
 __device__ __forceinline__ void gather(const Geo &g, int s, int tile, int n, const float *f,
                                        float *traces)
 {
@@ -139,7 +172,7 @@ __global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a)
     __syncthreads();
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {
-        const float4 gx = ld4g(g.Gx + x);
+        const float4 dgx = ld4g(g.dGx + x);
         const int src = g.src_pt[s];
         const float wsn = g.ws[a.n];
 #pragma unroll
@@ -147,14 +180,13 @@ __global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a)
             const int zl = threadIdx.y + r * BY, z = z0 + zl;
             if (z >= g.NZ) break;
             const long long cell = (long long)z * g.pitch + x;
-            float4 q = lap4(su, zl + HALO, xl + HALO, g.idz2, g.idx2);
-            add_source(q, src, (int)cell, wsn);
-            const float gz = g.Gz[z];
-            const float4 G = make_float4(gz * gx.x, gz * gx.y, gz * gx.z, gz * gx.w);
+            float4 T = stencil4(su, zl + HALO, xl + HALO, g.rz);
+            add_source(T, src, (int)cell, wsn);
+            const float4 dG = sponge4(g.dGz[z], dgx);
             const float4 uc = ld4s(su, zl + HALO, xl + HALO);
             const float4 up = ld4g(a.u_prev + base + cell);
-            const float4 W = ld4g(a.W + cell);
-            st4g(a.u_next + base + cell, leapfrog(G, uc, up, W, q));
+            const float4 m = ld4g(a.m + cell);
+            st4g(a.u_next + base + cell, leapfrog(dG, uc, up, T, m, g));
             if (a.ck_cur) {
                 st4g(a.ck_cur + base + cell, uc);
                 st4g(a.ck_prev + base + cell, up);
@@ -180,7 +212,7 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a)
     __syncthreads();
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {
-        const float4 gx = ld4g(g.Gx + x);
+        const float4 dgx = ld4g(g.dGx + x);
         const int src = g.src_pt[s];
         const float wsn = g.ws[a.n];
 #pragma unroll
@@ -188,24 +220,23 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a)
             const int zl = threadIdx.y + r * BY, z = z0 + zl;
             if (z >= g.NZ) break;
             const long long cell = (long long)z * g.pitch + x;
-            float4 q = lap4(su, zl + HALO, xl + HALO, g.idz2, g.idx2);
-            add_source(q, src, (int)cell, wsn);
-            const float4 qd = lap4(sd, zl + HALO, xl + HALO, g.idz2, g.idx2);
-            const float gz = g.Gz[z];
-            const float4 G = make_float4(gz * gx.x, gz * gx.y, gz * gx.z, gz * gx.w);
-            const float4 W = ld4g(a.W + cell);
+            float4 T = stencil4(su, zl + HALO, xl + HALO, g.rz);
+            add_source(T, src, (int)cell, wsn);
+            float4 Td = stencil4(sd, zl + HALO, xl + HALO, g.rz);
             const float4 rho = ld4g(a.rho + cell);
+            // scattered source: W L du - W rho (L u + s)  ->  K (T_d - rho T) / m
+            Td.x -= rho.x * T.x;
+            Td.y -= rho.y * T.y;
+            Td.z -= rho.z * T.z;
+            Td.w -= rho.w * T.w;
+            const float4 dG = sponge4(g.dGz[z], dgx);
+            const float4 m = ld4g(a.m + cell);
             const float4 uc = ld4s(su, zl + HALO, xl + HALO);
             const float4 up = ld4g(a.u_prev + base + cell);
             const float4 dc = ld4s(sd, zl + HALO, xl + HALO);
             const float4 dp = ld4g(a.d_prev + base + cell);
-            float4 dn = leapfrog(G, dc, dp, W, qd);
-            dn.x -= G.x * W.x * rho.x * q.x;
-            dn.y -= G.y * W.y * rho.y * q.y;
-            dn.z -= G.z * W.z * rho.z * q.z;
-            dn.w -= G.w * W.w * rho.w * q.w;
-            st4g(a.u_next + base + cell, leapfrog(G, uc, up, W, q));
-            st4g(a.d_next + base + cell, dn);
+            st4g(a.u_next + base + cell, leapfrog(dG, uc, up, T, m, g));
+            st4g(a.d_next + base + cell, leapfrog(dG, dc, dp, Td, m, g));
             if (a.ck_cur) {
                 st4g(a.ck_cur + base + cell, uc);
                 st4g(a.ck_prev + base + cell, up);
@@ -241,13 +272,13 @@ __global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a)
         for (int i = r0 + tid; i < r1; i += BX * BY) {
             const int pt = g.trec_pt[i];
             const int zz = pt / g.pitch, xx = pt - zz * g.pitch;
-            sinj[zz - z0][xx - x0] = a.resid[tb + g.trec_col[i]];
+            sinj[zz - z0][xx - x0] = g.inj_scale * a.resid[tb + g.trec_col[i]];
         }
     }
     __syncthreads();
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x >= g.pitch) return;
-    const float4 gx = ld4g(g.Gx + x);
+    const float4 dgx = ld4g(g.dGx + x);
     const int src = g.src_pt[s];
     const float wsn = g.ws[a.n];
 #pragma unroll
@@ -255,47 +286,47 @@ __global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a)
         const int zl = threadIdx.y + r * BY, z = z0 + zl;
         if (z >= g.NZ) break;
         const long long cell = (long long)z * g.pitch + x;
-        float4 rhs = lap4(sz, zl + HALO, xl + HALO, g.idz2, g.idx2);
+        float4 Tz = stencil4(sz, zl + HALO, xl + HALO, g.rz);
         if (has_rec) {
             const float4 inj = *reinterpret_cast<const float4 *>(&sinj[zl][xl]);
-            rhs.x += inj.x; rhs.y += inj.y; rhs.z += inj.z; rhs.w += inj.w;
+            Tz.x += inj.x; Tz.y += inj.y; Tz.z += inj.z; Tz.w += inj.w;
         }
-        const float gz = g.Gz[z];
-        const float4 G = make_float4(gz * gx.x, gz * gx.y, gz * gx.z, gz * gx.w);
-        const float4 W = ld4g(a.W + cell);
+        const float4 dG = sponge4(g.dGz[z], dgx);
+        const float4 m = ld4g(a.m + cell);
         const float4 z1 = ld4s(sz, zl + HALO, xl + HALO);
         const float4 z2 = ld4g(a.z2n + base + cell);
-        const float4 zn = leapfrog(G, z1, z2, W, rhs);
-        float4 qu = lap4(su, zl + HALO, xl + HALO, g.idz2, g.idx2);
-        add_source(qu, src, (int)cell, wsn);
+        const float4 zn = leapfrog(dG, z1, z2, Tz, m, g);
+        float4 Tu = stencil4(su, zl + HALO, xl + HALO, g.rz);
+        add_source(Tu, src, (int)cell, wsn);
+        // L u + s = Tu * tscale; FWI scale -1/m, Born scale -1
         float4 sc;
         if (a.born) {
-            sc = make_float4(-1.f, -1.f, -1.f, -1.f);
+            sc = make_float4(-g.tscale, -g.tscale, -g.tscale, -g.tscale);
         } else {
-            sc = make_float4(-W.x * g.inv_dt2, -W.y * g.inv_dt2, -W.z * g.inv_dt2, -W.w * g.inv_dt2);
+            sc = make_float4(-g.tscale / m.x, -g.tscale / m.y, -g.tscale / m.z, -g.tscale / m.w);
         }
         float4 im = ld4g(a.img + base + cell);
-        im.x += sc.x * zn.x * qu.x;
-        im.y += sc.y * zn.y * qu.y;
-        im.z += sc.z * zn.z * qu.z;
-        im.w += sc.w * zn.w * qu.w;
+        im.x = fmaf(sc.x * zn.x, Tu.x, im.x);
+        im.y = fmaf(sc.y * zn.y, Tu.y, im.y);
+        im.z = fmaf(sc.z * zn.z, Tu.z, im.z);
+        im.w = fmaf(sc.w * zn.w, Tu.w, im.w);
         st4g(a.img + base + cell, im);
         st4g(a.z2n + base + cell, zn);
     }
 }
 
-// W = dt^2/m and E(rho) on the padded grid from the physical arrays
-// (extension E = clamp to the nearest physical cell); flags bad models:
-// bit 0 non-finite or non-positive m, bit 1 CFL above 0.55.
-__global__ void k_prep(const Geo g, int nz, int nx, const float *m, const float *rho, float dt2,
-                       float mcfl, float *W, float *rho_pad, int *err)
+// m and E(rho) on the padded grid from the physical arrays (extension E =
+// clamp to the nearest physical cell); flags bad models: bit 0 non-finite or
+// non-positive m, bit 1 a velocity above the plan's CFL limit (m < mcfl).
+__global__ void k_prep(const Geo g, int nz, int nx, const float *m, const float *rho, float mcfl,
+                       float *m_pad, float *rho_pad, int *err)
 {
     const long long N = (long long)g.NZ * g.pitch;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         const int z = (int)(i / g.pitch), x = (int)(i - (long long)z * g.pitch);
         if (x >= g.NX) {
-            W[i] = 0.f;
+            m_pad[i] = 1.f;      // pitch padding: finite, and the sponge zeroes the field there
             if (rho_pad) rho_pad[i] = 0.f;
             continue;
         }
@@ -303,7 +334,7 @@ __global__ void k_prep(const Geo g, int nz, int nx, const float *m, const float 
         const float mv = m[(long long)jz * nx + jx];
         if (!(mv > 0.f) || !isfinite(mv)) atomicOr(err, 1);
         else if (mv < mcfl) atomicOr(err, 2);
-        W[i] = dt2 / mv;
+        m_pad[i] = mv;
         if (rho_pad) rho_pad[i] = rho[(long long)jz * nx + jx];
     }
 }
@@ -329,25 +360,25 @@ __global__ void k_shot_sum(const Geo g, int nz, int nx, const float *img, float 
 static size_t born_smem() { return 2 * SH * SW * sizeof(float); }
 static size_t adj_smem() { return (2 * SH * SW + TZ * TX) * sizeof(float); }
 
-void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float dt2,
-                 float mcfl, float *W, float *rho_pad, int *err, cudaStream_t st)
-{
-    count_launch();
-    k_prep<<<1216, 256, 0, st>>>(g, nz, nx, m, rho, dt2, mcfl, W, rho_pad, err);
-}
-
-void launch_fwd(const Geo &g, const FwdArgs &a, cudaStream_t st)
-{
-    count_launch();
-    k_fwd<<<dim3(g.ntiles, g.S), dim3(BX, BY), 0, st>>>(g, a);
-}
-
 cudaError_t init_kernels()
 {
     cudaError_t e = cudaFuncSetAttribute(k_born, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)born_smem());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem());
     return e;
+}
+
+void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float mcfl,
+                 float *m_pad, float *rho_pad, int *err, cudaStream_t st)
+{
+    count_launch();
+    k_prep<<<1216, 256, 0, st>>>(g, nz, nx, m, rho, mcfl, m_pad, rho_pad, err);
+}
+
+void launch_fwd(const Geo &g, const FwdArgs &a, cudaStream_t st)
+{
+    count_launch();
+    k_fwd<<<dim3(g.ntiles, g.S), dim3(BX, BY), 0, st>>>(g, a);
 }
 
 void launch_born(const Geo &g, const BornArgs &a, cudaStream_t st)

@@ -37,8 +37,13 @@ class AAInversion:
     """
 
     def __init__(self, plan, d_obs, p0, M, eta=None, eta_factor=1e-4, bounds=None,
-                 lambdas=LAMBDAS, c1=ARMIJO_C1, mode=aafwi.MODE_FWI, m0=None, line_search=True):
+                 lambdas=LAMBDAS, c1=ARMIJO_C1, mode=aafwi.MODE_FWI, m0=None, line_search=True,
+                 grad_fn=None, misfit_fn=None):
+        """grad_fn(x, g_out, reuse) -> J and misfit_fn(x) -> J replace the wave-
+        equation objective (plan / d_obs unused then): Alg. 2 applies to any
+        fixed-point map G(p) = p - eta grad J(p)."""
         self.plan, self.d_obs, self.M = plan, d_obs, M
+        self.grad_fn, self.misfit_fn = grad_fn, misfit_fn
         self.mode, self.m0 = mode, m0
         self.lsrtm = mode == aafwi.MODE_LSRTM
         self.lo, self.hi = (float(bounds[0]), float(bounds[1])) if bounds is not None else (0.0, 0.0)
@@ -48,7 +53,8 @@ class AAInversion:
         self.grad = torch.empty_like(self.p)
         self.p_tilde = torch.empty_like(self.p)
         self.p_bar = torch.empty_like(self.p)
-        self.dsyn = torch.empty(plan.trace_count, dtype=torch.float32, device=self.p.device)
+        self.dsyn = (torch.empty(plan.trace_count, dtype=torch.float32, device=self.p.device)
+                     if plan is not None else None)
         self.J = self._gradient(self.p, False)
         self.J0 = self.J
         self.n_forward, self.n_adjoint = 1, 1
@@ -60,11 +66,15 @@ class AAInversion:
         self.history = {"J": [self.J], "lam": [], "Mk": []}
 
     def _gradient(self, x, reuse):
+        if self.grad_fn is not None:
+            return self.grad_fn(x, self.grad, reuse)
         if self.lsrtm:
             return self.plan.adjoint_gradient(self.mode, self.m0, x, self.d_obs, self.grad)
         return self.plan.adjoint_gradient(self.mode, x, None, self.d_obs, self.grad, reuse_forward=reuse)
 
     def _misfit_only(self, x):
+        if self.misfit_fn is not None:
+            return self.misfit_fn(x)
         if self.lsrtm:
             self.plan.born_forward(self.m0, x, self.dsyn)
         else:
@@ -83,7 +93,7 @@ class AAInversion:
                     Jc = self._misfit_only(self.cand)
                     self.n_forward += 1
                     if Jc <= self.J + self.c1 * min(0.0, dot):
-                        lam, reuse = trial, not self.lsrtm
+                        lam, reuse = trial, not self.lsrtm and self.grad_fn is None
                         break
             else:
                 lam = 1.0
@@ -106,14 +116,16 @@ class AAInversion:
 
 
 def aa_fwi(plan, d_obs, p0, M, iters, eta=None, eta_factor=1e-4, bounds=None, lambdas=LAMBDAS,
-           c1=ARMIJO_C1, mode=aafwi.MODE_FWI, m0=None, line_search=True, target=None, callback=None):
+           c1=ARMIJO_C1, mode=aafwi.MODE_FWI, m0=None, line_search=True, target=None, callback=None,
+           grad_fn=None, misfit_fn=None):
     """Run Alg. 2 for ``iters`` iterations (or until J/J_0 <= target).
 
     Returns a dict with J (J[k] = J(p_k)), lam, Mk, eta, the final p and grad
     (device), n_forward / n_adjoint pass counts and wall seconds per iteration.
     """
     t0 = time.perf_counter()
-    run = AAInversion(plan, d_obs, p0, M, eta, eta_factor, bounds, lambdas, c1, mode, m0, line_search)
+    run = AAInversion(plan, d_obs, p0, M, eta, eta_factor, bounds, lambdas, c1, mode, m0, line_search,
+                      grad_fn, misfit_fn)
     ts = [time.perf_counter() - t0]
     for k in range(iters):
         J = run.step()
