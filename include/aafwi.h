@@ -194,6 +194,33 @@ int aafwi_aa_combine(aafwi_aa *aa, double lambda, const float *p_tilde, const fl
  * used to fix eta = factor * max|p_0| / max|grad J(p_0)|. */
 int aafwi_absmax(const float *x, size_t n, double *host_out, aafwi_stream stream);
 
+/* ---- misfit without device allocation ----------------------------------- */
+
+/* The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they run -- a host framework that owns
+ * the whole device budget through its own pool or caching allocator, or a
+ * latency-bound loop that must not pay the device-wide synchronisation of
+ * cudaMalloc / cudaFree.
+ *
+ * Same result as aafwi_misfit (resid = d_syn - d_obs, J = 1/2 sum resid^2 in
+ * FP64; partial sums over fixed chunks, so the last bits of J may differ from
+ * aafwi_misfit's), without a plan and without allocating: the scratch (FP64
+ * partial sums and J) is a 512 KB file-scope __device__ array of the library,
+ * held on every GPU that loads the library until the process exits.
+ *   d_syn, d_obs: device FP32 [n]; resid: device FP32 [n] or NULL;
+ *   J_dev: device double (written on the stream) or NULL; J_host: host double
+ *   (the call synchronises the stream) or NULL; at least one of the two.
+ * n must lie in [1, AAFWI_MISFIT_NOALLOC_MAX_SAMPLES]; larger inputs return
+ * AAFWI_ERR_ARG with a message (aafwi_last_error(NULL)) and launch nothing.
+ * The first call on a device looks up the array's device address once for
+ * that device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array and every call overwrites it, so
+ * calls whose kernels overlap on the GPU (other streams, other host threads)
+ * race: serialise them on one stream. */
+#define AAFWI_MISFIT_NOALLOC_MAX_SAMPLES (1LL << 32)
+int aafwi_misfit_noalloc(const float *d_syn, const float *d_obs, long long n, float *resid,
+                         double *J_dev, double *J_host, aafwi_stream stream);
+
 /* ---- instrumentation ---------------------------------------------------- */
 
 /* Number of CUDA kernels this library has launched in this process (a host-

@@ -24,7 +24,7 @@ EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aa
            "aafwi_model_forward", "aafwi_born_forward", "aafwi_misfit", "aafwi_adjoint_gradient",
            "aafwi_born_adjoint", "aafwi_fwi_adjoint", "aafwi_read_misfit", "aafwi_aa_create", "aafwi_aa_destroy",
            "aafwi_aa_set_eta", "aafwi_aa_step", "aafwi_aa_combine", "aafwi_absmax",
-           "aafwi_launch_count")
+           "aafwi_launch_count", "aafwi_misfit_noalloc")
 
 
 class AafwiError(RuntimeError):
@@ -89,6 +89,7 @@ def load(path=LIB_PATH):
         "aafwi_aa_combine": ([P, D, P, P, P, ctypes.c_float, ctypes.c_float, P, P], I),
         "aafwi_absmax": ([P, Z, P, P], I),
         "aafwi_launch_count": ([], ctypes.c_ulonglong),
+        "aafwi_misfit_noalloc": ([P, P, ctypes.c_longlong, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -240,6 +241,21 @@ class AA:
                                        float(lo), float(hi), ctypes.byref(dot) if want_dot else None,
                                        _stream(stream)))
         return dot.value if want_dot else None
+
+
+MISFIT_NOALLOC_MAX_SAMPLES = 1 << 32
+
+
+def misfit_noalloc(d_syn, d_obs, resid=None, J_dev=None, sync=True, n=None, stream=None):
+    """aafwi_misfit_noalloc: the misfit with the library's static scratch (no
+    device allocation; for callers that cannot allocate).  Returns J (sync)."""
+    J = ctypes.c_double()
+    n = d_syn.numel() if n is None else int(n)
+    _check(load().aafwi_misfit_noalloc(_f32(d_syn), _f32(d_obs), n,
+                                       _f32(resid) if resid is not None else None,
+                                       _ptr(J_dev) if J_dev is not None else None,
+                                       ctypes.byref(J) if sync else None, _stream(stream)))
+    return J.value if sync else None
 
 
 def launch_count():

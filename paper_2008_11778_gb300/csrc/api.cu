@@ -216,6 +216,8 @@ int finish_sync(aafwi_plan *p, double *J_host, cudaStream_t st)
 
 }  // namespace
 
+void aafwi::set_call_error(const std::string &msg) { g_create_error = msg; }
+
 extern "C" {
 
 const char *aafwi_last_error(const aafwi_plan *plan)

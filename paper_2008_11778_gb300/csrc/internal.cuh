@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 namespace aafwi {
 
@@ -83,6 +84,9 @@ struct AdjArgs {
 // Number of kernels this library has launched (host-side count).
 extern std::atomic<unsigned long long> g_launch_count;
 inline void count_launch(unsigned n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
+
+// Message returned by aafwi_last_error(NULL) for calls made without a plan.
+void set_call_error(const std::string &msg);
 
 cudaError_t init_kernels();  // per-device kernel attributes (dynamic shared memory)
 void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float mcfl,
