@@ -354,6 +354,25 @@ def cpu_baseline(prob):
             "seconds": dt}
 
 
+def ncu_case():
+    """A small case of the benchmark's kernels for ncu --set full captures: the
+    batched geometry (all 32 shots, 400 x 150) cut to 64 time steps; one
+    forward sweep and one adjoint sweep reusing it."""
+    import torch
+    from paper_2008_11778_gb300 import aafwi, synth
+    prob = synth.batched()
+    g = prob.geom.with_nt(64)
+    plan = aafwi.Plan(g, c_max=prob.c_bounds[1])
+    m = torch.as_tensor(prob.m_start.astype(np.float32), device="cuda")
+    d_obs = torch.zeros(plan.trace_count, device="cuda")
+    grad = torch.empty_like(m)
+    plan.model_forward(m)
+    J = plan.adjoint_gradient(aafwi.MODE_FWI, m, None, d_obs, grad, reuse_forward=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": "batched-400x150-32shots-64steps", "J": J,
+                      "launches": aafwi.launch_count()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,8 +382,11 @@ def main():
     ap.add_argument("--kernel-reps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true", help="small case for ncu captures")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.ncu_case:
+        ncu_case()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

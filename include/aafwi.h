@@ -48,7 +48,7 @@ extern "C" {
 #define AAFWI_ERR_CFL       2   /* c_max*dt/min(dx,dz) above the stability limit 0.55 */
 #define AAFWI_ERR_OOB       3   /* source / receiver outside the physical grid */
 #define AAFWI_ERR_NAN       4   /* model has a non-finite or non-positive value */
-#define AAFWI_ERR_TIMEOUT   5   /* a bounded device-side wait ran out */
+#define AAFWI_ERR_TIMEOUT   5   /* a bounded device-side wait ran out (persistent sweeps) */
 #define AAFWI_ERR_CUDA      6   /* a CUDA runtime call failed */
 #define AAFWI_ERR_NOMEM     7   /* workspace does not fit the budget / device */
 #define AAFWI_ERR_STATE     8   /* call out of order (e.g. reuse without a stored forward) */
@@ -92,7 +92,15 @@ typedef struct {
     int checkpoint_every;        /* 0: planner picks (1 = keep every step if it fits,
                                     else k ~ sqrt(2 nt)); 1: force full history */
     int tile_z, tile_x;          /* 0: defaults / autotuned; else a supported tile */
+    int engine;                  /* AAFWI_ENGINE_*: how FWI sweeps are launched */
 } aafwi_plan_opts;
+
+/* plan engines */
+#define AAFWI_ENGINE_AUTO       0   /* persistent when the plan qualifies, else per step */
+#define AAFWI_ENGINE_PER_STEP   1   /* one launch per time step (all shots) */
+#define AAFWI_ENGINE_PERSISTENT 2   /* one cooperative launch per sweep; ARG if the
+                                       plan does not qualify (full history, strips of
+                                       the shots' rows fitting shared memory) */
 
 typedef struct {
     int NZ, NX, pitch;           /* padded grid and row pitch (floats) */
@@ -103,6 +111,8 @@ typedef struct {
     size_t workspace_bytes;
     int tile_z, tile_x;
     int n_tiles;                 /* tiles per shot */
+    int engine;                  /* AAFWI_ENGINE_PER_STEP or AAFWI_ENGINE_PERSISTENT */
+    int persist_ctas;            /* strips of the persistent sweeps (0 if per step) */
 } aafwi_plan_info;
 
 /* ---- plan -------------------------------------------------------------- */
@@ -117,6 +127,13 @@ int aafwi_plan_create(const aafwi_grid *grid, const aafwi_shots *shots,
 void aafwi_plan_destroy(aafwi_plan *plan);
 int aafwi_plan_get_info(const aafwi_plan *plan, aafwi_plan_info *info);
 const char *aafwi_last_error(const aafwi_plan *plan);
+
+/* Failure-detection test hook (not part of the method): from sweep step
+ * `step` on, strip 0 of the persistent sweeps stops publishing its progress,
+ * so its neighbours' bounded waits run out (about a second) and the call
+ * reports AAFWI_ERR_TIMEOUT; the CUDA context stays usable.  step < 0 turns
+ * the hook off.  STATE if the plan has no persistent sweeps. */
+int aafwi_plan_set_stall(aafwi_plan *plan, int step);
 
 /* ---- wave-equation operators (Sec. 2.2) -------------------------------- */
 

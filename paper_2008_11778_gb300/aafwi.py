@@ -21,6 +21,7 @@ REUSE_FORWARD = 1
 
 # every entry point declared in include/aafwi.h
 EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aafwi_last_error",
+           "aafwi_plan_set_stall",
            "aafwi_model_forward", "aafwi_born_forward", "aafwi_misfit", "aafwi_adjoint_gradient",
            "aafwi_born_adjoint", "aafwi_fwi_adjoint", "aafwi_read_misfit", "aafwi_aa_create", "aafwi_aa_destroy",
            "aafwi_aa_set_eta", "aafwi_aa_step", "aafwi_aa_combine", "aafwi_absmax",
@@ -45,9 +46,12 @@ class Shots(ctypes.Structure):
                 ("rec_iz", ctypes.c_void_p), ("rec_ix", ctypes.c_void_p)]
 
 
+ENGINE_AUTO, ENGINE_PER_STEP, ENGINE_PERSISTENT = 0, 1, 2
+
+
 class PlanOpts(ctypes.Structure):
     _fields_ = [("max_workspace_bytes", ctypes.c_size_t), ("checkpoint_every", ctypes.c_int),
-                ("tile_z", ctypes.c_int), ("tile_x", ctypes.c_int)]
+                ("tile_z", ctypes.c_int), ("tile_x", ctypes.c_int), ("engine", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -55,7 +59,8 @@ class PlanInfo(ctypes.Structure):
                 ("S", ctypes.c_int), ("nt_max", ctypes.c_int), ("trace_count", ctypes.c_longlong),
                 ("checkpoint_every", ctypes.c_int), ("n_checkpoints", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_size_t), ("tile_z", ctypes.c_int),
-                ("tile_x", ctypes.c_int), ("n_tiles", ctypes.c_int)]
+                ("tile_x", ctypes.c_int), ("n_tiles", ctypes.c_int), ("engine", ctypes.c_int),
+                ("persist_ctas", ctypes.c_int)]
 
 
 _lib = None
@@ -74,6 +79,7 @@ def load(path=LIB_PATH):
         "aafwi_plan_create": ([P, P, P, P, P], I),
         "aafwi_plan_destroy": ([P], None),
         "aafwi_plan_get_info": ([P, P], I),
+        "aafwi_plan_set_stall": ([P, I], I),
         "aafwi_last_error": ([P], ctypes.c_char_p),
         "aafwi_model_forward": ([P, P, P, P], I),
         "aafwi_born_forward": ([P, P, P, P, P], I),
@@ -130,7 +136,7 @@ def _f32(t):
 class Plan:
     """Owns an aafwi_plan: geometry, workspace and the wave-equation operators."""
 
-    def __init__(self, geom, c_max, max_workspace_bytes=0, checkpoint_every=0):
+    def __init__(self, geom, c_max, max_workspace_bytes=0, checkpoint_every=0, engine=ENGINE_AUTO):
         L = load()
         self.geom = geom
         i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
@@ -141,7 +147,7 @@ class Plan:
         g = Grid(int(geom.nx), int(geom.nz), int(geom.nb), float(geom.dx), float(geom.dz),
                  float(geom.dt), float(c_max))
         s = Shots(len(self._keep[0]), *[ptr(a) for a in self._keep[:6]])
-        o = PlanOpts(int(max_workspace_bytes), int(checkpoint_every), 0, 0)
+        o = PlanOpts(int(max_workspace_bytes), int(checkpoint_every), 0, 0, int(engine))
         h = ctypes.c_void_p()
         _check(L.aafwi_plan_create(ctypes.byref(g), ctypes.byref(s), ptr(self._keep[6]),
                                    ctypes.byref(o), ctypes.byref(h)))
@@ -161,6 +167,10 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def set_stall(self, step):
+        """Failure-detection test hook (see aafwi_plan_set_stall)."""
+        _check(load().aafwi_plan_set_stall(self.h, int(step)), self.h)
 
     # --- operators ---------------------------------------------------------
     def model_forward(self, m, d_out=None, stream=None):

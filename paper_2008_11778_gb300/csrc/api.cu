@@ -55,6 +55,12 @@ struct aafwi_plan {
     size_t ws_bytes = 0;
     bool fwd_valid = false;
     const float *fwd_model = nullptr;
+    // persistent engine
+    bool persist = false;           // FWI sweeps run as one cooperative launch each
+    bool hist_T = false;            // history holds T^n (persistent forward) rather than u^n
+    PGeo pgeo{};
+    size_t psmem = 0;
+    int stall_step = -1;            // test hook (aafwi_plan_set_stall)
     std::string msg;
 };
 
@@ -124,9 +130,22 @@ float *seg_u(aafwi_plan *p, int j, int a, int n)
     return slot(p->rbuf, ps, n - a - 1);
 }
 
+int run_persist_forward(aafwi_plan *p, float *traces, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(p->pgeo.flags, 0, p->pgeo.P * sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "memset");
+    PFwdArgs a{p->m_pad, p->hist, traces, p->nt_max, p->stall_step};
+    e = launch_fwd_persist(p->geo, p->pgeo, a, p->psmem, st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "persistent forward launch");
+    p->hist_T = true;
+    return AAFWI_OK;
+}
+
 // Forward sweep over all shots (born: u and du together); traces -> dsyn.
 int run_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
 {
+    if (p->persist && !born) return run_persist_forward(p, traces, st);
+    p->hist_T = false;
     const long long ps = (long long)p->S * p->field;
     if (!p->full && cudaMemsetAsync(p->fbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
@@ -164,8 +183,17 @@ int run_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
 int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
 {
     const long long ps = (long long)p->S * p->field;
-    if (cudaMemsetAsync(p->zbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess ||
-        cudaMemsetAsync(p->img, 0, ps * sizeof(float), st) != cudaSuccess)
+    if (cudaMemsetAsync(p->img, 0, ps * sizeof(float), st) != cudaSuccess)
+        return cuda_fail(p, cudaGetLastError(), "memset");
+    if (p->hist_T) {
+        cudaError_t e = cudaMemsetAsync(p->pgeo.flags, 0, p->pgeo.P * sizeof(unsigned), st);
+        if (e != cudaSuccess) return cuda_fail(p, e, "memset");
+        PAdjArgs a{p->m_pad, p->hist, resid, p->img, p->nt_max, born ? 1 : 0, p->stall_step};
+        e = launch_adj_persist(p->geo, p->pgeo, a, p->psmem, st);
+        if (e != cudaSuccess) return cuda_fail(p, e, "persistent adjoint launch");
+        return AAFWI_OK;
+    }
+    if (cudaMemsetAsync(p->zbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
     auto adj = [&](int n, const float *u) {
         AdjArgs a{p->m_pad, slot(p->zbuf, ps, (n + 1) & 1), slot(p->zbuf, ps, n & 1), u, resid, p->img,
@@ -209,8 +237,99 @@ int finish_sync(aafwi_plan *p, double *J_host, cudaStream_t st)
         p->fwd_valid = false;
         cudaMemsetAsync(p->err, 0, sizeof(int), st);
         if (err & 1) return fail(p, AAFWI_ERR_NAN, "model has a non-finite or non-positive value");
+        if (err & 4) return fail(p, AAFWI_ERR_TIMEOUT, "a persistent sweep's bounded wait ran out");
         return fail(p, AAFWI_ERR_CFL, "model velocity exceeds the CFL limit of the plan");
     }
+    return AAFWI_OK;
+}
+
+// Decide whether FWI sweeps run persistently and build the strip tables.
+// Returns 0 (engine chosen) or an error code when PERSISTENT was required.
+int setup_persist(aafwi_plan *p, int engine, const aafwi_shots *sh, std::string *why)
+{
+    p->persist = false;
+    if (engine == AAFWI_ENGINE_PER_STEP) return AAFWI_OK;
+    auto no = [&](const char *m) {
+        if (engine == AAFWI_ENGINE_PERSISTENT) {
+            *why = std::string("persistent engine not available: ") + m;
+            return AAFWI_ERR_ARG;
+        }
+        return AAFWI_OK;
+    };
+    if (!p->full) return no("needs the full wavefield history");
+    int dev = 0, sms = 0, coop = 0, smem_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop || sms < 1) return no("cooperative launch unsupported");
+    const int W4 = p->pitch / 4;
+    const long long R = (long long)p->S * p->NZ;
+    const int rows_cap = PT * PGMAX / W4;               // rows a CTA's threads can own
+    int P = (int)std::min<long long>(sms, R / 4);        // strips of at least 4 rows
+    if (P < 1) return no("grid too small");
+    const int rows_max = (int)((R + P - 1) / P);
+    if (rows_max > rows_cap) return no("strips exceed the threads of a CTA");
+    // strips and receiver slots
+    std::vector<int> row0(P + 1);
+    for (int c = 0; c <= P; ++c) row0[c] = (int)(R * c / P);
+    std::vector<int> grp_slot((size_t)R * W4, -1);
+    std::vector<std::vector<std::pair<long long, int4>>> per(P);   // (group, cols) per strip
+    std::vector<std::vector<int>> idx(P);
+    for (int s = 0; s < p->S; ++s) {
+        for (int j = sh->rec_off[s]; j < sh->rec_off[s + 1]; ++j) {
+            const long long gr = (long long)s * p->NZ + sh->rec_iz[j] + p->nb;
+            const int px = sh->rec_ix[j] + p->nb;
+            const long long grp = gr * W4 + px / 4;
+            const int c = (int)(std::upper_bound(row0.begin(), row0.end(), (int)gr) - row0.begin()) - 1;
+            int k = -1;
+            for (size_t q = 0; q < per[c].size(); ++q)
+                if (per[c][q].first == grp) k = (int)q;
+            if (k < 0) {
+                per[c].push_back({grp, make_int4(-1, -1, -1, -1)});
+                k = (int)per[c].size() - 1;
+            }
+            int *lanes = &per[c][k].second.x;
+            lanes[px % 4] = j - sh->rec_off[s];
+        }
+    }
+    std::vector<int> slot_off(P + 1, 0), slot_group;
+    std::vector<int4> slot_cols;
+    int slots_max = 0;
+    for (int c = 0; c < P; ++c) {
+        for (auto &e : per[c]) {
+            grp_slot[e.first] = (int)slot_group.size();
+            slot_group.push_back((int)e.first);
+            slot_cols.push_back(e.second);
+        }
+        slot_off[c + 1] = (int)slot_group.size();
+        slots_max = std::max<int>(slots_max, (int)per[c].size());
+    }
+    const size_t smem = persist_smem(p->geo, rows_max, slots_max);
+    if ((long long)smem > smem_optin) return no("strips do not fit shared memory");
+    if (init_persist_kernels(smem) != cudaSuccess) {
+        cudaGetLastError();
+        return no("kernel attributes");
+    }
+    if (slot_group.empty()) {
+        slot_group.push_back(0);
+        slot_cols.push_back(make_int4(-1, -1, -1, -1));
+    }
+    PGeo &pg = p->pgeo;
+    int *d_row0, *d_gs, *d_so, *d_sg;
+    int4 *d_sc;
+    bool ok = upload(p->bufs, &d_row0, row0) && upload(p->bufs, &d_gs, grp_slot) &&
+              upload(p->bufs, &d_so, slot_off) && upload(p->bufs, &d_sg, slot_group) &&
+              upload(p->bufs, &d_sc, slot_cols) &&
+              dalloc(p->bufs, &pg.exch, (size_t)2 * P * 8 * p->pitch) && dalloc(p->bufs, &pg.flags, P);
+    if (!ok) return no("allocation");
+    pg.P = P;
+    pg.rows_max = rows_max;
+    pg.slot = (long long)p->S * p->field;
+    pg.row0 = d_row0; pg.grp_slot = d_gs; pg.slot_off = d_so; pg.slot_group = d_sg; pg.slot_cols = d_sc;
+    pg.err = p->err;
+    p->psmem = smem;
+    p->persist = true;
     return AAFWI_OK;
 }
 
@@ -396,6 +515,15 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     G.inj_scale = (float)t5040;
     G.nt = d_nt; G.src_pt = d_src; G.ws = d_ws; G.dGz = d_Gz; G.dGx = d_Gx;
     G.trec_off = d_toff; G.trec_pt = d_tpt; G.trec_col = d_tcol; G.tr_off = d_troff; G.nrec = d_nrec;
+    {
+        std::string why;
+        const int rc = setup_persist(p, o.engine, sh, &why);
+        if (rc) {
+            free_bufs(p->bufs);
+            delete p;
+            return fail(nullptr, rc, why);
+        }
+    }
     *out = p;
     return AAFWI_OK;
 }
@@ -405,6 +533,14 @@ void aafwi_plan_destroy(aafwi_plan *p)
     if (!p) return;
     free_bufs(p->bufs);
     delete p;
+}
+
+int aafwi_plan_set_stall(aafwi_plan *p, int step)
+{
+    if (!p) return AAFWI_ERR_ARG;
+    if (!p->persist && step >= 0) return fail(p, AAFWI_ERR_STATE, "plan has no persistent sweeps");
+    p->stall_step = step < 0 ? -1 : step;
+    return AAFWI_OK;
 }
 
 int aafwi_plan_get_info(const aafwi_plan *p, aafwi_plan_info *info)
@@ -418,6 +554,8 @@ int aafwi_plan_get_info(const aafwi_plan *p, aafwi_plan_info *info)
     info->workspace_bytes = p->ws_bytes;
     info->tile_z = TZ; info->tile_x = TX;
     info->n_tiles = p->geo.ntiles;
+    info->engine = p->persist ? AAFWI_ENGINE_PERSISTENT : AAFWI_ENGINE_PER_STEP;
+    info->persist_ctas = p->persist ? p->pgeo.P : 0;
     return AAFWI_OK;
 }
 

@@ -96,6 +96,45 @@ void launch_born(const Geo &g, const BornArgs &a, cudaStream_t st);
 void launch_adj(const Geo &g, const AdjArgs &a, cudaStream_t st);
 void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, float *out, cudaStream_t st);
 
+// Persistent sweeps (persist_kernels.cu): one cooperative launch per sweep,
+// one CTA of PT threads per strip of rows; each thread owns at most PGMAX
+// float4 groups of its strip.
+constexpr int PT = 512;
+constexpr int PGMAX = 10;
+struct PGeo {
+    int P;                         // strips (CTAs)
+    int rows_max;                  // max rows of a strip
+    long long slot;                // floats per history slot (S * field)
+    const int *row0;               // [P+1] strip row ranges in global rows (shot * NZ + z)
+    const int *grp_slot;           // [S*NZ*pitch/4] receiver slot of a float4 group, or -1
+    const int *slot_off;           // [P+1] slots of each strip
+    const int *slot_group;         // [slots] global group index of a slot
+    const int4 *slot_cols;         // [slots] receiver index per lane (-1: none)
+    float *exch;                   // [2][P][8][pitch] strip edge rows
+    unsigned *flags;               // [P] completed steps of each strip
+    int *err;                      // bit 2: a bounded wait ran out
+};
+struct PFwdArgs {
+    const float *m;                // padded model [NZ][pitch]
+    float *hist;                   // slot n+1 <- T^n = 5040 dx^2 (L u^n + s^n); slot 0 untouched
+    float *traces;                 // CSR gather target or null
+    int nt;                        // steps (max over shots)
+    int stall_step;                // test hook: strip 0 stops publishing at this step (-1: never)
+};
+struct PAdjArgs {
+    const float *m;
+    const float *hist;             // T^n (slot n+1) from the forward sweep
+    const float *resid;            // CSR residual traces
+    float *img;                    // per-shot accumulators [S][field]
+    int nt;
+    int born;
+    int stall_step;                // test hook, as in PFwdArgs
+};
+size_t persist_smem(const Geo &g, int rows_max, int slots_max);
+cudaError_t init_persist_kernels(size_t smem);
+cudaError_t launch_fwd_persist(const Geo &g, const PGeo &pg, const PFwdArgs &a, size_t smem, cudaStream_t st);
+cudaError_t launch_adj_persist(const Geo &g, const PGeo &pg, const PAdjArgs &a, size_t smem, cudaStream_t st);
+
 // Reductions (FP64 accumulation, deterministic two-pass).
 constexpr int RED_BLOCKS = 608;    // 4 x 152 SMs
 void launch_misfit(const float *d_syn, const float *d_obs, float *resid, long long n,

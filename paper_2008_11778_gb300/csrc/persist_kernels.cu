@@ -1,0 +1,362 @@
+// persist_kernels.cu -- one persistent, cooperative launch per sweep: the
+// forward sweep (eq. FWD) and the adjoint sweep with the imaging condition
+// (eqs. FWI_adj, adj_grad1) of every shot, all time steps, in one kernel.
+//
+// Decomposition: the rows of all shots (global row = shot * NZ + z) are cut
+// into P contiguous strips, one per CTA (P <= number of SMs, one CTA per SM,
+// co-resident by cooperative launch).  A strip's field lives in shared memory
+// for the whole sweep (plus 4 halo rows above and below) and the previous
+// time level in registers, so a time step touches HBM only for what the
+// method must keep: the forward writes T^n = 5040 dx^2 (L u^n + s^n) of every
+// cell to history slot n+1 (slot 0 stays the zero field u^0 that the per-step
+// engine starts from; T^n is the quantity the imaging condition needs), the
+// adjoint reads it back and accumulates the image.  Neighbouring strips
+// exchange their 4 edge rows each step through a double-buffered global
+// buffer and per-CTA step counters (release / acquire); every wait is bounded
+// and reports AAFWI_ERR_TIMEOUT through the plan's error word instead of
+// hanging.  The arithmetic per cell is that of wave_kernels.cu, in the same
+// order, so results are bitwise equal to the one-launch-per-step path.
+#include "internal.cuh"
+
+namespace aafwi {
+
+constexpr float PA1 = 8064.f;
+constexpr float PA2 = -1008.f;
+constexpr float PA3 = 128.f;
+constexpr float PA4 = -9.f;
+constexpr long long SPIN_LIMIT = 1LL << 22;   // x >= 64 ns sleep: about a second
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ float pd2(float c, float a, float b) { return (a - c) + (b - c); }
+
+// Thread 0 waits until both neighbours have completed `target` steps; the
+// whole CTA learns the outcome.  Returns false on timeout or a raised error.
+__device__ bool wait_neighbours(const PGeo &pg, int c, unsigned target, int *abort_sh)
+{
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        for (int side = -1; side <= 1 && ok; side += 2) {
+            const int nb = c + side;
+            if (nb < 0 || nb >= pg.P) continue;
+            long long it = 0;
+            while (ld_acquire(pg.flags + nb) < target) {
+                if (++it > SPIN_LIMIT || (*(volatile int *)pg.err & 4)) {   // own or a neighbour's timeout
+                    atomicOr(pg.err, 4);
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        *abort_sh = ok ? 0 : 1;
+    }
+    __syncthreads();
+    return *abort_sh == 0;
+}
+
+__device__ __forceinline__ void publish(const PGeo &pg, int c, unsigned steps)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(pg.flags + c, steps);
+    }
+}
+
+// Copy the neighbours' edge rows (exchange buffer `par`) into the halo rows.
+__device__ void load_halo(const Geo &g, const PGeo &pg, float *tile, int c, int nr, int par)
+{
+    const int W4 = g.pitch / 4;
+    for (int i = threadIdx.x; i < 8 * W4; i += blockDim.x) {
+        const int h = i / W4, x4 = i - h * W4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        int dst;
+        if (h < 4) {  // rows -4..-1: bottom edge rows (slots 4..7) of CTA c-1
+            if (c > 0)
+                v = __ldcg(reinterpret_cast<const float4 *>(pg.exch + (((long long)par * pg.P + c - 1) * 8 + 4 + h) * g.pitch) + x4);
+            dst = h;
+        } else {      // rows nr..nr+3: top edge rows (slots 0..3) of CTA c+1
+            if (c + 1 < pg.P)
+                v = __ldcg(reinterpret_cast<const float4 *>(pg.exch + (((long long)par * pg.P + c + 1) * 8 + h - 4) * g.pitch) + x4);
+            dst = nr + h;
+        }
+        reinterpret_cast<float4 *>(tile + (long long)dst * g.pitch)[x4] = v;
+    }
+}
+
+// Publish own rows 0..3 and nr-4..nr-1 of the tile to exchange buffer `par`.
+__device__ void store_edges(const Geo &g, const PGeo &pg, const float *tile, int c, int nr, int par)
+{
+    const int W4 = g.pitch / 4;
+    for (int i = threadIdx.x; i < 8 * W4; i += blockDim.x) {
+        const int h = i / W4, x4 = i - h * W4;
+        const int src = h < 4 ? 4 + h : nr + h - 4;   // tile index of own row h or nr-8+h
+        const float4 v = reinterpret_cast<const float4 *>(tile + (long long)src * g.pitch)[x4];
+        __stcg(reinterpret_cast<float4 *>(pg.exch + (((long long)par * pg.P + c) * 8 + h) * g.pitch) + x4, v);
+    }
+}
+
+// T = rz S_z + S_x at float4 group (tile row tr, column 4*x4) with the z
+// neighbours outside [0, NZ) of the cell's own shot read as zero.
+__device__ __forceinline__ float4 pstencil(const Geo &g, const float *tile, int tr, int x4, int z)
+{
+    const float4 *row = reinterpret_cast<const float4 *>(tile + (long long)tr * g.pitch);
+    const float4 M = row[x4];
+    const float4 L = x4 > 0 ? row[x4 - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 R = (x4 + 1) * 4 < g.pitch ? row[x4 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float v[12] = {L.x, L.y, L.z, L.w, M.x, M.y, M.z, M.w, R.x, R.y, R.z, R.w};
+    float sx[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float c = v[4 + i];
+        sx[i] = PA1 * pd2(c, v[3 + i], v[5 + i]) + PA2 * pd2(c, v[2 + i], v[6 + i])
+              + PA3 * pd2(c, v[1 + i], v[7 + i]) + PA4 * pd2(c, v[i], v[8 + i]);
+    }
+    float4 up[4], dn[4];
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        up[k - 1] = z - k >= 0 ? reinterpret_cast<const float4 *>(tile + (long long)(tr - k) * g.pitch)[x4] : zero;
+        dn[k - 1] = z + k < g.NZ ? reinterpret_cast<const float4 *>(tile + (long long)(tr + k) * g.pitch)[x4] : zero;
+    }
+    float4 o;
+    o.x = g.rz * (PA1 * pd2(M.x, up[0].x, dn[0].x) + PA2 * pd2(M.x, up[1].x, dn[1].x) + PA3 * pd2(M.x, up[2].x, dn[2].x) + PA4 * pd2(M.x, up[3].x, dn[3].x)) + sx[0];
+    o.y = g.rz * (PA1 * pd2(M.y, up[0].y, dn[0].y) + PA2 * pd2(M.y, up[1].y, dn[1].y) + PA3 * pd2(M.y, up[2].y, dn[2].y) + PA4 * pd2(M.y, up[3].y, dn[3].y)) + sx[1];
+    o.z = g.rz * (PA1 * pd2(M.z, up[0].z, dn[0].z) + PA2 * pd2(M.z, up[1].z, dn[1].z) + PA3 * pd2(M.z, up[2].z, dn[2].z) + PA4 * pd2(M.z, up[3].z, dn[3].z)) + sx[2];
+    o.w = g.rz * (PA1 * pd2(M.w, up[0].w, dn[0].w) + PA2 * pd2(M.w, up[1].w, dn[1].w) + PA3 * pd2(M.w, up[2].w, dn[2].w) + PA4 * pd2(M.w, up[3].w, dn[3].w)) + sx[3];
+    return o;
+}
+
+__device__ __forceinline__ float pstep1(float dG, float cur, float prev, float T, float m, float Khi, float Klo)
+{
+    const float y = T / m;
+    const float wq = fmaf(Khi, y, Klo * y);
+    const float gp = prev - dG * prev;
+    const float t = ((cur - gp) + cur) + wq;
+    return t - dG * t;
+}
+
+__device__ __forceinline__ float4 pleap(const Geo &g, float4 dG, float4 cur, float4 prev, float4 T, float4 m)
+{
+    return make_float4(pstep1(dG.x, cur.x, prev.x, T.x, m.x, g.Khi, g.Klo),
+                       pstep1(dG.y, cur.y, prev.y, T.y, m.y, g.Khi, g.Klo),
+                       pstep1(dG.z, cur.z, prev.z, T.z, m.z, g.Khi, g.Klo),
+                       pstep1(dG.w, cur.w, prev.w, T.w, m.w, g.Khi, g.Klo));
+}
+
+__device__ __forceinline__ float4 psponge(const Geo &g, int z, int x)
+{
+    const float dz = g.dGz[z];
+    const float4 dx = *reinterpret_cast<const float4 *>(g.dGx + x);
+    return make_float4(dz + dx.x - dz * dx.x, dz + dx.y - dz * dx.y, dz + dx.z - dz * dx.z,
+                       dz + dx.w - dz * dx.w);
+}
+
+__device__ __forceinline__ void padd_source(float4 &q, int src, int pt, float w)
+{
+    const int d = src - pt;
+    if (d >= 0 && d < 4) {
+        if (d == 0) q.x += w;
+        else if (d == 1) q.y += w;
+        else if (d == 2) q.z += w;
+        else q.w += w;
+    }
+}
+
+// Shared layout: two tiles of (rows_max + 8) x pitch floats (time levels n
+// and n+1, each with 4 halo rows above and below), then rin[slots_max]
+// float4 (adjoint residual injection).  The model is read through L1/L2.
+__global__ void __launch_bounds__(PT, 1) k_fwd_persist(const Geo g, const PGeo pg, const PFwdArgs a)
+{
+    extern __shared__ __align__(16) float psm[];
+    __shared__ int abort_sh;
+    const int c = blockIdx.x;
+    const int r0 = pg.row0[c], nr = pg.row0[c + 1] - r0;
+    const int W4 = g.pitch / 4;
+    const long long tsz = (long long)(pg.rows_max + 8) * g.pitch;
+    float *tile[2] = {psm, psm + tsz};
+    const int ngr = nr * W4;
+    for (int i = threadIdx.x; i < 2 * (pg.rows_max + 8) * W4; i += PT)
+        reinterpret_cast<float4 *>(psm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 prev[PGMAX];
+#pragma unroll
+    for (int k = 0; k < PGMAX; ++k) prev[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    for (int n = 0; n < a.nt; ++n) {
+        const float *cur_t = tile[n & 1];
+        float *nxt_t = tile[(n + 1) & 1];
+        if (c == 0 && n == a.stall_step) return;   // test hook: leave the neighbours' waits unmet
+        if (n > 0) {
+            if (!wait_neighbours(pg, c, (unsigned)n, &abort_sh)) return;
+            load_halo(g, pg, tile[n & 1], c, nr, n & 1);
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < PGMAX; ++k) {
+            const int i = threadIdx.x + k * PT;
+            if (i >= ngr) break;
+            const int r = i / W4, x4 = i - r * W4;
+            const int gr = r0 + r, s = gr / g.NZ, z = gr - s * g.NZ;
+            const float4 cur = reinterpret_cast<const float4 *>(cur_t + (long long)(r + 4) * g.pitch)[x4];
+            float4 out = cur;
+            if (n < g.nt[s]) {
+                const int x = 4 * x4;
+                float4 T = pstencil(g, cur_t, r + 4, x4, z);
+                padd_source(T, g.src_pt[s], z * g.pitch + x, g.ws[n]);
+                const long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
+                __stcs(reinterpret_cast<float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell), T);
+                const float4 m = __ldg(reinterpret_cast<const float4 *>(a.m + (long long)z * g.pitch + x));
+                out = pleap(g, psponge(g, z, x), cur, prev[k], T, m);
+                prev[k] = cur;
+            }
+            reinterpret_cast<float4 *>(nxt_t + (long long)(r + 4) * g.pitch)[x4] = out;
+        }
+        __syncthreads();
+        store_edges(g, pg, nxt_t, c, nr, (n + 1) & 1);
+        if (a.traces) {
+            // receiver gather: sample n = u^{n+1}
+            const int s0 = pg.slot_off[c], s1 = pg.slot_off[c + 1];
+            for (int j = s0 + threadIdx.x; j < s1; j += PT) {
+                const int grp = pg.slot_group[j];           // global group index
+                const int gr = grp / W4, x4 = grp - gr * W4;
+                const int s = gr / g.NZ;
+                if (n >= g.nt[s]) continue;
+                const float4 v = reinterpret_cast<const float4 *>(nxt_t + (long long)(gr - r0 + 4) * g.pitch)[x4];
+                const int4 cols = pg.slot_cols[j];
+                const long long tb = g.tr_off[s] + (long long)n * g.nrec[s];
+                if (cols.x >= 0) a.traces[tb + cols.x] = v.x;
+                if (cols.y >= 0) a.traces[tb + cols.y] = v.y;
+                if (cols.z >= 0) a.traces[tb + cols.z] = v.z;
+                if (cols.w >= 0) a.traces[tb + cols.w] = v.w;
+            }
+        }
+        publish(pg, c, (unsigned)(n + 1));
+    }
+}
+
+__global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo pg, const PAdjArgs a)
+{
+    extern __shared__ __align__(16) float psm[];
+    __shared__ int abort_sh;
+    const int c = blockIdx.x;
+    const int r0 = pg.row0[c], nr = pg.row0[c + 1] - r0;
+    const int W4 = g.pitch / 4;
+    const long long tsz = (long long)(pg.rows_max + 8) * g.pitch;
+    float *tile[2] = {psm, psm + tsz};
+    float4 *rin = reinterpret_cast<float4 *>(psm + 2 * tsz);
+    const int ngr = nr * W4;
+    const int s0 = pg.slot_off[c], s1 = pg.slot_off[c + 1];
+    for (int i = threadIdx.x; i < 2 * (pg.rows_max + 8) * W4; i += PT)
+        reinterpret_cast<float4 *>(psm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 z2[PGMAX];
+#pragma unroll
+    for (int k = 0; k < PGMAX; ++k) z2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    for (int j = 0; j < a.nt; ++j) {
+        const int n = a.nt - 1 - j;
+        const float *cur_t = tile[j & 1];
+        float *nxt_t = tile[(j + 1) & 1];
+        if (c == 0 && j == a.stall_step) return;   // test hook: leave the neighbours' waits unmet
+        if (j > 0) {
+            if (!wait_neighbours(pg, c, (unsigned)j, &abort_sh)) return;
+            load_halo(g, pg, tile[j & 1], c, nr, j & 1);
+        }
+        // residual injection for this step: rin[slot] = inj_scale * r[n] per lane
+        for (int q = s0 + threadIdx.x; q < s1; q += PT) {
+            const int grp = pg.slot_group[q];
+            const int s = (grp / W4) / g.NZ;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (n < g.nt[s]) {
+                const int4 cols = pg.slot_cols[q];
+                const long long tb = g.tr_off[s] + (long long)n * g.nrec[s];
+                if (cols.x >= 0) v.x = g.inj_scale * a.resid[tb + cols.x];
+                if (cols.y >= 0) v.y = g.inj_scale * a.resid[tb + cols.y];
+                if (cols.z >= 0) v.z = g.inj_scale * a.resid[tb + cols.z];
+                if (cols.w >= 0) v.w = g.inj_scale * a.resid[tb + cols.w];
+            }
+            rin[q - s0] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < PGMAX; ++k) {
+            const int i = threadIdx.x + k * PT;
+            if (i >= ngr) break;
+            const int r = i / W4, x4 = i - r * W4;
+            const int gr = r0 + r, s = gr / g.NZ, z = gr - s * g.NZ;
+            const float4 cur = reinterpret_cast<const float4 *>(cur_t + (long long)(r + 4) * g.pitch)[x4];
+            float4 out = cur;
+            if (n < g.nt[s]) {
+                const int x = 4 * x4;
+                float4 Tz = pstencil(g, cur_t, r + 4, x4, z);
+                const int sl = __ldg(pg.grp_slot + (long long)r0 * W4 + i);
+                if (sl >= 0) {
+                    const float4 inj = rin[sl - s0];
+                    Tz.x += inj.x; Tz.y += inj.y; Tz.z += inj.z; Tz.w += inj.w;
+                }
+                const float4 m = __ldg(reinterpret_cast<const float4 *>(a.m + (long long)z * g.pitch + x));
+                const float4 zn = pleap(g, psponge(g, z, x), cur, z2[k], Tz, m);
+                const long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
+                const float4 Tu = __ldcs(reinterpret_cast<const float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell));
+                float4 sc;
+                if (a.born) {
+                    sc = make_float4(-g.tscale, -g.tscale, -g.tscale, -g.tscale);
+                } else {
+                    sc = make_float4(-g.tscale / m.x, -g.tscale / m.y, -g.tscale / m.z, -g.tscale / m.w);
+                }
+                float4 *ip = reinterpret_cast<float4 *>(a.img + cell);
+                float4 im = *ip;
+                im.x = fmaf(sc.x * zn.x, Tu.x, im.x);
+                im.y = fmaf(sc.y * zn.y, Tu.y, im.y);
+                im.z = fmaf(sc.z * zn.z, Tu.z, im.z);
+                im.w = fmaf(sc.w * zn.w, Tu.w, im.w);
+                *ip = im;
+                out = zn;
+                z2[k] = cur;
+            }
+            reinterpret_cast<float4 *>(nxt_t + (long long)(r + 4) * g.pitch)[x4] = out;
+        }
+        __syncthreads();
+        store_edges(g, pg, nxt_t, c, nr, (j + 1) & 1);
+        publish(pg, c, (unsigned)(j + 1));
+    }
+}
+
+size_t persist_smem(const Geo &g, int rows_max, int slots_max)
+{
+    return ((size_t)2 * (rows_max + 8) * g.pitch) * sizeof(float) + (size_t)slots_max * sizeof(float4);
+}
+
+cudaError_t init_persist_kernels(size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_adj_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+
+cudaError_t launch_fwd_persist(const Geo &g, const PGeo &pg, const PFwdArgs &a, size_t smem, cudaStream_t st)
+{
+    count_launch();
+    void *args[] = {(void *)&g, (void *)&pg, (void *)&a};
+    return cudaLaunchCooperativeKernel((void *)k_fwd_persist, dim3(pg.P), dim3(PT), args, smem, st);
+}
+
+cudaError_t launch_adj_persist(const Geo &g, const PGeo &pg, const PAdjArgs &a, size_t smem, cudaStream_t st)
+{
+    count_launch();
+    void *args[] = {(void *)&g, (void *)&pg, (void *)&a};
+    return cudaLaunchCooperativeKernel((void *)k_adj_persist, dim3(pg.P), dim3(PT), args, smem, st);
+}
+
+}  // namespace aafwi
