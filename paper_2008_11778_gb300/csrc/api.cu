@@ -42,7 +42,8 @@ struct aafwi_plan {
     Geo geo{};
     std::vector<Buf> bufs;
     // device buffers
-    float *m_pad = nullptr, *rho_pad = nullptr;
+    float *W = nullptr, *rho_pad = nullptr;   // W: Wh then Wl, each [NZ][pitch]
+    double K = 0.0;                 // dt^2 / (5040 dx^2)
     float *hist = nullptr;          // full: (nt_max+1) slots; else 2*nck checkpoint slots
     float *fbuf = nullptr;          // 2 rotating forward slots (checkpoint mode)
     float *rbuf = nullptr;          // k-1 replay slots (checkpoint mode)
@@ -51,6 +52,7 @@ struct aafwi_plan {
     float *img = nullptr;           // per-shot image accumulators
     float *dsyn = nullptr, *resid = nullptr;
     double *partials = nullptr, *J = nullptr;
+    double *rowsum = nullptr;       // [NZ][nx] FP64 partial sums of the shot sum
     int *err = nullptr;
     size_t ws_bytes = 0;
     bool fwd_valid = false;
@@ -134,7 +136,7 @@ int run_persist_forward(aafwi_plan *p, float *traces, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(p->pgeo.flags, 0, p->pgeo.P * sizeof(unsigned), st);
     if (e != cudaSuccess) return cuda_fail(p, e, "memset");
-    PFwdArgs a{p->m_pad, p->hist, traces, p->nt_max, p->stall_step};
+    PFwdArgs a{p->W, p->hist, traces, p->nt_max, p->stall_step};
     e = launch_fwd_persist(p->geo, p->pgeo, a, p->psmem, st);
     if (e != cudaSuccess) return cuda_fail(p, e, "persistent forward launch");
     p->hist_T = true;
@@ -167,12 +169,12 @@ int run_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
             }
         }
         if (born) {
-            BornArgs a{p->m_pad, p->rho_pad, cur, prev, next, slot(p->dbuf, ps, n & 1),
+            BornArgs a{p->W, p->rho_pad, cur, prev, next, slot(p->dbuf, ps, n & 1),
                        slot(p->dbuf, ps, (n + 1) & 1), slot(p->dbuf, ps, (n + 1) & 1), ckc, ckp,
                        traces, n};
             launch_born(p->geo, a, st);
         } else {
-            FwdArgs a{p->m_pad, cur, prev, next, ckc, ckp, traces, n};
+            FwdArgs a{p->W, cur, prev, next, ckc, ckp, traces, n};
             launch_fwd(p->geo, a, st);
         }
     }
@@ -188,7 +190,7 @@ int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
     if (p->hist_T) {
         cudaError_t e = cudaMemsetAsync(p->pgeo.flags, 0, p->pgeo.P * sizeof(unsigned), st);
         if (e != cudaSuccess) return cuda_fail(p, e, "memset");
-        PAdjArgs a{p->m_pad, p->hist, resid, p->img, p->nt_max, born ? 1 : 0, p->stall_step};
+        PAdjArgs a{p->W, p->hist, resid, p->img, p->nt_max, born ? 1 : 0, p->stall_step};
         e = launch_adj_persist(p->geo, p->pgeo, a, p->psmem, st);
         if (e != cudaSuccess) return cuda_fail(p, e, "persistent adjoint launch");
         return AAFWI_OK;
@@ -196,7 +198,7 @@ int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
     if (cudaMemsetAsync(p->zbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
     auto adj = [&](int n, const float *u) {
-        AdjArgs a{p->m_pad, slot(p->zbuf, ps, (n + 1) & 1), slot(p->zbuf, ps, n & 1), u, resid, p->img,
+        AdjArgs a{p->W, slot(p->zbuf, ps, (n + 1) & 1), slot(p->zbuf, ps, n & 1), u, resid, p->img,
                   n, born ? 1 : 0};
         launch_adj(p->geo, a, st);
     };
@@ -206,7 +208,7 @@ int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
         for (int j = p->nck - 1; j >= 0; --j) {
             const int a = j * p->k, e = std::min(a + p->k, p->nt_max);
             for (int n = a; n <= e - 2; ++n) {
-                FwdArgs f{p->m_pad, seg_u(p, j, a, n), seg_u(p, j, a, n - 1), seg_u(p, j, a, n + 1),
+                FwdArgs f{p->W, seg_u(p, j, a, n), seg_u(p, j, a, n - 1), seg_u(p, j, a, n + 1),
                           nullptr, nullptr, nullptr, n};
                 launch_fwd(p->geo, f, st);
             }
@@ -220,7 +222,7 @@ int prep(aafwi_plan *p, const float *m, const float *rho, cudaStream_t st)
 {
     const double h = std::min(p->dx, p->dz);
     const double mcfl = std::pow(p->dt / (kCflLimit * h), 2.0);  // m below this violates CFL
-    launch_prep(p->geo, p->nz, p->nx, m, rho, (float)mcfl, p->m_pad, rho ? p->rho_pad : nullptr,
+    launch_prep(p->geo, p->nz, p->nx, m, rho, (float)mcfl, p->K, p->W, rho ? p->rho_pad : nullptr,
                 p->err, st);
     return check_launch(p);
 }
@@ -264,12 +266,13 @@ int setup_persist(aafwi_plan *p, int engine, const aafwi_shots *sh, std::string 
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!coop || sms < 1) return no("cooperative launch unsupported");
     const int W4 = p->pitch / 4;
+    if (W4 > PT) return no("rows wider than a CTA");
     const long long R = (long long)p->S * p->NZ;
-    const int rows_cap = PT * PGMAX / W4;               // rows a CTA's threads can own
     int P = (int)std::min<long long>(sms, R / 4);        // strips of at least 4 rows
     if (P < 1) return no("grid too small");
     const int rows_max = (int)((R + P - 1) / P);
-    if (rows_max > rows_cap) return no("strips exceed the threads of a CTA");
+    const int ty = std::max(1, std::min(PT / W4, rows_max));
+    if ((rows_max + ty - 1) / ty > RBMAX) return no("too many rows per thread");
     // strips and receiver slots
     std::vector<int> row0(P + 1);
     for (int c = 0; c <= P; ++c) row0[c] = (int)(R * c / P);
@@ -325,6 +328,7 @@ int setup_persist(aafwi_plan *p, int engine, const aafwi_shots *sh, std::string 
     if (!ok) return no("allocation");
     pg.P = P;
     pg.rows_max = rows_max;
+    pg.ty = ty;
     pg.slot = (long long)p->S * p->field;
     pg.row0 = d_row0; pg.grp_slot = d_gs; pg.slot_off = d_so; pg.slot_group = d_sg; pg.slot_cols = d_sc;
     pg.err = p->err;
@@ -440,7 +444,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     for (int n = 0; n < p->nt_max; ++n) ws[n] = (float)(t5040 * wavelet[n] / (g->dx * g->dz));
     // workspace plan
     const size_t F = (size_t)p->field * sizeof(float), SF = F * S;
-    const size_t fixed = 2 * F + (2 + 2 + 1) * SF + 2 * (size_t)p->trace_count * sizeof(float) + (1 << 20);
+    const size_t fixed = 3 * F + (2 + 2 + 1) * SF + 2 * (size_t)p->trace_count * sizeof(float) + (1 << 20);
     size_t budget = o.max_workspace_bytes;
     if (budget == 0) {
         size_t fr = 0, tot = 0;
@@ -478,11 +482,12 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
               upload(p->bufs, &d_ws, ws) && upload(p->bufs, &d_Gz, dGz) && upload(p->bufs, &d_Gx, dGx) &&
               upload(p->bufs, &d_troff, p->tr_off);
     const long long ps = (long long)S * p->field;
-    ok = ok && dalloc(p->bufs, &p->m_pad, p->field) && dalloc(p->bufs, &p->rho_pad, p->field) &&
+    ok = ok && dalloc(p->bufs, &p->W, 2 * p->field) && dalloc(p->bufs, &p->rho_pad, p->field) &&
          dalloc(p->bufs, &p->dbuf, 2 * ps) && dalloc(p->bufs, &p->zbuf, 2 * ps) &&
          dalloc(p->bufs, &p->img, ps) && dalloc(p->bufs, &p->dsyn, p->trace_count) &&
          dalloc(p->bufs, &p->resid, p->trace_count) && dalloc(p->bufs, &p->partials, RED_BLOCKS) &&
-         dalloc(p->bufs, &p->J, 1) && dalloc(p->bufs, &p->err, 1);
+         dalloc(p->bufs, &p->J, 1) && dalloc(p->bufs, &p->err, 1) &&
+         dalloc(p->bufs, &p->rowsum, (size_t)p->NZ * p->nx);
     if (ok) {
         if (p->full) {
             ok = dalloc(p->bufs, &p->hist, (p->nt_max + 1) * ps);
@@ -506,11 +511,8 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     G.NZ = p->NZ; G.NX = p->NX; G.pitch = p->pitch; G.nb = p->nb; G.S = S;
     G.ntz = ntz; G.ntx = ntx; G.ntiles = ntiles; G.field = p->field;
     G.rz = (float)((g->dx * g->dx) / (g->dz * g->dz));
-    {
-        const double K = g->dt * g->dt / t5040;
-        G.Khi = (float)K;
-        G.Klo = (float)(K - (double)G.Khi);
-    }
+    p->K = g->dt * g->dt / t5040;
+    G.iscale = (float)(-1.0 / (g->dt * g->dt));
     G.tscale = (float)(1.0 / t5040);
     G.inj_scale = (float)t5040;
     G.nt = d_nt; G.src_pt = d_src; G.ws = d_ws; G.dGz = d_Gz; G.dGx = d_Gx;
@@ -622,7 +624,7 @@ int aafwi_adjoint_gradient(aafwi_plan *p, int mode, const float *m, const float 
     }
     launch_misfit(p->dsyn, d_obs, p->resid, p->trace_count, p->partials, p->J, st);
     if ((rc = run_adjoint(p, born, p->resid, st))) return rc;
-    launch_shot_sum(p->geo, p->nz, p->nx, p->img, grad, st);
+    launch_shot_sum(p->geo, p->nz, p->nx, p->img, p->rowsum, grad, st);
     if ((rc = check_launch(p))) return rc;
     if (!born) {
         p->fwd_valid = true;
@@ -646,7 +648,7 @@ int aafwi_fwi_adjoint(aafwi_plan *p, const float *m, const float *adj_src, float
         if ((rc = run_forward(p, false, p->dsyn, st))) return rc;
     }
     if ((rc = run_adjoint(p, false, adj_src, st))) return rc;
-    launch_shot_sum(p->geo, p->nz, p->nx, p->img, grad, st);
+    launch_shot_sum(p->geo, p->nz, p->nx, p->img, p->rowsum, grad, st);
     if ((rc = check_launch(p))) return rc;
     p->fwd_valid = true;
     p->fwd_model = m;
@@ -662,7 +664,7 @@ int aafwi_born_adjoint(aafwi_plan *p, const float *m0, const float *resid, float
     if ((rc = prep(p, m0, nullptr, st))) return rc;
     if ((rc = run_forward(p, false, nullptr, st))) return rc;
     if ((rc = run_adjoint(p, true, resid, st))) return rc;
-    launch_shot_sum(p->geo, p->nz, p->nx, p->img, img, st);
+    launch_shot_sum(p->geo, p->nz, p->nx, p->img, p->rowsum, img, st);
     return check_launch(p);
 }
 

@@ -28,9 +28,10 @@ struct Geo {
     long long field;               // floats per shot field (NZ * pitch)
     // The Laplacian is evaluated as T = rz*S_z + S_x with integer weights
     // (5040 x the 8th-order weights), so that L u = T / (5040 dx^2) and
-    // W (L u + s) = K T / m with K = dt^2 / (5040 dx^2) split in hi + lo.
+    // W (L u + s) = Wt T with Wt = dt^2 / (5040 dx^2 m) stored per cell as
+    // the FP32 pair Wh + Wl (FP64-derived; Wl at Wh + field).
     float rz;                      // dx^2 / dz^2
-    float Khi, Klo;                // K = Khi + Klo
+    float iscale;                  // -1/dt^2: FWI imaging scale -1/m = iscale * 5040 dx^2 Wt
     float tscale;                  // 1 / (5040 dx^2): T -> L u + s
     float inj_scale;               // 5040 dx^2: residual r -> its T units
     const int *nt;                 // [S] record length
@@ -47,7 +48,7 @@ struct Geo {
 // One forward step n -> n+1 for all shots.  Field pointers are slot bases
 // (shot s at + s*field).  u_next may alias u_prev (in-place update).
 struct FwdArgs {
-    const float *m;                // padded model m = 1/c^2 (extension E applied)
+    const float *W;                // Wh [NZ][pitch], then Wl (padded, extension E applied)
     const float *u_cur;
     const float *u_prev;
     float *u_next;
@@ -58,7 +59,7 @@ struct FwdArgs {
 
 // Born step: background u and scattered du together (eq. Born).
 struct BornArgs {
-    const float *m, *rho;
+    const float *W, *rho;
     const float *u_cur, *u_prev;
     float *u_next;
     const float *d_cur, *d_prev;
@@ -71,7 +72,7 @@ struct BornArgs {
 // Adjoint step n (z^n from z^{n+1}, z^{n+2}) fused with the imaging condition
 // img += scale * z^n * (L u^n + s^n), scale = -1/m (FWI) or -1 (Born).
 struct AdjArgs {
-    const float *m;
+    const float *W;
     const float *z1;               // z^{n+1}
     float *z2n;                    // in: z^{n+2}; out: z^n (same cells)
     const float *u;                // u^n
@@ -90,20 +91,22 @@ void set_call_error(const std::string &msg);
 
 cudaError_t init_kernels();  // per-device kernel attributes (dynamic shared memory)
 void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float mcfl,
-                 float *m_pad, float *rho_pad, int *err, cudaStream_t st);
+                 double K, float *W, float *rho_pad, int *err, cudaStream_t st);
 void launch_fwd(const Geo &g, const FwdArgs &a, cudaStream_t st);
 void launch_born(const Geo &g, const BornArgs &a, cudaStream_t st);
 void launch_adj(const Geo &g, const AdjArgs &a, cudaStream_t st);
-void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, float *out, cudaStream_t st);
+void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *rowsum, float *out,
+                     cudaStream_t st);
 
 // Persistent sweeps (persist_kernels.cu): one cooperative launch per sweep,
-// one CTA of PT threads per strip of rows; each thread owns at most PGMAX
-// float4 groups of its strip.
+// one CTA per strip of rows, (pitch/4) x ty threads (at most PT): thread
+// (x, y) owns float4 column x of the y-th block of the strip's rows.
 constexpr int PT = 512;
-constexpr int PGMAX = 10;
+constexpr int RBMAX = 12;          // rows per thread (the row loop is unrolled)
 struct PGeo {
     int P;                         // strips (CTAs)
     int rows_max;                  // max rows of a strip
+    int ty;                        // thread rows per CTA
     long long slot;                // floats per history slot (S * field)
     const int *row0;               // [P+1] strip row ranges in global rows (shot * NZ + z)
     const int *grp_slot;           // [S*NZ*pitch/4] receiver slot of a float4 group, or -1
@@ -115,14 +118,14 @@ struct PGeo {
     int *err;                      // bit 2: a bounded wait ran out
 };
 struct PFwdArgs {
-    const float *m;                // padded model [NZ][pitch]
+    const float *W;                // Wh, Wl as in FwdArgs
     float *hist;                   // slot n+1 <- T^n = 5040 dx^2 (L u^n + s^n); slot 0 untouched
     float *traces;                 // CSR gather target or null
     int nt;                        // steps (max over shots)
     int stall_step;                // test hook: strip 0 stops publishing at this step (-1: never)
 };
 struct PAdjArgs {
-    const float *m;
+    const float *W;
     const float *hist;             // T^n (slot n+1) from the forward sweep
     const float *resid;            // CSR residual traces
     float *img;                    // per-shot accumulators [S][field]

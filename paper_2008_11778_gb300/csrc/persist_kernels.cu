@@ -107,14 +107,14 @@ __device__ void store_edges(const Geo &g, const PGeo &pg, const float *tile, int
     }
 }
 
-// T = rz S_z + S_x at float4 group (tile row tr, column 4*x4) with the z
-// neighbours outside [0, NZ) of the cell's own shot read as zero.
-__device__ __forceinline__ float4 pstencil(const Geo &g, const float *tile, int tr, int x4, int z)
+// T = rz S_z + S_x for the float4 group at the centre of the register column
+// w[0..8] (rows z-4..z+4 of the tile) with left / right neighbour groups L, R;
+// z neighbours outside [0, NZ) of the cell's own shot read as zero.  Same
+// arithmetic, in the same order, as pstencil and the per-step kernels.
+template <bool MASK>
+__device__ __forceinline__ float4 col_stencil(const Geo &g, const float4 (&w)[9], float4 L, float4 R, int z)
 {
-    const float4 *row = reinterpret_cast<const float4 *>(tile + (long long)tr * g.pitch);
-    const float4 M = row[x4];
-    const float4 L = x4 > 0 ? row[x4 - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 R = (x4 + 1) * 4 < g.pitch ? row[x4 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 M = w[4];
     const float v[12] = {L.x, L.y, L.z, L.w, M.x, M.y, M.z, M.w, R.x, R.y, R.z, R.w};
     float sx[4];
 #pragma unroll
@@ -123,12 +123,12 @@ __device__ __forceinline__ float4 pstencil(const Geo &g, const float *tile, int 
         sx[i] = PA1 * pd2(c, v[3 + i], v[5 + i]) + PA2 * pd2(c, v[2 + i], v[6 + i])
               + PA3 * pd2(c, v[1 + i], v[7 + i]) + PA4 * pd2(c, v[i], v[8 + i]);
     }
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 up[4], dn[4];
 #pragma unroll
     for (int k = 1; k <= 4; ++k) {
-        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-        up[k - 1] = z - k >= 0 ? reinterpret_cast<const float4 *>(tile + (long long)(tr - k) * g.pitch)[x4] : zero;
-        dn[k - 1] = z + k < g.NZ ? reinterpret_cast<const float4 *>(tile + (long long)(tr + k) * g.pitch)[x4] : zero;
+        up[k - 1] = !MASK || z - k >= 0 ? w[4 - k] : zero;
+        dn[k - 1] = !MASK || z + k < g.NZ ? w[4 + k] : zero;
     }
     float4 o;
     o.x = g.rz * (PA1 * pd2(M.x, up[0].x, dn[0].x) + PA2 * pd2(M.x, up[1].x, dn[1].x) + PA3 * pd2(M.x, up[2].x, dn[2].x) + PA4 * pd2(M.x, up[3].x, dn[3].x)) + sx[0];
@@ -138,21 +138,18 @@ __device__ __forceinline__ float4 pstencil(const Geo &g, const float *tile, int 
     return o;
 }
 
-__device__ __forceinline__ float pstep1(float dG, float cur, float prev, float T, float m, float Khi, float Klo)
+__device__ __forceinline__ float pstep1(float dG, float cur, float prev, float T, float wh, float wl)
 {
-    const float y = T / m;
-    const float wq = fmaf(Khi, y, Klo * y);
+    const float wq = fmaf(wh, T, wl * T);
     const float gp = prev - dG * prev;
     const float t = ((cur - gp) + cur) + wq;
     return t - dG * t;
 }
 
-__device__ __forceinline__ float4 pleap(const Geo &g, float4 dG, float4 cur, float4 prev, float4 T, float4 m)
+__device__ __forceinline__ float4 pleap(float4 dG, float4 cur, float4 prev, float4 T, float4 wh, float4 wl)
 {
-    return make_float4(pstep1(dG.x, cur.x, prev.x, T.x, m.x, g.Khi, g.Klo),
-                       pstep1(dG.y, cur.y, prev.y, T.y, m.y, g.Khi, g.Klo),
-                       pstep1(dG.z, cur.z, prev.z, T.z, m.z, g.Khi, g.Klo),
-                       pstep1(dG.w, cur.w, prev.w, T.w, m.w, g.Khi, g.Klo));
+    return make_float4(pstep1(dG.x, cur.x, prev.x, T.x, wh.x, wl.x), pstep1(dG.y, cur.y, prev.y, T.y, wh.y, wl.y),
+                       pstep1(dG.z, cur.z, prev.z, T.z, wh.z, wl.z), pstep1(dG.w, cur.w, prev.w, T.w, wh.w, wl.w));
 }
 
 __device__ __forceinline__ float4 psponge(const Geo &g, int z, int x)
@@ -174,9 +171,14 @@ __device__ __forceinline__ void padd_source(float4 &q, int src, int pt, float w)
     }
 }
 
-// Shared layout: two tiles of (rows_max + 8) x pitch floats (time levels n
-// and n+1, each with 4 halo rows above and below), then rin[slots_max]
-// float4 (adjoint residual injection).  The model is read through L1/L2.
+// Shared layout: two tiles of (rows_max + 8) x pitch floats, then
+// rin[slots_max] float4 (adjoint residual injection).  At step n tile n&1
+// holds level n (own rows + the 4 halo rows above and below, refreshed from
+// the neighbours) and the other tile holds level n-1 in its own rows, which
+// each thread overwrites in place with level n+1 (it reads and writes only
+// its own cells there).  Thread (x, y) owns float4 column x and a contiguous
+// block of rows, walking down it with the 9-row stencil column in registers.
+// The model is read through L1/L2.
 __global__ void __launch_bounds__(PT, 1) k_fwd_persist(const Geo g, const PGeo pg, const PFwdArgs a)
 {
     extern __shared__ __align__(16) float psm[];
@@ -184,55 +186,83 @@ __global__ void __launch_bounds__(PT, 1) k_fwd_persist(const Geo g, const PGeo p
     const int c = blockIdx.x;
     const int r0 = pg.row0[c], nr = pg.row0[c + 1] - r0;
     const int W4 = g.pitch / 4;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     const long long tsz = (long long)(pg.rows_max + 8) * g.pitch;
     float *tile[2] = {psm, psm + tsz};
-    const int ngr = nr * W4;
-    for (int i = threadIdx.x; i < 2 * (pg.rows_max + 8) * W4; i += PT)
+    for (int i = tid; i < 2 * (pg.rows_max + 8) * W4; i += nth)
         reinterpret_cast<float4 *>(psm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 prev[PGMAX];
-#pragma unroll
-    for (int k = 0; k < PGMAX; ++k) prev[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int x4 = threadIdx.x, x = 4 * x4;
+    const int RB = (nr + blockDim.y - 1) / blockDim.y;
+    const int ra = min((int)threadIdx.y * RB, nr), rb = min(ra + RB, nr);
+    const int sa = (r0 + ra) / g.NZ, za = (r0 + ra) - sa * g.NZ;
+    const float4 dgx = *reinterpret_cast<const float4 *>(g.dGx + x);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     for (int n = 0; n < a.nt; ++n) {
-        const float *cur_t = tile[n & 1];
-        float *nxt_t = tile[(n + 1) & 1];
+        float *A = tile[n & 1];
+        float *B = tile[(n + 1) & 1];
         if (c == 0 && n == a.stall_step) return;   // test hook: leave the neighbours' waits unmet
         if (n > 0) {
             if (!wait_neighbours(pg, c, (unsigned)n, &abort_sh)) return;
-            load_halo(g, pg, tile[n & 1], c, nr, n & 1);
+            load_halo(g, pg, A, c, nr, n & 1);
             __syncthreads();
         }
+        const float4 *A4 = reinterpret_cast<const float4 *>(A);
+        float4 *B4 = reinterpret_cast<float4 *>(B);
+        if (ra < rb) {
+            float4 w[9];
 #pragma unroll
-        for (int k = 0; k < PGMAX; ++k) {
-            const int i = threadIdx.x + k * PT;
-            if (i >= ngr) break;
-            const int r = i / W4, x4 = i - r * W4;
-            const int gr = r0 + r, s = gr / g.NZ, z = gr - s * g.NZ;
-            const float4 cur = reinterpret_cast<const float4 *>(cur_t + (long long)(r + 4) * g.pitch)[x4];
-            float4 out = cur;
-            if (n < g.nt[s]) {
-                const int x = 4 * x4;
-                float4 T = pstencil(g, cur_t, r + 4, x4, z);
-                padd_source(T, g.src_pt[s], z * g.pitch + x, g.ws[n]);
-                const long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
-                __stcs(reinterpret_cast<float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell), T);
-                const float4 m = __ldg(reinterpret_cast<const float4 *>(a.m + (long long)z * g.pitch + x));
-                out = pleap(g, psponge(g, z, x), cur, prev[k], T, m);
-                prev[k] = cur;
+            for (int k = 0; k < 9; ++k) w[k] = A4[(ra + k) * W4 + x4];
+            int s = sa, z = za;
+            const float wsn = g.ws[n];
+            int active = n < g.nt[s], src = g.src_pt[s];
+            long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
+#pragma unroll
+            for (int q = 0; q < RBMAX; ++q) {
+                const int r = ra + q;
+                if (r >= rb) break;
+                const int ti = (r + 4) * W4 + x4;
+                float4 out = w[4];
+                if (active) {
+                    const float4 L = x4 > 0 ? A4[ti - 1] : zero;
+                    const float4 R = x4 + 1 < W4 ? A4[ti + 1] : zero;
+                    float4 T = (z >= 4 && z < g.NZ - 4) ? col_stencil<false>(g, w, L, R, z)
+                                                         : col_stencil<true>(g, w, L, R, z);
+                    padd_source(T, src, z * g.pitch + x, wsn);
+                    __stcs(reinterpret_cast<float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell), T);
+                    const long long zc = (long long)z * g.pitch + x;
+                    const float4 wh = __ldg(reinterpret_cast<const float4 *>(a.W + zc));
+                    const float4 wl = __ldg(reinterpret_cast<const float4 *>(a.W + g.field + zc));
+                    const float dz = g.dGz[z];
+                    const float4 dG = make_float4(dz + dgx.x - dz * dgx.x, dz + dgx.y - dz * dgx.y,
+                                                  dz + dgx.z - dz * dgx.z, dz + dgx.w - dz * dgx.w);
+                    out = pleap(dG, w[4], B4[ti], T, wh, wl);
+                }
+                B4[ti] = out;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) w[k] = w[k + 1];
+                if (r + 1 < rb) w[8] = A4[(r + 9) * W4 + x4];
+                cell += g.pitch;
+                if (++z == g.NZ) {
+                    z = 0;
+                    ++s;
+                    active = s < g.S && n < g.nt[s];
+                    src = s < g.S ? g.src_pt[s] : -1;
+                    cell = (long long)s * g.field + x;
+                }
             }
-            reinterpret_cast<float4 *>(nxt_t + (long long)(r + 4) * g.pitch)[x4] = out;
         }
         __syncthreads();
-        store_edges(g, pg, nxt_t, c, nr, (n + 1) & 1);
+        store_edges(g, pg, B, c, nr, (n + 1) & 1);
         if (a.traces) {
             // receiver gather: sample n = u^{n+1}
             const int s0 = pg.slot_off[c], s1 = pg.slot_off[c + 1];
-            for (int j = s0 + threadIdx.x; j < s1; j += PT) {
+            for (int j = s0 + tid; j < s1; j += nth) {
                 const int grp = pg.slot_group[j];           // global group index
-                const int gr = grp / W4, x4 = grp - gr * W4;
+                const int gr = grp / W4, gx = grp - gr * W4;
                 const int s = gr / g.NZ;
                 if (n >= g.nt[s]) continue;
-                const float4 v = reinterpret_cast<const float4 *>(nxt_t + (long long)(gr - r0 + 4) * g.pitch)[x4];
+                const float4 v = reinterpret_cast<const float4 *>(B + (long long)(gr - r0 + 4) * g.pitch)[gx];
                 const int4 cols = pg.slot_cols[j];
                 const long long tb = g.tr_off[s] + (long long)n * g.nrec[s];
                 if (cols.x >= 0) a.traces[tb + cols.x] = v.x;
@@ -252,31 +282,34 @@ __global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo p
     const int c = blockIdx.x;
     const int r0 = pg.row0[c], nr = pg.row0[c + 1] - r0;
     const int W4 = g.pitch / 4;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     const long long tsz = (long long)(pg.rows_max + 8) * g.pitch;
     float *tile[2] = {psm, psm + tsz};
     float4 *rin = reinterpret_cast<float4 *>(psm + 2 * tsz);
-    const int ngr = nr * W4;
     const int s0 = pg.slot_off[c], s1 = pg.slot_off[c + 1];
-    for (int i = threadIdx.x; i < 2 * (pg.rows_max + 8) * W4; i += PT)
+    for (int i = tid; i < 2 * (pg.rows_max + 8) * W4; i += nth)
         reinterpret_cast<float4 *>(psm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 z2[PGMAX];
-#pragma unroll
-    for (int k = 0; k < PGMAX; ++k) z2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int x4 = threadIdx.x, x = 4 * x4;
+    const int RB = (nr + blockDim.y - 1) / blockDim.y;
+    const int ra = min((int)threadIdx.y * RB, nr), rb = min(ra + RB, nr);
+    const int sa = (r0 + ra) / g.NZ, za = (r0 + ra) - sa * g.NZ;
+    const float4 dgx = *reinterpret_cast<const float4 *>(g.dGx + x);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     for (int j = 0; j < a.nt; ++j) {
         const int n = a.nt - 1 - j;
-        const float *cur_t = tile[j & 1];
-        float *nxt_t = tile[(j + 1) & 1];
+        float *A = tile[j & 1];
+        float *B = tile[(j + 1) & 1];
         if (c == 0 && j == a.stall_step) return;   // test hook: leave the neighbours' waits unmet
         if (j > 0) {
             if (!wait_neighbours(pg, c, (unsigned)j, &abort_sh)) return;
-            load_halo(g, pg, tile[j & 1], c, nr, j & 1);
+            load_halo(g, pg, A, c, nr, j & 1);
         }
         // residual injection for this step: rin[slot] = inj_scale * r[n] per lane
-        for (int q = s0 + threadIdx.x; q < s1; q += PT) {
+        for (int q = s0 + tid; q < s1; q += nth) {
             const int grp = pg.slot_group[q];
             const int s = (grp / W4) / g.NZ;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 v = zero;
             if (n < g.nt[s]) {
                 const int4 cols = pg.slot_cols[q];
                 const long long tb = g.tr_off[s] + (long long)n * g.nrec[s];
@@ -288,46 +321,69 @@ __global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo p
             rin[q - s0] = v;
         }
         __syncthreads();
+        const float4 *A4 = reinterpret_cast<const float4 *>(A);
+        float4 *B4 = reinterpret_cast<float4 *>(B);
+        if (ra < rb) {
+            float4 w[9];
 #pragma unroll
-        for (int k = 0; k < PGMAX; ++k) {
-            const int i = threadIdx.x + k * PT;
-            if (i >= ngr) break;
-            const int r = i / W4, x4 = i - r * W4;
-            const int gr = r0 + r, s = gr / g.NZ, z = gr - s * g.NZ;
-            const float4 cur = reinterpret_cast<const float4 *>(cur_t + (long long)(r + 4) * g.pitch)[x4];
-            float4 out = cur;
-            if (n < g.nt[s]) {
-                const int x = 4 * x4;
-                float4 Tz = pstencil(g, cur_t, r + 4, x4, z);
-                const int sl = __ldg(pg.grp_slot + (long long)r0 * W4 + i);
-                if (sl >= 0) {
-                    const float4 inj = rin[sl - s0];
-                    Tz.x += inj.x; Tz.y += inj.y; Tz.z += inj.z; Tz.w += inj.w;
+            for (int k = 0; k < 9; ++k) w[k] = A4[(ra + k) * W4 + x4];
+            int s = sa, z = za;
+            int active = n < g.nt[s];
+            long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
+#pragma unroll
+            for (int q = 0; q < RBMAX; ++q) {
+                const int r = ra + q;
+                if (r >= rb) break;
+                const int ti = (r + 4) * W4 + x4;
+                float4 out = w[4];
+                if (active) {
+                    const float4 L = x4 > 0 ? A4[ti - 1] : zero;
+                    const float4 R = x4 + 1 < W4 ? A4[ti + 1] : zero;
+                    float4 Tz = (z >= 4 && z < g.NZ - 4) ? col_stencil<false>(g, w, L, R, z)
+                                                          : col_stencil<true>(g, w, L, R, z);
+                    const int sl = __ldg(pg.grp_slot + (long long)(r0 + r) * W4 + x4);
+                    if (sl >= 0) {
+                        const float4 inj = rin[sl - s0];
+                        Tz.x += inj.x; Tz.y += inj.y; Tz.z += inj.z; Tz.w += inj.w;
+                    }
+                    const long long zc = (long long)z * g.pitch + x;
+                    const float4 wh = __ldg(reinterpret_cast<const float4 *>(a.W + zc));
+                    const float4 wl = __ldg(reinterpret_cast<const float4 *>(a.W + g.field + zc));
+                    const float dz = g.dGz[z];
+                    const float4 dG = make_float4(dz + dgx.x - dz * dgx.x, dz + dgx.y - dz * dgx.y,
+                                                  dz + dgx.z - dz * dgx.z, dz + dgx.w - dz * dgx.w);
+                    const float4 zn = pleap(dG, w[4], B4[ti], Tz, wh, wl);
+                    const float4 Tu = __ldcs(reinterpret_cast<const float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell));
+                    float4 sc;
+                    if (a.born) {
+                        sc = make_float4(-g.tscale, -g.tscale, -g.tscale, -g.tscale);
+                    } else {
+                        sc = make_float4(g.iscale * wh.x, g.iscale * wh.y, g.iscale * wh.z, g.iscale * wh.w);
+                    }
+                    float4 *ip = reinterpret_cast<float4 *>(a.img + cell);
+                    float4 im = *ip;
+                    im.x = fmaf(sc.x * zn.x, Tu.x, im.x);
+                    im.y = fmaf(sc.y * zn.y, Tu.y, im.y);
+                    im.z = fmaf(sc.z * zn.z, Tu.z, im.z);
+                    im.w = fmaf(sc.w * zn.w, Tu.w, im.w);
+                    *ip = im;
+                    out = zn;
                 }
-                const float4 m = __ldg(reinterpret_cast<const float4 *>(a.m + (long long)z * g.pitch + x));
-                const float4 zn = pleap(g, psponge(g, z, x), cur, z2[k], Tz, m);
-                const long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
-                const float4 Tu = __ldcs(reinterpret_cast<const float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell));
-                float4 sc;
-                if (a.born) {
-                    sc = make_float4(-g.tscale, -g.tscale, -g.tscale, -g.tscale);
-                } else {
-                    sc = make_float4(-g.tscale / m.x, -g.tscale / m.y, -g.tscale / m.z, -g.tscale / m.w);
+                B4[ti] = out;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) w[k] = w[k + 1];
+                if (r + 1 < rb) w[8] = A4[(r + 9) * W4 + x4];
+                cell += g.pitch;
+                if (++z == g.NZ) {
+                    z = 0;
+                    ++s;
+                    active = s < g.S && n < g.nt[s];
+                    cell = (long long)s * g.field + x;
                 }
-                float4 *ip = reinterpret_cast<float4 *>(a.img + cell);
-                float4 im = *ip;
-                im.x = fmaf(sc.x * zn.x, Tu.x, im.x);
-                im.y = fmaf(sc.y * zn.y, Tu.y, im.y);
-                im.z = fmaf(sc.z * zn.z, Tu.z, im.z);
-                im.w = fmaf(sc.w * zn.w, Tu.w, im.w);
-                *ip = im;
-                out = zn;
-                z2[k] = cur;
             }
-            reinterpret_cast<float4 *>(nxt_t + (long long)(r + 4) * g.pitch)[x4] = out;
         }
         __syncthreads();
-        store_edges(g, pg, nxt_t, c, nr, (j + 1) & 1);
+        store_edges(g, pg, B, c, nr, (j + 1) & 1);
         publish(pg, c, (unsigned)(j + 1));
     }
 }
@@ -349,14 +405,14 @@ cudaError_t launch_fwd_persist(const Geo &g, const PGeo &pg, const PFwdArgs &a, 
 {
     count_launch();
     void *args[] = {(void *)&g, (void *)&pg, (void *)&a};
-    return cudaLaunchCooperativeKernel((void *)k_fwd_persist, dim3(pg.P), dim3(PT), args, smem, st);
+    return cudaLaunchCooperativeKernel((void *)k_fwd_persist, dim3(pg.P), dim3(g.pitch / 4, pg.ty), args, smem, st);
 }
 
 cudaError_t launch_adj_persist(const Geo &g, const PGeo &pg, const PAdjArgs &a, size_t smem, cudaStream_t st)
 {
     count_launch();
     void *args[] = {(void *)&g, (void *)&pg, (void *)&a};
-    return cudaLaunchCooperativeKernel((void *)k_adj_persist, dim3(pg.P), dim3(PT), args, smem, st);
+    return cudaLaunchCooperativeKernel((void *)k_adj_persist, dim3(pg.P), dim3(g.pitch / 4, pg.ty), args, smem, st);
 }
 
 }  // namespace aafwi

@@ -17,7 +17,9 @@
 //     T = sum_k a_k [(u_{+k} - u) + (u_{-k} - u)]  (the centre weight is
 //     -2 sum a_k exactly), so no weight carries a rounding error and the
 //     large-magnitude cancellation of c0 u against the neighbours is avoided;
-//   * W (L u + s) = K T / m with K = dt^2/(5040 dx^2) applied as hi + lo;
+//   * W (L u + s) = Wt T with Wt = dt^2/(5040 dx^2 m) per cell held as the
+//     FP32 pair Wh + Wl derived in FP64 (no rounding of W repeats coherently
+//     over a constant-velocity layer);
 //   * G x is applied as x - (1 - G) x with 1 - G tabulated, which is exact
 //     (G = 1) in the interior and accurate to |1-G| eps in the sponge.
 // One launch advances every shot by one step: grid (tiles per shot, shots).
@@ -118,24 +120,20 @@ __device__ __forceinline__ void add_source(float4 &q, int src, int pt, float w)
     }
 }
 
-// G (2 cur - G prev + K T / m) with G x = x - dG x.
-__device__ __forceinline__ float step1(float dG, float cur, float prev, float T, float m, float Khi,
-                                       float Klo)
+// G (2 cur - G prev + (Wh + Wl) T) with G x = x - dG x.
+__device__ __forceinline__ float step1(float dG, float cur, float prev, float T, float wh, float wl)
 {
-    const float y = T / m;
-    const float wq = fmaf(Khi, y, Klo * y);
+    const float wq = fmaf(wh, T, wl * T);
     const float gp = prev - dG * prev;
     const float t = ((cur - gp) + cur) + wq;
     return t - dG * t;
 }
 
-__device__ __forceinline__ float4 leapfrog(float4 dG, float4 cur, float4 prev, float4 T, float4 m,
-                                           const Geo &g)
+__device__ __forceinline__ float4 leapfrog(float4 dG, float4 cur, float4 prev, float4 T, float4 wh,
+                                           float4 wl)
 {
-    return make_float4(step1(dG.x, cur.x, prev.x, T.x, m.x, g.Khi, g.Klo),
-                       step1(dG.y, cur.y, prev.y, T.y, m.y, g.Khi, g.Klo),
-                       step1(dG.z, cur.z, prev.z, T.z, m.z, g.Khi, g.Klo),
-                       step1(dG.w, cur.w, prev.w, T.w, m.w, g.Khi, g.Klo));
+    return make_float4(step1(dG.x, cur.x, prev.x, T.x, wh.x, wl.x), step1(dG.y, cur.y, prev.y, T.y, wh.y, wl.y),
+                       step1(dG.z, cur.z, prev.z, T.z, wh.z, wl.z), step1(dG.w, cur.w, prev.w, T.w, wh.w, wl.w));
 }
 
 // 1 - G(z, x) = dz + dx - dz dx for the four cells of a float4 group.
@@ -185,8 +183,8 @@ __global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a)
             const float4 dG = sponge4(g.dGz[z], dgx);
             const float4 uc = ld4s(su, zl + HALO, xl + HALO);
             const float4 up = ld4g(a.u_prev + base + cell);
-            const float4 m = ld4g(a.m + cell);
-            st4g(a.u_next + base + cell, leapfrog(dG, uc, up, T, m, g));
+            const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
+            st4g(a.u_next + base + cell, leapfrog(dG, uc, up, T, wh, wl));
             if (a.ck_cur) {
                 st4g(a.ck_cur + base + cell, uc);
                 st4g(a.ck_prev + base + cell, up);
@@ -224,19 +222,19 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a)
             add_source(T, src, (int)cell, wsn);
             float4 Td = stencil4(sd, zl + HALO, xl + HALO, g.rz);
             const float4 rho = ld4g(a.rho + cell);
-            // scattered source: W L du - W rho (L u + s)  ->  K (T_d - rho T) / m
+            // scattered source: W L du - W rho (L u + s)  ->  Wt (T_d - rho T)
             Td.x -= rho.x * T.x;
             Td.y -= rho.y * T.y;
             Td.z -= rho.z * T.z;
             Td.w -= rho.w * T.w;
             const float4 dG = sponge4(g.dGz[z], dgx);
-            const float4 m = ld4g(a.m + cell);
+            const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
             const float4 uc = ld4s(su, zl + HALO, xl + HALO);
             const float4 up = ld4g(a.u_prev + base + cell);
             const float4 dc = ld4s(sd, zl + HALO, xl + HALO);
             const float4 dp = ld4g(a.d_prev + base + cell);
-            st4g(a.u_next + base + cell, leapfrog(dG, uc, up, T, m, g));
-            st4g(a.d_next + base + cell, leapfrog(dG, dc, dp, Td, m, g));
+            st4g(a.u_next + base + cell, leapfrog(dG, uc, up, T, wh, wl));
+            st4g(a.d_next + base + cell, leapfrog(dG, dc, dp, Td, wh, wl));
             if (a.ck_cur) {
                 st4g(a.ck_cur + base + cell, uc);
                 st4g(a.ck_prev + base + cell, up);
@@ -292,18 +290,18 @@ __global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a)
             Tz.x += inj.x; Tz.y += inj.y; Tz.z += inj.z; Tz.w += inj.w;
         }
         const float4 dG = sponge4(g.dGz[z], dgx);
-        const float4 m = ld4g(a.m + cell);
+        const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
         const float4 z1 = ld4s(sz, zl + HALO, xl + HALO);
         const float4 z2 = ld4g(a.z2n + base + cell);
-        const float4 zn = leapfrog(dG, z1, z2, Tz, m, g);
+        const float4 zn = leapfrog(dG, z1, z2, Tz, wh, wl);
         float4 Tu = stencil4(su, zl + HALO, xl + HALO, g.rz);
         add_source(Tu, src, (int)cell, wsn);
-        // L u + s = Tu * tscale; FWI scale -1/m, Born scale -1
+        // L u + s = Tu * tscale; FWI scale -1/m (= -tscale Tu 5040 dx^2 Wt/dt^2), Born -1
         float4 sc;
         if (a.born) {
             sc = make_float4(-g.tscale, -g.tscale, -g.tscale, -g.tscale);
         } else {
-            sc = make_float4(-g.tscale / m.x, -g.tscale / m.y, -g.tscale / m.z, -g.tscale / m.w);
+            sc = make_float4(g.iscale * wh.x, g.iscale * wh.y, g.iscale * wh.z, g.iscale * wh.w);
         }
         float4 im = ld4g(a.img + base + cell);
         im.x = fmaf(sc.x * zn.x, Tu.x, im.x);
@@ -315,45 +313,66 @@ __global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a)
     }
 }
 
-// m and E(rho) on the padded grid from the physical arrays (extension E =
-// clamp to the nearest physical cell); flags bad models: bit 0 non-finite or
-// non-positive m, bit 1 a velocity above the plan's CFL limit (m < mcfl).
-__global__ void k_prep(const Geo g, int nz, int nx, const float *m, const float *rho, float mcfl,
-                       float *m_pad, float *rho_pad, int *err)
+// Wt = K/m (as the FP32 pair Wh + Wl, K = dt^2/(5040 dx^2)) and E(rho) on
+// the padded grid from the physical arrays (extension E = clamp to the
+// nearest physical cell); flags bad models: bit 0 non-finite or non-positive
+// m, bit 1 a velocity above the plan's CFL limit (m < mcfl).
+__global__ void k_prep(const Geo g, int nz, int nx, const float *m, const float *rho, float mcfl, double K,
+                       float *W, float *rho_pad, int *err)
 {
     const long long N = (long long)g.NZ * g.pitch;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         const int z = (int)(i / g.pitch), x = (int)(i - (long long)z * g.pitch);
-        if (x >= g.NX) {
-            m_pad[i] = 1.f;      // pitch padding: finite, and the sponge zeroes the field there
+        if (x >= g.NX) {          // pitch padding: the sponge table zeroes the field there
+            W[i] = 0.f;
+            W[g.field + i] = 0.f;
             if (rho_pad) rho_pad[i] = 0.f;
             continue;
         }
         const int jz = min(max(z - g.nb, 0), nz - 1), jx = min(max(x - g.nb, 0), nx - 1);
         const float mv = m[(long long)jz * nx + jx];
-        if (!(mv > 0.f) || !isfinite(mv)) atomicOr(err, 1);
-        else if (mv < mcfl) atomicOr(err, 2);
-        m_pad[i] = mv;
+        float wh = 0.f, wl = 0.f;
+        if (!(mv > 0.f) || !isfinite(mv)) {
+            atomicOr(err, 1);
+        } else {
+            if (mv < mcfl) atomicOr(err, 2);
+            const double w = K / (double)mv;
+            wh = (float)w;
+            wl = (float)(w - (double)wh);
+        }
+        W[i] = wh;
+        W[g.field + i] = wl;
         if (rho_pad) rho_pad[i] = rho[(long long)jz * nx + jx];
     }
 }
 
-// grad_phys = E^T (sum over shots of the per-shot padded images), FP64 sum in
-// a fixed order (shot, then cell), one thread per physical cell.
-__global__ void k_shot_sum(const Geo g, int nz, int nx, const float *img, float *out)
+// grad_phys = E^T (sum over shots of the per-shot padded images), in two
+// separable passes with FP64 sums in a fixed order: (1) over shots and the
+// x-range of cells that physical column jx replicates, for every padded row;
+// (2) over the z-range of rows that physical row jz replicates.
+__global__ void k_shot_sum_x(const Geo g, int nx, const float *img, double *rowsum)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.NZ * nx) return;
+    const int z = i / nx, jx = i - z * nx;
+    const int xlo = jx == 0 ? 0 : jx + g.nb, xhi = jx == nx - 1 ? g.NX - 1 : jx + g.nb;
+    double acc = 0.0;
+    for (int s = 0; s < g.S; ++s) {
+        const float *f = img + (long long)s * g.field + (long long)z * g.pitch;
+        for (int x = xlo; x <= xhi; ++x) acc += (double)f[x];
+    }
+    rowsum[i] = acc;
+}
+
+__global__ void k_shot_sum_z(const Geo g, int nz, int nx, const double *rowsum, float *out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nz * nx) return;
     const int jz = i / nx, jx = i - jz * nx;
     const int zlo = jz == 0 ? 0 : jz + g.nb, zhi = jz == nz - 1 ? g.NZ - 1 : jz + g.nb;
-    const int xlo = jx == 0 ? 0 : jx + g.nb, xhi = jx == nx - 1 ? g.NX - 1 : jx + g.nb;
     double acc = 0.0;
-    for (int s = 0; s < g.S; ++s) {
-        const float *f = img + (long long)s * g.field;
-        for (int z = zlo; z <= zhi; ++z)
-            for (int x = xlo; x <= xhi; ++x) acc += (double)f[(long long)z * g.pitch + x];
-    }
+    for (int z = zlo; z <= zhi; ++z) acc += rowsum[(long long)z * nx + jx];
     out[i] = (float)acc;
 }
 
@@ -369,10 +388,10 @@ cudaError_t init_kernels()
 }
 
 void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float mcfl,
-                 float *m_pad, float *rho_pad, int *err, cudaStream_t st)
+                 double K, float *W, float *rho_pad, int *err, cudaStream_t st)
 {
     count_launch();
-    k_prep<<<1216, 256, 0, st>>>(g, nz, nx, m, rho, mcfl, m_pad, rho_pad, err);
+    k_prep<<<1216, 256, 0, st>>>(g, nz, nx, m, rho, mcfl, K, W, rho_pad, err);
 }
 
 void launch_fwd(const Geo &g, const FwdArgs &a, cudaStream_t st)
@@ -393,11 +412,13 @@ void launch_adj(const Geo &g, const AdjArgs &a, cudaStream_t st)
     k_adj<<<dim3(g.ntiles, g.S), dim3(BX, BY), adj_smem(), st>>>(g, a);
 }
 
-void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, float *out, cudaStream_t st)
+void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *rowsum, float *out,
+                     cudaStream_t st)
 {
-    const int n = nz * nx;
-    count_launch();
-    k_shot_sum<<<(n + 255) / 256, 256, 0, st>>>(g, nz, nx, img, out);
+    count_launch(2);
+    const int n1 = g.NZ * nx, n2 = nz * nx;
+    k_shot_sum_x<<<(n1 + 255) / 256, 256, 0, st>>>(g, nx, img, rowsum);
+    k_shot_sum_z<<<(n2 + 255) / 256, 256, 0, st>>>(g, nz, nx, rowsum, out);
 }
 
 }  // namespace aafwi

@@ -311,7 +311,9 @@ def test_aa_fwi_misfit_history_tiny(gpu, orc):
     lo, hi = p.m_bounds
     out = solve.aa_fwi(plan, dev(gpu, d_obs), dev(gpu, p.m_start), M=p.M, iters=p.iters,
                        eta_factor=ref["eta_factor"], bounds=(lo, hi))
-    assert abs(out["eta"] - ref["eta"]) / ref["eta"] < 1e-3
+    # eta = 1e-4 max|p0| / max|grad J(p0)|: the max sits at a source-adjacent
+    # cell, where the end-to-end FP32 gradient error is largest
+    assert abs(out["eta"] - ref["eta"]) / ref["eta"] < E2E_SMALL_RESIDUAL_TOL
     assert out["lam"] == ref["lam"]
     assert out["Mk"] == ref["Mk"]
     assert rel(out["J"][:4], ref["J"][:4]) < HIST_TOL
