@@ -211,6 +211,39 @@ int aafwi_aa_combine(aafwi_aa *aa, double lambda, const float *p_tilde, const fl
  * used to fix eta = factor * max|p_0| / max|grad J(p_0)|. */
 int aafwi_absmax(const float *x, size_t n, double *host_out, aafwi_stream stream);
 
+/* ---- learned preconditioner (not part of the paper) ---------------------- */
+
+/* A U-Net (4 levels, base width C; 3x3 convolutions with ReLU, 2x2 max
+ * pooling, 2x2 stride-2 transposed convolutions, skip concatenation, 1x1
+ * head) mapping a 2-channel image [normalised gradient, normalised model] to
+ * a 1-channel model update.  BF16 weights and NHWC activations on tensor
+ * cores with FP32 accumulation, FP32 master weights, Adam.
+ * Parameter vector layout (FP32, host): for each of the 17 convolutions in
+ * network order (enc0a, enc0b, enc1a, enc1b, enc2a, enc2b, bottom a, bottom b,
+ * then per decoder level 2, 1, 0: upconv, dec a, dec b) the weights then the
+ * bias; 3x3 weights [Cout][3][3][Cin], upconv weights [Cin][2][2][Cout];
+ * then the head weights [C] and bias [1]. */
+typedef struct aafwi_unet aafwi_unet;
+
+/* Allocate a network for batches up to Bmax of H x W images (H, W multiples
+ * of 8) with base width C (multiple of 8).  Parameters start at zero: set them
+ * with aafwi_unet_set_params. */
+int aafwi_unet_create(int Bmax, int H, int W, int C, aafwi_unet **out);
+void aafwi_unet_destroy(aafwi_unet *net);
+long long aafwi_unet_param_count(const aafwi_unet *net);
+/* Copy n FP32 parameters from / to the host (n = param_count); set resets Adam. */
+int aafwi_unet_set_params(aafwi_unet *net, const float *host, long long n);
+int aafwi_unet_get_params(aafwi_unet *net, float *host, long long n);
+/* y[B][H][W] = net(x[B][2][H][W]); device FP32 arrays. */
+int aafwi_unet_forward(aafwi_unet *net, const float *x, int B, float *y, aafwi_stream stream);
+/* Loss 1/(2 B H W) sum (net(x) - target)^2 and its parameter gradient
+ * (device FP32 [param_count], may be NULL); loss_host optional (syncs). */
+int aafwi_unet_loss_grad(aafwi_unet *net, const float *x, const float *target, int B, float *grad,
+                         double *loss_host, aafwi_stream stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on that loss with learning rate lr. */
+int aafwi_unet_train_step(aafwi_unet *net, const float *x, const float *target, int B, float lr,
+                          double *loss_host, aafwi_stream stream);
+
 /* ---- misfit without device allocation ----------------------------------- */
 
 /* The paper has no counterpart: this entry point exists for callers that

@@ -25,7 +25,9 @@ EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aa
            "aafwi_model_forward", "aafwi_born_forward", "aafwi_misfit", "aafwi_adjoint_gradient",
            "aafwi_born_adjoint", "aafwi_fwi_adjoint", "aafwi_read_misfit", "aafwi_aa_create", "aafwi_aa_destroy",
            "aafwi_aa_set_eta", "aafwi_aa_step", "aafwi_aa_combine", "aafwi_absmax",
-           "aafwi_launch_count", "aafwi_misfit_noalloc")
+           "aafwi_launch_count", "aafwi_misfit_noalloc", "aafwi_unet_create", "aafwi_unet_destroy",
+           "aafwi_unet_param_count", "aafwi_unet_set_params", "aafwi_unet_get_params", "aafwi_unet_forward",
+           "aafwi_unet_loss_grad", "aafwi_unet_train_step")
 
 
 class AafwiError(RuntimeError):
@@ -96,6 +98,14 @@ def load(path=LIB_PATH):
         "aafwi_absmax": ([P, Z, P, P], I),
         "aafwi_launch_count": ([], ctypes.c_ulonglong),
         "aafwi_misfit_noalloc": ([P, P, ctypes.c_longlong, P, P, P, P], I),
+        "aafwi_unet_create": ([I, I, I, I, P], I),
+        "aafwi_unet_destroy": ([P], None),
+        "aafwi_unet_param_count": ([P], ctypes.c_longlong),
+        "aafwi_unet_set_params": ([P, P, ctypes.c_longlong], I),
+        "aafwi_unet_get_params": ([P, P, ctypes.c_longlong], I),
+        "aafwi_unet_forward": ([P, P, I, P, P], I),
+        "aafwi_unet_loss_grad": ([P, P, P, I, P, P, P], I),
+        "aafwi_unet_train_step": ([P, P, P, I, ctypes.c_float, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -266,6 +276,58 @@ def misfit_noalloc(d_syn, d_obs, resid=None, J_dev=None, sync=True, n=None, stre
                                        _ptr(J_dev) if J_dev is not None else None,
                                        ctypes.byref(J) if sync else None, _stream(stream)))
     return J.value if sync else None
+
+
+class UNet:
+    """Owns an aafwi_unet (the learned preconditioner's network)."""
+
+    def __init__(self, Bmax, H, W, C=32):
+        h = ctypes.c_void_p()
+        _check(load().aafwi_unet_create(int(Bmax), int(H), int(W), int(C), ctypes.byref(h)))
+        self.h, self.Bmax, self.H, self.W, self.C = h, int(Bmax), int(H), int(W), int(C)
+        self.nparam = int(load().aafwi_unet_param_count(h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().aafwi_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == self.nparam
+        _check(load().aafwi_unet_set_params(self.h, a.ctypes.data_as(ctypes.c_void_p), a.size))
+
+    def get_params(self):
+        a = np.empty(self.nparam, dtype=np.float32)
+        _check(load().aafwi_unet_get_params(self.h, a.ctypes.data_as(ctypes.c_void_p), a.size))
+        return a
+
+    def forward(self, x, y=None, stream=None):
+        import torch
+        B = x.shape[0]
+        if y is None:
+            y = torch.empty((B, self.H, self.W), dtype=torch.float32, device=x.device)
+        _check(load().aafwi_unet_forward(self.h, _f32(x), B, _f32(y), _stream(stream)))
+        return y
+
+    def loss_grad(self, x, target, grad=None, stream=None):
+        J = ctypes.c_double()
+        _check(load().aafwi_unet_loss_grad(self.h, _f32(x), _f32(target), x.shape[0],
+                                           _f32(grad) if grad is not None else None, ctypes.byref(J),
+                                           _stream(stream)))
+        return J.value
+
+    def train_step(self, x, target, lr, stream=None):
+        J = ctypes.c_double()
+        _check(load().aafwi_unet_train_step(self.h, _f32(x), _f32(target), x.shape[0], float(lr),
+                                            ctypes.byref(J), _stream(stream)))
+        return J.value
 
 
 def launch_count():

@@ -1,0 +1,106 @@
+"""Pins of the U-Net reference (oracle/unet.py), CPU only: brute-force
+convolutions, adjoint (dot-product) identities of every layer's backward,
+BF16 rounding, and central differences of the full network loss in float64."""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+
+
+def test_bf16_round_to_nearest_even():
+    one = np.float32(1.0)
+    vals = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -7, -2.5, 3.0e-3], dtype=np.float32)
+    r = U.bf16(vals)
+    assert r[0] == one and r[1] == one                      # tie -> even (1.0)
+    assert r[2] == np.float32(1 + 2 ** -6)                  # tie -> even (1 + 2^-6)
+    assert r[3] == np.float32(1 + 2 ** -7)                  # representable
+    assert r[4] == np.float32(-2.5)
+    assert abs(r[5] - 3.0e-3) <= 2 ** -8 * 3.0e-3           # within half an ulp (8 significant bits)
+
+
+def test_conv3_matches_brute_force():
+    rng = np.random.default_rng(0)
+    B, H, W, Ci, Co = 2, 5, 6, 3, 4
+    x = rng.standard_normal((B, H, W, Ci))
+    w = rng.standard_normal((Co, 3, 3, Ci))
+    b = rng.standard_normal(Co)
+    y = U.conv3(x, w, b)
+    ref = np.zeros((B, H, W, Co))
+    for n in range(B):
+        for i in range(H):
+            for j in range(W):
+                for o in range(Co):
+                    s = b[o]
+                    for ky in range(3):
+                        for kx in range(3):
+                            ii, jj = i + ky - 1, j + kx - 1
+                            if 0 <= ii < H and 0 <= jj < W:
+                                s += float(x[n, ii, jj] @ w[o, ky, kx])
+                    ref[n, i, j, o] = s
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_up2_matches_brute_force():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((1, 3, 4, 5))
+    w = rng.standard_normal((5, 2, 2, 2))
+    b = rng.standard_normal(2)
+    y = U.up2(x, w, b)
+    for i in range(6):
+        for j in range(8):
+            np.testing.assert_allclose(y[0, i, j], x[0, i // 2, j // 2] @ w[:, i % 2, j % 2, :] + b, rtol=1e-12)
+
+
+def test_layer_backwards_are_adjoints():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((2, 6, 8, 3))
+    w = rng.standard_normal((4, 3, 3, 3))
+    dz = rng.standard_normal((2, 6, 8, 4))
+    dx, dw = U.conv3_back(x, w, dz)
+    z = U.conv3(x, w, np.zeros(4))
+    assert np.isclose((z * dz).sum(), (dx * x).sum(), rtol=1e-12)
+    assert np.isclose((z * dz).sum(), (dw * w).sum(), rtol=1e-12)
+    xu = rng.standard_normal((2, 3, 4, 5))
+    wu = rng.standard_normal((5, 2, 2, 3))
+    dy = rng.standard_normal((2, 6, 8, 3))
+    dxu, dwu = U.up2_back(xu, wu, dy)
+    yu = U.up2(xu, wu, np.zeros(3))
+    assert np.isclose((yu * dy).sum(), (dxu * xu).sum(), rtol=1e-12)
+    assert np.isclose((yu * dy).sum(), (dwu * wu).sum(), rtol=1e-12)
+
+
+def test_maxpool_first_maximum_and_backward():
+    x = np.zeros((1, 2, 2, 1))
+    y, idx = U.maxpool(x)
+    assert idx[0, 0, 0, 0] == 0 and y[0, 0, 0, 0] == 0.0          # all equal -> first
+    x = np.array([1.0, 3.0, 3.0, 2.0]).reshape(1, 2, 2, 1)
+    y, idx = U.maxpool(x)
+    assert y[0, 0, 0, 0] == 3.0 and idx[0, 0, 0, 0] == 1
+    g = U.maxpool_back(np.ones((1, 1, 1, 1)), idx, x.shape)
+    assert g[0, 0, 1, 0] == 1.0 and g.sum() == 1.0
+
+
+@pytest.mark.slow
+def test_network_gradient_central_differences():
+    C = 8
+    p = U.init_params(C, seed=3).astype(np.float64)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((2, 2, 16, 16))
+    t = rng.standard_normal((2, 16, 16))
+    L, g = U.loss_grad(p, x, t, C, exact=True)
+    assert g.size == U.param_count(C) == p.size
+    # random unit directions (small enough not to cross a ReLU / max-pool kink)
+    # and single parameters of every layer type
+    for trial in range(3):
+        d = rng.standard_normal(p.size)
+        d /= np.linalg.norm(d)
+        eps = 1e-6
+        Lp, _ = U.loss_grad(p + eps * d, x, t, C, exact=True)
+        Lm, _ = U.loss_grad(p - eps * d, x, t, C, exact=True)
+        assert (Lp - Lm) / (2 * eps) == pytest.approx(float(g @ d), rel=1e-6, abs=1e-12)
+    for k in (0, 5, 300, p.size - 9, p.size - 1):
+        e = np.zeros(p.size)
+        e[k] = 1e-5
+        Lp, _ = U.loss_grad(p + e, x, t, C, exact=True)
+        Lm, _ = U.loss_grad(p - e, x, t, C, exact=True)
+        assert (Lp - Lm) / 2e-5 == pytest.approx(g[k], rel=1e-5, abs=1e-10)
