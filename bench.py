@@ -268,6 +268,10 @@ def run_ours(args):
                                    "us_per_time_step": 1e3 * kt["fwd_ms"] / nt}}
 
     e2e = run_e2e(plan, prob, dev, args.e2e_steps) if args.e2e_steps > 0 else None
+    learned_cmp = None
+    if args.learned_eval > 0:
+        plan.close()
+        learned_cmp = learned_vs_plain(args.learned_eval, args.learned_target, args.learned_max_iters)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob)
@@ -285,6 +289,7 @@ def run_ours(args):
                            "fwi_iterations_per_s": args.steps / (ms_total / 1e3),
                            "J_over_J0": run.J / run.J0},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "learned_vs_plain": learned_cmp,
                 "clocks": clk, "host_wall_s": wall}
         print(json.dumps(line), flush=True)
     run.close()
@@ -354,6 +359,26 @@ def run_e2e(plan, prob, dev, steps):
             "ms_per_step": ms, "call": "aafwi_adjoint_gradient (FWI) with host-resident m and d_obs"}
 
 
+def learned_vs_plain(n_eval, target, max_iters):
+    """Second half of the metric: wall seconds (same GPU) for plain AA(10) and
+    for AA(10) with the trained learned preconditioner to reach J/J0 <= target
+    on held-out 400 x 150 models (16 shots, 2500 steps)."""
+    from paper_2008_11778_gb300 import learned
+    params, meta = learned.load_weights()
+    rows = learned.compare(params, n_eval, target, max_iters, log=lambda *a: None)
+    sp = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in rows]
+    return {"metric": "wall-s to J/J0 <= %g, learned vs plain AA(10)" % target, "target": target,
+            "max_iters": max_iters, "models": len(rows),
+            "plain_s": [r["plain"]["seconds"] for r in rows],
+            "learned_s": [r["learned"]["seconds"] for r in rows],
+            "plain_reached": [bool(r["plain"]["reached"]) for r in rows],
+            "learned_reached": [bool(r["learned"]["reached"]) for r in rows],
+            "plain_iters": [r["plain"]["iterations"] for r in rows],
+            "learned_iters": [r["learned"]["iterations"] for r in rows],
+            "median_speedup": float(np.median(sp)),
+            "training": {k: float(v) for k, v in meta.items()}}
+
+
 def cpu_baseline(prob):
     import oracle
     cores = oracle.num_threads()
@@ -392,6 +417,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="small case for ncu captures")
+    ap.add_argument("--learned-eval", type=int, default=2, help="held-out models for learned vs plain AA")
+    ap.add_argument("--learned-target", type=float, default=0.1)
+    ap.add_argument("--learned-max-iters", type=int, default=60)
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case()

@@ -244,6 +244,18 @@ int aafwi_unet_loss_grad(aafwi_unet *net, const float *x, const float *target, i
 int aafwi_unet_train_step(aafwi_unet *net, const float *x, const float *target, int B, float lr,
                           double *loss_host, aafwi_stream stream);
 
+/* Network input of the learned step from a gradient and a model (device FP32
+ * [nz][nx]): stats (device double[3]) = (max|grad|, mean m, std m) and
+ * x[2][H][W] = (grad / max|grad|, (m - mean) / std) on the top-left nz x nx
+ * corner of the H x W network grid, zero elsewhere. */
+int aafwi_learned_features(const float *grad, const float *m, int nz, int nx, int H, int W, float *x,
+                           double *stats, aafwi_stream stream);
+/* Learned step: out = clip(m + std_m * delta[:nz, :nx], lo, hi) (no clip when
+ * lo >= hi); delta is the network output [H][W], stats from
+ * aafwi_learned_features. */
+int aafwi_learned_apply(const float *m, const float *delta, int nz, int nx, int W, const double *stats, float lo,
+                        float hi, float *out, aafwi_stream stream);
+
 /* ---- misfit without device allocation ----------------------------------- */
 
 /* The paper has no counterpart: this entry point exists for callers that

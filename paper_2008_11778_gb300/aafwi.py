@@ -27,7 +27,7 @@ EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aa
            "aafwi_aa_set_eta", "aafwi_aa_step", "aafwi_aa_combine", "aafwi_absmax",
            "aafwi_launch_count", "aafwi_misfit_noalloc", "aafwi_unet_create", "aafwi_unet_destroy",
            "aafwi_unet_param_count", "aafwi_unet_set_params", "aafwi_unet_get_params", "aafwi_unet_forward",
-           "aafwi_unet_loss_grad", "aafwi_unet_train_step")
+           "aafwi_unet_loss_grad", "aafwi_unet_train_step", "aafwi_learned_features", "aafwi_learned_apply")
 
 
 class AafwiError(RuntimeError):
@@ -106,6 +106,8 @@ def load(path=LIB_PATH):
         "aafwi_unet_forward": ([P, P, I, P, P], I),
         "aafwi_unet_loss_grad": ([P, P, P, I, P, P, P], I),
         "aafwi_unet_train_step": ([P, P, P, I, ctypes.c_float, P, P], I),
+        "aafwi_learned_features": ([P, P, I, I, I, I, P, P, P], I),
+        "aafwi_learned_apply": ([P, P, I, I, I, P, ctypes.c_float, ctypes.c_float, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -328,6 +330,20 @@ class UNet:
         _check(load().aafwi_unet_train_step(self.h, _f32(x), _f32(target), x.shape[0], float(lr),
                                             ctypes.byref(J), _stream(stream)))
         return J.value
+
+
+def learned_features(grad, m, H, W, x, stats, stream=None):
+    """aafwi_learned_features: network input x[2][H][W] and stats (device double[3])."""
+    nz, nx = m.shape
+    _check(load().aafwi_learned_features(_f32(grad), _f32(m), nz, nx, int(H), int(W), _f32(x), _ptr(stats),
+                                         _stream(stream)))
+
+
+def learned_apply(m, delta, stats, out, lo=0.0, hi=0.0, stream=None):
+    """aafwi_learned_apply: out = clip(m + std_m * delta)."""
+    nz, nx = m.shape
+    _check(load().aafwi_learned_apply(_f32(m), _f32(delta), nz, nx, int(delta.shape[-1]), _ptr(stats),
+                                      float(lo), float(hi), _f32(out), _stream(stream)))
 
 
 def launch_count():

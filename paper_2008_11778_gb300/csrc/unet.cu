@@ -281,6 +281,67 @@ __global__ void k_to_bf16(const float *a, long long n, bf16 *b)
     GRID_LOOP(i, n) b[i] = __float2bfloat16_rn(a[i]);
 }
 
+// Learned-step features: stats = (max|g|, mean m, std m) in FP64 (one block),
+// then x[0] = g / max|g|, x[1] = (m - mean) / std on the network grid
+// [H][W] (zero outside the model's nz x nx corner).
+__global__ void k_feat_stats(const float *g, const float *m, long long n, double *stats)
+{
+    __shared__ double s0[ET], s1[ET], s2[ET];
+    double gm = 0.0, sm = 0.0, sq = 0.0;
+    for (long long i = threadIdx.x; i < n; i += ET) {
+        gm = fmax(gm, fabs((double)g[i]));
+        sm += (double)m[i];
+        sq += (double)m[i] * m[i];
+    }
+    s0[threadIdx.x] = gm;
+    s1[threadIdx.x] = sm;
+    s2[threadIdx.x] = sq;
+    __syncthreads();
+    for (int o = ET / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s0[threadIdx.x] = fmax(s0[threadIdx.x], s0[threadIdx.x + o]);
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mean = s1[0] / n;
+        stats[0] = s0[0] > 0 ? s0[0] : 1.0;
+        stats[1] = mean;
+        const double var = s2[0] / n - mean * mean;
+        stats[2] = var > 0 ? sqrt(var) : 1.0;
+    }
+}
+
+__global__ void k_feat(const float *g, const float *m, int nz, int nx, int H, int W, const double *stats, float *x)
+{
+    const long long n = (long long)H * W;
+    GRID_LOOP(i, n) {
+        const int z = (int)(i / W), c = (int)(i % W);
+        float a = 0.f, b = 0.f;
+        if (z < nz && c < nx) {
+            const long long j = (long long)z * nx + c;
+            a = (float)(g[j] / stats[0]);
+            b = (float)((m[j] - stats[1]) / stats[2]);
+        }
+        x[i] = a;
+        x[n + i] = b;
+    }
+}
+
+// out = clip(m + std_m * delta, lo, hi) on the model's nz x nx corner of [H][W]
+__global__ void k_apply(const float *m, const float *delta, int nz, int nx, int W, const double *stats,
+                        float lo, float hi, float *out)
+{
+    GRID_LOOP(i, (long long)nz * nx) {
+        const int z = (int)(i / nx), c = (int)(i % nx);
+        float v = (float)(m[i] + stats[2] * delta[(long long)z * W + c]);
+        if (lo < hi) v = fminf(fmaxf(v, lo), hi);
+        out[i] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 
 struct Conv {
@@ -620,6 +681,33 @@ int aafwi_unet_loss_grad(aafwi_unet *u, const float *x, const float *target, int
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
     if (e != cudaSuccess) return uerr(u, AAFWI_ERR_CUDA, std::string("unet_loss_grad: ") + cudaGetErrorString(e));
+    return AAFWI_OK;
+}
+
+int aafwi_learned_features(const float *grad, const float *m, int nz, int nx, int H, int W, float *x,
+                           double *stats, aafwi_stream stream)
+{
+    if (!grad || !m || !x || !stats || nz < 1 || nx < 1 || H < nz || W < nx)
+        return uerr(nullptr, AAFWI_ERR_ARG, "learned_features: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    count_launch(2);
+    k_feat_stats<<<1, ET, 0, st>>>(grad, m, (long long)nz * nx, stats);
+    k_feat<<<nblk((long long)H * W), ET, 0, st>>>(grad, m, nz, nx, H, W, stats, x);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return uerr(nullptr, AAFWI_ERR_CUDA, cudaGetErrorString(e));
+    return AAFWI_OK;
+}
+
+int aafwi_learned_apply(const float *m, const float *delta, int nz, int nx, int W, const double *stats, float lo,
+                        float hi, float *out, aafwi_stream stream)
+{
+    if (!m || !delta || !stats || !out || nz < 1 || nx < 1 || W < nx)
+        return uerr(nullptr, AAFWI_ERR_ARG, "learned_apply: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    count_launch();
+    k_apply<<<nblk((long long)nz * nx), ET, 0, st>>>(m, delta, nz, nx, W, stats, lo, hi, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return uerr(nullptr, AAFWI_ERR_CUDA, cudaGetErrorString(e));
     return AAFWI_OK;
 }
 

@@ -22,7 +22,8 @@ stand in for them with the shapes, sizes and structure of each workload:
             +800 m/s elliptic lenses; 200 shots with uneven apertures,
             Ricker 12 Hz, dt 0.8 ms, 6000 steps.
   learned   256 x 96, dx 20 m models from the batched generator (training),
-            16 shots, Ricker 10 Hz, dt 1.5 ms, 1500 steps.
+            16 shots, Ricker 10 Hz, dt 1.5 ms, 1500 steps; held-out 400 x 150
+            evaluation models of the same generator, 2500 steps.
 
 Sources and receivers sit one cell below the top of the physical grid; shot
 s of S is at column round((s + 1/2) nx / S).  Seeds are 1000*id + 2008.
@@ -274,6 +275,19 @@ def learned_model(seed, nz=96, nx=256, nb=NB_DEFAULT):
     c_start = _smooth(c_true, 6.0)
     g = surface_geometry(nz, nx, nb, 20.0, 1.5e-3, 10.0, 1500, 16)
     return Problem("learned-%dx%d-%d" % (nx, nz, seed), g, c_true, c_start, M=10, iters=30,
+                   c_bounds=(0.8 * c_true.min(), 1.2 * c_true.max()))
+
+
+def learned_eval_model(seed, nz=150, nx=400, nb=NB_DEFAULT):
+    """A held-out evaluation model of the learned preconditioner: 400 x 150,
+    the training generator's structure and acquisition (dx 20 m, 16 shots,
+    Ricker 10 Hz, dt 1.5 ms) with a record long enough for the wider spread
+    (2500 steps)."""
+    rng = np.random.default_rng(seed)
+    c_true = layered_faulted(nz, nx, 12, 1500.0, 4500.0, 2, rng, throw=(3, 9))
+    c_start = _smooth(c_true, 6.0)
+    g = surface_geometry(nz, nx, nb, 20.0, 1.5e-3, 10.0, 2500, 16)
+    return Problem("learned-eval-%dx%d-%d" % (nx, nz, seed), g, c_true, c_start, M=10, iters=30,
                    c_bounds=(0.8 * c_true.min(), 1.2 * c_true.max()))
 
 
