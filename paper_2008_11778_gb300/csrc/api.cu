@@ -271,8 +271,9 @@ int setup_persist(aafwi_plan *p, int engine, const aafwi_shots *sh, std::string 
     int P = (int)std::min<long long>(sms, R / 4);        // strips of at least 4 rows
     if (P < 1) return no("grid too small");
     const int rows_max = (int)((R + P - 1) / P);
-    const int ty = std::max(1, std::min(PT / W4, rows_max));
-    if ((rows_max + ty - 1) / ty > RBMAX) return no("too many rows per thread");
+    const int inner = std::max(0, rows_max - 8);           // rows of phase 1 (no halo)
+    const int ty = std::max(1, std::min(PT / W4, std::max(1, inner)));
+    if ((inner + ty - 1) / ty > RBMAX) return no("too many rows per thread");
     // strips and receiver slots
     std::vector<int> row0(P + 1);
     for (int c = 0; c <= P; ++c) row0[c] = (int)(R * c / P);

@@ -176,84 +176,168 @@ __device__ __forceinline__ void padd_source(float4 &q, int src, int pt, float w)
 // holds level n (own rows + the 4 halo rows above and below, refreshed from
 // the neighbours) and the other tile holds level n-1 in its own rows, which
 // each thread overwrites in place with level n+1 (it reads and writes only
-// its own cells there).  Thread (x, y) owns float4 column x and a contiguous
-// block of rows, walking down it with the 9-row stencil column in registers.
+// its own cells there).
+// A step runs in two phases so that the neighbour handshake overlaps work:
+//  1. the interior rows [4, nr-4), which need no halo: thread (x, y) owns
+//     float4 column x of the y-th block of them and walks down it with the
+//     9-row stencil column in registers;
+//  2. after the neighbours' edge rows arrive, the 8 edge rows, one float4
+//     group per thread at a time.
 // The model is read through L1/L2.
+
+struct Strip {
+    int r0, nr, W4, ra, rb, ne;
+};
+
+__device__ __forceinline__ Strip strip_of(const Geo &g, const PGeo &pg, int c)
+{
+    Strip t;
+    t.r0 = pg.row0[c];
+    t.nr = pg.row0[c + 1] - t.r0;
+    t.W4 = g.pitch / 4;
+    const int ni = t.nr >= 8 ? t.nr - 8 : 0;
+    const int RB = (ni + blockDim.y - 1) / blockDim.y;
+    t.ra = 4 + min((int)threadIdx.y * RB, ni);
+    t.rb = 4 + min((int)threadIdx.y * RB + RB, ni);
+    t.ne = t.nr >= 8 ? 8 : t.nr;
+    return t;
+}
+
+__device__ __forceinline__ int edge_row(const Strip &t, int e) { return (t.nr < 8 || e < 4) ? e : t.nr - 8 + e; }
+
+__device__ __forceinline__ float4 sponge_at(const Geo &g, int z, float4 dgx)
+{
+    const float dz = g.dGz[z];
+    return make_float4(dz + dgx.x - dz * dgx.x, dz + dgx.y - dz * dgx.y, dz + dgx.z - dz * dgx.z,
+                       dz + dgx.w - dz * dgx.w);
+}
+
+// Forward update of float4 group (tile row r + 4, column x4) of shot s, depth z.
+__device__ __forceinline__ void fwd_cell(const Geo &g, const PGeo &pg, const PFwdArgs &a, int n, const float4 *A4,
+                                         float4 *B4, const float4 (&w)[9], int W4, int x4, int r, int s, int z,
+                                         float wsn, float4 dgx)
+{
+    const int ti = (r + 4) * W4 + x4;
+    float4 out = w[4];
+    if (n < g.nt[s]) {
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int x = 4 * x4;
+        const float4 L = x4 > 0 ? A4[ti - 1] : zero;
+        const float4 R = x4 + 1 < W4 ? A4[ti + 1] : zero;
+        float4 T = (z >= 4 && z < g.NZ - 4) ? col_stencil<false>(g, w, L, R, z) : col_stencil<true>(g, w, L, R, z);
+        padd_source(T, g.src_pt[s], z * g.pitch + x, wsn);
+        const long long zc = (long long)z * g.pitch + x;
+        const long long cell = (long long)s * g.field + zc;
+        __stcs(reinterpret_cast<float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell), T);
+        const float4 wh = __ldg(reinterpret_cast<const float4 *>(a.W + zc));
+        const float4 wl = __ldg(reinterpret_cast<const float4 *>(a.W + g.field + zc));
+        out = pleap(sponge_at(g, z, dgx), w[4], B4[ti], T, wh, wl);
+    }
+    B4[ti] = out;
+}
+
+// Adjoint update and imaging of float4 group (tile row r + 4, column x4).
+__device__ __forceinline__ void adj_cell(const Geo &g, const PGeo &pg, const PAdjArgs &a, int n, const float4 *A4,
+                                         float4 *B4, const float4 *rin, int s0, const float4 (&w)[9], int W4, int x4,
+                                         int gr, int r, int s, int z, float4 dgx)
+{
+    const int ti = (r + 4) * W4 + x4;
+    float4 out = w[4];
+    if (n < g.nt[s]) {
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int x = 4 * x4;
+        const float4 L = x4 > 0 ? A4[ti - 1] : zero;
+        const float4 R = x4 + 1 < W4 ? A4[ti + 1] : zero;
+        float4 Tz = (z >= 4 && z < g.NZ - 4) ? col_stencil<false>(g, w, L, R, z) : col_stencil<true>(g, w, L, R, z);
+        const int sl = __ldg(pg.grp_slot + (long long)gr * W4 + x4);
+        if (sl >= 0) {
+            const float4 inj = rin[sl - s0];
+            Tz.x += inj.x; Tz.y += inj.y; Tz.z += inj.z; Tz.w += inj.w;
+        }
+        const long long zc = (long long)z * g.pitch + x;
+        const long long cell = (long long)s * g.field + zc;
+        const float4 wh = __ldg(reinterpret_cast<const float4 *>(a.W + zc));
+        const float4 wl = __ldg(reinterpret_cast<const float4 *>(a.W + g.field + zc));
+        const float4 zn = pleap(sponge_at(g, z, dgx), w[4], B4[ti], Tz, wh, wl);
+        const float4 Tu = __ldcs(reinterpret_cast<const float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell));
+        float4 sc;
+        if (a.born) {
+            sc = make_float4(-g.tscale, -g.tscale, -g.tscale, -g.tscale);
+        } else {
+            sc = make_float4(g.iscale * wh.x, g.iscale * wh.y, g.iscale * wh.z, g.iscale * wh.w);
+        }
+        float4 *ip = reinterpret_cast<float4 *>(a.img + cell);
+        float4 im = *ip;
+        im.x = fmaf(sc.x * zn.x, Tu.x, im.x);
+        im.y = fmaf(sc.y * zn.y, Tu.y, im.y);
+        im.z = fmaf(sc.z * zn.z, Tu.z, im.z);
+        im.w = fmaf(sc.w * zn.w, Tu.w, im.w);
+        *ip = im;
+        out = zn;
+    }
+    B4[ti] = out;
+}
+
 __global__ void __launch_bounds__(PT, 1) k_fwd_persist(const Geo g, const PGeo pg, const PFwdArgs a)
 {
     extern __shared__ __align__(16) float psm[];
     __shared__ int abort_sh;
     const int c = blockIdx.x;
-    const int r0 = pg.row0[c], nr = pg.row0[c + 1] - r0;
-    const int W4 = g.pitch / 4;
+    const Strip t = strip_of(g, pg, c);
+    const int W4 = t.W4;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     const long long tsz = (long long)(pg.rows_max + 8) * g.pitch;
     float *tile[2] = {psm, psm + tsz};
     for (int i = tid; i < 2 * (pg.rows_max + 8) * W4; i += nth)
         reinterpret_cast<float4 *>(psm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int x4 = threadIdx.x, x = 4 * x4;
-    const int RB = (nr + blockDim.y - 1) / blockDim.y;
-    const int ra = min((int)threadIdx.y * RB, nr), rb = min(ra + RB, nr);
-    const int sa = (r0 + ra) / g.NZ, za = (r0 + ra) - sa * g.NZ;
-    const float4 dgx = *reinterpret_cast<const float4 *>(g.dGx + x);
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int x4 = threadIdx.x;
+    const int sa = (t.r0 + t.ra) / g.NZ, za = (t.r0 + t.ra) - sa * g.NZ;
+    const float4 dgx = *reinterpret_cast<const float4 *>(g.dGx + 4 * x4);
     __syncthreads();
     for (int n = 0; n < a.nt; ++n) {
         float *A = tile[n & 1];
         float *B = tile[(n + 1) & 1];
         if (c == 0 && n == a.stall_step) return;   // test hook: leave the neighbours' waits unmet
-        if (n > 0) {
-            if (!wait_neighbours(pg, c, (unsigned)n, &abort_sh)) return;
-            load_halo(g, pg, A, c, nr, n & 1);
-            __syncthreads();
-        }
         const float4 *A4 = reinterpret_cast<const float4 *>(A);
         float4 *B4 = reinterpret_cast<float4 *>(B);
-        if (ra < rb) {
+        const float wsn = g.ws[n];
+        // phase 1: interior rows, no halo needed
+        if (t.ra < t.rb) {
             float4 w[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) w[k] = A4[(ra + k) * W4 + x4];
+            for (int k = 0; k < 9; ++k) w[k] = A4[(t.ra + k) * W4 + x4];
             int s = sa, z = za;
-            const float wsn = g.ws[n];
-            int active = n < g.nt[s], src = g.src_pt[s];
-            long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
 #pragma unroll
             for (int q = 0; q < RBMAX; ++q) {
-                const int r = ra + q;
-                if (r >= rb) break;
-                const int ti = (r + 4) * W4 + x4;
-                float4 out = w[4];
-                if (active) {
-                    const float4 L = x4 > 0 ? A4[ti - 1] : zero;
-                    const float4 R = x4 + 1 < W4 ? A4[ti + 1] : zero;
-                    float4 T = (z >= 4 && z < g.NZ - 4) ? col_stencil<false>(g, w, L, R, z)
-                                                         : col_stencil<true>(g, w, L, R, z);
-                    padd_source(T, src, z * g.pitch + x, wsn);
-                    __stcs(reinterpret_cast<float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell), T);
-                    const long long zc = (long long)z * g.pitch + x;
-                    const float4 wh = __ldg(reinterpret_cast<const float4 *>(a.W + zc));
-                    const float4 wl = __ldg(reinterpret_cast<const float4 *>(a.W + g.field + zc));
-                    const float dz = g.dGz[z];
-                    const float4 dG = make_float4(dz + dgx.x - dz * dgx.x, dz + dgx.y - dz * dgx.y,
-                                                  dz + dgx.z - dz * dgx.z, dz + dgx.w - dz * dgx.w);
-                    out = pleap(dG, w[4], B4[ti], T, wh, wl);
-                }
-                B4[ti] = out;
+                const int r = t.ra + q;
+                if (r >= t.rb) break;
+                fwd_cell(g, pg, a, n, A4, B4, w, W4, x4, r, s, z, wsn, dgx);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) w[k] = w[k + 1];
-                if (r + 1 < rb) w[8] = A4[(r + 9) * W4 + x4];
-                cell += g.pitch;
+                if (r + 1 < t.rb) w[8] = A4[(r + 9) * W4 + x4];
                 if (++z == g.NZ) {
                     z = 0;
                     ++s;
-                    active = s < g.S && n < g.nt[s];
-                    src = s < g.S ? g.src_pt[s] : -1;
-                    cell = (long long)s * g.field + x;
                 }
             }
         }
+        // phase 2: neighbours' edge rows, then the strip's own edge rows
+        if (n > 0) {
+            if (!wait_neighbours(pg, c, (unsigned)n, &abort_sh)) return;
+            load_halo(g, pg, A, c, t.nr, n & 1);
+        }
         __syncthreads();
-        store_edges(g, pg, B, c, nr, (n + 1) & 1);
+        for (int i = tid; i < t.ne * W4; i += nth) {
+            const int e = i / W4, ex = i - e * W4;
+            const int r = edge_row(t, e);
+            const int gr = t.r0 + r, s = gr / g.NZ, z = gr - s * g.NZ;
+            float4 w[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) w[k] = A4[(r + k) * W4 + ex];
+            fwd_cell(g, pg, a, n, A4, B4, w, W4, ex, r, s, z, wsn, *reinterpret_cast<const float4 *>(g.dGx + 4 * ex));
+        }
+        __syncthreads();
+        store_edges(g, pg, B, c, t.nr, (n + 1) & 1);
         if (a.traces) {
             // receiver gather: sample n = u^{n+1}
             const int s0 = pg.slot_off[c], s1 = pg.slot_off[c + 1];
@@ -262,7 +346,7 @@ __global__ void __launch_bounds__(PT, 1) k_fwd_persist(const Geo g, const PGeo p
                 const int gr = grp / W4, gx = grp - gr * W4;
                 const int s = gr / g.NZ;
                 if (n >= g.nt[s]) continue;
-                const float4 v = reinterpret_cast<const float4 *>(B + (long long)(gr - r0 + 4) * g.pitch)[gx];
+                const float4 v = reinterpret_cast<const float4 *>(B + (long long)(gr - t.r0 + 4) * g.pitch)[gx];
                 const int4 cols = pg.slot_cols[j];
                 const long long tb = g.tr_off[s] + (long long)n * g.nrec[s];
                 if (cols.x >= 0) a.traces[tb + cols.x] = v.x;
@@ -280,8 +364,8 @@ __global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo p
     extern __shared__ __align__(16) float psm[];
     __shared__ int abort_sh;
     const int c = blockIdx.x;
-    const int r0 = pg.row0[c], nr = pg.row0[c + 1] - r0;
-    const int W4 = g.pitch / 4;
+    const Strip t = strip_of(g, pg, c);
+    const int W4 = t.W4;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     const long long tsz = (long long)(pg.rows_max + 8) * g.pitch;
     float *tile[2] = {psm, psm + tsz};
@@ -289,11 +373,9 @@ __global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo p
     const int s0 = pg.slot_off[c], s1 = pg.slot_off[c + 1];
     for (int i = tid; i < 2 * (pg.rows_max + 8) * W4; i += nth)
         reinterpret_cast<float4 *>(psm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int x4 = threadIdx.x, x = 4 * x4;
-    const int RB = (nr + blockDim.y - 1) / blockDim.y;
-    const int ra = min((int)threadIdx.y * RB, nr), rb = min(ra + RB, nr);
-    const int sa = (r0 + ra) / g.NZ, za = (r0 + ra) - sa * g.NZ;
-    const float4 dgx = *reinterpret_cast<const float4 *>(g.dGx + x);
+    const int x4 = threadIdx.x;
+    const int sa = (t.r0 + t.ra) / g.NZ, za = (t.r0 + t.ra) - sa * g.NZ;
+    const float4 dgx = *reinterpret_cast<const float4 *>(g.dGx + 4 * x4);
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     for (int j = 0; j < a.nt; ++j) {
@@ -301,10 +383,6 @@ __global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo p
         float *A = tile[j & 1];
         float *B = tile[(j + 1) & 1];
         if (c == 0 && j == a.stall_step) return;   // test hook: leave the neighbours' waits unmet
-        if (j > 0) {
-            if (!wait_neighbours(pg, c, (unsigned)j, &abort_sh)) return;
-            load_halo(g, pg, A, c, nr, j & 1);
-        }
         // residual injection for this step: rin[slot] = inj_scale * r[n] per lane
         for (int q = s0 + tid; q < s1; q += nth) {
             const int grp = pg.slot_group[q];
@@ -323,67 +401,44 @@ __global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo p
         __syncthreads();
         const float4 *A4 = reinterpret_cast<const float4 *>(A);
         float4 *B4 = reinterpret_cast<float4 *>(B);
-        if (ra < rb) {
+        // phase 1: interior rows, no halo needed
+        if (t.ra < t.rb) {
             float4 w[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) w[k] = A4[(ra + k) * W4 + x4];
+            for (int k = 0; k < 9; ++k) w[k] = A4[(t.ra + k) * W4 + x4];
             int s = sa, z = za;
-            int active = n < g.nt[s];
-            long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
 #pragma unroll
             for (int q = 0; q < RBMAX; ++q) {
-                const int r = ra + q;
-                if (r >= rb) break;
-                const int ti = (r + 4) * W4 + x4;
-                float4 out = w[4];
-                if (active) {
-                    const float4 L = x4 > 0 ? A4[ti - 1] : zero;
-                    const float4 R = x4 + 1 < W4 ? A4[ti + 1] : zero;
-                    float4 Tz = (z >= 4 && z < g.NZ - 4) ? col_stencil<false>(g, w, L, R, z)
-                                                          : col_stencil<true>(g, w, L, R, z);
-                    const int sl = __ldg(pg.grp_slot + (long long)(r0 + r) * W4 + x4);
-                    if (sl >= 0) {
-                        const float4 inj = rin[sl - s0];
-                        Tz.x += inj.x; Tz.y += inj.y; Tz.z += inj.z; Tz.w += inj.w;
-                    }
-                    const long long zc = (long long)z * g.pitch + x;
-                    const float4 wh = __ldg(reinterpret_cast<const float4 *>(a.W + zc));
-                    const float4 wl = __ldg(reinterpret_cast<const float4 *>(a.W + g.field + zc));
-                    const float dz = g.dGz[z];
-                    const float4 dG = make_float4(dz + dgx.x - dz * dgx.x, dz + dgx.y - dz * dgx.y,
-                                                  dz + dgx.z - dz * dgx.z, dz + dgx.w - dz * dgx.w);
-                    const float4 zn = pleap(dG, w[4], B4[ti], Tz, wh, wl);
-                    const float4 Tu = __ldcs(reinterpret_cast<const float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell));
-                    float4 sc;
-                    if (a.born) {
-                        sc = make_float4(-g.tscale, -g.tscale, -g.tscale, -g.tscale);
-                    } else {
-                        sc = make_float4(g.iscale * wh.x, g.iscale * wh.y, g.iscale * wh.z, g.iscale * wh.w);
-                    }
-                    float4 *ip = reinterpret_cast<float4 *>(a.img + cell);
-                    float4 im = *ip;
-                    im.x = fmaf(sc.x * zn.x, Tu.x, im.x);
-                    im.y = fmaf(sc.y * zn.y, Tu.y, im.y);
-                    im.z = fmaf(sc.z * zn.z, Tu.z, im.z);
-                    im.w = fmaf(sc.w * zn.w, Tu.w, im.w);
-                    *ip = im;
-                    out = zn;
-                }
-                B4[ti] = out;
+                const int r = t.ra + q;
+                if (r >= t.rb) break;
+                adj_cell(g, pg, a, n, A4, B4, rin, s0, w, W4, x4, t.r0 + r, r, s, z, dgx);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) w[k] = w[k + 1];
-                if (r + 1 < rb) w[8] = A4[(r + 9) * W4 + x4];
-                cell += g.pitch;
+                if (r + 1 < t.rb) w[8] = A4[(r + 9) * W4 + x4];
                 if (++z == g.NZ) {
                     z = 0;
                     ++s;
-                    active = s < g.S && n < g.nt[s];
-                    cell = (long long)s * g.field + x;
                 }
             }
         }
+        // phase 2: neighbours' edge rows, then the strip's own edge rows
+        if (j > 0) {
+            if (!wait_neighbours(pg, c, (unsigned)j, &abort_sh)) return;
+            load_halo(g, pg, A, c, t.nr, j & 1);
+        }
         __syncthreads();
-        store_edges(g, pg, B, c, nr, (j + 1) & 1);
+        for (int i = tid; i < t.ne * W4; i += nth) {
+            const int e = i / W4, ex = i - e * W4;
+            const int r = edge_row(t, e);
+            const int gr = t.r0 + r, s = gr / g.NZ, z = gr - s * g.NZ;
+            float4 w[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) w[k] = A4[(r + k) * W4 + ex];
+            adj_cell(g, pg, a, n, A4, B4, rin, s0, w, W4, ex, gr, r, s, z,
+                     *reinterpret_cast<const float4 *>(g.dGx + 4 * ex));
+        }
+        __syncthreads();
+        store_edges(g, pg, B, c, t.nr, (j + 1) & 1);
         publish(pg, c, (unsigned)(j + 1));
     }
 }
