@@ -93,6 +93,9 @@ typedef struct {
                                     else k ~ sqrt(2 nt)); 1: force full history */
     int tile_z, tile_x;          /* 0: defaults / autotuned; else a supported tile */
     int engine;                  /* AAFWI_ENGINE_*: how FWI sweeps are launched */
+    int no_graphs;               /* 0: the per-step sweeps (one launch per time step) are
+                                    captured into CUDA graphs once per plan, sweep kind and
+                                    caller buffer, and replayed; 1: launched kernel by kernel */
 } aafwi_plan_opts;
 
 /* plan engines */
@@ -284,6 +287,34 @@ int aafwi_misfit_noalloc(const float *d_syn, const float *d_obs, long long n, fl
                          double *J_dev, double *J_host, aafwi_stream stream);
 
 /* ---- instrumentation ---------------------------------------------------- */
+
+/* ---- autotuner (launch configuration of the sweeps; the paper has no
+ * counterpart) ------------------------------------------------------------ */
+
+typedef struct {
+    int engine;      /* AAFWI_ENGINE_PER_STEP or AAFWI_ENGINE_PERSISTENT */
+    int tile_z;      /* per-step tile rows (16, 32 or 64); 0 for the persistent engine */
+    double ms;       /* median CUDA-event time of one forward sweep plus one FWI
+                        adjoint sweep reusing it, over the first `steps` steps */
+} aafwi_tune_entry;
+
+/* Time the launch configurations a plan of this geometry may use and return
+ * the fastest as plan options.  Candidates: the per-step engine with each tile
+ * height, and the persistent engine when a plan with these options keeps the
+ * full history and its strips fit on chip (base->engine, when not AUTO,
+ * restricts the candidates to that engine).  Each candidate is a temporary
+ * plan over the same shots with every record length cut to `steps` (the
+ * sweeps' time grows in proportion to the steps), timed `reps` times after one
+ * warm-up on the device model m [nz][nx] (FP32, m = 1/c^2) with zero observed
+ * data, on a stream of its own.
+ * base: options copied into *best (NULL = defaults), which gets the winner's
+ * engine and tile_z; table: the first table_cap candidates timed (may be NULL
+ * when table_cap is 0); *n_entries: number of candidates timed.
+ * Synchronises the device.  Errors: ARG, CFL, NAN (model), NOMEM, CUDA. */
+int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, const double *wavelet,
+                   const float *m, int steps, int reps, const aafwi_plan_opts *base,
+                   aafwi_tune_entry *table, int table_cap, int *n_entries,
+                   aafwi_plan_opts *best);
 
 /* Number of CUDA kernels this library has launched in this process (a host-
  * side counter incremented at every launch; memsets and copies excluded). */

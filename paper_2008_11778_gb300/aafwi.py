@@ -6,6 +6,8 @@ kernels.  There is no CPU fallback: if the library cannot be loaded the
 import of the symbols raises.
 """
 import ctypes
+import hashlib
+import json
 import os
 
 import numpy as np
@@ -27,7 +29,8 @@ EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aa
            "aafwi_aa_set_eta", "aafwi_aa_step", "aafwi_aa_combine", "aafwi_absmax",
            "aafwi_launch_count", "aafwi_misfit_noalloc", "aafwi_unet_create", "aafwi_unet_destroy",
            "aafwi_unet_param_count", "aafwi_unet_set_params", "aafwi_unet_get_params", "aafwi_unet_forward",
-           "aafwi_unet_loss_grad", "aafwi_unet_train_step", "aafwi_learned_features", "aafwi_learned_apply")
+           "aafwi_unet_loss_grad", "aafwi_unet_train_step", "aafwi_learned_features", "aafwi_learned_apply",
+           "aafwi_autotune")
 
 
 class AafwiError(RuntimeError):
@@ -53,7 +56,12 @@ ENGINE_AUTO, ENGINE_PER_STEP, ENGINE_PERSISTENT = 0, 1, 2
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("max_workspace_bytes", ctypes.c_size_t), ("checkpoint_every", ctypes.c_int),
-                ("tile_z", ctypes.c_int), ("tile_x", ctypes.c_int), ("engine", ctypes.c_int)]
+                ("tile_z", ctypes.c_int), ("tile_x", ctypes.c_int), ("engine", ctypes.c_int),
+                ("no_graphs", ctypes.c_int)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("engine", ctypes.c_int), ("tile_z", ctypes.c_int), ("ms", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -108,6 +116,7 @@ def load(path=LIB_PATH):
         "aafwi_unet_train_step": ([P, P, P, I, ctypes.c_float, P, P], I),
         "aafwi_learned_features": ([P, P, I, I, I, I, P, P, P], I),
         "aafwi_learned_apply": ([P, P, I, I, I, P, ctypes.c_float, ctypes.c_float, P, P], I),
+        "aafwi_autotune": ([P, P, P, P, I, I, P, P, I, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -145,23 +154,118 @@ def _f32(t):
     return _ptr(t)
 
 
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _geom_structs(geom, c_max):
+    """(Grid, Shots, arrays kept alive) of a geometry; the last kept array is
+    the FP64 wavelet."""
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    keep = [i32(geom.src_iz), i32(geom.src_ix), i32(geom.nt), i32(geom.rec_off),
+            i32(geom.rec_iz), i32(geom.rec_ix), np.ascontiguousarray(geom.wavelet, dtype=np.float64)]
+    g = Grid(int(geom.nx), int(geom.nz), int(geom.nb), float(geom.dx), float(geom.dz),
+             float(geom.dt), float(c_max))
+    s = Shots(len(keep[0]), *[_np_ptr(a) for a in keep[:6]])
+    return g, s, keep
+
+
+# ---- autotuner ---------------------------------------------------------------
+
+def tune_key(geom, c_max, device_name, sm_count, engine=ENGINE_AUTO, max_workspace_bytes=0):
+    """Cache key of a tuning: the device and everything the plan's launch
+    configuration depends on (grid, shots, receivers, record lengths)."""
+    h = hashlib.sha1()
+    for a in (geom.src_iz, geom.src_ix, geom.nt, geom.rec_off, geom.rec_iz, geom.rec_ix):
+        h.update(np.ascontiguousarray(a, dtype=np.int32).tobytes())
+    return "%s|sm%d|%dx%d|nb%d|S%d|nt%d|e%d|ws%d|%s" % (
+        device_name, int(sm_count), int(geom.nx), int(geom.nz), int(geom.nb), len(geom.src_iz),
+        int(np.max(geom.nt)), int(engine), int(max_workspace_bytes), h.hexdigest()[:16])
+
+
+def default_tune_cache():
+    return os.environ.get("AAFWI_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "aafwi", "tune.json"))
+
+
+def cache_lookup(path, key):
+    try:
+        with open(path) as f:
+            return json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+
+
+def cache_store(path, key, value):
+    """Add one entry (read-modify-write, replaced atomically)."""
+    data = {}
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        data = {}
+    data[key] = value
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = "%s.%d.tmp" % (path, os.getpid())
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def run_autotune(geom, c_max, m, steps=64, reps=3, engine=ENGINE_AUTO, max_workspace_bytes=0):
+    """aafwi_autotune: {"engine", "tile_z", "table": [(engine, tile_z, ms), ...]}."""
+    L = load()
+    g, s, keep = _geom_structs(geom, c_max)
+    base = PlanOpts(int(max_workspace_bytes), 0, 0, 0, int(engine), 0)
+    best = PlanOpts()
+    table = (TuneEntry * 8)()
+    n = ctypes.c_int()
+    _check(L.aafwi_autotune(ctypes.byref(g), ctypes.byref(s), _np_ptr(keep[6]), _f32(m), int(steps),
+                            int(reps), ctypes.byref(base), table, 8, ctypes.byref(n), ctypes.byref(best)))
+    return {"engine": int(best.engine), "tile_z": int(best.tile_z), "steps": int(steps),
+            "table": [(int(table[i].engine), int(table[i].tile_z), float(table[i].ms)) for i in range(n.value)]}
+
+
+def autotune(geom, c_max, m, steps=64, reps=3, engine=ENGINE_AUTO, max_workspace_bytes=0, cache_path=None,
+             tuner=None, device=None):
+    """Launch configuration for plans of this geometry on this device: from the
+    cache when present, else timed by the library (and stored)."""
+    if device is None:
+        import torch
+        prop = torch.cuda.get_device_properties(m.device)
+        device = (prop.name, prop.multi_processor_count)
+    path = cache_path or default_tune_cache()
+    key = tune_key(geom, c_max, device[0], device[1], engine, max_workspace_bytes)
+    hit = cache_lookup(path, key)
+    if hit is not None:
+        return dict(hit, cached=True)
+    tuner = tuner or run_autotune
+    res = json.loads(json.dumps(tuner(geom, c_max, m, steps=steps, reps=reps, engine=engine,
+                                      max_workspace_bytes=max_workspace_bytes)))   # as stored
+    cache_store(path, key, res)
+    return dict(res, cached=False)
+
+
 class Plan:
     """Owns an aafwi_plan: geometry, workspace and the wave-equation operators."""
 
-    def __init__(self, geom, c_max, max_workspace_bytes=0, checkpoint_every=0, engine=ENGINE_AUTO):
+    def __init__(self, geom, c_max, max_workspace_bytes=0, checkpoint_every=0, engine=ENGINE_AUTO,
+                 graphs=True, tile_z=0, tune_model=None, tune_cache=None):
+        """tune_model: a device model m [nz][nx]; when given, the engine and
+        tile height come from autotune() (cached in tune_cache, default
+        $AAFWI_TUNE_CACHE or ~/.cache/aafwi/tune.json)."""
         L = load()
         self.geom = geom
-        i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
-        self._keep = [i32(geom.src_iz), i32(geom.src_ix), i32(geom.nt), i32(geom.rec_off),
-                      i32(geom.rec_iz), i32(geom.rec_ix),
-                      np.ascontiguousarray(geom.wavelet, dtype=np.float64)]
-        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-        g = Grid(int(geom.nx), int(geom.nz), int(geom.nb), float(geom.dx), float(geom.dz),
-                 float(geom.dt), float(c_max))
-        s = Shots(len(self._keep[0]), *[ptr(a) for a in self._keep[:6]])
-        o = PlanOpts(int(max_workspace_bytes), int(checkpoint_every), 0, 0, int(engine))
+        if tune_model is not None:
+            t = autotune(geom, c_max, tune_model, engine=engine, max_workspace_bytes=max_workspace_bytes,
+                         cache_path=tune_cache)
+            engine, tile_z = t["engine"], t["tile_z"]
+            self.tuning = t
+        g, s, self._keep = _geom_structs(geom, c_max)
+        o = PlanOpts(int(max_workspace_bytes), int(checkpoint_every), int(tile_z), 0, int(engine),
+                     0 if graphs else 1)
         h = ctypes.c_void_p()
-        _check(L.aafwi_plan_create(ctypes.byref(g), ctypes.byref(s), ptr(self._keep[6]),
+        _check(L.aafwi_plan_create(ctypes.byref(g), ctypes.byref(s), _np_ptr(self._keep[6]),
                                    ctypes.byref(o), ctypes.byref(h)))
         self.h = h
         info = PlanInfo()

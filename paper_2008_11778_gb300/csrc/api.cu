@@ -63,6 +63,17 @@ struct aafwi_plan {
     PGeo pgeo{};
     size_t psmem = 0;
     int stall_step = -1;            // test hook (aafwi_plan_set_stall)
+    // CUDA graphs of the per-step sweeps (one launch per time step): each
+    // (sweep kind, caller buffer) is captured once and then replayed
+    bool graphs = true;
+    struct SweepGraph {
+        int kind;                   // SWEEP_*
+        const void *ptr;            // the caller buffer the sweep reads or writes
+        cudaGraphExec_t exec;
+        unsigned long long kernels; // kernel launches per replay
+    };
+    std::vector<SweepGraph> sweep_graphs;   // most recently used last
+    cudaStream_t cap = nullptr;     // capture stream
     std::string msg;
 };
 
@@ -116,6 +127,62 @@ bool upload(std::vector<Buf> &bufs, T **out, const std::vector<T> &h)
 
 float *slot(float *base, long long per_slot, long long i) { return base + per_slot * i; }
 
+enum { SWEEP_FWD = 0, SWEEP_BORN = 1, SWEEP_ADJ = 2, SWEEP_ADJ_BORN = 3 };
+constexpr size_t kMaxSweepGraphs = 8;
+
+void drop_graphs(aafwi_plan *p)
+{
+    for (auto &gr : p->sweep_graphs) cudaGraphExecDestroy(gr.exec);
+    p->sweep_graphs.clear();
+    if (p->cap) cudaStreamDestroy(p->cap);
+    p->cap = nullptr;
+}
+
+// Run body(stream) -- a sweep of per-step launches -- through the plan's
+// graph cache: capture it on the plan's capture stream the first time this
+// (kind, ptr) is seen, then replay the instantiated graph on st.
+template <class F>
+int run_graph(aafwi_plan *p, int kind, const void *ptr, cudaStream_t st, F body)
+{
+    auto &gs = p->sweep_graphs;
+    size_t i = 0;
+    while (i < gs.size() && !(gs[i].kind == kind && gs[i].ptr == ptr)) ++i;
+    if (i == gs.size()) {
+        if (!p->cap && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_fail(p, cudaGetLastError(), "capture stream");
+        unsigned long long kernels = 0;
+        cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(p, e, "begin capture");
+        g_capture_count = &kernels;
+        const int rc = body(p->cap);
+        g_capture_count = nullptr;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(p->cap, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(p, e, "end capture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(p, e, "graph instantiate");
+        if (gs.size() == kMaxSweepGraphs) {
+            cudaGraphExecDestroy(gs.front().exec);
+            gs.erase(gs.begin());
+        }
+        gs.push_back({kind, ptr, exec, kernels});
+        i = gs.size() - 1;
+    } else if (i + 1 != gs.size()) {
+        std::rotate(gs.begin() + i, gs.begin() + i + 1, gs.end());   // most recently used last
+        i = gs.size() - 1;
+    }
+    cudaError_t e = cudaGraphLaunch(gs[i].exec, st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "graph launch");
+    count_launch((unsigned)gs[i].kernels);
+    return AAFWI_OK;
+}
+
 int check_launch(aafwi_plan *p)
 {
     cudaError_t e = cudaGetLastError();
@@ -143,11 +210,9 @@ int run_persist_forward(aafwi_plan *p, float *traces, cudaStream_t st)
     return AAFWI_OK;
 }
 
-// Forward sweep over all shots (born: u and du together); traces -> dsyn.
-int run_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
+// Per-step forward sweep over all shots (born: u and du together).
+int sweep_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
 {
-    if (p->persist && !born) return run_persist_forward(p, traces, st);
-    p->hist_T = false;
     const long long ps = (long long)p->S * p->field;
     if (!p->full && cudaMemsetAsync(p->fbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
@@ -181,20 +246,23 @@ int run_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
     return check_launch(p);
 }
 
-// Adjoint sweep with imaging into p->img (born: scale -1, else -1/m).
-int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
+// Forward sweep over all shots (born: u and du together); traces -> CSR.
+int run_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
+{
+    if (p->persist && !born) return run_persist_forward(p, traces, st);
+    p->hist_T = false;
+    if (!p->graphs) return sweep_forward(p, born, traces, st);
+    return run_graph(p, born ? SWEEP_BORN : SWEEP_FWD, traces, st,
+                     [&](cudaStream_t cs) { return sweep_forward(p, born, traces, cs); });
+}
+
+// Per-step adjoint sweep with imaging into p->img (checkpoint mode: segment
+// replays from the stored checkpoints in between).
+int sweep_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
 {
     const long long ps = (long long)p->S * p->field;
     if (cudaMemsetAsync(p->img, 0, ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
-    if (p->hist_T) {
-        cudaError_t e = cudaMemsetAsync(p->pgeo.flags, 0, p->pgeo.P * sizeof(unsigned), st);
-        if (e != cudaSuccess) return cuda_fail(p, e, "memset");
-        PAdjArgs a{p->W, p->hist, resid, p->img, p->nt_max, born ? 1 : 0, p->stall_step};
-        e = launch_adj_persist(p->geo, p->pgeo, a, p->psmem, st);
-        if (e != cudaSuccess) return cuda_fail(p, e, "persistent adjoint launch");
-        return AAFWI_OK;
-    }
     if (cudaMemsetAsync(p->zbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
     auto adj = [&](int n, const float *u) {
@@ -216,6 +284,25 @@ int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
         }
     }
     return check_launch(p);
+}
+
+// Adjoint sweep with imaging into p->img (born: scale -1, else -1/m).
+int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
+{
+    if (p->hist_T) {
+        const long long ps = (long long)p->S * p->field;
+        if (cudaMemsetAsync(p->img, 0, ps * sizeof(float), st) != cudaSuccess)
+            return cuda_fail(p, cudaGetLastError(), "memset");
+        cudaError_t e = cudaMemsetAsync(p->pgeo.flags, 0, p->pgeo.P * sizeof(unsigned), st);
+        if (e != cudaSuccess) return cuda_fail(p, e, "memset");
+        PAdjArgs a{p->W, p->hist, resid, p->img, p->nt_max, born ? 1 : 0, p->stall_step};
+        e = launch_adj_persist(p->geo, p->pgeo, a, p->psmem, st);
+        if (e != cudaSuccess) return cuda_fail(p, e, "persistent adjoint launch");
+        return AAFWI_OK;
+    }
+    if (!p->graphs) return sweep_adjoint(p, born, resid, st);
+    return run_graph(p, born ? SWEEP_ADJ_BORN : SWEEP_ADJ, resid, st,
+                     [&](cudaStream_t cs) { return sweep_adjoint(p, born, resid, cs); });
 }
 
 int prep(aafwi_plan *p, const float *m, const float *rho, cudaStream_t st)
@@ -330,6 +417,7 @@ int setup_persist(aafwi_plan *p, int engine, const aafwi_shots *sh, std::string 
     pg.P = P;
     pg.rows_max = rows_max;
     pg.ty = ty;
+    pg.slots_max = slots_max;
     pg.slot = (long long)p->S * p->field;
     pg.row0 = d_row0; pg.grp_slot = d_gs; pg.slot_off = d_so; pg.slot_group = d_sg; pg.slot_cols = d_sc;
     pg.err = p->err;
@@ -341,6 +429,25 @@ int setup_persist(aafwi_plan *p, int engine, const aafwi_shots *sh, std::string 
 }  // namespace
 
 void aafwi::set_call_error(const std::string &msg) { g_create_error = msg; }
+
+// Workspace of a plan: buffers every plan holds, the full-history size, the
+// budget, and whether the full history is kept (else checkpoints).
+WorkspacePlan aafwi::workspace_plan(long long field, int S, int nt_max, long long trace_count,
+                                    const aafwi_plan_opts &o)
+{
+    WorkspacePlan w;
+    const size_t F = (size_t)field * sizeof(float), SF = F * S;
+    w.fixed = 3 * F + (2 + 2 + 1) * SF + 2 * (size_t)trace_count * sizeof(float) + (1 << 20);
+    w.budget = o.max_workspace_bytes;
+    if (w.budget == 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        w.budget = (size_t)(0.85 * (double)fr);
+    }
+    w.full_bytes = w.fixed + (size_t)(nt_max + 1) * SF;
+    w.full = o.checkpoint_every == 1 || (o.checkpoint_every == 0 && w.full_bytes <= w.budget);
+    return w;
+}
 
 extern "C" {
 
@@ -371,6 +478,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     }
     auto *p = new aafwi_plan();
     cudaGetDevice(&p->device);
+    p->graphs = o.no_graphs == 0;
     p->nx = g->nx; p->nz = g->nz; p->nb = g->nb;
     p->dx = g->dx; p->dz = g->dz; p->dt = g->dt;
     p->NZ = g->nz + 2 * g->nb;
@@ -390,6 +498,15 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
         return fail(nullptr, AAFWI_ERR_ARG, "rec_off[0] must be 0");
     }
     // tiles
+    if (o.tile_z != 0 && !tile_z_supported(o.tile_z)) {
+        delete p;
+        return fail(nullptr, AAFWI_ERR_ARG, "tile_z must be 0 (default), 16, 32 or 64");
+    }
+    if (o.tile_x != 0 && o.tile_x != TX) {
+        delete p;
+        return fail(nullptr, AAFWI_ERR_ARG, "tile_x must be 0 (default) or 128");
+    }
+    const int TZ = o.tile_z ? o.tile_z : TZ_DEFAULT;
     const int ntz = (p->NZ + TZ - 1) / TZ, ntx = (p->pitch + TX - 1) / TX, ntiles = ntz * ntx;
     // sources, receivers, per-tile receiver lists, trace offsets
     std::vector<int> src_pt(S), nrec(S);
@@ -444,17 +561,11 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     const double t5040 = 5040.0 * g->dx * g->dx;
     for (int n = 0; n < p->nt_max; ++n) ws[n] = (float)(t5040 * wavelet[n] / (g->dx * g->dz));
     // workspace plan
-    const size_t F = (size_t)p->field * sizeof(float), SF = F * S;
-    const size_t fixed = 3 * F + (2 + 2 + 1) * SF + 2 * (size_t)p->trace_count * sizeof(float) + (1 << 20);
-    size_t budget = o.max_workspace_bytes;
-    if (budget == 0) {
-        size_t fr = 0, tot = 0;
-        cudaMemGetInfo(&fr, &tot);
-        budget = (size_t)(0.85 * (double)fr);
-    }
-    const size_t full_bytes = fixed + (size_t)(p->nt_max + 1) * SF;
+    const WorkspacePlan wp = workspace_plan(p->field, S, p->nt_max, p->trace_count, o);
+    const size_t SF = (size_t)p->field * sizeof(float) * S;
+    const size_t fixed = wp.fixed, budget = wp.budget, full_bytes = wp.full_bytes;
     int k = o.checkpoint_every;
-    if (k == 1 || (k == 0 && full_bytes <= budget)) {
+    if (wp.full) {
         p->full = true;
         p->k = 1;
         p->ws_bytes = full_bytes;
@@ -510,7 +621,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     }
     Geo &G = p->geo;
     G.NZ = p->NZ; G.NX = p->NX; G.pitch = p->pitch; G.nb = p->nb; G.S = S;
-    G.ntz = ntz; G.ntx = ntx; G.ntiles = ntiles; G.field = p->field;
+    G.tz = TZ; G.ntz = ntz; G.ntx = ntx; G.ntiles = ntiles; G.field = p->field;
     G.rz = (float)((g->dx * g->dx) / (g->dz * g->dz));
     p->K = g->dt * g->dt / t5040;
     G.iscale = (float)(-1.0 / (g->dt * g->dt));
@@ -534,6 +645,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
 void aafwi_plan_destroy(aafwi_plan *p)
 {
     if (!p) return;
+    drop_graphs(p);
     free_bufs(p->bufs);
     delete p;
 }
@@ -555,7 +667,7 @@ int aafwi_plan_get_info(const aafwi_plan *p, aafwi_plan_info *info)
     info->checkpoint_every = p->k;
     info->n_checkpoints = p->nck;
     info->workspace_bytes = p->ws_bytes;
-    info->tile_z = TZ; info->tile_x = TX;
+    info->tile_z = p->geo.tz; info->tile_x = TX;
     info->n_tiles = p->geo.ntiles;
     info->engine = p->persist ? AAFWI_ENGINE_PERSISTENT : AAFWI_ENGINE_PER_STEP;
     info->persist_ctas = p->persist ? p->pgeo.P : 0;

@@ -1,0 +1,140 @@
+// autotune.cu -- choice of the sweeps' launch configuration (engine, tile
+// height of the per-step kernels) by timing short sweeps of temporary plans
+// of the same geometry.  Host code over the public entry points only.
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace aafwi;
+
+namespace {
+
+struct Candidate {
+    int engine, tile_z;
+};
+
+struct Scratch {
+    float *d_obs = nullptr, *grad = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Scratch()
+    {
+        if (d_obs) cudaFree(d_obs);
+        if (grad) cudaFree(grad);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st) cudaStreamDestroy(st);
+    }
+};
+
+int tune_fail(int code, const char *msg)
+{
+    set_call_error(msg);
+    return code;
+}
+
+// Median time of `reps` (forward sweep + adjoint sweep reusing it) on plan p.
+int time_plan(aafwi_plan *p, const float *m, Scratch &sc, int reps, double *ms)
+{
+    double J = 0.0;
+    int rc = aafwi_adjoint_gradient(p, AAFWI_MODE_FWI, m, nullptr, sc.d_obs, sc.grad, &J, 0, sc.st);   // warm-up
+    if (rc) return rc;
+    std::vector<double> t;
+    for (int r = 0; r < reps; ++r) {
+        if (cudaEventRecord(sc.e0, sc.st) != cudaSuccess) return AAFWI_ERR_CUDA;
+        if ((rc = aafwi_model_forward(p, m, nullptr, sc.st))) return rc;
+        if ((rc = aafwi_adjoint_gradient(p, AAFWI_MODE_FWI, m, nullptr, sc.d_obs, sc.grad, nullptr,
+                                         AAFWI_REUSE_FORWARD, sc.st)))
+            return rc;
+        if (cudaEventRecord(sc.e1, sc.st) != cudaSuccess || cudaEventSynchronize(sc.e1) != cudaSuccess)
+            return AAFWI_ERR_CUDA;
+        float f = 0.f;
+        cudaEventElapsedTime(&f, sc.e0, sc.e1);
+        t.push_back(f);
+    }
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return aafwi_read_misfit(p, &J, sc.st);   // surfaces a NaN / CFL flag raised by the runs
+}
+
+}  // namespace
+
+extern "C" int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, const double *wavelet,
+                              const float *m, int steps, int reps, const aafwi_plan_opts *base,
+                              aafwi_tune_entry *table, int table_cap, int *n_entries, aafwi_plan_opts *best)
+{
+    if (!grid || !shots || !wavelet || !m || !best || steps < 1 || reps < 1 || table_cap < 0 ||
+        (table_cap > 0 && !table) || !shots->nt || shots->S < 1 || !shots->rec_off)
+        return tune_fail(AAFWI_ERR_ARG, "autotune: invalid argument");
+    aafwi_plan_opts o{};
+    if (base) o = *base;
+    const int S = shots->S;
+    // would a plan of the full record keep the full history?
+    const int NZ = grid->nz + 2 * grid->nb, pitch = (grid->nx + 2 * grid->nb + 31) / 32 * 32;
+    int nt_max = 0;
+    long long traces = 0;
+    std::vector<int> nt(shots->nt, shots->nt + S);
+    for (int s = 0; s < S; ++s) {
+        nt_max = std::max(nt_max, nt[s]);
+        traces += (long long)nt[s] * (shots->rec_off[s + 1] - shots->rec_off[s]);
+        nt[s] = std::min(nt[s], steps);
+    }
+    const bool full = workspace_plan((long long)NZ * pitch, S, nt_max, traces, o).full;
+    std::vector<Candidate> cands;
+    if (o.engine != AAFWI_ENGINE_PERSISTENT)
+        for (int tz : {16, 32, 64}) cands.push_back({AAFWI_ENGINE_PER_STEP, tz});
+    if (o.engine != AAFWI_ENGINE_PER_STEP && full) cands.push_back({AAFWI_ENGINE_PERSISTENT, 0});
+    if (cands.empty()) return tune_fail(AAFWI_ERR_ARG, "autotune: the persistent engine needs the full history");
+    aafwi_shots sh = *shots;
+    sh.nt = nt.data();
+    Scratch sc;
+    if (cudaStreamCreateWithFlags(&sc.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&sc.e0) != cudaSuccess || cudaEventCreate(&sc.e1) != cudaSuccess)
+        return tune_fail(AAFWI_ERR_CUDA, "autotune: stream / events");
+    int ntimed = 0;
+    double best_ms = -1.0;
+    Candidate win{};
+    for (const Candidate &c : cands) {
+        aafwi_plan_opts co = o;
+        co.engine = c.engine;
+        co.tile_z = c.tile_z;
+        co.checkpoint_every = 1;
+        aafwi_plan *p = nullptr;
+        int rc = aafwi_plan_create(grid, &sh, wavelet, &co, &p);
+        if (rc == AAFWI_ERR_ARG && c.engine == AAFWI_ENGINE_PERSISTENT) continue;   // strips do not qualify
+        if (rc) return rc;
+        aafwi_plan_info info{};
+        aafwi_plan_get_info(p, &info);
+        if (!sc.d_obs) {
+            const size_t nt_bytes = std::max<long long>(info.trace_count, 1) * sizeof(float);
+            if (cudaMalloc(&sc.d_obs, nt_bytes) != cudaSuccess ||
+                cudaMalloc(&sc.grad, (size_t)grid->nz * grid->nx * sizeof(float)) != cudaSuccess ||
+                cudaMemset(sc.d_obs, 0, nt_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                aafwi_plan_destroy(p);
+                return tune_fail(AAFWI_ERR_NOMEM, "autotune: scratch buffers");
+            }
+        }
+        double ms = 0.0;
+        rc = time_plan(p, m, sc, reps, &ms);
+        if (rc) {
+            set_call_error(aafwi_last_error(p));
+            aafwi_plan_destroy(p);
+            return rc;
+        }
+        aafwi_plan_destroy(p);
+        if (ntimed < table_cap) table[ntimed] = {c.engine, c.tile_z, ms};
+        ++ntimed;
+        if (best_ms < 0 || ms < best_ms) {
+            best_ms = ms;
+            win = c;
+        }
+    }
+    if (n_entries) *n_entries = ntimed;
+    if (ntimed == 0) return tune_fail(AAFWI_ERR_ARG, "autotune: no configuration qualifies");
+    *best = o;
+    best->engine = win.engine;
+    best->tile_z = win.tile_z;
+    return AAFWI_OK;
+}

@@ -7,23 +7,27 @@
 #include <cstdint>
 #include <string>
 
+#include "../../include/aafwi.h"
+
 namespace aafwi {
 
-// Tile of one CTA: TZ rows x TX columns of one shot, 256 threads laid out
-// 32 (x) x 8 (z); a thread owns 4 consecutive columns (one float4) on TZ/8
-// rows.  HALO = stencil radius of the 8th-order Laplacian.
+// Tile of one CTA of the per-step kernels: tz rows x TX columns of one shot,
+// 256 threads laid out 32 (x) x 8 (z); a thread owns 4 consecutive columns
+// (one float4) on tz/8 rows.  tz is a plan parameter (16, 32 or 64; the
+// kernels are instantiated for each).  HALO = stencil radius of the
+// 8th-order Laplacian.
 constexpr int HALO = 4;
 constexpr int TX = 128;
-constexpr int TZ = 32;
+constexpr int TZ_DEFAULT = 32;
 constexpr int BX = 32;
 constexpr int BY = 8;
-constexpr int RZ = TZ / BY;
 constexpr int SW = TX + 2 * HALO;      // shared tile row length (floats)
-constexpr int SH = TZ + 2 * HALO;      // shared tile rows
+inline bool tile_z_supported(int tz) { return tz == 16 || tz == 32 || tz == 64; }
 
 // Per-plan geometry, all pointers device.
 struct Geo {
     int NZ, NX, pitch, nb, S;
+    int tz;                        // tile rows of the per-step kernels
     int ntz, ntx, ntiles;          // tiles per shot along z, x; total
     long long field;               // floats per shot field (NZ * pitch)
     // The Laplacian is evaluated as T = rz*S_z + S_x with integer weights
@@ -84,10 +88,25 @@ struct AdjArgs {
 
 // Number of kernels this library has launched (host-side count).
 extern std::atomic<unsigned long long> g_launch_count;
-inline void count_launch(unsigned n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
+// While a sweep is being captured into a CUDA graph its launches are counted
+// here instead (the graph adds them to g_launch_count each time it runs).
+extern thread_local unsigned long long *g_capture_count;
+inline void count_launch(unsigned n = 1)
+{
+    if (g_capture_count) *g_capture_count += n;
+    else g_launch_count.fetch_add(n, std::memory_order_relaxed);
+}
 
 // Message returned by aafwi_last_error(NULL) for calls made without a plan.
 void set_call_error(const std::string &msg);
+
+// Workspace of a plan (api.cu): what every plan holds, the full-history size,
+// the budget (opts or 85 % of free memory) and whether the full history fits.
+struct WorkspacePlan {
+    size_t fixed, full_bytes, budget;
+    bool full;
+};
+WorkspacePlan workspace_plan(long long field, int S, int nt_max, long long trace_count, const aafwi_plan_opts &o);
 
 cudaError_t init_kernels();  // per-device kernel attributes (dynamic shared memory)
 void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float mcfl,
@@ -101,12 +120,13 @@ void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *row
 // Persistent sweeps (persist_kernels.cu): one cooperative launch per sweep,
 // one CTA per strip of rows, (pitch/4) x ty threads (at most PT): thread
 // (x, y) owns float4 column x of the y-th block of the strip's rows.
-constexpr int PT = 512;
+constexpr int PT = 448;            // 14 warps: up to 144 registers a thread
 constexpr int RBMAX = 12;          // rows per thread (the row loop is unrolled)
 struct PGeo {
     int P;                         // strips (CTAs)
     int rows_max;                  // max rows of a strip
     int ty;                        // thread rows per CTA
+    int slots_max;                 // max receiver slots of a strip
     long long slot;                // floats per history slot (S * field)
     const int *row0;               // [P+1] strip row ranges in global rows (shot * NZ + z)
     const int *grp_slot;           // [S*NZ*pitch/4] receiver slot of a float4 group, or -1

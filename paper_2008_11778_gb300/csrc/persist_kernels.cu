@@ -152,14 +152,6 @@ __device__ __forceinline__ float4 pleap(float4 dG, float4 cur, float4 prev, floa
                        pstep1(dG.z, cur.z, prev.z, T.z, wh.z, wl.z), pstep1(dG.w, cur.w, prev.w, T.w, wh.w, wl.w));
 }
 
-__device__ __forceinline__ float4 psponge(const Geo &g, int z, int x)
-{
-    const float dz = g.dGz[z];
-    const float4 dx = *reinterpret_cast<const float4 *>(g.dGx + x);
-    return make_float4(dz + dx.x - dz * dx.x, dz + dx.y - dz * dx.y, dz + dx.z - dz * dx.z,
-                       dz + dx.w - dz * dx.w);
-}
-
 __device__ __forceinline__ void padd_source(float4 &q, int src, int pt, float w)
 {
     const int d = src - pt;
@@ -172,7 +164,8 @@ __device__ __forceinline__ void padd_source(float4 &q, int src, int pt, float w)
 }
 
 // Shared layout: two tiles of (rows_max + 8) x pitch floats, then
-// rin[slots_max] float4 (adjoint residual injection).  At step n tile n&1
+// rin[2][slots_max] float4 (adjoint residual injection, double-buffered by
+// step parity), then SlotInfo[slots_max].  At step n tile n&1
 // holds level n (own rows + the 4 halo rows above and below, refreshed from
 // the neighbours) and the other tile holds level n-1 in its own rows, which
 // each thread overwrites in place with level n+1 (it reads and writes only
@@ -188,6 +181,48 @@ __device__ __forceinline__ void padd_source(float4 &q, int src, int pt, float w)
 struct Strip {
     int r0, nr, W4, ra, rb, ne;
 };
+
+// Receiver slot of a strip, resolved once per launch into shared memory so
+// that the per-step gather / injection needs no chain of dependent global
+// loads: lanes' receiver columns, the shot's trace base and receiver count,
+// its record length, and the float4 group's index in the tile.
+struct SlotInfo {
+    int4 cols;
+    long long tb;                 // trace offset of the shot's sample 0
+    int nrec, nts, ti, pad;
+};
+
+__device__ void load_slots(const Geo &g, const PGeo &pg, const Strip &t, int s0, int s1, SlotInfo *si)
+{
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    for (int q = s0 + tid; q < s1; q += nth) {
+        const int grp = pg.slot_group[q];                 // global group index
+        const int gr = grp / t.W4, gx = grp - gr * t.W4;
+        const int s = gr / g.NZ;
+        SlotInfo v;
+        v.cols = pg.slot_cols[q];
+        v.tb = g.tr_off[s];
+        v.nrec = g.nrec[s];
+        v.nts = g.nt[s];
+        v.ti = (gr - t.r0 + 4) * t.W4 + gx;
+        v.pad = 0;
+        si[q - s0] = v;
+    }
+}
+
+// inj_scale * r[n] at the four lanes of a slot (zero outside its shot's record).
+__device__ __forceinline__ float4 slot_resid(const Geo &g, const float *resid, const SlotInfo &v, int n)
+{
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (n >= 0 && n < v.nts) {
+        const float *rp = resid + v.tb + (long long)n * v.nrec;
+        if (v.cols.x >= 0) r.x = g.inj_scale * __ldcs(rp + v.cols.x);
+        if (v.cols.y >= 0) r.y = g.inj_scale * __ldcs(rp + v.cols.y);
+        if (v.cols.z >= 0) r.z = g.inj_scale * __ldcs(rp + v.cols.z);
+        if (v.cols.w >= 0) r.w = g.inj_scale * __ldcs(rp + v.cols.w);
+    }
+    return r;
+}
 
 __device__ __forceinline__ Strip strip_of(const Geo &g, const PGeo &pg, int c)
 {
@@ -205,74 +240,102 @@ __device__ __forceinline__ Strip strip_of(const Geo &g, const PGeo &pg, int c)
 
 __device__ __forceinline__ int edge_row(const Strip &t, int e) { return (t.nr < 8 || e < 4) ? e : t.nr - 8 + e; }
 
-__device__ __forceinline__ float4 sponge_at(const Geo &g, int z, float4 dgx)
+// Per-row model data of a float4 group: W = Wh + Wl and the sponge row factor.
+struct RowW {
+    float4 wh, wl;
+    float dz;
+};
+
+__device__ __forceinline__ RowW load_roww(const Geo &g, const float *W, int z, int x)
 {
-    const float dz = g.dGz[z];
+    const long long zc = (long long)z * g.pitch + x;
+    RowW q;
+    q.wh = __ldg(reinterpret_cast<const float4 *>(W + zc));
+    q.wl = __ldg(reinterpret_cast<const float4 *>(W + g.field + zc));
+    q.dz = __ldg(g.dGz + z);
+    return q;
+}
+
+__device__ __forceinline__ float4 sponge_of(float dz, float4 dgx)
+{
     return make_float4(dz + dgx.x - dz * dgx.x, dz + dgx.y - dz * dgx.y, dz + dgx.z - dz * dgx.z,
                        dz + dgx.w - dz * dgx.w);
+}
+
+// L2 prefetch of `bytes` (a multiple of 16, 16-byte aligned) starting at p.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // Forward update of float4 group (tile row r + 4, column x4) of shot s, depth z.
 __device__ __forceinline__ void fwd_cell(const Geo &g, const PGeo &pg, const PFwdArgs &a, int n, const float4 *A4,
                                          float4 *B4, const float4 (&w)[9], int W4, int x4, int r, int s, int z,
-                                         float wsn, float4 dgx)
+                                         float wsn, float4 dgx, int nts, int srcpt, const RowW &q)
 {
     const int ti = (r + 4) * W4 + x4;
     float4 out = w[4];
-    if (n < g.nt[s]) {
+    if (n < nts) {
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         const int x = 4 * x4;
         const float4 L = x4 > 0 ? A4[ti - 1] : zero;
         const float4 R = x4 + 1 < W4 ? A4[ti + 1] : zero;
         float4 T = (z >= 4 && z < g.NZ - 4) ? col_stencil<false>(g, w, L, R, z) : col_stencil<true>(g, w, L, R, z);
-        padd_source(T, g.src_pt[s], z * g.pitch + x, wsn);
-        const long long zc = (long long)z * g.pitch + x;
-        const long long cell = (long long)s * g.field + zc;
+        padd_source(T, srcpt, z * g.pitch + x, wsn);
+        const long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
         __stcs(reinterpret_cast<float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell), T);
-        const float4 wh = __ldg(reinterpret_cast<const float4 *>(a.W + zc));
-        const float4 wl = __ldg(reinterpret_cast<const float4 *>(a.W + g.field + zc));
-        out = pleap(sponge_at(g, z, dgx), w[4], B4[ti], T, wh, wl);
+        out = pleap(sponge_of(q.dz, dgx), w[4], B4[ti], T, q.wh, q.wl);
     }
     B4[ti] = out;
 }
 
 // Adjoint update and imaging of float4 group (tile row r + 4, column x4).
+// Image accumulation (imode): 0 none this step; 1 z^n T^n; 2 first the
+// previous step's z^{n+1} T^{n+1} (z^{n+1} is the centre w[4] of the register
+// column), then z^n T^n.  Pairs halve the image read-modify-write traffic
+// while every cell receives the same sequence of fused multiply-adds.
 __device__ __forceinline__ void adj_cell(const Geo &g, const PGeo &pg, const PAdjArgs &a, int n, const float4 *A4,
                                          float4 *B4, const float4 *rin, int s0, const float4 (&w)[9], int W4, int x4,
-                                         int gr, int r, int s, int z, float4 dgx)
+                                         int r, int s, int z, float4 dgx, int nts, const RowW &q, int imode,
+                                         float4 Tu, float4 Tu1, int sl)
 {
     const int ti = (r + 4) * W4 + x4;
     float4 out = w[4];
-    if (n < g.nt[s]) {
+    if (n < nts) {
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         const int x = 4 * x4;
         const float4 L = x4 > 0 ? A4[ti - 1] : zero;
         const float4 R = x4 + 1 < W4 ? A4[ti + 1] : zero;
         float4 Tz = (z >= 4 && z < g.NZ - 4) ? col_stencil<false>(g, w, L, R, z) : col_stencil<true>(g, w, L, R, z);
-        const int sl = __ldg(pg.grp_slot + (long long)gr * W4 + x4);
         if (sl >= 0) {
             const float4 inj = rin[sl - s0];
             Tz.x += inj.x; Tz.y += inj.y; Tz.z += inj.z; Tz.w += inj.w;
         }
-        const long long zc = (long long)z * g.pitch + x;
-        const long long cell = (long long)s * g.field + zc;
-        const float4 wh = __ldg(reinterpret_cast<const float4 *>(a.W + zc));
-        const float4 wl = __ldg(reinterpret_cast<const float4 *>(a.W + g.field + zc));
-        const float4 zn = pleap(sponge_at(g, z, dgx), w[4], B4[ti], Tz, wh, wl);
-        const float4 Tu = __ldcs(reinterpret_cast<const float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell));
+        const long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
+        const float4 wh = q.wh;
+        const float4 zn = pleap(sponge_of(q.dz, dgx), w[4], B4[ti], Tz, q.wh, q.wl);
         float4 sc;
         if (a.born) {
             sc = make_float4(-g.tscale, -g.tscale, -g.tscale, -g.tscale);
         } else {
             sc = make_float4(g.iscale * wh.x, g.iscale * wh.y, g.iscale * wh.z, g.iscale * wh.w);
         }
-        float4 *ip = reinterpret_cast<float4 *>(a.img + cell);
-        float4 im = *ip;
-        im.x = fmaf(sc.x * zn.x, Tu.x, im.x);
-        im.y = fmaf(sc.y * zn.y, Tu.y, im.y);
-        im.z = fmaf(sc.z * zn.z, Tu.z, im.z);
-        im.w = fmaf(sc.w * zn.w, Tu.w, im.w);
-        *ip = im;
+        if (imode != 0) {
+            float4 *ip = reinterpret_cast<float4 *>(a.img + cell);
+            float4 im = *ip;
+            if (imode == 2 && n + 1 < nts) {
+                const float4 z1 = w[4];
+                im.x = fmaf(sc.x * z1.x, Tu1.x, im.x);
+                im.y = fmaf(sc.y * z1.y, Tu1.y, im.y);
+                im.z = fmaf(sc.z * z1.z, Tu1.z, im.z);
+                im.w = fmaf(sc.w * z1.w, Tu1.w, im.w);
+            }
+            im.x = fmaf(sc.x * zn.x, Tu.x, im.x);
+            im.y = fmaf(sc.y * zn.y, Tu.y, im.y);
+            im.z = fmaf(sc.z * zn.z, Tu.z, im.z);
+            im.w = fmaf(sc.w * zn.w, Tu.w, im.w);
+            *ip = im;
+        }
         out = zn;
     }
     B4[ti] = out;
@@ -288,8 +351,11 @@ __global__ void __launch_bounds__(PT, 1) k_fwd_persist(const Geo g, const PGeo p
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     const long long tsz = (long long)(pg.rows_max + 8) * g.pitch;
     float *tile[2] = {psm, psm + tsz};
+    const int s0 = pg.slot_off[c], s1 = pg.slot_off[c + 1];
+    SlotInfo *si = reinterpret_cast<SlotInfo *>(psm + 2 * tsz + 8LL * pg.slots_max);
     for (int i = tid; i < 2 * (pg.rows_max + 8) * W4; i += nth)
         reinterpret_cast<float4 *>(psm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    load_slots(g, pg, t, s0, s1, si);
     const int x4 = threadIdx.x;
     const int sa = (t.r0 + t.ra) / g.NZ, za = (t.r0 + t.ra) - sa * g.NZ;
     const float4 dgx = *reinterpret_cast<const float4 *>(g.dGx + 4 * x4);
@@ -307,17 +373,26 @@ __global__ void __launch_bounds__(PT, 1) k_fwd_persist(const Geo g, const PGeo p
 #pragma unroll
             for (int k = 0; k < 9; ++k) w[k] = A4[(t.ra + k) * W4 + x4];
             int s = sa, z = za;
+            int nts = g.nt[s], srcpt = g.src_pt[s];
+            RowW cur = load_roww(g, a.W, z, 4 * x4);
 #pragma unroll
             for (int q = 0; q < RBMAX; ++q) {
                 const int r = t.ra + q;
                 if (r >= t.rb) break;
-                fwd_cell(g, pg, a, n, A4, B4, w, W4, x4, r, s, z, wsn, dgx);
+                // the next row's model data is loaded one row ahead
+                const int zn = z + 1 == g.NZ ? 0 : z + 1;
+                RowW nxt;
+                if (r + 1 < t.rb) nxt = load_roww(g, a.W, zn, 4 * x4);
+                fwd_cell(g, pg, a, n, A4, B4, w, W4, x4, r, s, z, wsn, dgx, nts, srcpt, cur);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) w[k] = w[k + 1];
                 if (r + 1 < t.rb) w[8] = A4[(r + 9) * W4 + x4];
-                if (++z == g.NZ) {
-                    z = 0;
+                cur = nxt;
+                z = zn;
+                if (zn == 0 && r + 1 < t.rb) {
                     ++s;
+                    nts = g.nt[s];
+                    srcpt = g.src_pt[s];
                 }
             }
         }
@@ -334,25 +409,22 @@ __global__ void __launch_bounds__(PT, 1) k_fwd_persist(const Geo g, const PGeo p
             float4 w[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) w[k] = A4[(r + k) * W4 + ex];
-            fwd_cell(g, pg, a, n, A4, B4, w, W4, ex, r, s, z, wsn, *reinterpret_cast<const float4 *>(g.dGx + 4 * ex));
+            fwd_cell(g, pg, a, n, A4, B4, w, W4, ex, r, s, z, wsn, *reinterpret_cast<const float4 *>(g.dGx + 4 * ex),
+                     g.nt[s], g.src_pt[s], load_roww(g, a.W, z, 4 * ex));
         }
         __syncthreads();
         store_edges(g, pg, B, c, t.nr, (n + 1) & 1);
         if (a.traces) {
             // receiver gather: sample n = u^{n+1}
-            const int s0 = pg.slot_off[c], s1 = pg.slot_off[c + 1];
-            for (int j = s0 + tid; j < s1; j += nth) {
-                const int grp = pg.slot_group[j];           // global group index
-                const int gr = grp / W4, gx = grp - gr * W4;
-                const int s = gr / g.NZ;
-                if (n >= g.nt[s]) continue;
-                const float4 v = reinterpret_cast<const float4 *>(B + (long long)(gr - t.r0 + 4) * g.pitch)[gx];
-                const int4 cols = pg.slot_cols[j];
-                const long long tb = g.tr_off[s] + (long long)n * g.nrec[s];
-                if (cols.x >= 0) a.traces[tb + cols.x] = v.x;
-                if (cols.y >= 0) a.traces[tb + cols.y] = v.y;
-                if (cols.z >= 0) a.traces[tb + cols.z] = v.z;
-                if (cols.w >= 0) a.traces[tb + cols.w] = v.w;
+            for (int j = tid; j < s1 - s0; j += nth) {
+                const SlotInfo v = si[j];
+                if (n >= v.nts) continue;
+                const float4 u = B4[v.ti];
+                float *tp = a.traces + v.tb + (long long)n * v.nrec;
+                if (v.cols.x >= 0) tp[v.cols.x] = u.x;
+                if (v.cols.y >= 0) tp[v.cols.y] = u.y;
+                if (v.cols.z >= 0) tp[v.cols.z] = u.z;
+                if (v.cols.w >= 0) tp[v.cols.w] = u.w;
             }
         }
         publish(pg, c, (unsigned)(n + 1));
@@ -369,10 +441,15 @@ __global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo p
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     const long long tsz = (long long)(pg.rows_max + 8) * g.pitch;
     float *tile[2] = {psm, psm + tsz};
-    float4 *rin = reinterpret_cast<float4 *>(psm + 2 * tsz);
+    float4 *rin2 = reinterpret_cast<float4 *>(psm + 2 * tsz);   // [2][slots_max]
     const int s0 = pg.slot_off[c], s1 = pg.slot_off[c + 1];
+    SlotInfo *si = reinterpret_cast<SlotInfo *>(psm + 2 * tsz + 8LL * pg.slots_max);
     for (int i = tid; i < 2 * (pg.rows_max + 8) * W4; i += nth)
         reinterpret_cast<float4 *>(psm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    load_slots(g, pg, t, s0, s1, si);
+    __syncthreads();
+    // injection of the first step (n = nt-1); later steps are loaded one step ahead
+    for (int q = tid; q < s1 - s0; q += nth) rin2[q] = slot_resid(g, a.resid, si[q], a.nt - 1);
     const int x4 = threadIdx.x;
     const int sa = (t.r0 + t.ra) / g.NZ, za = (t.r0 + t.ra) - sa * g.NZ;
     const float4 dgx = *reinterpret_cast<const float4 *>(g.dGx + 4 * x4);
@@ -383,21 +460,23 @@ __global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo p
         float *A = tile[j & 1];
         float *B = tile[(j + 1) & 1];
         if (c == 0 && j == a.stall_step) return;   // test hook: leave the neighbours' waits unmet
-        // residual injection for this step: rin[slot] = inj_scale * r[n] per lane
-        for (int q = s0 + tid; q < s1; q += nth) {
-            const int grp = pg.slot_group[q];
-            const int s = (grp / W4) / g.NZ;
-            float4 v = zero;
-            if (n < g.nt[s]) {
-                const int4 cols = pg.slot_cols[q];
-                const long long tb = g.tr_off[s] + (long long)n * g.nrec[s];
-                if (cols.x >= 0) v.x = g.inj_scale * a.resid[tb + cols.x];
-                if (cols.y >= 0) v.y = g.inj_scale * a.resid[tb + cols.y];
-                if (cols.z >= 0) v.z = g.inj_scale * a.resid[tb + cols.z];
-                if (cols.w >= 0) v.w = g.inj_scale * a.resid[tb + cols.w];
-            }
-            rin[q - s0] = v;
+        // image pairs (n+1, n) at odd j; a last even step images alone
+        const int imode = (j & 1) ? 2 : (j == a.nt - 1 ? 1 : 0);
+        if (imode == 0) {   // the strip's T^n, T^{n-1} (slots n+1, n) into L2 for the next step, 16 KB per thread
+            const unsigned bytes = (unsigned)t.nr * g.pitch * 4u;
+            const unsigned off = (unsigned)(tid >> 1) * 16384u;
+            if (off < bytes)
+                prefetch_l2(reinterpret_cast<const char *>(a.hist + (long long)(n + 1 - (tid & 1)) * pg.slot +
+                                                           (long long)t.r0 * g.pitch) + off,
+                            min(16384u, bytes - off));
         }
+        // residual injection of this step: rin[slot] = inj_scale * r[n] per lane
+        // (written during the previous step); the next step's is loaded now
+        // and stored after this step's cells (a thread's first slot only,
+        // any further ones at the end of the step)
+        const float4 *rin = rin2 + (j & 1) * pg.slots_max;
+        float4 *rnext = rin2 + ((j + 1) & 1) * pg.slots_max;
+        const float4 rnx = tid < s1 - s0 ? slot_resid(g, a.resid, si[tid], n - 1) : zero;
         __syncthreads();
         const float4 *A4 = reinterpret_cast<const float4 *>(A);
         float4 *B4 = reinterpret_cast<float4 *>(B);
@@ -407,17 +486,42 @@ __global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo p
 #pragma unroll
             for (int k = 0; k < 9; ++k) w[k] = A4[(t.ra + k) * W4 + x4];
             int s = sa, z = za;
+            int nts = g.nt[s];
+            const float *hn = a.hist + (long long)(n + 1) * pg.slot + 4 * x4;   // T^n; T^{n+1} one slot on
+            const long long g0 = (long long)(t.r0 + t.ra) * g.pitch;
+            RowW cur = load_roww(g, a.W, z, 4 * x4);
+            float4 Tu = zero, Tu1 = zero;
+            if (imode != 0) Tu = __ldcs(reinterpret_cast<const float4 *>(hn + g0));
+            if (imode == 2) Tu1 = __ldcs(reinterpret_cast<const float4 *>(hn + pg.slot + g0));
+            int sl = __ldg(pg.grp_slot + (long long)(t.r0 + t.ra) * W4 + x4);
 #pragma unroll
             for (int q = 0; q < RBMAX; ++q) {
                 const int r = t.ra + q;
                 if (r >= t.rb) break;
-                adj_cell(g, pg, a, n, A4, B4, rin, s0, w, W4, x4, t.r0 + r, r, s, z, dgx);
+                // the next row's model data, stored T and receiver slot are loaded one row ahead
+                const int zn = z + 1 == g.NZ ? 0 : z + 1;
+                RowW nxt;
+                float4 Tun = zero, Tun1 = zero;
+                int sln;
+                if (r + 1 < t.rb) {
+                    const long long go = g0 + (long long)(q + 1) * g.pitch;
+                    nxt = load_roww(g, a.W, zn, 4 * x4);
+                    if (imode != 0) Tun = __ldcs(reinterpret_cast<const float4 *>(hn + go));
+                    if (imode == 2) Tun1 = __ldcs(reinterpret_cast<const float4 *>(hn + pg.slot + go));
+                    sln = __ldg(pg.grp_slot + (long long)(t.r0 + r + 1) * W4 + x4);
+                }
+                adj_cell(g, pg, a, n, A4, B4, rin, s0, w, W4, x4, r, s, z, dgx, nts, cur, imode, Tu, Tu1, sl);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) w[k] = w[k + 1];
                 if (r + 1 < t.rb) w[8] = A4[(r + 9) * W4 + x4];
-                if (++z == g.NZ) {
-                    z = 0;
+                cur = nxt;
+                Tu = Tun;
+                Tu1 = Tun1;
+                sl = sln;
+                z = zn;
+                if (zn == 0 && r + 1 < t.rb) {
                     ++s;
+                    nts = g.nt[s];
                 }
             }
         }
@@ -434,10 +538,15 @@ __global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo p
             float4 w[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) w[k] = A4[(r + k) * W4 + ex];
-            adj_cell(g, pg, a, n, A4, B4, rin, s0, w, W4, ex, gr, r, s, z,
-                     *reinterpret_cast<const float4 *>(g.dGx + 4 * ex));
+            const float *hc = a.hist + (long long)(n + 1) * pg.slot + (long long)gr * g.pitch + 4 * ex;
+            const float4 Tu = imode != 0 ? __ldcs(reinterpret_cast<const float4 *>(hc)) : zero;
+            const float4 Tu1 = imode == 2 ? __ldcs(reinterpret_cast<const float4 *>(hc + pg.slot)) : zero;
+            adj_cell(g, pg, a, n, A4, B4, rin, s0, w, W4, ex, r, s, z, *reinterpret_cast<const float4 *>(g.dGx + 4 * ex),
+                     g.nt[s], load_roww(g, a.W, z, 4 * ex), imode, Tu, Tu1, __ldg(pg.grp_slot + (long long)gr * W4 + ex));
         }
         __syncthreads();
+        if (tid < s1 - s0) rnext[tid] = rnx;
+        for (int q = tid + nth; q < s1 - s0; q += nth) rnext[q] = slot_resid(g, a.resid, si[q], n - 1);
         store_edges(g, pg, B, c, t.nr, (j + 1) & 1);
         publish(pg, c, (unsigned)(j + 1));
     }
@@ -445,7 +554,8 @@ __global__ void __launch_bounds__(PT, 1) k_adj_persist(const Geo g, const PGeo p
 
 size_t persist_smem(const Geo &g, int rows_max, int slots_max)
 {
-    return ((size_t)2 * (rows_max + 8) * g.pitch) * sizeof(float) + (size_t)slots_max * sizeof(float4);
+    return ((size_t)2 * (rows_max + 8) * g.pitch) * sizeof(float) +
+           (size_t)slots_max * (2 * sizeof(float4) + sizeof(SlotInfo));
 }
 
 cudaError_t init_persist_kernels(size_t smem)

@@ -23,15 +23,16 @@
 //   * G x is applied as x - (1 - G) x with 1 - G tabulated, which is exact
 //     (G = 1) in the interior and accurate to |1-G| eps in the sponge.
 // One launch advances every shot by one step: grid (tiles per shot, shots).
-// A CTA stages its TZ x TX tile plus a 4-cell halo of each stencil input in
+// A CTA stages its tz x TX tile plus a 4-cell halo of each stencil input in
 // shared memory with 128-bit loads; each thread owns one float4 column group
-// on TZ/8 rows.  Source injection, receiver gather and residual injection are
+// on tz/8 rows.  Source injection, receiver gather and residual injection are
 // fused into the same launch through a per-(shot, tile) receiver list.
 #include "internal.cuh"
 
 namespace aafwi {
 
 std::atomic<unsigned long long> g_launch_count{0};
+thread_local unsigned long long *g_capture_count = nullptr;
 
 // 5040 x Fornberg's 8th-order central weights for the second derivative at
 // offsets 1..4 (the centre weight is -2 x their sum).
@@ -57,8 +58,9 @@ __device__ __forceinline__ void st4g(float *p, float4 v)
     *reinterpret_cast<float4 *>(p) = v;
 }
 
-// Stage rows z0-4 .. z0+TZ+3 and columns x0-4 .. x0+TX+3 of field f (row
+// Stage rows z0-4 .. z0+SH-5 and columns x0-4 .. x0+TX+3 of field f (row
 // pitch g.pitch) into s; cells outside the padded grid read as zero.
+template <int SH>
 __device__ __forceinline__ void load_tile(Tile *s, const float *f, int z0, int x0, const Geo &g)
 {
     const int tid = threadIdx.y * BX + threadIdx.x;
@@ -157,8 +159,10 @@ __device__ __forceinline__ void gather(const Geo &g, int s, int tile, int n, con
         traces[tb + g.trec_col[i]] = f[g.trec_pt[i]];
 }
 
+template <int RZ>
 __global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a)
 {
+    constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y;
     if (a.n >= g.nt[s]) return;
     const int tile = blockIdx.x;
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a)
     const int z0 = tzi * TZ, x0 = txi * TX;
     __shared__ __align__(16) float su[SH][SW];
     const long long base = (long long)s * g.field;
-    load_tile(su, a.u_cur + base, z0, x0, g);
+    load_tile<SH>(su, a.u_cur + base, z0, x0, g);
     __syncthreads();
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {
@@ -194,8 +198,10 @@ __global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a)
     if (a.traces) gather(g, s, tile, a.n, a.u_next + base, a.traces);
 }
 
+template <int RZ>
 __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a)
 {
+    constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y;
     if (a.n >= g.nt[s]) return;
     const int tile = blockIdx.x;
@@ -205,8 +211,8 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a)
     Tile *su = reinterpret_cast<Tile *>(smem);
     Tile *sd = su + SH;
     const long long base = (long long)s * g.field;
-    load_tile(su, a.u_cur + base, z0, x0, g);
-    load_tile(sd, a.d_cur + base, z0, x0, g);
+    load_tile<SH>(su, a.u_cur + base, z0, x0, g);
+    load_tile<SH>(sd, a.d_cur + base, z0, x0, g);
     __syncthreads();
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {
@@ -244,8 +250,10 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a)
     if (a.traces) gather(g, s, tile, a.n, a.d_next + base, a.traces);
 }
 
+template <int RZ>
 __global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a)
 {
+    constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y;
     if (a.n >= g.nt[s]) return;
     const int tile = blockIdx.x;
@@ -256,8 +264,8 @@ __global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a)
     Tile *su = sz + SH;
     float(*sinj)[TX] = reinterpret_cast<float(*)[TX]>(smem + 2 * SH * SW);
     const long long base = (long long)s * g.field;
-    load_tile(sz, a.z1 + base, z0, x0, g);
-    load_tile(su, a.u + base, z0, x0, g);
+    load_tile<SH>(sz, a.z1 + base, z0, x0, g);
+    load_tile<SH>(su, a.u + base, z0, x0, g);
     const int t = s * g.ntiles + tile;
     const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
     const bool has_rec = r1 > r0;
@@ -376,14 +384,26 @@ __global__ void k_shot_sum_z(const Geo g, int nz, int nx, const double *rowsum, 
     out[i] = (float)acc;
 }
 
-static size_t born_smem() { return 2 * SH * SW * sizeof(float); }
-static size_t adj_smem() { return (2 * SH * SW + TZ * TX) * sizeof(float); }
+template <int RZ>
+static size_t born_smem() { return 2 * (RZ * BY + 2 * HALO) * SW * sizeof(float); }
+template <int RZ>
+static size_t adj_smem() { return (2 * (RZ * BY + 2 * HALO) * SW + RZ * BY * TX) * sizeof(float); }
+
+template <int RZ>
+static cudaError_t init_tile_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_born<RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)born_smem<RZ>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_adj<RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem<RZ>());
+    return e;
+}
 
 cudaError_t init_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_born, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)born_smem());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem());
+    cudaError_t e = init_tile_kernels<2>();
+    if (e == cudaSuccess) e = init_tile_kernels<4>();
+    if (e == cudaSuccess) e = init_tile_kernels<8>();
     return e;
 }
 
@@ -397,19 +417,28 @@ void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho,
 void launch_fwd(const Geo &g, const FwdArgs &a, cudaStream_t st)
 {
     count_launch();
-    k_fwd<<<dim3(g.ntiles, g.S), dim3(BX, BY), 0, st>>>(g, a);
+    const dim3 grid(g.ntiles, g.S), block(BX, BY);
+    if (g.tz == 16) k_fwd<2><<<grid, block, 0, st>>>(g, a);
+    else if (g.tz == 64) k_fwd<8><<<grid, block, 0, st>>>(g, a);
+    else k_fwd<4><<<grid, block, 0, st>>>(g, a);
 }
 
 void launch_born(const Geo &g, const BornArgs &a, cudaStream_t st)
 {
     count_launch();
-    k_born<<<dim3(g.ntiles, g.S), dim3(BX, BY), born_smem(), st>>>(g, a);
+    const dim3 grid(g.ntiles, g.S), block(BX, BY);
+    if (g.tz == 16) k_born<2><<<grid, block, born_smem<2>(), st>>>(g, a);
+    else if (g.tz == 64) k_born<8><<<grid, block, born_smem<8>(), st>>>(g, a);
+    else k_born<4><<<grid, block, born_smem<4>(), st>>>(g, a);
 }
 
 void launch_adj(const Geo &g, const AdjArgs &a, cudaStream_t st)
 {
     count_launch();
-    k_adj<<<dim3(g.ntiles, g.S), dim3(BX, BY), adj_smem(), st>>>(g, a);
+    const dim3 grid(g.ntiles, g.S), block(BX, BY);
+    if (g.tz == 16) k_adj<2><<<grid, block, adj_smem<2>(), st>>>(g, a);
+    else if (g.tz == 64) k_adj<8><<<grid, block, adj_smem<8>(), st>>>(g, a);
+    else k_adj<4><<<grid, block, adj_smem<4>(), st>>>(g, a);
 }
 
 void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *rowsum, float *out,
