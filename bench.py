@@ -248,23 +248,25 @@ def run_ours(args):
     peak, peak_kind = read_peaks()
     nt = int(g.nt.max())
     pts_sweep = sum(active_points(g, n) for n in range(nt))
-    persistent = plan.info.engine == aafwi.ENGINE_PERSISTENT
-    per_sweep = 1 if persistent else nt
-    adj_bytes = BYTES_ADJ * pts_sweep / per_sweep
-    fwd_bytes = BYTES_FWD * pts_sweep / per_sweep
-    adj_ms = kt["adj_ms"] / per_sweep
-    fwd_ms = kt["fwd_ms"] / per_sweep
+    eng = plan.info.engine
+    adj_per_sweep = 1 if eng in (aafwi.ENGINE_PERSISTENT, aafwi.ENGINE_HYBRID) else nt
+    fwd_per_sweep = 1 if eng == aafwi.ENGINE_PERSISTENT else nt
+    adj_bytes = BYTES_ADJ * pts_sweep / adj_per_sweep
+    fwd_bytes = BYTES_FWD * pts_sweep / fwd_per_sweep
+    adj_ms = kt["adj_ms"] / adj_per_sweep
+    fwd_ms = kt["fwd_ms"] / fwd_per_sweep
     adj_gbs = adj_bytes / (adj_ms * 1e-3) / 1e9
     fwd_gbs = fwd_bytes / (fwd_ms * 1e-3) / 1e9
-    adj_name = "k_adj_persist" if persistent else "k_adj"
-    fwd_name = "k_fwd_persist" if persistent else "k_fwd"
+    adj_name = "k_adj_persist" if adj_per_sweep == 1 else "k_adj"
+    fwd_name = "k_fwd_persist" if fwd_per_sweep == 1 else "k_fwd"
     traffic = traffic_record(adj_name)
     roofline = {"bound": "hbm", "kernel": adj_name + " (adjoint sweep + imaging)", "achieved": adj_gbs,
                 "peak": peak, "unit": "GB/s", "frac": adj_gbs / peak, "peak_kind": peak_kind,
                 "traffic": traffic, "bytes_per_launch": adj_bytes, "ms_per_launch": adj_ms,
-                "launches_per_sweep": per_sweep, "us_per_time_step": 1e3 * kt["adj_ms"] / nt,
+                "launches_per_sweep": adj_per_sweep, "us_per_time_step": 1e3 * kt["adj_ms"] / nt,
                 "forward_kernel": {"kernel": fwd_name, "achieved": fwd_gbs, "frac": fwd_gbs / peak,
                                    "bytes_per_launch": fwd_bytes, "ms_per_launch": fwd_ms,
+                                   "launches_per_sweep": fwd_per_sweep,
                                    "us_per_time_step": 1e3 * kt["fwd_ms"] / nt}}
 
     e2e = run_e2e(plan, prob, dev, args.e2e_steps) if args.e2e_steps > 0 else None

@@ -104,6 +104,8 @@ typedef struct {
 #define AAFWI_ENGINE_PERSISTENT 2   /* one cooperative launch per sweep; ARG if the
                                        plan does not qualify (full history, strips of
                                        the shots' rows fitting shared memory) */
+#define AAFWI_ENGINE_HYBRID     3   /* forward sweeps per step, adjoint sweeps as one
+                                       cooperative launch (same conditions) */
 
 typedef struct {
     int NZ, NX, pitch;           /* padded grid and row pitch (floats) */
@@ -114,7 +116,7 @@ typedef struct {
     size_t workspace_bytes;
     int tile_z, tile_x;
     int n_tiles;                 /* tiles per shot */
-    int engine;                  /* AAFWI_ENGINE_PER_STEP or AAFWI_ENGINE_PERSISTENT */
+    int engine;                  /* AAFWI_ENGINE_PER_STEP, _PERSISTENT or _HYBRID */
     int persist_ctas;            /* strips of the persistent sweeps (0 if per step) */
 } aafwi_plan_info;
 
@@ -292,17 +294,18 @@ int aafwi_misfit_noalloc(const float *d_syn, const float *d_obs, long long n, fl
  * counterpart) ------------------------------------------------------------ */
 
 typedef struct {
-    int engine;      /* AAFWI_ENGINE_PER_STEP or AAFWI_ENGINE_PERSISTENT */
-    int tile_z;      /* per-step tile rows (16, 32 or 64); 0 for the persistent engine */
+    int engine;      /* AAFWI_ENGINE_PER_STEP, _PERSISTENT or _HYBRID */
+    int tile_z;      /* tile rows of the per-step forward (16, 32 or 64); 0 for PERSISTENT */
     double ms;       /* median CUDA-event time of one forward sweep plus one FWI
                         adjoint sweep reusing it, over the first `steps` steps */
 } aafwi_tune_entry;
 
 /* Time the launch configurations a plan of this geometry may use and return
  * the fastest as plan options.  Candidates: the per-step engine with each tile
- * height, and the persistent engine when a plan with these options keeps the
- * full history and its strips fit on chip (base->engine, when not AUTO,
- * restricts the candidates to that engine).  Each candidate is a temporary
+ * height, and, when a plan with these options keeps the full history and its
+ * strips fit on chip, the persistent engine and the hybrid engine with each
+ * tile height (base->engine, when not AUTO, restricts the candidates to that
+ * engine).  Each candidate is a temporary
  * plan over the same shots with every record length cut to `steps` (the
  * sweeps' time grows in proportion to the steps), timed `reps` times after one
  * warm-up on the device model m [nz][nx] (FP32, m = 1/c^2) with zero observed

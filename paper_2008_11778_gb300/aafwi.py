@@ -51,7 +51,7 @@ class Shots(ctypes.Structure):
                 ("rec_iz", ctypes.c_void_p), ("rec_ix", ctypes.c_void_p)]
 
 
-ENGINE_AUTO, ENGINE_PER_STEP, ENGINE_PERSISTENT = 0, 1, 2
+ENGINE_AUTO, ENGINE_PER_STEP, ENGINE_PERSISTENT, ENGINE_HYBRID = 0, 1, 2, 3
 
 
 class PlanOpts(ctypes.Structure):
@@ -218,10 +218,10 @@ def run_autotune(geom, c_max, m, steps=64, reps=3, engine=ENGINE_AUTO, max_works
     g, s, keep = _geom_structs(geom, c_max)
     base = PlanOpts(int(max_workspace_bytes), 0, 0, 0, int(engine), 0)
     best = PlanOpts()
-    table = (TuneEntry * 8)()
+    table = (TuneEntry * 16)()
     n = ctypes.c_int()
     _check(L.aafwi_autotune(ctypes.byref(g), ctypes.byref(s), _np_ptr(keep[6]), _f32(m), int(steps),
-                            int(reps), ctypes.byref(base), table, 8, ctypes.byref(n), ctypes.byref(best)))
+                            int(reps), ctypes.byref(base), table, 16, ctypes.byref(n), ctypes.byref(best)))
     return {"engine": int(best.engine), "tile_z": int(best.tile_z), "steps": int(steps),
             "table": [(int(table[i].engine), int(table[i].tile_z), float(table[i].ms)) for i in range(n.value)]}
 

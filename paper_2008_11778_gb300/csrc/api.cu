@@ -44,9 +44,9 @@ struct aafwi_plan {
     // device buffers
     float *W = nullptr, *rho_pad = nullptr;   // W: Wh then Wl, each [NZ][pitch]
     double K = 0.0;                 // dt^2 / (5040 dx^2)
-    float *hist = nullptr;          // full: (nt_max+1) slots; else 2*nck checkpoint slots
-    float *fbuf = nullptr;          // 2 rotating forward slots (checkpoint mode)
-    float *rbuf = nullptr;          // k-1 replay slots (checkpoint mode)
+    float *hist = nullptr;          // full: T^n in slot n+1 (nt_max+1 slots); else 2*nck checkpoint slots
+    float *fbuf = nullptr;          // 2 rotating forward slots (u^n, u^{n-1}; in place)
+    float *rbuf = nullptr;          // k replay slots of T (checkpoint mode)
     float *dbuf = nullptr;          // 2 rotating Born slots
     float *zbuf = nullptr;          // 2 rotating adjoint slots
     float *img = nullptr;           // per-shot image accumulators
@@ -58,8 +58,9 @@ struct aafwi_plan {
     bool fwd_valid = false;
     const float *fwd_model = nullptr;
     // persistent engine
-    bool persist = false;           // FWI sweeps run as one cooperative launch each
-    bool hist_T = false;            // history holds T^n (persistent forward) rather than u^n
+    bool persist_fwd = false;       // FWI forward sweeps: one cooperative launch each
+    bool persist_adj = false;       // adjoint sweeps: one cooperative launch each
+    bool hist_T = false;            // the history holds T^n of the last forward sweep
     PGeo pgeo{};
     size_t psmem = 0;
     int stall_step = -1;            // test hook (aafwi_plan_set_stall)
@@ -190,15 +191,6 @@ int check_launch(aafwi_plan *p)
     return AAFWI_OK;
 }
 
-// Pointer to u^n in checkpoint mode while processing segment j (first step a).
-float *seg_u(aafwi_plan *p, int j, int a, int n)
-{
-    const long long ps = (long long)p->S * p->field;
-    if (n == a) return slot(p->hist, ps, 2LL * j);
-    if (n == a - 1) return slot(p->hist, ps, 2LL * j + 1);
-    return slot(p->rbuf, ps, n - a - 1);
-}
-
 int run_persist_forward(aafwi_plan *p, float *traces, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(p->pgeo.flags, 0, p->pgeo.P * sizeof(unsigned), st);
@@ -206,40 +198,36 @@ int run_persist_forward(aafwi_plan *p, float *traces, cudaStream_t st)
     PFwdArgs a{p->W, p->hist, traces, p->nt_max, p->stall_step};
     e = launch_fwd_persist(p->geo, p->pgeo, a, p->psmem, st);
     if (e != cudaSuccess) return cuda_fail(p, e, "persistent forward launch");
-    p->hist_T = true;
     return AAFWI_OK;
 }
 
-// Per-step forward sweep over all shots (born: u and du together).
+// Per-step forward sweep over all shots (born: u and du together).  u^n and
+// u^{n-1} rotate in fbuf (u^{n+1} overwrites u^{n-1} in place); with the full
+// history T^n goes to history slot n+1, else (u^n, u^{n-1}) are checkpointed
+// every k steps.
 int sweep_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
 {
     const long long ps = (long long)p->S * p->field;
-    if (!p->full && cudaMemsetAsync(p->fbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
+    if (cudaMemsetAsync(p->fbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
     if (born && cudaMemsetAsync(p->dbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
     for (int n = 0; n < p->nt_max; ++n) {
-        float *cur, *prev, *next, *ckc = nullptr, *ckp = nullptr;
+        float *cur = slot(p->fbuf, ps, n & 1), *prev = slot(p->fbuf, ps, (n + 1) & 1), *next = prev;
+        float *ckc = nullptr, *ckp = nullptr, *tout = nullptr;
         if (p->full) {
-            cur = slot(p->hist, ps, n);
-            prev = slot(p->hist, ps, n > 0 ? n - 1 : 0);
-            next = slot(p->hist, ps, n + 1);
-        } else {
-            cur = slot(p->fbuf, ps, n & 1);
-            prev = slot(p->fbuf, ps, (n + 1) & 1);
-            next = prev;
-            if (n % p->k == 0) {
-                ckc = slot(p->hist, ps, 2LL * (n / p->k));
-                ckp = slot(p->hist, ps, 2LL * (n / p->k) + 1);
-            }
+            tout = slot(p->hist, ps, n + 1);
+        } else if (n % p->k == 0) {
+            ckc = slot(p->hist, ps, 2LL * (n / p->k));
+            ckp = slot(p->hist, ps, 2LL * (n / p->k) + 1);
         }
         if (born) {
             BornArgs a{p->W, p->rho_pad, cur, prev, next, slot(p->dbuf, ps, n & 1),
                        slot(p->dbuf, ps, (n + 1) & 1), slot(p->dbuf, ps, (n + 1) & 1), ckc, ckp,
-                       traces, n};
+                       traces, tout, n};
             launch_born(p->geo, a, st);
         } else {
-            FwdArgs a{p->W, cur, prev, next, ckc, ckp, traces, n};
+            FwdArgs a{p->W, cur, prev, next, ckc, ckp, traces, tout, n};
             launch_fwd(p->geo, a, st);
         }
     }
@@ -249,11 +237,15 @@ int sweep_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
 // Forward sweep over all shots (born: u and du together); traces -> CSR.
 int run_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
 {
-    if (p->persist && !born) return run_persist_forward(p, traces, st);
     p->hist_T = false;
-    if (!p->graphs) return sweep_forward(p, born, traces, st);
-    return run_graph(p, born ? SWEEP_BORN : SWEEP_FWD, traces, st,
-                     [&](cudaStream_t cs) { return sweep_forward(p, born, traces, cs); });
+    int rc;
+    if (p->persist_fwd && !born) rc = run_persist_forward(p, traces, st);
+    else if (!p->graphs) rc = sweep_forward(p, born, traces, st);
+    else
+        rc = run_graph(p, born ? SWEEP_BORN : SWEEP_FWD, traces, st,
+                       [&](cudaStream_t cs) { return sweep_forward(p, born, traces, cs); });
+    p->hist_T = rc == AAFWI_OK && p->full;
+    return rc;
 }
 
 // Per-step adjoint sweep with imaging into p->img (checkpoint mode: segment
@@ -265,22 +257,29 @@ int sweep_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
         return cuda_fail(p, cudaGetLastError(), "memset");
     if (cudaMemsetAsync(p->zbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
-    auto adj = [&](int n, const float *u) {
-        AdjArgs a{p->W, slot(p->zbuf, ps, (n + 1) & 1), slot(p->zbuf, ps, n & 1), u, resid, p->img,
+    auto adj = [&](int n, const float *T) {
+        AdjArgs a{p->W, slot(p->zbuf, ps, (n + 1) & 1), slot(p->zbuf, ps, n & 1), T, resid, p->img,
                   n, born ? 1 : 0};
         launch_adj(p->geo, a, st);
     };
     if (p->full) {
-        for (int n = p->nt_max - 1; n >= 0; --n) adj(n, slot(p->hist, ps, n));
+        for (int n = p->nt_max - 1; n >= 0; --n) adj(n, slot(p->hist, ps, n + 1));
     } else {
+        // segment j = steps [a, e): replay the forward from its checkpoint
+        // (u^a, u^{a-1}) storing T^a .. T^{e-1} in rbuf, then step back
+        // through it.  u^m, m > a, rotates in fbuf (checkpoints stay intact).
         for (int j = p->nck - 1; j >= 0; --j) {
             const int a = j * p->k, e = std::min(a + p->k, p->nt_max);
-            for (int n = a; n <= e - 2; ++n) {
-                FwdArgs f{p->W, seg_u(p, j, a, n), seg_u(p, j, a, n - 1), seg_u(p, j, a, n + 1),
-                          nullptr, nullptr, nullptr, n};
+            auto U = [&](int m) {
+                return m == a ? slot(p->hist, ps, 2LL * j)
+                              : m == a - 1 ? slot(p->hist, ps, 2LL * j + 1) : slot(p->fbuf, ps, m & 1);
+            };
+            for (int n = a; n < e; ++n) {
+                FwdArgs f{p->W, U(n), U(n - 1), slot(p->fbuf, ps, (n + 1) & 1), nullptr, nullptr, nullptr,
+                          slot(p->rbuf, ps, n - a), n};
                 launch_fwd(p->geo, f, st);
             }
-            for (int n = e - 1; n >= a; --n) adj(n, seg_u(p, j, a, n));
+            for (int n = e - 1; n >= a; --n) adj(n, slot(p->rbuf, ps, n - a));
         }
     }
     return check_launch(p);
@@ -289,7 +288,7 @@ int sweep_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
 // Adjoint sweep with imaging into p->img (born: scale -1, else -1/m).
 int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
 {
-    if (p->hist_T) {
+    if (p->persist_adj && p->hist_T) {
         const long long ps = (long long)p->S * p->field;
         if (cudaMemsetAsync(p->img, 0, ps * sizeof(float), st) != cudaSuccess)
             return cuda_fail(p, cudaGetLastError(), "memset");
@@ -332,14 +331,14 @@ int finish_sync(aafwi_plan *p, double *J_host, cudaStream_t st)
     return AAFWI_OK;
 }
 
-// Decide whether FWI sweeps run persistently and build the strip tables.
-// Returns 0 (engine chosen) or an error code when PERSISTENT was required.
+// Decide which sweeps run persistently and build the strip tables.  Returns
+// 0 (engine chosen) or an error code when PERSISTENT or HYBRID was required.
 int setup_persist(aafwi_plan *p, int engine, const aafwi_shots *sh, std::string *why)
 {
-    p->persist = false;
+    p->persist_fwd = p->persist_adj = false;
     if (engine == AAFWI_ENGINE_PER_STEP) return AAFWI_OK;
     auto no = [&](const char *m) {
-        if (engine == AAFWI_ENGINE_PERSISTENT) {
+        if (engine == AAFWI_ENGINE_PERSISTENT || engine == AAFWI_ENGINE_HYBRID) {
             *why = std::string("persistent engine not available: ") + m;
             return AAFWI_ERR_ARG;
         }
@@ -422,7 +421,8 @@ int setup_persist(aafwi_plan *p, int engine, const aafwi_shots *sh, std::string 
     pg.row0 = d_row0; pg.grp_slot = d_gs; pg.slot_off = d_so; pg.slot_group = d_sg; pg.slot_cols = d_sc;
     pg.err = p->err;
     p->psmem = smem;
-    p->persist = true;
+    p->persist_fwd = engine != AAFWI_ENGINE_HYBRID;
+    p->persist_adj = true;
     return AAFWI_OK;
 }
 
@@ -437,7 +437,8 @@ WorkspacePlan aafwi::workspace_plan(long long field, int S, int nt_max, long lon
 {
     WorkspacePlan w;
     const size_t F = (size_t)field * sizeof(float), SF = F * S;
-    w.fixed = 3 * F + (2 + 2 + 1) * SF + 2 * (size_t)trace_count * sizeof(float) + (1 << 20);
+    // W pair + rho; fbuf, dbuf, zbuf (2 slots each) + img; dsyn + resid
+    w.fixed = 3 * F + (2 + 2 + 2 + 1) * SF + 2 * (size_t)trace_count * sizeof(float) + (1 << 20);
     w.budget = o.max_workspace_bytes;
     if (w.budget == 0) {
         size_t fr = 0, tot = 0;
@@ -574,7 +575,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
         p->full = false;
         p->k = k;
         p->nck = (p->nt_max + k - 1) / k;
-        p->ws_bytes = fixed + (size_t)(2 * p->nck + (k - 1) + 2) * SF;
+        p->ws_bytes = fixed + (size_t)(2 * p->nck + k) * SF;
     }
     if (p->ws_bytes > budget) {
         char b[200];
@@ -595,7 +596,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
               upload(p->bufs, &d_troff, p->tr_off);
     const long long ps = (long long)S * p->field;
     ok = ok && dalloc(p->bufs, &p->W, 2 * p->field) && dalloc(p->bufs, &p->rho_pad, p->field) &&
-         dalloc(p->bufs, &p->dbuf, 2 * ps) && dalloc(p->bufs, &p->zbuf, 2 * ps) &&
+         dalloc(p->bufs, &p->dbuf, 2 * ps) && dalloc(p->bufs, &p->zbuf, 2 * ps) && dalloc(p->bufs, &p->fbuf, 2 * ps) &&
          dalloc(p->bufs, &p->img, ps) && dalloc(p->bufs, &p->dsyn, p->trace_count) &&
          dalloc(p->bufs, &p->resid, p->trace_count) && dalloc(p->bufs, &p->partials, RED_BLOCKS) &&
          dalloc(p->bufs, &p->J, 1) && dalloc(p->bufs, &p->err, 1) &&
@@ -604,8 +605,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
         if (p->full) {
             ok = dalloc(p->bufs, &p->hist, (p->nt_max + 1) * ps);
         } else {
-            ok = dalloc(p->bufs, &p->hist, 2LL * p->nck * ps) && dalloc(p->bufs, &p->fbuf, 2 * ps) &&
-                 dalloc(p->bufs, &p->rbuf, std::max(1, p->k - 1) * ps);
+            ok = dalloc(p->bufs, &p->hist, 2LL * p->nck * ps) && dalloc(p->bufs, &p->rbuf, (long long)p->k * ps);
         }
     }
     if (!ok) {
@@ -653,7 +653,7 @@ void aafwi_plan_destroy(aafwi_plan *p)
 int aafwi_plan_set_stall(aafwi_plan *p, int step)
 {
     if (!p) return AAFWI_ERR_ARG;
-    if (!p->persist && step >= 0) return fail(p, AAFWI_ERR_STATE, "plan has no persistent sweeps");
+    if (!p->persist_adj && step >= 0) return fail(p, AAFWI_ERR_STATE, "plan has no persistent sweeps");
     p->stall_step = step < 0 ? -1 : step;
     return AAFWI_OK;
 }
@@ -669,8 +669,9 @@ int aafwi_plan_get_info(const aafwi_plan *p, aafwi_plan_info *info)
     info->workspace_bytes = p->ws_bytes;
     info->tile_z = p->geo.tz; info->tile_x = TX;
     info->n_tiles = p->geo.ntiles;
-    info->engine = p->persist ? AAFWI_ENGINE_PERSISTENT : AAFWI_ENGINE_PER_STEP;
-    info->persist_ctas = p->persist ? p->pgeo.P : 0;
+    info->engine = p->persist_fwd ? AAFWI_ENGINE_PERSISTENT
+                   : p->persist_adj ? AAFWI_ENGINE_HYBRID : AAFWI_ENGINE_PER_STEP;
+    info->persist_ctas = p->persist_adj ? p->pgeo.P : 0;
     return AAFWI_OK;
 }
 

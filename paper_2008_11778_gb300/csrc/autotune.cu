@@ -1,5 +1,5 @@
-// autotune.cu -- choice of the sweeps' launch configuration (engine, tile
-// height of the per-step kernels) by timing short sweeps of temporary plans
+// autotune.cu -- choice of the sweeps' launch configuration (engine: per
+// step, persistent or hybrid; tile height of the per-step kernels) by timing short sweeps of temporary plans
 // of the same geometry.  Host code over the public entry points only.
 #include <algorithm>
 #include <vector>
@@ -82,10 +82,13 @@ extern "C" int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, 
     }
     const bool full = workspace_plan((long long)NZ * pitch, S, nt_max, traces, o).full;
     std::vector<Candidate> cands;
-    if (o.engine != AAFWI_ENGINE_PERSISTENT)
+    auto allowed = [&](int e) { return o.engine == AAFWI_ENGINE_AUTO || o.engine == e; };
+    if (allowed(AAFWI_ENGINE_PER_STEP))
         for (int tz : {16, 32, 64}) cands.push_back({AAFWI_ENGINE_PER_STEP, tz});
-    if (o.engine != AAFWI_ENGINE_PER_STEP && full) cands.push_back({AAFWI_ENGINE_PERSISTENT, 0});
-    if (cands.empty()) return tune_fail(AAFWI_ERR_ARG, "autotune: the persistent engine needs the full history");
+    if (full && allowed(AAFWI_ENGINE_PERSISTENT)) cands.push_back({AAFWI_ENGINE_PERSISTENT, 0});
+    if (full && allowed(AAFWI_ENGINE_HYBRID))
+        for (int tz : {16, 32, 64}) cands.push_back({AAFWI_ENGINE_HYBRID, tz});
+    if (cands.empty()) return tune_fail(AAFWI_ERR_ARG, "autotune: the persistent engines need the full history");
     aafwi_shots sh = *shots;
     sh.nt = nt.data();
     Scratch sc;
@@ -102,7 +105,7 @@ extern "C" int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, 
         co.checkpoint_every = 1;
         aafwi_plan *p = nullptr;
         int rc = aafwi_plan_create(grid, &sh, wavelet, &co, &p);
-        if (rc == AAFWI_ERR_ARG && c.engine == AAFWI_ENGINE_PERSISTENT) continue;   // strips do not qualify
+        if (rc == AAFWI_ERR_ARG && c.engine != AAFWI_ENGINE_PER_STEP) continue;   // strips do not qualify
         if (rc) return rc;
         aafwi_plan_info info{};
         aafwi_plan_get_info(p, &info);

@@ -58,6 +58,7 @@ struct FwdArgs {
     float *u_next;
     float *ck_cur, *ck_prev;       // checkpoint targets for (u^n, u^{n-1}) or null
     float *traces;                 // gather target (CSR) or null
+    float *t_out;                  // T^n = 5040 dx^2 (L u^n + s^n) target (slot base) or null
     int n;
 };
 
@@ -70,16 +71,18 @@ struct BornArgs {
     float *d_next;
     float *ck_cur, *ck_prev;
     float *traces;                 // scattered-field gather
+    float *t_out;                  // T^n of the background field (slot base) or null
     int n;
 };
 
 // Adjoint step n (z^n from z^{n+1}, z^{n+2}) fused with the imaging condition
-// img += scale * z^n * (L u^n + s^n), scale = -1/m (FWI) or -1 (Born).
+// img += scale * z^n * (L u^n + s^n), scale = -1/m (FWI) or -1 (Born), with
+// L u^n + s^n read as the forward sweep's stored T^n / (5040 dx^2).
 struct AdjArgs {
     const float *W;
     const float *z1;               // z^{n+1}
     float *z2n;                    // in: z^{n+2}; out: z^n (same cells)
-    const float *u;                // u^n
+    const float *T;                // T^n (slot base)
     const float *resid;            // CSR residual traces
     float *img;                    // per-shot accumulators [S][field]
     int n;

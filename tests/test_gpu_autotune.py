@@ -57,6 +57,7 @@ def test_autotune_picks_the_fastest_and_plans_follow_it(A, orc, tmp_path):
     kinds = {(e, t) for e, t, _ in res["table"]}
     assert {(A.ENGINE_PER_STEP, 16), (A.ENGINE_PER_STEP, 32), (A.ENGINE_PER_STEP, 64)} <= kinds
     assert (A.ENGINE_PERSISTENT, 0) in kinds                      # the tiny plan keeps its full history
+    assert {(A.ENGINE_HYBRID, 16), (A.ENGINE_HYBRID, 32), (A.ENGINE_HYBRID, 64)} <= kinds
     assert all(ms > 0 for _, _, ms in res["table"])
     best = min(res["table"], key=lambda e: e[2])
     assert (res["engine"], res["tile_z"]) == (best[0], best[1])

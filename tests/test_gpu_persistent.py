@@ -41,24 +41,30 @@ def test_persistent_equals_per_step_bitwise(A, orc, make):
     c_max = 3000.0
     per = A.Plan(g, c_max, engine=A.ENGINE_PER_STEP)
     pst = A.Plan(g, c_max, engine=A.ENGINE_PERSISTENT)
+    hyb = A.Plan(g, c_max, engine=A.ENGINE_HYBRID)
     assert per.info.engine == A.ENGINE_PER_STEP and pst.info.engine == A.ENGINE_PERSISTENT
+    assert hyb.info.engine == A.ENGINE_HYBRID
     m = torch.as_tensor(p.m_start.astype(np.float32), device="cuda")
-    d1 = torch.empty(per.trace_count, device="cuda")
-    d2 = torch.empty(pst.trace_count, device="cuda")
-    per.model_forward(m, d1)
-    pst.model_forward(m, d2)
-    assert torch.equal(d1, d2)
     d_obs = torch.as_tensor(orc.forward(g, p.m_true).astype(np.float32), device="cuda")
-    g1, g2 = torch.empty_like(m), torch.empty_like(m)
-    J1 = per.adjoint_gradient(0, m, None, d_obs, g1)
-    J2 = pst.adjoint_gradient(0, m, None, d_obs, g2)
-    assert J1 == J2 and torch.equal(g1, g2)
     r = torch.as_tensor(np.random.default_rng(1).standard_normal(per.trace_count).astype(np.float32),
                         device="cuda")
-    i1, i2 = torch.empty_like(m), torch.empty_like(m)
-    per.born_adjoint(m, r, i1)
-    pst.born_adjoint(m, r, i2)
-    assert torch.equal(i1, i2)
+    rho = torch.as_tensor(np.random.default_rng(2).uniform(-0.1, 0.1, (g.nz, g.nx)).astype(np.float32),
+                          device="cuda")
+
+    def run(plan):
+        d = torch.empty(plan.trace_count, device="cuda")
+        plan.model_forward(m, d)
+        gr, im, gl = torch.empty_like(m), torch.empty_like(m), torch.empty_like(m)
+        J = plan.adjoint_gradient(0, m, None, d_obs, gr)
+        plan.born_adjoint(m, r, im)
+        Jl = plan.adjoint_gradient(1, m, rho, d_obs, gl)      # Born forward per step, adjoint per engine
+        return d, J, gr, im, Jl, gl
+
+    ref = run(per)
+    for plan in (pst, hyb):
+        out = run(plan)
+        for a, b in zip(ref, out):
+            assert (torch.equal(a, b) if torch.is_tensor(a) else a == b)
 
 
 def test_batched_plan_runs_persistent(A):
