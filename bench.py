@@ -182,6 +182,19 @@ def active_points(geom, n):
     return int((geom.nt > n).sum()) * geom.NZ * geom.NX
 
 
+ENGINES = {"auto": 0, "per_step": 1, "persistent": 2, "hybrid": 3}
+ENGINE_NAMES = {v: k for k, v in ENGINES.items()}
+
+
+def make_plan(aafwi, prob, g, m_tune, args):
+    """The benchmark's plan: the library's autotuned launch configuration
+    (timed on short sweeps of this geometry before the timed region), or the
+    engine / tile height given on the command line."""
+    if args.engine == "tuned":
+        return aafwi.Plan(g, c_max=prob.c_bounds[1], tune_model=m_tune, tune_cache=args.tune_cache)
+    return aafwi.Plan(g, c_max=prob.c_bounds[1], engine=ENGINES[args.engine], tile_z=args.tile_z)
+
+
 def run_ours(args):
     import torch
     from paper_2008_11778_gb300 import aafwi, solve, synth
@@ -194,7 +207,9 @@ def run_ours(args):
     prob = synth.batched()
     g = prob.geom
     lo, hi = prob.m_bounds
-    plan = aafwi.Plan(g, c_max=prob.c_bounds[1])
+    m_start = torch.as_tensor(prob.m_start.astype(np.float32), device=dev)
+    plan = make_plan(aafwi, prob, g, m_start, args)
+    tuning = getattr(plan, "tuning", None)
     # observed data from this library's own forward on the true model
     m_true = torch.as_tensor(prob.m_true.astype(np.float32), device=dev)
     d_obs = torch.empty(plan.trace_count, device=dev)
@@ -285,6 +300,11 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "grid": [g.nz, g.nx], "padded": [g.NZ, g.NX],
                            "shots": g.S, "nt": int(g.nt.max()), "M": prob.M,
                            "checkpoint_every": plan.info.checkpoint_every,
+                           "engine": ENGINE_NAMES.get(plan.info.engine, plan.info.engine),
+                           "tile_z": plan.info.tile_z,
+                           "autotune": None if tuning is None else {
+                               "steps": tuning.get("steps"), "cached": tuning.get("cached"),
+                               "table_ms": [[ENGINE_NAMES.get(e, e), t, ms] for e, t, ms in tuning["table"]]},
                            "l2": "inputs larger than L2 (wavefield history %.1f GB)" % (
                                plan.info.workspace_bytes / 1e9),
                            "passes": {"forward": nf, "adjoint": na},
@@ -390,15 +410,16 @@ def cpu_baseline(prob):
             "seconds": dt}
 
 
-def ncu_case():
+def ncu_case(args):
     """A small case of the benchmark's kernels for ncu --set full captures: the
     batched geometry (all 32 shots, 400 x 150) cut to 64 time steps; one
-    forward sweep and one adjoint sweep reusing it."""
+    forward sweep and one adjoint sweep reusing it, with the engine and tile
+    height given on the command line (the benchmark line's config)."""
     import torch
     from paper_2008_11778_gb300 import aafwi, synth
     prob = synth.batched()
     g = prob.geom.with_nt(64)
-    plan = aafwi.Plan(g, c_max=prob.c_bounds[1])
+    plan = aafwi.Plan(g, c_max=prob.c_bounds[1], engine=ENGINES.get(args.engine, 0), tile_z=args.tile_z)
     m = torch.as_tensor(prob.m_start.astype(np.float32), device="cuda")
     d_obs = torch.zeros(plan.trace_count, device="cuda")
     grad = torch.empty_like(m)
@@ -406,6 +427,7 @@ def ncu_case():
     J = plan.adjoint_gradient(aafwi.MODE_FWI, m, None, d_obs, grad, reuse_forward=True)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": "batched-400x150-32shots-64steps", "J": J,
+                      "engine": ENGINE_NAMES.get(plan.info.engine), "tile_z": plan.info.tile_z,
                       "launches": aafwi.launch_count()}))
 
 
@@ -419,12 +441,16 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="small case for ncu captures")
-    ap.add_argument("--learned-eval", type=int, default=2, help="held-out models for learned vs plain AA")
-    ap.add_argument("--learned-target", type=float, default=0.1)
-    ap.add_argument("--learned-max-iters", type=int, default=60)
+    ap.add_argument("--engine", default="tuned", choices=["tuned"] + list(ENGINES),
+                    help="sweep engine: the library's autotuner (default) or a fixed one")
+    ap.add_argument("--tile-z", type=int, default=0, help="per-step tile rows with a fixed engine")
+    ap.add_argument("--tune-cache", default=None, help="autotuner cache file (default: the library's)")
+    ap.add_argument("--learned-eval", type=int, default=3, help="held-out models for learned vs plain AA")
+    ap.add_argument("--learned-target", type=float, default=1e-2)
+    ap.add_argument("--learned-max-iters", type=int, default=120)
     args = ap.parse_args()
     if args.ncu_case:
-        ncu_case()
+        ncu_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -50,6 +50,8 @@ struct aafwi_plan {
     float *dbuf = nullptr;          // 2 rotating Born slots
     float *zbuf = nullptr;          // 2 rotating adjoint slots
     float *img = nullptr;           // per-shot image accumulators
+    // TMA descriptors of the buffers the per-step kernels stage tiles from
+    CUtensorMap tm_f{}, tm_d{}, tm_z{}, tm_ck{};   // fbuf, dbuf, zbuf (2 slots), checkpoints
     float *dsyn = nullptr, *resid = nullptr;
     double *partials = nullptr, *J = nullptr;
     double *rowsum = nullptr;       // [NZ][nx] FP64 partial sums of the shot sum
@@ -213,7 +215,8 @@ int sweep_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
     if (born && cudaMemsetAsync(p->dbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
     for (int n = 0; n < p->nt_max; ++n) {
-        float *cur = slot(p->fbuf, ps, n & 1), *prev = slot(p->fbuf, ps, (n + 1) & 1), *next = prev;
+        const int cur = n & 1;     // u^n in fbuf slot n&1; u^{n-1} and u^{n+1} in the other
+        float *prev = slot(p->fbuf, ps, (n + 1) & 1), *next = prev;
         float *ckc = nullptr, *ckp = nullptr, *tout = nullptr;
         if (p->full) {
             tout = slot(p->hist, ps, n + 1);
@@ -222,13 +225,13 @@ int sweep_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
             ckp = slot(p->hist, ps, 2LL * (n / p->k) + 1);
         }
         if (born) {
-            BornArgs a{p->W, p->rho_pad, cur, prev, next, slot(p->dbuf, ps, n & 1),
+            BornArgs a{p->W, p->rho_pad, cur, prev, next, n & 1,
                        slot(p->dbuf, ps, (n + 1) & 1), slot(p->dbuf, ps, (n + 1) & 1), ckc, ckp,
                        traces, tout, n};
-            launch_born(p->geo, a, st);
+            launch_born(p->geo, a, p->tm_f, p->tm_d, st);
         } else {
             FwdArgs a{p->W, cur, prev, next, ckc, ckp, traces, tout, n};
-            launch_fwd(p->geo, a, st);
+            launch_fwd(p->geo, a, p->tm_f, st);
         }
     }
     return check_launch(p);
@@ -258,9 +261,8 @@ int sweep_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
     if (cudaMemsetAsync(p->zbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
     auto adj = [&](int n, const float *T) {
-        AdjArgs a{p->W, slot(p->zbuf, ps, (n + 1) & 1), slot(p->zbuf, ps, n & 1), T, resid, p->img,
-                  n, born ? 1 : 0};
-        launch_adj(p->geo, a, st);
+        AdjArgs a{p->W, (n + 1) & 1, slot(p->zbuf, ps, n & 1), T, resid, p->img, n, born ? 1 : 0};
+        launch_adj(p->geo, a, p->tm_z, st);
     };
     if (p->full) {
         for (int n = p->nt_max - 1; n >= 0; --n) adj(n, slot(p->hist, ps, n + 1));
@@ -275,9 +277,10 @@ int sweep_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
                               : m == a - 1 ? slot(p->hist, ps, 2LL * j + 1) : slot(p->fbuf, ps, m & 1);
             };
             for (int n = a; n < e; ++n) {
-                FwdArgs f{p->W, U(n), U(n - 1), slot(p->fbuf, ps, (n + 1) & 1), nullptr, nullptr, nullptr,
-                          slot(p->rbuf, ps, n - a), n};
-                launch_fwd(p->geo, f, st);
+                // u^n: checkpoint slot 2j (n = a) or fbuf slot n&1
+                FwdArgs f{p->W, n == a ? 2 * j : (n & 1), U(n - 1), slot(p->fbuf, ps, (n + 1) & 1), nullptr,
+                          nullptr, nullptr, slot(p->rbuf, ps, n - a), n};
+                launch_fwd(p->geo, f, n == a ? p->tm_ck : p->tm_f, st);
             }
             for (int n = e - 1; n >= a; --n) adj(n, slot(p->rbuf, ps, n - a));
         }
@@ -622,6 +625,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     Geo &G = p->geo;
     G.NZ = p->NZ; G.NX = p->NX; G.pitch = p->pitch; G.nb = p->nb; G.S = S;
     G.tz = TZ; G.ntz = ntz; G.ntx = ntx; G.ntiles = ntiles; G.field = p->field;
+    G.err = p->err;
     G.rz = (float)((g->dx * g->dx) / (g->dz * g->dz));
     p->K = g->dt * g->dt / t5040;
     G.iscale = (float)(-1.0 / (g->dt * g->dt));
@@ -629,6 +633,19 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     G.inj_scale = (float)t5040;
     G.nt = d_nt; G.src_pt = d_src; G.ws = d_ws; G.dGz = d_Gz; G.dGx = d_Gx;
     G.trec_off = d_toff; G.trec_pt = d_tpt; G.trec_col = d_tcol; G.tr_off = d_troff; G.nrec = d_nrec;
+    {
+        std::string why;
+        bool mk = encode_tile_map(&p->tm_f, p->fbuf, p->NX, p->NZ, p->pitch, p->field, S, 2, TZ, &why) &&
+                  encode_tile_map(&p->tm_d, p->dbuf, p->NX, p->NZ, p->pitch, p->field, S, 2, TZ, &why) &&
+                  encode_tile_map(&p->tm_z, p->zbuf, p->NX, p->NZ, p->pitch, p->field, S, 2, TZ, &why);
+        if (mk && !p->full)
+            mk = encode_tile_map(&p->tm_ck, p->hist, p->NX, p->NZ, p->pitch, p->field, S, 2 * p->nck, TZ, &why);
+        if (!mk) {
+            free_bufs(p->bufs);
+            delete p;
+            return fail(nullptr, AAFWI_ERR_CUDA, "tile descriptors: " + why);
+        }
+    }
     {
         std::string why;
         const int rc = setup_persist(p, o.engine, sh, &why);

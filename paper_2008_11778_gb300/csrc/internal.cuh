@@ -1,6 +1,7 @@
 // internal.cuh -- kernel argument blocks and launchers shared by the CUDA
 // translation units of libaafwi.so.  Not part of the public ABI (aafwi.h).
 #pragma once
+#include <cuda.h>              // CUtensorMap (TMA descriptors)
 #include <cuda_runtime.h>
 #include <atomic>
 #include <cstddef>
@@ -24,10 +25,18 @@ constexpr int BY = 8;
 constexpr int SW = TX + 2 * HALO;      // shared tile row length (floats)
 inline bool tile_z_supported(int tz) { return tz == 16 || tz == 32 || tz == 64; }
 
+// The per-step kernels stage their input tile (tz + 8 rows x SW columns, the
+// 4-cell halo included) with one TMA copy from a 4D tensor map of a field
+// buffer: (x < NX, z < NZ, shot, slot) with row pitch `pitch`; cells outside
+// the padded grid (negative or beyond NX / NZ) arrive as zeros.
+bool encode_tile_map(CUtensorMap *m, const float *base, int NX, int NZ, int pitch, long long field, int S,
+                     int slots, int tile_rows, std::string *why);
+
 // Per-plan geometry, all pointers device.
 struct Geo {
     int NZ, NX, pitch, nb, S;
     int tz;                        // tile rows of the per-step kernels
+    int *err;                      // error word (bit 2: a bounded wait ran out)
     int ntz, ntx, ntiles;          // tiles per shot along z, x; total
     long long field;               // floats per shot field (NZ * pitch)
     // The Laplacian is evaluated as T = rz*S_z + S_x with integer weights
@@ -53,7 +62,7 @@ struct Geo {
 // (shot s at + s*field).  u_next may alias u_prev (in-place update).
 struct FwdArgs {
     const float *W;                // Wh [NZ][pitch], then Wl (padded, extension E applied)
-    const float *u_cur;
+    int cur_slot;                  // slot of u^n in the tile map
     const float *u_prev;
     float *u_next;
     float *ck_cur, *ck_prev;       // checkpoint targets for (u^n, u^{n-1}) or null
@@ -65,9 +74,11 @@ struct FwdArgs {
 // Born step: background u and scattered du together (eq. Born).
 struct BornArgs {
     const float *W, *rho;
-    const float *u_cur, *u_prev;
+    int u_slot;                    // slot of u^n in the u tile map
+    const float *u_prev;
     float *u_next;
-    const float *d_cur, *d_prev;
+    int d_slot;                    // slot of du^n in the du tile map
+    const float *d_prev;
     float *d_next;
     float *ck_cur, *ck_prev;
     float *traces;                 // scattered-field gather
@@ -80,7 +91,7 @@ struct BornArgs {
 // L u^n + s^n read as the forward sweep's stored T^n / (5040 dx^2).
 struct AdjArgs {
     const float *W;
-    const float *z1;               // z^{n+1}
+    int z1_slot;                   // slot of z^{n+1} in the z tile map
     float *z2n;                    // in: z^{n+2}; out: z^n (same cells)
     const float *T;                // T^n (slot base)
     const float *resid;            // CSR residual traces
@@ -114,9 +125,10 @@ WorkspacePlan workspace_plan(long long field, int S, int nt_max, long long trace
 cudaError_t init_kernels();  // per-device kernel attributes (dynamic shared memory)
 void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float mcfl,
                  double K, float *W, float *rho_pad, int *err, cudaStream_t st);
-void launch_fwd(const Geo &g, const FwdArgs &a, cudaStream_t st);
-void launch_born(const Geo &g, const BornArgs &a, cudaStream_t st);
-void launch_adj(const Geo &g, const AdjArgs &a, cudaStream_t st);
+void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, cudaStream_t st);
+void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d,
+                 cudaStream_t st);
+void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, cudaStream_t st);
 void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *rowsum, float *out,
                      cudaStream_t st);
 

@@ -30,6 +30,8 @@
 // shared memory with 128-bit loads; each thread owns one float4 column group
 // on tz/8 rows.  Source injection, receiver gather and residual injection are
 // fused into the same launch through a per-(shot, tile) receiver list.
+#include <cudaTypedefs.h>   // PFN_cuTensorMapEncodeTiled
+
 #include "internal.cuh"
 
 namespace aafwi {
@@ -61,29 +63,55 @@ __device__ __forceinline__ void st4g(float *p, float4 v)
     *reinterpret_cast<float4 *>(p) = v;
 }
 
-// Stage rows z0-4 .. z0+SH-5 and columns x0-4 .. x0+TX+3 of field f (row
-// pitch g.pitch) into s; cells outside the padded grid read as zero.
-template <int SH>
-__device__ __forceinline__ void load_tile(Tile *s, const float *f, int z0, int x0, const Geo &g)
+// ---- TMA staging of a tile ------------------------------------------------
+
+constexpr long long TMA_WAIT_LIMIT = 1LL << 20;   // try_wait rounds before giving up
+
+__device__ __forceinline__ unsigned smem_addr(const void *p)
 {
-    const int tid = threadIdx.y * BX + threadIdx.x;
-    constexpr int CH = SW / 4;
-    for (int i = tid; i < SH * CH; i += BX * BY) {
-        const int r = i / CH, c = i - r * CH;
-        const int z = z0 - HALO + r;
-        const int x = x0 - HALO + 4 * c;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (z >= 0 && z < g.NZ && x >= 0 && x < g.pitch) {
-            v = ld4g(f + (long long)z * g.pitch + x);
-            if (x + 3 >= g.NX) {
-                if (x >= g.NX) v.x = 0.f;
-                if (x + 1 >= g.NX) v.y = 0.f;
-                if (x + 2 >= g.NX) v.z = 0.f;
-                v.w = 0.f;
-            }
-        }
-        *reinterpret_cast<float4 *>(&s[r][4 * c]) = v;
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// Thread (0, 0) arms the CTA's mbarrier for `bytes` and issues the tile
+// copies (rows z0-4 .. z0+SH-5, columns x0-4 .. x0+TX+3 of shot s in the given
+// slots); every thread then waits for them.  x0-4 is a multiple of 4 floats
+// (16 bytes), as TMA requires; z0-4 may be negative (zero fill).  Returns false
+// (and raises bit 2 of the error word) if the copies do not land within the
+// wait limit.
+template <int SH>
+__device__ __forceinline__ bool stage_tiles(unsigned long long *bar, int ntiles, Tile *s0, const CUtensorMap *m0,
+                                            int slot0, Tile *s1, const CUtensorMap *m1, int slot1, int x0, int z0,
+                                            int s, int *err)
+{
+    const unsigned b = smem_addr(bar);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const unsigned bytes = (unsigned)(ntiles * SH * SW * sizeof(float));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(s0)),
+                     "l"(reinterpret_cast<unsigned long long>(m0)), "r"(x0 - HALO), "r"(z0 - HALO), "r"(s),
+                     "r"(slot0), "r"(b)
+                     : "memory");
+        if (ntiles == 2)
+            asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                         " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(s1)),
+                         "l"(reinterpret_cast<unsigned long long>(m1)), "r"(x0 - HALO), "r"(z0 - HALO), "r"(s),
+                         "r"(slot1), "r"(b)
+                         : "memory");
     }
+    __syncthreads();   // the barrier is initialised before anyone waits on it
+    bool ok = false;
+    for (long long i = 0; i < TMA_WAIT_LIMIT && !ok; ++i) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+                     " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(b) : "memory");
+        ok = done != 0;
+    }
+    if (!ok) atomicOr(err, 4);
+    return __syncthreads_and(ok) != 0;   // the whole CTA takes the same branch
 }
 
 __device__ __forceinline__ float d2(float c, float a, float b) { return (a - c) + (b - c); }
@@ -163,7 +191,7 @@ __device__ __forceinline__ void gather(const Geo &g, int s, int tile, int n, con
 }
 
 template <int RZ>
-__global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a)
+__global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a, const __grid_constant__ CUtensorMap tm_u)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y;
@@ -171,10 +199,10 @@ __global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a)
     const int tile = blockIdx.x;
     const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
     const int z0 = tzi * TZ, x0 = txi * TX;
-    __shared__ __align__(16) float su[SH][SW];
+    __shared__ __align__(128) float su[SH][SW];
+    __shared__ unsigned long long bar;
     const long long base = (long long)s * g.field;
-    load_tile<SH>(su, a.u_cur + base, z0, x0, g);
-    __syncthreads();
+    if (!stage_tiles<SH>(&bar, 1, su, &tm_u, a.cur_slot, nullptr, nullptr, 0, x0, z0, s, g.err)) return;
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {
         const float4 dgx = ld4g(g.dGx + x);
@@ -203,7 +231,8 @@ __global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a)
 }
 
 template <int RZ>
-__global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a)
+__global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, const __grid_constant__ CUtensorMap tm_u,
+                                                 const __grid_constant__ CUtensorMap tm_d)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y;
@@ -211,13 +240,12 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a)
     const int tile = blockIdx.x;
     const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
     const int z0 = tzi * TZ, x0 = txi * TX;
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
+    __shared__ unsigned long long bar;
     Tile *su = reinterpret_cast<Tile *>(smem);
-    Tile *sd = su + SH;
+    Tile *sd = su + SH;      // SH * SW * 4 bytes on: a multiple of 128
     const long long base = (long long)s * g.field;
-    load_tile<SH>(su, a.u_cur + base, z0, x0, g);
-    load_tile<SH>(sd, a.d_cur + base, z0, x0, g);
-    __syncthreads();
+    if (!stage_tiles<SH>(&bar, 2, su, &tm_u, a.u_slot, sd, &tm_d, a.d_slot, x0, z0, s, g.err)) return;
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {
         const float4 dgx = ld4g(g.dGx + x);
@@ -256,7 +284,7 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a)
 }
 
 template <int RZ>
-__global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a)
+__global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a, const __grid_constant__ CUtensorMap tm_z)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y;
@@ -264,11 +292,12 @@ __global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a)
     const int tile = blockIdx.x;
     const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
     const int z0 = tzi * TZ, x0 = txi * TX;
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
+    __shared__ unsigned long long bar;
     Tile *sz = reinterpret_cast<Tile *>(smem);
     float(*sinj)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW);
     const long long base = (long long)s * g.field;
-    load_tile<SH>(sz, a.z1 + base, z0, x0, g);
+    if (!stage_tiles<SH>(&bar, 1, sz, &tm_z, a.z1_slot, nullptr, nullptr, 0, x0, z0, s, g.err)) return;
     const int t = s * g.ntiles + tile;
     const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
     const bool has_rec = r1 > r0;
@@ -414,31 +443,60 @@ void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho,
     k_prep<<<1216, 256, 0, st>>>(g, nz, nx, m, rho, mcfl, K, W, rho_pad, err);
 }
 
-void launch_fwd(const Geo &g, const FwdArgs &a, cudaStream_t st)
+bool encode_tile_map(CUtensorMap *m, const float *base, int NX, int NZ, int pitch, long long field, int S,
+                     int slots, int tile_rows, std::string *why)
 {
-    count_launch();
-    const dim3 grid(g.ntiles, g.S), block(BX, BY);
-    if (g.tz == 16) k_fwd<2><<<grid, block, 0, st>>>(g, a);
-    else if (g.tz == 64) k_fwd<8><<<grid, block, 0, st>>>(g, a);
-    else k_fwd<4><<<grid, block, 0, st>>>(g, a);
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            *why = "cuTensorMapEncodeTiled not available";
+            return false;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)NX, (cuuint64_t)NZ, (cuuint64_t)S, (cuuint64_t)slots};
+    const cuuint64_t strides[3] = {(cuuint64_t)pitch * 4, (cuuint64_t)field * 4, (cuuint64_t)field * S * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)SW, (cuuint32_t)(tile_rows + 2 * HALO), 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *why = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+        return false;
+    }
+    return true;
 }
 
-void launch_born(const Geo &g, const BornArgs &a, cudaStream_t st)
+void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, cudaStream_t st)
 {
     count_launch();
     const dim3 grid(g.ntiles, g.S), block(BX, BY);
-    if (g.tz == 16) k_born<2><<<grid, block, born_smem<2>(), st>>>(g, a);
-    else if (g.tz == 64) k_born<8><<<grid, block, born_smem<8>(), st>>>(g, a);
-    else k_born<4><<<grid, block, born_smem<4>(), st>>>(g, a);
+    if (g.tz == 16) k_fwd<2><<<grid, block, 0, st>>>(g, a, tm_u);
+    else if (g.tz == 64) k_fwd<8><<<grid, block, 0, st>>>(g, a, tm_u);
+    else k_fwd<4><<<grid, block, 0, st>>>(g, a, tm_u);
 }
 
-void launch_adj(const Geo &g, const AdjArgs &a, cudaStream_t st)
+void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d, cudaStream_t st)
 {
     count_launch();
     const dim3 grid(g.ntiles, g.S), block(BX, BY);
-    if (g.tz == 16) k_adj<2><<<grid, block, adj_smem<2>(), st>>>(g, a);
-    else if (g.tz == 64) k_adj<8><<<grid, block, adj_smem<8>(), st>>>(g, a);
-    else k_adj<4><<<grid, block, adj_smem<4>(), st>>>(g, a);
+    if (g.tz == 16) k_born<2><<<grid, block, born_smem<2>(), st>>>(g, a, tm_u, tm_d);
+    else if (g.tz == 64) k_born<8><<<grid, block, born_smem<8>(), st>>>(g, a, tm_u, tm_d);
+    else k_born<4><<<grid, block, born_smem<4>(), st>>>(g, a, tm_u, tm_d);
+}
+
+void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, cudaStream_t st)
+{
+    count_launch();
+    const dim3 grid(g.ntiles, g.S), block(BX, BY);
+    if (g.tz == 16) k_adj<2><<<grid, block, adj_smem<2>(), st>>>(g, a, tm_z);
+    else if (g.tz == 64) k_adj<8><<<grid, block, adj_smem<8>(), st>>>(g, a, tm_z);
+    else k_adj<4><<<grid, block, adj_smem<4>(), st>>>(g, a, tm_z);
 }
 
 void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *rowsum, float *out,

@@ -1,7 +1,7 @@
 """The trained learned preconditioner (weights committed under
 paper_2008_11778_gb300/weights, produced by `python -m
 paper_2008_11778_gb300.learned`) against plain AA(10) on a held-out
-400 x 150 model: wall seconds and iterations to J/J0 <= 0.1 on the same GPU."""
+400 x 150 model: wall seconds and iterations to J/J0 <= 1e-2 on the same GPU."""
 import numpy as np
 import pytest
 
@@ -46,7 +46,7 @@ def test_learned_step_features_and_apply(mods):
 def test_learned_aa_beats_plain_aa_on_held_out_model(mods):
     aafwi, learned = mods
     params, meta = learned.load_weights()
-    rows = learned.compare(params, n_eval=1, target=0.1, max_iters=60, log=lambda *a: None)
+    rows = learned.compare(params, n_eval=1, target=1e-2, max_iters=120, log=lambda *a: None)
     r = rows[0]
     assert r["learned"]["reached"]
     assert r["learned"]["learned_steps"] >= 1
