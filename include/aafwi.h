@@ -96,6 +96,9 @@ typedef struct {
     int no_graphs;               /* 0: the per-step sweeps (one launch per time step) are
                                     captured into CUDA graphs once per plan, sweep kind and
                                     caller buffer, and replayed; 1: launched kernel by kernel */
+    int shots_per_batch;         /* 0: planner picks -- all shots if their workspace fits, else
+                                    batches of shots run one after another (full history while a
+                                    batch still fills the GPU, else checkpoints); > 0: this many */
 } aafwi_plan_opts;
 
 /* plan engines */
@@ -118,6 +121,9 @@ typedef struct {
     int n_tiles;                 /* tiles per shot */
     int engine;                  /* AAFWI_ENGINE_PER_STEP, _PERSISTENT or _HYBRID */
     int persist_ctas;            /* strips of the persistent sweeps (0 if per step) */
+    int shots_per_batch, n_batches;   /* the plan's shot batches (1 batch: all shots at once;
+                                         more: the stored forward is not kept between calls,
+                                         AAFWI_REUSE_FORWARD returns STATE) */
 } aafwi_plan_info;
 
 /* ---- plan -------------------------------------------------------------- */

@@ -32,6 +32,7 @@ struct Buf {
 struct aafwi_plan {
     int device = 0;
     int nx = 0, nz = 0, nb = 0, NZ = 0, NX = 0, pitch = 0, S = 0, nt_max = 0;
+    int Sb = 0, nbatch = 1;         // shots per batch (the wavefield buffers hold Sb shots), batches
     double dx = 0, dz = 0, dt = 0;
     std::vector<int> nt;
     std::vector<long long> tr_off;
@@ -50,8 +51,11 @@ struct aafwi_plan {
     float *dbuf = nullptr;          // 2 rotating Born slots
     float *zbuf = nullptr;          // 2 rotating adjoint slots
     float *img = nullptr;           // per-shot image accumulators
-    // TMA descriptors of the buffers the per-step kernels stage tiles from
-    CUtensorMap tm_f{}, tm_d{}, tm_z{}, tm_ck{};   // fbuf, dbuf, zbuf (2 slots), checkpoints
+    // TMA descriptors of the buffers the per-step kernels stage from: halo
+    // boxes of fbuf, dbuf, zbuf and the checkpoints; interior boxes of fbuf,
+    // zbuf, the checkpoints and the T history / replay buffer
+    CUtensorMap tm_f{}, tm_d{}, tm_z{}, tm_ck{};
+    CUtensorMap tm_fi{}, tm_zi{}, tm_cki{}, tm_t{};
     float *dsyn = nullptr, *resid = nullptr;
     double *partials = nullptr, *J = nullptr;
     double *rowsum = nullptr;       // [NZ][nx] FP64 partial sums of the shot sum
@@ -131,7 +135,7 @@ bool upload(std::vector<Buf> &bufs, T **out, const std::vector<T> &h)
 float *slot(float *base, long long per_slot, long long i) { return base + per_slot * i; }
 
 enum { SWEEP_FWD = 0, SWEEP_BORN = 1, SWEEP_ADJ = 2, SWEEP_ADJ_BORN = 3 };
-constexpr size_t kMaxSweepGraphs = 8;
+constexpr size_t kMaxSweepGraphs = 8;   // per batch
 
 void drop_graphs(aafwi_plan *p)
 {
@@ -170,7 +174,7 @@ int run_graph(aafwi_plan *p, int kind, const void *ptr, cudaStream_t st, F body)
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(p, e, "graph instantiate");
-        if (gs.size() == kMaxSweepGraphs) {
+        if (gs.size() >= kMaxSweepGraphs * (size_t)p->nbatch) {
             cudaGraphExecDestroy(gs.front().exec);
             gs.erase(gs.begin());
         }
@@ -203,13 +207,22 @@ int run_persist_forward(aafwi_plan *p, float *traces, cudaStream_t st)
     return AAFWI_OK;
 }
 
-// Per-step forward sweep over all shots (born: u and du together).  u^n and
-// u^{n-1} rotate in fbuf (u^{n+1} overwrites u^{n-1} in place); with the full
-// history T^n goes to history slot n+1, else (u^n, u^{n-1}) are checkpointed
-// every k steps.
-int sweep_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
+// Geometry of batch b (shots b*Sb .. ; the per-shot tables stay global).
+Geo batch_geo(const aafwi_plan *p, int b)
 {
-    const long long ps = (long long)p->S * p->field;
+    Geo g = p->geo;
+    g.shot0 = b * p->Sb;
+    g.S = std::min(p->Sb, p->S - g.shot0);
+    return g;
+}
+
+// Per-step forward sweep over the batch's shots (born: u and du together).
+// u^n and u^{n-1} rotate in fbuf (u^{n+1} overwrites u^{n-1} in place); with
+// the full history T^n goes to history slot n+1, else (u^n, u^{n-1}) are
+// checkpointed every k steps.
+int sweep_forward(aafwi_plan *p, const Geo &g, bool born, float *traces, cudaStream_t st)
+{
+    const long long ps = (long long)p->Sb * p->field;
     if (cudaMemsetAsync(p->fbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
     if (born && cudaMemsetAsync(p->dbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
@@ -228,71 +241,70 @@ int sweep_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
             BornArgs a{p->W, p->rho_pad, cur, prev, next, n & 1,
                        slot(p->dbuf, ps, (n + 1) & 1), slot(p->dbuf, ps, (n + 1) & 1), ckc, ckp,
                        traces, tout, n};
-            launch_born(p->geo, a, p->tm_f, p->tm_d, st);
+            launch_born(g, a, p->tm_f, p->tm_d, st);
         } else {
-            FwdArgs a{p->W, cur, prev, next, ckc, ckp, traces, tout, n};
-            launch_fwd(p->geo, a, p->tm_f, st);
+            FwdArgs a{p->W, cur, (n + 1) & 1, next, ckc, ckp, traces, tout, n};
+            launch_fwd(g, a, p->tm_f, p->tm_fi, st);
         }
     }
     return check_launch(p);
 }
 
-// Forward sweep over all shots (born: u and du together); traces -> CSR.
-int run_forward(aafwi_plan *p, bool born, float *traces, cudaStream_t st)
+// Forward sweep over batch b (born: u and du together); traces -> CSR.
+int run_forward(aafwi_plan *p, int b, bool born, float *traces, cudaStream_t st)
 {
     p->hist_T = false;
     int rc;
+    const Geo g = batch_geo(p, b);
     if (p->persist_fwd && !born) rc = run_persist_forward(p, traces, st);
-    else if (!p->graphs) rc = sweep_forward(p, born, traces, st);
+    else if (!p->graphs) rc = sweep_forward(p, g, born, traces, st);
     else
-        rc = run_graph(p, born ? SWEEP_BORN : SWEEP_FWD, traces, st,
-                       [&](cudaStream_t cs) { return sweep_forward(p, born, traces, cs); });
+        rc = run_graph(p, (born ? SWEEP_BORN : SWEEP_FWD) + 4 * b, traces, st,
+                       [&](cudaStream_t cs) { return sweep_forward(p, g, born, traces, cs); });
     p->hist_T = rc == AAFWI_OK && p->full;
     return rc;
 }
 
 // Per-step adjoint sweep with imaging into p->img (checkpoint mode: segment
 // replays from the stored checkpoints in between).
-int sweep_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
+int sweep_adjoint(aafwi_plan *p, const Geo &g, bool born, const float *resid, cudaStream_t st)
 {
-    const long long ps = (long long)p->S * p->field;
+    const long long ps = (long long)p->Sb * p->field;
     if (cudaMemsetAsync(p->img, 0, ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
     if (cudaMemsetAsync(p->zbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
-    auto adj = [&](int n, const float *T) {
-        AdjArgs a{p->W, (n + 1) & 1, slot(p->zbuf, ps, n & 1), T, resid, p->img, n, born ? 1 : 0};
-        launch_adj(p->geo, a, p->tm_z, st);
+    auto adj = [&](int n, int t_slot) {   // T^n in slot t_slot of the T map
+        AdjArgs a{p->W, (n + 1) & 1, n & 1, slot(p->zbuf, ps, n & 1), t_slot, resid, p->img, n, born ? 1 : 0};
+        launch_adj(g, a, p->tm_z, p->tm_zi, p->tm_t, st);
     };
     if (p->full) {
-        for (int n = p->nt_max - 1; n >= 0; --n) adj(n, slot(p->hist, ps, n + 1));
+        for (int n = p->nt_max - 1; n >= 0; --n) adj(n, n + 1);
     } else {
         // segment j = steps [a, e): replay the forward from its checkpoint
         // (u^a, u^{a-1}) storing T^a .. T^{e-1} in rbuf, then step back
         // through it.  u^m, m > a, rotates in fbuf (checkpoints stay intact).
         for (int j = p->nck - 1; j >= 0; --j) {
             const int a = j * p->k, e = std::min(a + p->k, p->nt_max);
-            auto U = [&](int m) {
-                return m == a ? slot(p->hist, ps, 2LL * j)
-                              : m == a - 1 ? slot(p->hist, ps, 2LL * j + 1) : slot(p->fbuf, ps, m & 1);
-            };
+            // u^m: checkpoint slot 2j (m = a), 2j+1 (m = a-1), else fbuf slot m&1
+            auto ck = [&](int m) { return m == a || m == a - 1; };
+            auto uslot = [&](int m) { return m == a ? 2 * j : m == a - 1 ? 2 * j + 1 : (m & 1); };
             for (int n = a; n < e; ++n) {
-                // u^n: checkpoint slot 2j (n = a) or fbuf slot n&1
-                FwdArgs f{p->W, n == a ? 2 * j : (n & 1), U(n - 1), slot(p->fbuf, ps, (n + 1) & 1), nullptr,
+                FwdArgs f{p->W, uslot(n), uslot(n - 1), slot(p->fbuf, ps, (n + 1) & 1), nullptr,
                           nullptr, nullptr, slot(p->rbuf, ps, n - a), n};
-                launch_fwd(p->geo, f, n == a ? p->tm_ck : p->tm_f, st);
+                launch_fwd(g, f, ck(n) ? p->tm_ck : p->tm_f, ck(n - 1) ? p->tm_cki : p->tm_fi, st);
             }
-            for (int n = e - 1; n >= a; --n) adj(n, slot(p->rbuf, ps, n - a));
+            for (int n = e - 1; n >= a; --n) adj(n, n - a);
         }
     }
     return check_launch(p);
 }
 
-// Adjoint sweep with imaging into p->img (born: scale -1, else -1/m).
-int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
+// Adjoint sweep of batch b with imaging into p->img (born: scale -1, else -1/m).
+int run_adjoint(aafwi_plan *p, int b, bool born, const float *resid, cudaStream_t st)
 {
     if (p->persist_adj && p->hist_T) {
-        const long long ps = (long long)p->S * p->field;
+        const long long ps = (long long)p->Sb * p->field;
         if (cudaMemsetAsync(p->img, 0, ps * sizeof(float), st) != cudaSuccess)
             return cuda_fail(p, cudaGetLastError(), "memset");
         cudaError_t e = cudaMemsetAsync(p->pgeo.flags, 0, p->pgeo.P * sizeof(unsigned), st);
@@ -302,9 +314,10 @@ int run_adjoint(aafwi_plan *p, bool born, const float *resid, cudaStream_t st)
         if (e != cudaSuccess) return cuda_fail(p, e, "persistent adjoint launch");
         return AAFWI_OK;
     }
-    if (!p->graphs) return sweep_adjoint(p, born, resid, st);
-    return run_graph(p, born ? SWEEP_ADJ_BORN : SWEEP_ADJ, resid, st,
-                     [&](cudaStream_t cs) { return sweep_adjoint(p, born, resid, cs); });
+    const Geo g = batch_geo(p, b);
+    if (!p->graphs) return sweep_adjoint(p, g, born, resid, st);
+    return run_graph(p, (born ? SWEEP_ADJ_BORN : SWEEP_ADJ) + 4 * b, resid, st,
+                     [&](cudaStream_t cs) { return sweep_adjoint(p, g, born, resid, cs); });
 }
 
 int prep(aafwi_plan *p, const float *m, const float *rho, cudaStream_t st)
@@ -348,6 +361,7 @@ int setup_persist(aafwi_plan *p, int engine, const aafwi_shots *sh, std::string 
         return AAFWI_OK;
     };
     if (!p->full) return no("needs the full wavefield history");
+    if (p->nbatch > 1) return no("the shots do not fit in one batch");
     int dev = 0, sms = 0, coop = 0, smem_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -433,24 +447,65 @@ int setup_persist(aafwi_plan *p, int engine, const aafwi_shots *sh, std::string 
 
 void aafwi::set_call_error(const std::string &msg) { g_create_error = msg; }
 
-// Workspace of a plan: buffers every plan holds, the full-history size, the
-// budget, and whether the full history is kept (else checkpoints).
-WorkspacePlan aafwi::workspace_plan(long long field, int S, int nt_max, long long trace_count,
-                                    const aafwi_plan_opts &o)
+// Layout of a plan's workspace: how many shots the wavefield buffers hold
+// (shot batches), full T history or checkpoints, and the bytes.
+//   * Full history for all shots if it fits the budget.
+//   * Else full history for batches of shots, if a batch still covers at
+//     least kMinBatchCells grid points per time step (enough to fill the GPU):
+//     no replay sweep is needed.
+//   * Else checkpoints every k ~ sqrt(2 nt) steps for the largest batch that fits.
+// opts.checkpoint_every = 1 forces the full history, >= 2 checkpoints every
+// that many steps; opts.shots_per_batch > 0 fixes the batch size.
+PlanLayout aafwi::plan_layout(long long field, long long cells, int S, int nt_max, long long trace_count,
+                              const aafwi_plan_opts &o)
 {
-    WorkspacePlan w;
-    const size_t F = (size_t)field * sizeof(float), SF = F * S;
-    // W pair + rho; fbuf, dbuf, zbuf (2 slots each) + img; dsyn + resid
-    w.fixed = 3 * F + (2 + 2 + 2 + 1) * SF + 2 * (size_t)trace_count * sizeof(float) + (1 << 20);
-    w.budget = o.max_workspace_bytes;
-    if (w.budget == 0) {
+    constexpr long long kMinBatchCells = 4LL << 20;
+    PlanLayout L{};
+    size_t budget = o.max_workspace_bytes;
+    if (budget == 0) {
         size_t fr = 0, tot = 0;
         cudaMemGetInfo(&fr, &tot);
-        w.budget = (size_t)(0.85 * (double)fr);
+        budget = (size_t)(0.85 * (double)fr);
     }
-    w.full_bytes = w.fixed + (size_t)(nt_max + 1) * SF;
-    w.full = o.checkpoint_every == 1 || (o.checkpoint_every == 0 && w.full_bytes <= w.budget);
-    return w;
+    L.budget = budget;
+    const size_t F = (size_t)field * sizeof(float);
+    auto fixed = [&](int Sb) {   // W pair + rho; fbuf, dbuf, zbuf (2 slots each) + img; dsyn + resid
+        return 3 * F + (2 + 2 + 2 + 1) * F * Sb + 2 * (size_t)trace_count * sizeof(float) + (1 << 20);
+    };
+    const int k = o.checkpoint_every >= 2 ? o.checkpoint_every
+                                          : std::max(2, (int)std::lround(std::sqrt(2.0 * nt_max)));
+    const int nck = (nt_max + k - 1) / k;
+    auto full_bytes = [&](int Sb) { return fixed(Sb) + (size_t)(nt_max + 1) * F * Sb; };
+    auto ck_bytes = [&](int Sb) { return fixed(Sb) + (size_t)(2 * nck + k) * F * Sb; };
+    auto take = [&](int Sb, bool full) {
+        L.Sb = Sb;
+        L.nbatch = (S + Sb - 1) / Sb;
+        L.full = full;
+        L.k = full ? 1 : k;
+        L.nck = full ? 0 : nck;
+        L.bytes = full ? full_bytes(Sb) : ck_bytes(Sb);
+        L.fits = L.bytes <= budget;
+        return L;
+    };
+    std::vector<int> sizes;   // candidate batch sizes, largest first
+    if (o.shots_per_batch > 0) {
+        sizes.push_back(std::min(S, o.shots_per_batch));
+    } else {
+        for (int nb = 1; nb <= S; ++nb) {
+            const int Sb = (S + nb - 1) / nb;
+            if (sizes.empty() || Sb != sizes.back()) sizes.push_back(Sb);
+        }
+    }
+    if (o.checkpoint_every <= 1) {
+        for (int Sb : sizes)
+            if (full_bytes(Sb) <= budget &&
+                (o.checkpoint_every == 1 || Sb == S || Sb == sizes.front() || Sb * cells >= kMinBatchCells))
+                return take(Sb, true);
+        if (o.checkpoint_every == 1) return take(sizes.back(), true);   // does not fit: reported by the caller
+    }
+    for (int Sb : sizes)
+        if (ck_bytes(Sb) <= budget) return take(Sb, false);
+    return take(sizes.back(), false);
 }
 
 extern "C" {
@@ -565,22 +620,15 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     const double t5040 = 5040.0 * g->dx * g->dx;
     for (int n = 0; n < p->nt_max; ++n) ws[n] = (float)(t5040 * wavelet[n] / (g->dx * g->dz));
     // workspace plan
-    const WorkspacePlan wp = workspace_plan(p->field, S, p->nt_max, p->trace_count, o);
-    const size_t SF = (size_t)p->field * sizeof(float) * S;
-    const size_t fixed = wp.fixed, budget = wp.budget, full_bytes = wp.full_bytes;
-    int k = o.checkpoint_every;
-    if (wp.full) {
-        p->full = true;
-        p->k = 1;
-        p->ws_bytes = full_bytes;
-    } else {
-        if (k <= 1) k = std::max(2, (int)std::lround(std::sqrt(2.0 * p->nt_max)));
-        p->full = false;
-        p->k = k;
-        p->nck = (p->nt_max + k - 1) / k;
-        p->ws_bytes = fixed + (size_t)(2 * p->nck + k) * SF;
-    }
-    if (p->ws_bytes > budget) {
+    const PlanLayout lay = plan_layout(p->field, (long long)p->NZ * p->NX, S, p->nt_max, p->trace_count, o);
+    p->Sb = lay.Sb;
+    p->nbatch = lay.nbatch;
+    p->full = lay.full;
+    p->k = lay.k;
+    p->nck = lay.nck;
+    p->ws_bytes = lay.bytes;
+    const size_t budget = lay.budget;
+    if (!lay.fits) {
         char b[200];
         snprintf(b, sizeof b, "workspace %.2f GB exceeds the budget %.2f GB", p->ws_bytes / 1e9, budget / 1e9);
         delete p;
@@ -597,7 +645,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
               upload(p->bufs, &d_tcol, trec_col_nz) && upload(p->bufs, &d_nrec, nrec) &&
               upload(p->bufs, &d_ws, ws) && upload(p->bufs, &d_Gz, dGz) && upload(p->bufs, &d_Gx, dGx) &&
               upload(p->bufs, &d_troff, p->tr_off);
-    const long long ps = (long long)S * p->field;
+    const long long ps = (long long)p->Sb * p->field;   // one slot: the batch's shots
     ok = ok && dalloc(p->bufs, &p->W, 2 * p->field) && dalloc(p->bufs, &p->rho_pad, p->field) &&
          dalloc(p->bufs, &p->dbuf, 2 * ps) && dalloc(p->bufs, &p->zbuf, 2 * ps) && dalloc(p->bufs, &p->fbuf, 2 * ps) &&
          dalloc(p->bufs, &p->img, ps) && dalloc(p->bufs, &p->dsyn, p->trace_count) &&
@@ -623,7 +671,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
         return cuda_fail(nullptr, e, "plan initialisation");
     }
     Geo &G = p->geo;
-    G.NZ = p->NZ; G.NX = p->NX; G.pitch = p->pitch; G.nb = p->nb; G.S = S;
+    G.NZ = p->NZ; G.NX = p->NX; G.pitch = p->pitch; G.nb = p->nb; G.S = p->Sb; G.shot0 = 0;
     G.tz = TZ; G.ntz = ntz; G.ntx = ntx; G.ntiles = ntiles; G.field = p->field;
     G.err = p->err;
     G.rz = (float)((g->dx * g->dx) / (g->dz * g->dz));
@@ -635,11 +683,16 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     G.trec_off = d_toff; G.trec_pt = d_tpt; G.trec_col = d_tcol; G.tr_off = d_troff; G.nrec = d_nrec;
     {
         std::string why;
-        bool mk = encode_tile_map(&p->tm_f, p->fbuf, p->NX, p->NZ, p->pitch, p->field, S, 2, TZ, &why) &&
-                  encode_tile_map(&p->tm_d, p->dbuf, p->NX, p->NZ, p->pitch, p->field, S, 2, TZ, &why) &&
-                  encode_tile_map(&p->tm_z, p->zbuf, p->NX, p->NZ, p->pitch, p->field, S, 2, TZ, &why);
+        auto map = [&](CUtensorMap *m, const float *buf, int slots, bool halo) {
+            return encode_tile_map(m, buf, p->NX, p->NZ, p->pitch, p->field, p->Sb, slots, TZ, halo, &why);
+        };
+        bool mk = map(&p->tm_f, p->fbuf, 2, true) && map(&p->tm_fi, p->fbuf, 2, false) &&
+                  map(&p->tm_d, p->dbuf, 2, true) && map(&p->tm_z, p->zbuf, 2, true) &&
+                  map(&p->tm_zi, p->zbuf, 2, false);
+        if (mk && p->full) mk = map(&p->tm_t, p->hist, p->nt_max + 1, false);
         if (mk && !p->full)
-            mk = encode_tile_map(&p->tm_ck, p->hist, p->NX, p->NZ, p->pitch, p->field, S, 2 * p->nck, TZ, &why);
+            mk = map(&p->tm_ck, p->hist, 2 * p->nck, true) && map(&p->tm_cki, p->hist, 2 * p->nck, false) &&
+                 map(&p->tm_t, p->rbuf, p->k, false);
         if (!mk) {
             free_bufs(p->bufs);
             delete p;
@@ -689,6 +742,8 @@ int aafwi_plan_get_info(const aafwi_plan *p, aafwi_plan_info *info)
     info->engine = p->persist_fwd ? AAFWI_ENGINE_PERSISTENT
                    : p->persist_adj ? AAFWI_ENGINE_HYBRID : AAFWI_ENGINE_PER_STEP;
     info->persist_ctas = p->persist_adj ? p->pgeo.P : 0;
+    info->shots_per_batch = p->Sb;
+    info->n_batches = p->nbatch;
     return AAFWI_OK;
 }
 
@@ -699,11 +754,12 @@ int aafwi_model_forward(aafwi_plan *p, const float *m, float *d_out, aafwi_strea
     int rc;
     p->fwd_valid = false;
     if ((rc = prep(p, m, nullptr, st))) return rc;
-    if ((rc = run_forward(p, false, p->dsyn, st))) return rc;
+    for (int b = 0; b < p->nbatch; ++b)
+        if ((rc = run_forward(p, b, false, p->dsyn, st))) return rc;
     if (d_out && d_out != p->dsyn &&
         cudaMemcpyAsync(d_out, p->dsyn, p->trace_count * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "copy traces");
-    p->fwd_valid = true;
+    p->fwd_valid = p->nbatch == 1;   // with batches only the last batch's wavefield is kept
     p->fwd_model = m;
     return AAFWI_OK;
 }
@@ -715,7 +771,8 @@ int aafwi_born_forward(aafwi_plan *p, const float *m0, const float *rho, float *
     int rc;
     p->fwd_valid = false;
     if ((rc = prep(p, m0, rho, st))) return rc;
-    if ((rc = run_forward(p, true, d_out, st))) return rc;
+    for (int b = 0; b < p->nbatch; ++b)
+        if ((rc = run_forward(p, b, true, d_out, st))) return rc;
     return AAFWI_OK;
 }
 
@@ -736,6 +793,49 @@ int aafwi_read_misfit(aafwi_plan *p, double *J_host, aafwi_stream stream)
     return finish_sync(p, J_host, (cudaStream_t)stream);
 }
 
+namespace {
+
+// CSR trace range [first, first + count) of batch b.
+void batch_traces(const aafwi_plan *p, int b, long long *first, long long *count)
+{
+    const int s0 = b * p->Sb, s1 = std::min(p->S, s0 + p->Sb);
+    *first = p->tr_off[s0];
+    *count = (s1 < p->S ? p->tr_off[s1] : p->trace_count) - *first;
+}
+
+// Adjoint sweeps of every batch (the forward of each batch first -- the Born
+// pair when fwd_born -- unless the stored one is reused), imaging (Born scale
+// when adj_born), shot sum and E^T into out.  With d_obs the adjoint source is
+// the residual d_syn - d_obs of each batch (and J is formed over all traces),
+// else adj_src.
+int gradient_pass(aafwi_plan *p, bool fwd_born, bool adj_born, bool reuse, const float *d_obs, const float *adj_src,
+                  float *out, cudaStream_t st)
+{
+    int rc;
+    for (int b = 0; b < p->nbatch; ++b) {
+        if (!reuse && (rc = run_forward(p, b, fwd_born, d_obs ? p->dsyn : nullptr, st))) return rc;
+        const float *r = adj_src;
+        if (d_obs) {
+            if (p->nbatch == 1) {
+                launch_misfit(p->dsyn, d_obs, p->resid, p->trace_count, p->partials, p->J, st);
+            } else {
+                long long first, count;
+                batch_traces(p, b, &first, &count);
+                launch_misfit(p->dsyn + first, d_obs + first, p->resid + first, count, p->partials, p->J, st);
+            }
+            r = p->resid;
+        }
+        if ((rc = run_adjoint(p, b, adj_born, r, st))) return rc;
+        launch_shot_sum(batch_geo(p, b), p->nz, p->nx, p->img, p->rowsum, b > 0,
+                        b + 1 == p->nbatch ? out : nullptr, st);
+    }
+    if (d_obs && p->nbatch > 1)   // J over all traces, in the same order as without batches
+        launch_misfit(p->dsyn, d_obs, nullptr, p->trace_count, p->partials, p->J, st);
+    return check_launch(p);
+}
+
+}  // namespace
+
 int aafwi_adjoint_gradient(aafwi_plan *p, int mode, const float *m, const float *rho, const float *d_obs,
                            float *grad, double *J_host, int flags, aafwi_stream stream)
 {
@@ -745,20 +845,17 @@ int aafwi_adjoint_gradient(aafwi_plan *p, int mode, const float *m, const float 
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
     const bool born = mode == AAFWI_MODE_LSRTM;
-    if (!born && (flags & AAFWI_REUSE_FORWARD)) {
+    const bool reuse = !born && (flags & AAFWI_REUSE_FORWARD);
+    if (reuse) {
         if (!p->fwd_valid || p->fwd_model != m)
             return fail(p, AAFWI_ERR_STATE, "no stored forward wavefield for this model");
     } else {
         p->fwd_valid = false;
         if ((rc = prep(p, m, born ? rho : nullptr, st))) return rc;
-        if ((rc = run_forward(p, born, p->dsyn, st))) return rc;
     }
-    launch_misfit(p->dsyn, d_obs, p->resid, p->trace_count, p->partials, p->J, st);
-    if ((rc = run_adjoint(p, born, p->resid, st))) return rc;
-    launch_shot_sum(p->geo, p->nz, p->nx, p->img, p->rowsum, grad, st);
-    if ((rc = check_launch(p))) return rc;
+    if ((rc = gradient_pass(p, born, born, reuse, d_obs, nullptr, grad, st))) return rc;
     if (!born) {
-        p->fwd_valid = true;
+        p->fwd_valid = p->nbatch == 1;
         p->fwd_model = m;
     }
     return finish_sync(p, J_host, st);
@@ -770,18 +867,16 @@ int aafwi_fwi_adjoint(aafwi_plan *p, const float *m, const float *adj_src, float
     if (!p || !m || !adj_src || !grad) return fail(p, AAFWI_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
-    if (flags & AAFWI_REUSE_FORWARD) {
+    const bool reuse = flags & AAFWI_REUSE_FORWARD;
+    if (reuse) {
         if (!p->fwd_valid || p->fwd_model != m)
             return fail(p, AAFWI_ERR_STATE, "no stored forward wavefield for this model");
     } else {
         p->fwd_valid = false;
         if ((rc = prep(p, m, nullptr, st))) return rc;
-        if ((rc = run_forward(p, false, p->dsyn, st))) return rc;
     }
-    if ((rc = run_adjoint(p, false, adj_src, st))) return rc;
-    launch_shot_sum(p->geo, p->nz, p->nx, p->img, p->rowsum, grad, st);
-    if ((rc = check_launch(p))) return rc;
-    p->fwd_valid = true;
+    if ((rc = gradient_pass(p, false, false, reuse, nullptr, adj_src, grad, st))) return rc;
+    p->fwd_valid = p->nbatch == 1;
     p->fwd_model = m;
     return AAFWI_OK;
 }
@@ -793,10 +888,7 @@ int aafwi_born_adjoint(aafwi_plan *p, const float *m0, const float *resid, float
     int rc;
     p->fwd_valid = false;
     if ((rc = prep(p, m0, nullptr, st))) return rc;
-    if ((rc = run_forward(p, false, nullptr, st))) return rc;
-    if ((rc = run_adjoint(p, true, resid, st))) return rc;
-    launch_shot_sum(p->geo, p->nz, p->nx, p->img, p->rowsum, img, st);
-    return check_launch(p);
+    return gradient_pass(p, false, true, false, nullptr, resid, img, st);
 }
 
 // ---------------------------------------------------------------------------

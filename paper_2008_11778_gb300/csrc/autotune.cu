@@ -80,7 +80,9 @@ extern "C" int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, 
         traces += (long long)nt[s] * (shots->rec_off[s + 1] - shots->rec_off[s]);
         nt[s] = std::min(nt[s], steps);
     }
-    const bool full = workspace_plan((long long)NZ * pitch, S, nt_max, traces, o).full;
+    const int NX = grid->nx + 2 * grid->nb;
+    const PlanLayout lay = plan_layout((long long)NZ * pitch, (long long)NZ * NX, S, nt_max, traces, o);
+    const bool full = lay.full && lay.nbatch == 1;   // what the persistent engines need
     std::vector<Candidate> cands;
     auto allowed = [&](int e) { return o.engine == AAFWI_ENGINE_AUTO || o.engine == e; };
     if (allowed(AAFWI_ENGINE_PER_STEP))
@@ -88,7 +90,8 @@ extern "C" int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, 
     if (full && allowed(AAFWI_ENGINE_PERSISTENT)) cands.push_back({AAFWI_ENGINE_PERSISTENT, 0});
     if (full && allowed(AAFWI_ENGINE_HYBRID))
         for (int tz : {16, 32, 64}) cands.push_back({AAFWI_ENGINE_HYBRID, tz});
-    if (cands.empty()) return tune_fail(AAFWI_ERR_ARG, "autotune: the persistent engines need the full history");
+    if (cands.empty())
+        return tune_fail(AAFWI_ERR_ARG, "autotune: the persistent engines need the full history of all shots at once");
     aafwi_shots sh = *shots;
     sh.nt = nt.data();
     Scratch sc;

@@ -25,16 +25,19 @@ constexpr int BY = 8;
 constexpr int SW = TX + 2 * HALO;      // shared tile row length (floats)
 inline bool tile_z_supported(int tz) { return tz == 16 || tz == 32 || tz == 64; }
 
-// The per-step kernels stage their input tile (tz + 8 rows x SW columns, the
-// 4-cell halo included) with one TMA copy from a 4D tensor map of a field
-// buffer: (x < NX, z < NZ, shot, slot) with row pitch `pitch`; cells outside
-// the padded grid (negative or beyond NX / NZ) arrive as zeros.
+// The per-step kernels stage their inputs with TMA copies from 4D tensor
+// maps of the field buffers: (x < NX, z < NZ, shot, slot) with row pitch
+// `pitch`.  A halo map's box is a tile with its 4-cell halo (tz + 8 rows x SW
+// columns), an interior map's box the tile alone (tz x TX); cells outside the
+// padded grid (negative or beyond NX / NZ) arrive as zeros.
 bool encode_tile_map(CUtensorMap *m, const float *base, int NX, int NZ, int pitch, long long field, int S,
-                     int slots, int tile_rows, std::string *why);
+                     int slots, int tile_rows, bool halo, std::string *why);
 
 // Per-plan geometry, all pointers device.
 struct Geo {
-    int NZ, NX, pitch, nb, S;
+    int NZ, NX, pitch, nb;
+    int S;                         // shots of this launch (a batch); field buffers hold them at s * field
+    int shot0;                     // global index of the batch's first shot (per-shot tables are global)
     int tz;                        // tile rows of the per-step kernels
     int *err;                      // error word (bit 2: a bounded wait ran out)
     int ntz, ntx, ntiles;          // tiles per shot along z, x; total
@@ -62,8 +65,8 @@ struct Geo {
 // (shot s at + s*field).  u_next may alias u_prev (in-place update).
 struct FwdArgs {
     const float *W;                // Wh [NZ][pitch], then Wl (padded, extension E applied)
-    int cur_slot;                  // slot of u^n in the tile map
-    const float *u_prev;
+    int cur_slot;                  // slot of u^n in the (halo) tile map
+    int prev_slot;                 // slot of u^{n-1} in the interior map
     float *u_next;
     float *ck_cur, *ck_prev;       // checkpoint targets for (u^n, u^{n-1}) or null
     float *traces;                 // gather target (CSR) or null
@@ -91,9 +94,10 @@ struct BornArgs {
 // L u^n + s^n read as the forward sweep's stored T^n / (5040 dx^2).
 struct AdjArgs {
     const float *W;
-    int z1_slot;                   // slot of z^{n+1} in the z tile map
-    float *z2n;                    // in: z^{n+2}; out: z^n (same cells)
-    const float *T;                // T^n (slot base)
+    int z1_slot;                   // slot of z^{n+1} in the z (halo) tile map
+    int z2_slot;                   // slot of z^{n+2} in the z interior map
+    float *z2n;                    // out: z^n over z^{n+2} (same cells)
+    int t_slot;                    // slot of T^n in the T interior map
     const float *resid;            // CSR residual traces
     float *img;                    // per-shot accumulators [S][field]
     int n;
@@ -114,22 +118,30 @@ inline void count_launch(unsigned n = 1)
 // Message returned by aafwi_last_error(NULL) for calls made without a plan.
 void set_call_error(const std::string &msg);
 
-// Workspace of a plan (api.cu): what every plan holds, the full-history size,
-// the budget (opts or 85 % of free memory) and whether the full history fits.
-struct WorkspacePlan {
-    size_t fixed, full_bytes, budget;
+// Workspace layout of a plan (api.cu): shots per batch, full history or
+// checkpoints, bytes against the budget (opts or 85 % of free memory).
+struct PlanLayout {
+    int Sb, nbatch;
     bool full;
+    int k, nck;
+    size_t bytes, budget;
+    bool fits;
 };
-WorkspacePlan workspace_plan(long long field, int S, int nt_max, long long trace_count, const aafwi_plan_opts &o);
+PlanLayout plan_layout(long long field, long long cells, int S, int nt_max, long long trace_count,
+                       const aafwi_plan_opts &o);
 
 cudaError_t init_kernels();  // per-device kernel attributes (dynamic shared memory)
 void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float mcfl,
                  double K, float *W, float *rho_pad, int *err, cudaStream_t st);
-void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, cudaStream_t st);
+void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_p, cudaStream_t st);
 void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d,
                  cudaStream_t st);
-void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, cudaStream_t st);
-void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *rowsum, float *out,
+void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, const CUtensorMap &tm_z2,
+                const CUtensorMap &tm_t, cudaStream_t st);
+// Shot sum and E^T of the batch's images: rowsum (FP64 [NZ][nx]) = or +=
+// (accumulate) the sum over the batch's shots; the second pass, when out is
+// not null, folds rowsum over z into out [nz][nx].
+void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *rowsum, bool accumulate, float *out,
                      cudaStream_t st);
 
 // Persistent sweeps (persist_kernels.cu): one cooperative launch per sweep,

@@ -72,34 +72,34 @@ __device__ __forceinline__ unsigned smem_addr(const void *p)
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-// Thread (0, 0) arms the CTA's mbarrier for `bytes` and issues the tile
-// copies (rows z0-4 .. z0+SH-5, columns x0-4 .. x0+TX+3 of shot s in the given
-// slots); every thread then waits for them.  x0-4 is a multiple of 4 floats
-// (16 bytes), as TMA requires; z0-4 may be negative (zero fill).  Returns false
-// (and raises bit 2 of the error word) if the copies do not land within the
-// wait limit.
-template <int SH>
-__device__ __forceinline__ bool stage_tiles(unsigned long long *bar, int ntiles, Tile *s0, const CUtensorMap *m0,
-                                            int slot0, Tile *s1, const CUtensorMap *m1, int slot1, int x0, int z0,
-                                            int s, int *err)
+// One TMA tensor copy: destination in shared memory, descriptor, and the
+// start coordinates (x, z, shot, slot) of its box.  x is a multiple of 4
+// floats (16 bytes), as TMA requires; z may be negative (zero fill).
+struct Copy4 {
+    const void *dst;
+    const CUtensorMap *map;
+    int x, z, s, slot;
+};
+
+// Thread (0, 0) arms the CTA's mbarrier for `bytes` and issues the copies;
+// every thread then waits for them.  Returns false (and raises bit 2 of the
+// error word) if they do not land within the wait limit; the whole CTA
+// returns the same value.
+template <int N>
+__device__ __forceinline__ bool stage(unsigned long long *bar, const Copy4 (&cp)[N], unsigned bytes, int *err)
 {
     const unsigned b = smem_addr(bar);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const unsigned bytes = (unsigned)(ntiles * SH * SW * sizeof(float));
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
-        asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                     " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(s0)),
-                     "l"(reinterpret_cast<unsigned long long>(m0)), "r"(x0 - HALO), "r"(z0 - HALO), "r"(s),
-                     "r"(slot0), "r"(b)
-                     : "memory");
-        if (ntiles == 2)
+#pragma unroll
+        for (int i = 0; i < N; ++i)
             asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                         " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(s1)),
-                         "l"(reinterpret_cast<unsigned long long>(m1)), "r"(x0 - HALO), "r"(z0 - HALO), "r"(s),
-                         "r"(slot1), "r"(b)
+                         " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(cp[i].dst)),
+                         "l"(reinterpret_cast<unsigned long long>(cp[i].map)), "r"(cp[i].x), "r"(cp[i].z),
+                         "r"(cp[i].s), "r"(cp[i].slot), "r"(b)
                          : "memory");
     }
     __syncthreads();   // the barrier is initialised before anyone waits on it
@@ -191,22 +191,26 @@ __device__ __forceinline__ void gather(const Geo &g, int s, int tile, int n, con
 }
 
 template <int RZ>
-__global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a, const __grid_constant__ CUtensorMap tm_u)
+__global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a, const __grid_constant__ CUtensorMap tm_u,
+                                                const __grid_constant__ CUtensorMap tm_p)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
-    const int s = blockIdx.y;
-    if (a.n >= g.nt[s]) return;
+    const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
+    if (a.n >= g.nt[sg]) return;
     const int tile = blockIdx.x;
     const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
     const int z0 = tzi * TZ, x0 = txi * TX;
-    __shared__ __align__(128) float su[SH][SW];
+    extern __shared__ __align__(128) float smem[];
     __shared__ unsigned long long bar;
+    Tile *su = reinterpret_cast<Tile *>(smem);                              // u^n with halo
+    float(*sp)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW);        // u^{n-1}
     const long long base = (long long)s * g.field;
-    if (!stage_tiles<SH>(&bar, 1, su, &tm_u, a.cur_slot, nullptr, nullptr, 0, x0, z0, s, g.err)) return;
+    const Copy4 cp[2] = {{su, &tm_u, x0 - HALO, z0 - HALO, s, a.cur_slot}, {sp, &tm_p, x0, z0, s, a.prev_slot}};
+    if (!stage(&bar, cp, (unsigned)((SH * SW + TZ * TX) * sizeof(float)), g.err)) return;
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {
         const float4 dgx = ld4g(g.dGx + x);
-        const int src = g.src_pt[s];
+        const int src = g.src_pt[sg];
         const float wsn = g.ws[a.n];
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a, co
             if (a.t_out) __stcs(reinterpret_cast<float4 *>(a.t_out + base + cell), T);
             const float4 dG = sponge4(g.dGz[z], dgx);
             const float4 uc = ld4s(su, zl + HALO, xl + HALO);
-            const float4 up = ld4g(a.u_prev + base + cell);
+            const float4 up = *reinterpret_cast<const float4 *>(&sp[zl][xl]);
             const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
             st4g(a.u_next + base + cell, leapfrog(dG, uc, up, T, wh, wl));
             if (a.ck_cur) {
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(BX *BY) k_fwd(const Geo g, const FwdArgs a, co
             }
         }
     }
-    if (a.traces) gather(g, s, tile, a.n, a.u_next + base, a.traces);
+    if (a.traces) gather(g, sg, tile, a.n, a.u_next + base, a.traces);
 }
 
 template <int RZ>
@@ -235,8 +239,8 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
                                                  const __grid_constant__ CUtensorMap tm_d)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
-    const int s = blockIdx.y;
-    if (a.n >= g.nt[s]) return;
+    const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
+    if (a.n >= g.nt[sg]) return;
     const int tile = blockIdx.x;
     const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
     const int z0 = tzi * TZ, x0 = txi * TX;
@@ -245,11 +249,12 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
     Tile *su = reinterpret_cast<Tile *>(smem);
     Tile *sd = su + SH;      // SH * SW * 4 bytes on: a multiple of 128
     const long long base = (long long)s * g.field;
-    if (!stage_tiles<SH>(&bar, 2, su, &tm_u, a.u_slot, sd, &tm_d, a.d_slot, x0, z0, s, g.err)) return;
+    const Copy4 cp[2] = {{su, &tm_u, x0 - HALO, z0 - HALO, s, a.u_slot}, {sd, &tm_d, x0 - HALO, z0 - HALO, s, a.d_slot}};
+    if (!stage(&bar, cp, (unsigned)(2 * SH * SW * sizeof(float)), g.err)) return;
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {
         const float4 dgx = ld4g(g.dGx + x);
-        const int src = g.src_pt[s];
+        const int src = g.src_pt[sg];
         const float wsn = g.ws[a.n];
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
@@ -280,25 +285,31 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
             }
         }
     }
-    if (a.traces) gather(g, s, tile, a.n, a.d_next + base, a.traces);
+    if (a.traces) gather(g, sg, tile, a.n, a.d_next + base, a.traces);
 }
 
 template <int RZ>
-__global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a, const __grid_constant__ CUtensorMap tm_z)
+__global__ void __launch_bounds__(BX *BY, 5) k_adj(const Geo g, const AdjArgs a, const __grid_constant__ CUtensorMap tm_z,
+                                                const __grid_constant__ CUtensorMap tm_z2,
+                                                const __grid_constant__ CUtensorMap tm_t)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
-    const int s = blockIdx.y;
-    if (a.n >= g.nt[s]) return;
+    const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
+    if (a.n >= g.nt[sg]) return;
     const int tile = blockIdx.x;
     const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
     const int z0 = tzi * TZ, x0 = txi * TX;
     extern __shared__ __align__(128) float smem[];
     __shared__ unsigned long long bar;
-    Tile *sz = reinterpret_cast<Tile *>(smem);
-    float(*sinj)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW);
+    Tile *sz = reinterpret_cast<Tile *>(smem);                                   // z^{n+1} with halo
+    float(*sinj)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW);           // residual injection
+    float(*sz2)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW + TZ * TX);  // z^{n+2}
+    float(*st)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW + 2 * TZ * TX);  // T^n
     const long long base = (long long)s * g.field;
-    if (!stage_tiles<SH>(&bar, 1, sz, &tm_z, a.z1_slot, nullptr, nullptr, 0, x0, z0, s, g.err)) return;
-    const int t = s * g.ntiles + tile;
+    const Copy4 cp[3] = {{sz, &tm_z, x0 - HALO, z0 - HALO, s, a.z1_slot}, {sz2, &tm_z2, x0, z0, s, a.z2_slot},
+                         {st, &tm_t, x0, z0, s, a.t_slot}};
+    if (!stage(&bar, cp, (unsigned)((SH * SW + 2 * TZ * TX) * sizeof(float)), g.err)) return;
+    const int t = sg * g.ntiles + tile;
     const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
     const bool has_rec = r1 > r0;
     const int tid = threadIdx.y * BX + threadIdx.x;
@@ -306,7 +317,7 @@ __global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a, co
         for (int i = tid; i < TZ * TX / 4; i += BX * BY)
             reinterpret_cast<float4 *>(&sinj[0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
-        const long long tb = g.tr_off[s] + (long long)a.n * g.nrec[s];
+        const long long tb = g.tr_off[sg] + (long long)a.n * g.nrec[sg];
         for (int i = r0 + tid; i < r1; i += BX * BY) {
             const int pt = g.trec_pt[i];
             const int zz = pt / g.pitch, xx = pt - zz * g.pitch;
@@ -322,7 +333,7 @@ __global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a, co
         const int zl = threadIdx.y + r * BY, z = z0 + zl;
         if (z >= g.NZ) break;
         const long long cell = (long long)z * g.pitch + x;
-        const float4 Tu = __ldcs(reinterpret_cast<const float4 *>(a.T + base + cell));
+        const float4 Tu = *reinterpret_cast<const float4 *>(&st[zl][xl]);
         float4 Tz = stencil4(sz, zl + HALO, xl + HALO, g.rz);
         if (has_rec) {
             const float4 inj = *reinterpret_cast<const float4 *>(&sinj[zl][xl]);
@@ -331,7 +342,7 @@ __global__ void __launch_bounds__(BX *BY) k_adj(const Geo g, const AdjArgs a, co
         const float4 dG = sponge4(g.dGz[z], dgx);
         const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
         const float4 z1 = ld4s(sz, zl + HALO, xl + HALO);
-        const float4 z2 = ld4g(a.z2n + base + cell);
+        const float4 z2 = *reinterpret_cast<const float4 *>(&sz2[zl][xl]);
         const float4 zn = leapfrog(dG, z1, z2, Tz, wh, wl);
         // L u + s = Tu * tscale; FWI scale -1/m (= -tscale Tu 5040 dx^2 Wt/dt^2), Born -1
         float4 sc;
@@ -388,13 +399,13 @@ __global__ void k_prep(const Geo g, int nz, int nx, const float *m, const float 
 // separable passes with FP64 sums in a fixed order: (1) over shots and the
 // x-range of cells that physical column jx replicates, for every padded row;
 // (2) over the z-range of rows that physical row jz replicates.
-__global__ void k_shot_sum_x(const Geo g, int nx, const float *img, double *rowsum)
+__global__ void k_shot_sum_x(const Geo g, int nx, const float *img, double *rowsum, int accumulate)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.NZ * nx) return;
     const int z = i / nx, jx = i - z * nx;
     const int xlo = jx == 0 ? 0 : jx + g.nb, xhi = jx == nx - 1 ? g.NX - 1 : jx + g.nb;
-    double acc = 0.0;
+    double acc = accumulate ? rowsum[i] : 0.0;   // earlier batches' shots come first
     for (int s = 0; s < g.S; ++s) {
         const float *f = img + (long long)s * g.field + (long long)z * g.pitch;
         for (int x = xlo; x <= xhi; ++x) acc += (double)f[x];
@@ -414,15 +425,18 @@ __global__ void k_shot_sum_z(const Geo g, int nz, int nx, const double *rowsum, 
 }
 
 template <int RZ>
+static size_t fwd_smem() { return ((RZ * BY + 2 * HALO) * SW + RZ * BY * TX) * sizeof(float); }
+template <int RZ>
 static size_t born_smem() { return 2 * (RZ * BY + 2 * HALO) * SW * sizeof(float); }
 template <int RZ>
-static size_t adj_smem() { return ((RZ * BY + 2 * HALO) * SW + RZ * BY * TX) * sizeof(float); }
+static size_t adj_smem() { return ((RZ * BY + 2 * HALO) * SW + 3 * RZ * BY * TX) * sizeof(float); }
 
 template <int RZ>
 static cudaError_t init_tile_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_born<RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)born_smem<RZ>());
+    cudaError_t e = cudaFuncSetAttribute(k_fwd<RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<RZ>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_born<RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)born_smem<RZ>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_adj<RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem<RZ>());
     return e;
@@ -444,7 +458,7 @@ void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho,
 }
 
 bool encode_tile_map(CUtensorMap *m, const float *base, int NX, int NZ, int pitch, long long field, int S,
-                     int slots, int tile_rows, std::string *why)
+                     int slots, int tile_rows, bool halo, std::string *why)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -460,7 +474,7 @@ bool encode_tile_map(CUtensorMap *m, const float *base, int NX, int NZ, int pitc
     }
     const cuuint64_t dims[4] = {(cuuint64_t)NX, (cuuint64_t)NZ, (cuuint64_t)S, (cuuint64_t)slots};
     const cuuint64_t strides[3] = {(cuuint64_t)pitch * 4, (cuuint64_t)field * 4, (cuuint64_t)field * S * 4};
-    const cuuint32_t box[4] = {(cuuint32_t)SW, (cuuint32_t)(tile_rows + 2 * HALO), 1, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)(halo ? SW : TX), (cuuint32_t)(halo ? tile_rows + 2 * HALO : tile_rows), 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dims, strides, box,
                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -472,13 +486,13 @@ bool encode_tile_map(CUtensorMap *m, const float *base, int NX, int NZ, int pitc
     return true;
 }
 
-void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, cudaStream_t st)
+void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_p, cudaStream_t st)
 {
     count_launch();
     const dim3 grid(g.ntiles, g.S), block(BX, BY);
-    if (g.tz == 16) k_fwd<2><<<grid, block, 0, st>>>(g, a, tm_u);
-    else if (g.tz == 64) k_fwd<8><<<grid, block, 0, st>>>(g, a, tm_u);
-    else k_fwd<4><<<grid, block, 0, st>>>(g, a, tm_u);
+    if (g.tz == 16) k_fwd<2><<<grid, block, fwd_smem<2>(), st>>>(g, a, tm_u, tm_p);
+    else if (g.tz == 64) k_fwd<8><<<grid, block, fwd_smem<8>(), st>>>(g, a, tm_u, tm_p);
+    else k_fwd<4><<<grid, block, fwd_smem<4>(), st>>>(g, a, tm_u, tm_p);
 }
 
 void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d, cudaStream_t st)
@@ -490,22 +504,23 @@ void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const
     else k_born<4><<<grid, block, born_smem<4>(), st>>>(g, a, tm_u, tm_d);
 }
 
-void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, cudaStream_t st)
+void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, const CUtensorMap &tm_z2,
+                const CUtensorMap &tm_t, cudaStream_t st)
 {
     count_launch();
     const dim3 grid(g.ntiles, g.S), block(BX, BY);
-    if (g.tz == 16) k_adj<2><<<grid, block, adj_smem<2>(), st>>>(g, a, tm_z);
-    else if (g.tz == 64) k_adj<8><<<grid, block, adj_smem<8>(), st>>>(g, a, tm_z);
-    else k_adj<4><<<grid, block, adj_smem<4>(), st>>>(g, a, tm_z);
+    if (g.tz == 16) k_adj<2><<<grid, block, adj_smem<2>(), st>>>(g, a, tm_z, tm_z2, tm_t);
+    else if (g.tz == 64) k_adj<8><<<grid, block, adj_smem<8>(), st>>>(g, a, tm_z, tm_z2, tm_t);
+    else k_adj<4><<<grid, block, adj_smem<4>(), st>>>(g, a, tm_z, tm_z2, tm_t);
 }
 
-void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *rowsum, float *out,
+void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *rowsum, bool accumulate, float *out,
                      cudaStream_t st)
 {
-    count_launch(2);
+    count_launch(out ? 2 : 1);
     const int n1 = g.NZ * nx, n2 = nz * nx;
-    k_shot_sum_x<<<(n1 + 255) / 256, 256, 0, st>>>(g, nx, img, rowsum);
-    k_shot_sum_z<<<(n2 + 255) / 256, 256, 0, st>>>(g, nz, nx, rowsum, out);
+    k_shot_sum_x<<<(n1 + 255) / 256, 256, 0, st>>>(g, nx, img, rowsum, accumulate ? 1 : 0);
+    if (out) k_shot_sum_z<<<(n2 + 255) / 256, 256, 0, st>>>(g, nz, nx, rowsum, out);
 }
 
 }  // namespace aafwi

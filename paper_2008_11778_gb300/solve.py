@@ -93,7 +93,9 @@ class AAInversion:
                     Jc = self._misfit_only(self.cand)
                     self.n_forward += 1
                     if Jc <= self.J + self.c1 * min(0.0, dot):
-                        lam, reuse = trial, not self.lsrtm and self.grad_fn is None
+                        # a plan that runs its shots in batches keeps no forward to reuse
+                        lam, reuse = trial, (not self.lsrtm and self.grad_fn is None
+                                             and self.plan.keeps_forward)
                         break
             else:
                 lam = 1.0
