@@ -15,8 +15,14 @@ Contents, each following the paper's statement in its own order:
                    point p~ and the plain point p-bar.
   gmres_full       full-memory GMRES (Sec. 5.1, eqs. Krylov, GMRES), used to
                    pin AA on a linear problem.
+  gmres_restarted  restarted GMRES(M) (Sec. 5.1): the Krylov space is rebuilt
+                   from the latest iterate every M steps; operator as a function
+                   (the LSRTM normal operator L^T L of eq. LSRTM3).
+  lbfgs_direction  the L-BFGS two-loop recursion (Sec. 5.2, eqs. secant,
+                   lbfgs_update): -B_k g from the last M pairs (s_i, y_i).
+  lbfgs            L-BFGS(M) with the backtracking line search of aa_gd.
 
-Readings of points the paper leaves open (shared with the CUDA driver):
+Readings of points the paper leaves open (shared with the GPU drivers):
   * A_k / f_k are built from the gradients at the last M_k+1 ACCEPTED iterates;
     with a fixed eta the factor -eta cancels, so gamma = argmin||dG g - G_k||.
   * Rank safeguard: while min_j|R_jj| < RANK_TOL * max_j|R_jj| drop the oldest
@@ -28,6 +34,17 @@ Readings of points the paper leaves open (shared with the CUDA driver):
     [lo, hi] (physical velocity bounds mapped to m = 1/c^2), identically in
     every trial; the Armijo test is applied to the clipped point.
   * Alg. 2 input step p_1 = G(p_0) is taken without a line search.
+  * L-BFGS (the paper gives eqs. secant / lbfgs_update, not an algorithm):
+    the textbook two-loop recursion with initial matrix gamma_k I,
+    gamma_k = <s, y> / <y, y> of the newest pair; a pair enters the memory
+    only if <s, y> > 0; the first step (and any step without a pair) is the
+    plain gradient step p - eta grad, like Alg. 2's input step; trial points
+    p + lambda d, lambda in (1, 1/2, 1/4, 1/8), the same Armijo rule as
+    aa_gd; if none is accepted the plain gradient step is taken.
+  * Restarted GMRES(M): the iterate after Arnoldi step j of a cycle is
+    x_0 + V_j y_j with y_j minimising ||beta e_1 - H_j y|| (Sec. 5.1); a cycle
+    ends after M steps (or on a zero subdiagonal) and the next starts from
+    its last iterate.
 """
 import numpy as np
 
@@ -198,3 +215,106 @@ def gmres_full(A, b, x0, kmax):
         y = np.linalg.lstsq(H[:k + 2, :k + 1], e1, rcond=None)[0]
         xs.append(x0 + V[:, :k + 1] @ y)
     return xs
+
+
+# --------------------------------------------------------------------------
+# Restarted GMRES(M) (Sec. 5.1)
+# --------------------------------------------------------------------------
+
+def gmres_restarted(apply_A, b, x0, M, iters):
+    """Restarted GMRES(M) on A x = b with A given as a function.  Returns the
+    iterates after each Arnoldi step (iters of them, one operator application
+    each) and the residual norms ||b - A x|| the small problem predicts."""
+    x = np.asarray(x0, dtype=np.float64).copy()
+    b = np.asarray(b, dtype=np.float64)
+    xs, res = [], []
+    done = 0
+    while done < iters:
+        r0 = b - apply_A(x)
+        beta = np.linalg.norm(r0)
+        if beta == 0.0:
+            xs += [x.copy()] * (iters - done)
+            res += [0.0] * (iters - done)
+            break
+        V = [r0 / beta]
+        H = np.zeros((M + 1, M))
+        xc = x
+        for j in range(M):
+            if done == iters:
+                break
+            w = apply_A(V[j])
+            for i in range(j + 1):                 # modified Gram-Schmidt
+                H[i, j] = float(np.vdot(V[i], w))
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            e1 = np.zeros(j + 2)
+            e1[0] = beta
+            y = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
+            xc = x + np.column_stack(V[:j + 1]) @ y
+            xs.append(xc)
+            res.append(float(np.linalg.norm(e1 - H[:j + 2, :j + 1] @ y)))
+            done += 1
+            if H[j + 1, j] == 0.0:
+                break
+            V.append(w / H[j + 1, j])
+        x = xc
+    return xs, res
+
+
+# --------------------------------------------------------------------------
+# L-BFGS(M) (Sec. 5.2)
+# --------------------------------------------------------------------------
+
+def lbfgs_direction(g, S, Y):
+    """-B g by the two-loop recursion from the pairs (S[i], Y[i]), oldest
+    first; B_0 = gamma I with gamma = <s, y>/<y, y> of the newest pair."""
+    q = np.asarray(g, dtype=np.float64).copy()
+    a = []
+    for s, y in zip(reversed(S), reversed(Y)):
+        rho = 1.0 / float(np.vdot(y, s))
+        ai = rho * float(np.vdot(s, q))
+        q = q - ai * y
+        a.append((rho, ai))
+    gamma = float(np.vdot(S[-1], Y[-1]) / np.vdot(Y[-1], Y[-1])) if S else 1.0
+    r = gamma * q
+    for (s, y), (rho, ai) in zip(zip(S, Y), reversed(a)):
+        bi = rho * float(np.vdot(y, r))
+        r = r + (ai - bi) * s
+    return -r
+
+
+def lbfgs(grad_fn, p0, M, eta, iters, bounds=None, lambdas=LAMBDAS, c1=ARMIJO_C1, misfit_fn=None):
+    """L-BFGS(M) with the readings above; same return layout as aa_gd (lam =
+    the accepted step, 0 for a plain gradient step)."""
+    if misfit_fn is None:
+        misfit_fn = lambda p: grad_fn(p)[0]
+    clip = (lambda p: np.clip(p, bounds[0], bounds[1])) if bounds is not None else (lambda p: p)
+    p = np.asarray(p0, dtype=np.float64).copy()
+    J, g = grad_fn(p)
+    S, Y = [], []
+    out = {"p": [p], "J": [J], "lam": [], "n_trials": 0}
+    for k in range(iters):
+        lam = 0.0
+        if S:
+            d = lbfgs_direction(g, S, Y)
+            for trial in lambdas:
+                cand = clip(p + trial * d)
+                Jc = misfit_fn(cand)
+                out["n_trials"] += 1
+                if Jc <= J + c1 * min(0.0, float(np.vdot(g, cand - p))):
+                    lam = trial
+                    break
+        p_next = clip(p + lam * d) if lam > 0 else clip(p - eta * g)
+        J_next, g_next = grad_fn(p_next)
+        s, y = p_next - p, g_next - g
+        if float(np.vdot(s, y)) > 0.0:
+            S.append(s)
+            Y.append(y)
+            if len(S) > M:
+                S.pop(0)
+                Y.pop(0)
+        p, J, g = p_next, J_next, g_next
+        out["p"].append(p)
+        out["J"].append(J)
+        out["lam"].append(lam)
+    return out

@@ -148,3 +148,77 @@ def test_line_search_keeps_misfit_monotone_and_beats_sd():
     sd = aa.aa_gd(gf, np.zeros(30), M=0, eta=eta, iters=30)
     Jstar = gf(np.linalg.solve(A, b))[0]
     assert (J[-1] - Jstar) < 1e-3 * (sd["J"][-1] - Jstar)
+
+
+# ---------------------------------------------------- restarted GMRES, L-BFGS
+
+def test_restarted_gmres_without_restart_is_full_gmres():
+    rng = np.random.default_rng(21)
+    n = 30
+    A = np.eye(n) * 3 + rng.standard_normal((n, n)) / np.sqrt(n)
+    b = rng.standard_normal(n)
+    x0 = rng.standard_normal(n)
+    xs, res = aa.gmres_restarted(lambda v: A @ v, b, x0, M=12, iters=12)
+    ref = aa.gmres_full(A, b, x0, 12)
+    for a, r in zip(xs, ref):
+        np.testing.assert_allclose(a, r, rtol=1e-10, atol=1e-12)
+    for x, r in zip(xs, res):
+        assert abs(np.linalg.norm(b - A @ x) - r) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_restarted_gmres_cycles_minimise_over_their_krylov_space():
+    """Each iterate minimises ||b - A x|| over x_cycle + K_j(A, r_cycle) --
+    checked against a least-squares solve over the explicit (non-Arnoldi)
+    Krylov basis -- and the residual never grows across restarts."""
+    rng = np.random.default_rng(22)
+    n, M = 40, 3
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(np.linspace(1.0, 50.0, n)) @ Q.T
+    b = rng.standard_normal(n)
+    xs, res = aa.gmres_restarted(lambda v: A @ v, b, np.zeros(n), M=M, iters=12)
+    assert all(r2 <= r1 * (1 + 1e-12) for r1, r2 in zip(res, res[1:]))
+    x_cycle = np.zeros(n)
+    for c in range(4):
+        r0 = b - A @ x_cycle
+        K = np.column_stack([np.linalg.matrix_power(A, i) @ r0 for i in range(M)])
+        for j in range(1, M + 1):
+            y = np.linalg.lstsq(A @ K[:, :j], r0, rcond=None)[0]
+            best = x_cycle + K[:, :j] @ y
+            np.testing.assert_allclose(xs[c * M + j - 1], best, rtol=1e-7, atol=1e-9)
+        x_cycle = xs[c * M + M - 1]
+
+
+def test_two_loop_recursion_is_the_dense_bfgs_update():
+    """-B g from the two-loop recursion equals the product of explicit BFGS
+    inverse updates H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T from
+    gamma I, and the newest secant condition B y_k = s_k holds."""
+    rng = np.random.default_rng(23)
+    n, m = 25, 5
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(np.linspace(1.0, 20.0, n)) @ Q.T
+    S = [rng.standard_normal(n) for _ in range(m)]
+    Y = [A @ s for s in S]                        # curvature pairs of a convex quadratic
+    g = rng.standard_normal(n)
+    gamma = (S[-1] @ Y[-1]) / (Y[-1] @ Y[-1])
+    H = gamma * np.eye(n)
+    for s, y in zip(S, Y):
+        rho = 1.0 / (y @ s)
+        E = np.eye(n) - rho * np.outer(s, y)
+        H = E @ H @ E.T + rho * np.outer(s, s)
+    np.testing.assert_allclose(aa.lbfgs_direction(g, S, Y), -H @ g, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(-aa.lbfgs_direction(Y[-1], S, Y), S[-1], rtol=1e-10, atol=1e-12)
+
+
+def test_lbfgs_monotone_and_reaches_the_quadratic_minimiser():
+    rng = np.random.default_rng(24)
+    n = 60
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(np.linspace(1.0, 100.0, n)) @ Q.T
+    b = rng.standard_normal(n)
+    gf = lambda x: (0.5 * x @ A @ x - b @ x, A @ x - b)
+    out = aa.lbfgs(gf, np.zeros(n), M=10, eta=1.0 / 100.0, iters=60)
+    J = np.array(out["J"])
+    assert np.all(np.diff(J) <= 1e-12 * abs(J[0]) + 1e-15)
+    xs = np.linalg.solve(A, b)
+    assert np.linalg.norm(out["p"][-1] - xs) < 1e-6 * np.linalg.norm(xs)
+    assert sum(l == 1.0 for l in out["lam"]) >= len(out["lam"]) // 2   # mostly full steps
