@@ -37,10 +37,16 @@ Readings of points the paper leaves open (shared with the GPU drivers):
   * L-BFGS (the paper gives eqs. secant / lbfgs_update, not an algorithm):
     the textbook two-loop recursion with initial matrix gamma_k I,
     gamma_k = <s, y> / <y, y> of the newest pair; a pair enters the memory
-    only if <s, y> > 0; the first step (and any step without a pair) is the
-    plain gradient step p - eta grad, like Alg. 2's input step; trial points
-    p + lambda d, lambda in (1, 1/2, 1/4, 1/8), the same Armijo rule as
-    aa_gd; if none is accepted the plain gradient step is taken.
+    only if <s, y> > 0.  Without a pair the direction is -eta grad.  Line
+    search: the paper applies the Armijo rule and the curvature condition
+    (Sec. 4.1).  With curvature=False: lambda in (1, 1/2, 1/4, 1/8), the
+    same Armijo rule as aa_gd (a misfit per trial), the plain gradient step
+    if none passes.  With curvature=True (weak Wolfe, c2 = 0.9; a gradient
+    per trial): start at lambda = 1; Armijo failing halves the bracket,
+    J(p + lambda d) passing but <grad(p + lambda d), d> < c2 <grad, d>
+    doubles lambda (or bisects once bracketed); at most 12 trials, after
+    which the last point that passed Armijo is taken (else the plain
+    gradient step).  An accepted Wolfe point gives <s, y> > 0.
   * Restarted GMRES(M): the iterate after Arnoldi step j of a cycle is
     x_0 + V_j y_j with y_j minimising ||beta e_1 - H_j y|| (Sec. 5.1); a cycle
     ends after M steps (or on a zero subdiagonal) and the next starts from
@@ -109,8 +115,14 @@ def aa_gamma(A, f, rank_tol=RANK_TOL):
     return np.zeros(0), first
 
 
-def anderson_point(P, Gr, eta, rank_tol=RANK_TOL):
+def anderson_point(P, Gr, eta, rank_tol=RANK_TOL, beta=1.0, weights=None):
     """Alg. 2 steps 1-3 for the history P = [p_{k-Mk}..p_k], Gr = [G_{k-Mk}..G_k].
+
+    With a damping beta != 1 the AA point is Alg. 1's eq. AAupdate0,
+    (1 - beta) sum_i alpha_i p_i + beta sum_i alpha_i G(p_i), with alpha from
+    gamma (the same weights); beta = 1 is Alg. 2's step 3 below.
+    weights: the diagonal of a weighted l2 norm for the least squares of step 2
+    (Sec. 2.1 admits other norms): gamma = argmin sum_i w_i (dG gamma - G_k)_i^2.
 
     Returns (p_bar, p_tilde, gamma, Mk_used).
       p_bar   = G(p_k) = p_k - eta G_k                         (step 1, eq. GD)
@@ -127,7 +139,17 @@ def anderson_point(P, Gr, eta, rank_tol=RANK_TOL):
     if Mk == 0:
         return p_bar.reshape(shape), p_bar.reshape(shape).copy(), np.zeros(0), 0
     dG = np.stack([Gr[i + 1] - Gr[i] for i in range(Mk)], axis=1)
-    gamma, first = aa_gamma(dG, gk, rank_tol)
+    if weights is None:
+        gamma, first = aa_gamma(dG, gk, rank_tol)
+    else:
+        sw = np.sqrt(np.asarray(weights, dtype=np.float64).ravel())
+        gamma, first = aa_gamma(dG * sw[:, None], gk * sw, rank_tol)
+    if beta != 1.0:
+        Pk, Gk = P[first:], Gr[first:]
+        alpha = gamma_to_alpha(gamma)
+        p_tilde = aa_update_alpha(np.stack(Pk, axis=1), np.stack([p - eta * g for p, g in zip(Pk, Gk)], axis=1),
+                                  alpha, beta)
+        return p_bar.reshape(shape), np.asarray(p_tilde).reshape(shape), gamma, Mk - first
     p_tilde = p_bar.copy()
     for j, gj in enumerate(gamma):
         i = first + j
@@ -137,7 +159,7 @@ def anderson_point(P, Gr, eta, rank_tol=RANK_TOL):
 
 
 def aa_gd(grad_fn, p0, M, eta, iters, line_search=True, bounds=None,
-          lambdas=LAMBDAS, c1=ARMIJO_C1, rank_tol=RANK_TOL, misfit_fn=None):
+          lambdas=LAMBDAS, c1=ARMIJO_C1, rank_tol=RANK_TOL, misfit_fn=None, beta=1.0, weights=None):
     """Alg. 2: l2-based AA for gradient descent.
 
     grad_fn(p) -> (J, grad); misfit_fn(p) -> J (defaults to grad_fn(p)[0]).
@@ -158,7 +180,7 @@ def aa_gd(grad_fn, p0, M, eta, iters, line_search=True, bounds=None,
             p_next = clip(p - eta * g)       # Alg. 2 input: p_1 = G(p_0)
             lam, Mk, gamma = 0.0, 0, np.zeros(0)
         else:
-            p_bar, p_tilde, gamma, Mk = anderson_point(P, Gr, eta, rank_tol)
+            p_bar, p_tilde, gamma, Mk = anderson_point(P, Gr, eta, rank_tol, beta, weights)
             lam = 0.0
             if line_search and Mk > 0:
                 for trial in lambdas:
@@ -225,15 +247,17 @@ def gmres_restarted(apply_A, b, x0, M, iters):
     """Restarted GMRES(M) on A x = b with A given as a function.  Returns the
     iterates after each Arnoldi step (iters of them, one operator application
     each) and the residual norms ||b - A x|| the small problem predicts."""
-    x = np.asarray(x0, dtype=np.float64).copy()
-    b = np.asarray(b, dtype=np.float64)
+    shape = np.shape(x0)                          # unknowns of any shape, handled as flat vectors
+    A = lambda v: np.asarray(apply_A(v.reshape(shape)), dtype=np.float64).ravel()
+    x = np.asarray(x0, dtype=np.float64).ravel().copy()
+    b = np.asarray(b, dtype=np.float64).ravel()
     xs, res = [], []
     done = 0
     while done < iters:
-        r0 = b - apply_A(x)
+        r0 = b - A(x)
         beta = np.linalg.norm(r0)
         if beta == 0.0:
-            xs += [x.copy()] * (iters - done)
+            xs += [x.reshape(shape).copy()] * (iters - done)
             res += [0.0] * (iters - done)
             break
         V = [r0 / beta]
@@ -242,7 +266,7 @@ def gmres_restarted(apply_A, b, x0, M, iters):
         for j in range(M):
             if done == iters:
                 break
-            w = apply_A(V[j])
+            w = A(V[j])
             for i in range(j + 1):                 # modified Gram-Schmidt
                 H[i, j] = float(np.vdot(V[i], w))
                 w = w - H[i, j] * V[i]
@@ -251,7 +275,7 @@ def gmres_restarted(apply_A, b, x0, M, iters):
             e1[0] = beta
             y = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
             xc = x + np.column_stack(V[:j + 1]) @ y
-            xs.append(xc)
+            xs.append(xc.reshape(shape))
             res.append(float(np.linalg.norm(e1 - H[:j + 2, :j + 1] @ y)))
             done += 1
             if H[j + 1, j] == 0.0:
@@ -283,9 +307,32 @@ def lbfgs_direction(g, S, Y):
     return -r
 
 
-def lbfgs(grad_fn, p0, M, eta, iters, bounds=None, lambdas=LAMBDAS, c1=ARMIJO_C1, misfit_fn=None):
+def _wolfe_search(grad_fn, p, J, g, d, clip, c1, c2, max_trials, out):
+    """Weak-Wolfe bracketing search along d (see the readings); returns
+    (lambda, p_new, J_new, g_new) or None if no trial passed Armijo."""
+    lam, lo, hi = 1.0, 0.0, np.inf
+    gd = float(np.vdot(g, d))
+    best = None
+    for _ in range(max_trials):
+        cand = clip(p + lam * d)
+        Jc, gc = grad_fn(cand)
+        out["n_trials"] += 1
+        if not Jc <= J + c1 * min(0.0, float(np.vdot(g, cand - p))):
+            hi = lam
+        else:
+            best = (lam, cand, Jc, gc)
+            if float(np.vdot(gc, d)) >= c2 * gd:
+                return best
+            lo = lam
+        lam = 2.0 * lam if hi == np.inf else 0.5 * (lo + hi)
+    return best
+
+
+def lbfgs(grad_fn, p0, M, eta, iters, bounds=None, lambdas=LAMBDAS, c1=ARMIJO_C1, misfit_fn=None,
+          curvature=False, c2=0.9, max_trials=12):
     """L-BFGS(M) with the readings above; same return layout as aa_gd (lam =
-    the accepted step, 0 for a plain gradient step)."""
+    the accepted step, 0 for a plain gradient step; n_trials counts misfit
+    evaluations, or gradient evaluations with curvature=True)."""
     if misfit_fn is None:
         misfit_fn = lambda p: grad_fn(p)[0]
     clip = (lambda p: np.clip(p, bounds[0], bounds[1])) if bounds is not None else (lambda p: p)
@@ -295,17 +342,25 @@ def lbfgs(grad_fn, p0, M, eta, iters, bounds=None, lambdas=LAMBDAS, c1=ARMIJO_C1
     out = {"p": [p], "J": [J], "lam": [], "n_trials": 0}
     for k in range(iters):
         lam = 0.0
-        if S:
-            d = lbfgs_direction(g, S, Y)
-            for trial in lambdas:
-                cand = clip(p + trial * d)
-                Jc = misfit_fn(cand)
-                out["n_trials"] += 1
-                if Jc <= J + c1 * min(0.0, float(np.vdot(g, cand - p))):
-                    lam = trial
-                    break
-        p_next = clip(p + lam * d) if lam > 0 else clip(p - eta * g)
-        J_next, g_next = grad_fn(p_next)
+        d = lbfgs_direction(g, S, Y) if S else -eta * g
+        if curvature:
+            hit = _wolfe_search(grad_fn, p, J, g, d, clip, c1, c2, max_trials, out)
+            if hit is not None:
+                lam, p_next, J_next, g_next = hit
+            else:
+                p_next = clip(p - eta * g)
+                J_next, g_next = grad_fn(p_next)
+        else:
+            if S:
+                for trial in lambdas:
+                    cand = clip(p + trial * d)
+                    Jc = misfit_fn(cand)
+                    out["n_trials"] += 1
+                    if Jc <= J + c1 * min(0.0, float(np.vdot(g, cand - p))):
+                        lam = trial
+                        break
+            p_next = clip(p + lam * d) if lam > 0 else clip(p - eta * g)
+            J_next, g_next = grad_fn(p_next)
         s, y = p_next - p, g_next - g
         if float(np.vdot(s, y)) > 0.0:
             S.append(s)

@@ -222,3 +222,65 @@ def test_lbfgs_monotone_and_reaches_the_quadratic_minimiser():
     xs = np.linalg.solve(A, b)
     assert np.linalg.norm(out["p"][-1] - xs) < 1e-6 * np.linalg.norm(xs)
     assert sum(l == 1.0 for l in out["lam"]) >= len(out["lam"]) // 2   # mostly full steps
+
+
+def test_lbfgs_wolfe_search_keeps_curvature_on_a_nonconvex_start():
+    """On f(x) = sum(x^4)/4 - |x|^2/2 started near the local maximum at 0
+    (negative curvature along -grad), fixed small gradient steps give no pair
+    with <s, y> > 0 and the Armijo-only run never leaves steepest descent;
+    the weak-Wolfe search expands the step past the concave region, builds
+    pairs and reaches a minimiser (|x_i| = 1)."""
+    rng = np.random.default_rng(25)
+    n = 20
+    x0 = 1e-3 * rng.standard_normal(n)
+    f = lambda x: (0.25 * np.sum(x ** 4) - 0.5 * x @ x, x ** 3 - x)
+    eta = 1e-3
+    x1 = x0 - eta * f(x0)[1]
+    assert (x1 - x0) @ (f(x1)[1] - f(x0)[1]) < 0            # a plain step has no usable pair
+    out = aa.lbfgs(f, x0, M=5, eta=eta, iters=40, curvature=True)
+    J = np.array(out["J"])
+    assert np.all(np.diff(J) <= 1e-12)
+    assert np.allclose(np.abs(out["p"][-1]), 1.0, atol=1e-4)
+    pairs = sum((q - p) @ (f(q)[1] - f(p)[1]) > 0 for p, q in zip(out["p"], out["p"][1:]))
+    assert pairs >= len(out["lam"]) // 2
+    plain = aa.lbfgs(f, x0, M=5, eta=eta, iters=40, curvature=False)
+    assert all(l == 0.0 for l in plain["lam"]) and plain["J"][-1] > 0.5 * J[-1]
+
+
+def test_damped_anderson_point():
+    """beta = 1 of eq. AAupdate0 is Alg. 2's gamma form; beta = 0 is the same
+    combination of the iterates alone; any beta is the gamma form with the
+    step eta scaled by beta, p_k - beta eta G_k - sum gamma (dp - beta eta dG)."""
+    rng = np.random.default_rng(26)
+    n, m, eta = 50, 4, 0.1
+    P = [rng.standard_normal(n) for _ in range(m + 1)]
+    Gr = [rng.standard_normal(n) for _ in range(m + 1)]
+    pb, pt1, gam, Mk = aa.anderson_point(P, Gr, eta)
+    assert Mk == m                                     # full rank: no column dropped
+    GP = np.stack([p - eta * g for p, g in zip(P, Gr)], axis=1)
+    pt1b = aa.aa_update_alpha(np.stack(P, axis=1), GP, aa.gamma_to_alpha(gam), 1.0)
+    np.testing.assert_allclose(pt1b, pt1, rtol=1e-10, atol=1e-12)
+    for beta in (0.0, 0.3, 0.75):
+        _, ptb, g, _ = aa.anderson_point(P, Gr, eta, beta=beta)
+        ref = P[-1] - beta * eta * Gr[-1]
+        for j in range(len(g)):
+            ref = ref - g[j] * ((P[j + 1] - beta * eta * Gr[j + 1]) - (P[j] - beta * eta * Gr[j]))
+        np.testing.assert_allclose(ptb, ref, rtol=1e-10, atol=1e-12)
+    assert np.allclose(pb, P[-1] - eta * Gr[-1])
+
+
+def test_weighted_l2_gamma():
+    """A constant weight leaves gamma unchanged (scale invariance of the
+    minimiser); a 0/1 weight gives the gamma of the selected rows alone."""
+    rng = np.random.default_rng(27)
+    n, m, eta = 80, 4, 0.1
+    P = [rng.standard_normal(n) for _ in range(m + 1)]
+    Gr = [rng.standard_normal(n) for _ in range(m + 1)]
+    _, pt, g0, _ = aa.anderson_point(P, Gr, eta)
+    _, ptc, gc, _ = aa.anderson_point(P, Gr, eta, weights=np.full(n, 7.5))
+    np.testing.assert_allclose(gc, g0, rtol=1e-10)
+    np.testing.assert_allclose(ptc, pt, rtol=1e-10)
+    sel = rng.random(n) < 0.5
+    _, _, gs, _ = aa.anderson_point(P, Gr, eta, weights=sel.astype(float))
+    _, _, gr, _ = aa.anderson_point([p[sel] for p in P], [g[sel] for g in Gr], eta)
+    np.testing.assert_allclose(gs, gr, rtol=1e-10)
