@@ -198,6 +198,19 @@ int aafwi_aa_create(size_t n, int M, double eta, aafwi_aa **out);
 void aafwi_aa_destroy(aafwi_aa *aa);
 int aafwi_aa_set_eta(aafwi_aa *aa, double eta);
 
+/* Damping beta in [0, 1] of the AA point (Alg. 1 eq. AAupdate0): p_tilde =
+ * (1 - beta) sum alpha_i p_i + beta sum alpha_i G(p_i), i.e. the gamma form
+ * with eta scaled by beta; p_bar keeps eta.  Default 1 (Alg. 2).  ARG if
+ * beta is outside [0, 1]. */
+int aafwi_aa_set_beta(aafwi_aa *aa, double beta);
+
+/* Weighted l2 norm for the AA least-squares problem (Sec. 2.1): gamma =
+ * argmin sum_i w_i ((dG gamma - G_k)_i)^2 with the device FP32 weights w [n]
+ * (w_i >= 0; copied, the caller keeps its buffer); NULL restores the plain l2
+ * norm.  Only before the first aa_step (the Gram matrix is built
+ * incrementally with these weights): STATE otherwise. */
+int aafwi_aa_set_weights(aafwi_aa *aa, const float *w, aafwi_stream stream);
+
 /* Alg. 2 steps 1-3: append (p_k, grad_k) to the history (dropping the
  * oldest beyond M+1), then
  *   p_bar   = p_k - eta grad_k                                   (eq. GD)
@@ -295,6 +308,19 @@ int aafwi_misfit_noalloc(const float *d_syn, const float *d_obs, long long n, fl
                          double *J_dev, double *J_host, aafwi_stream stream);
 
 /* ---- instrumentation ---------------------------------------------------- */
+
+/* ---- vector operations of the comparison solvers (Sec. 5: restarted GMRES on
+ * the LSRTM normal equations, L-BFGS for FWI) ------------------------------ */
+
+/* <x, y> of two device FP32 vectors of length n, accumulated in FP64 in a
+ * fixed order (deterministic); result on the host (syncs the stream).
+ * Errors: ARG (NULL, n = 0), NOMEM, CUDA. */
+int aafwi_dot(const float *x, const float *y, size_t n, double *host_out, aafwi_stream stream);
+
+/* y = a x + b y on device FP32 vectors of length n (a, b rounded to FP32);
+ * asynchronous on the stream.  x and y may be the same vector.
+ * Errors: ARG, CUDA (launch). */
+int aafwi_axpby(double a, const float *x, double b, float *y, size_t n, aafwi_stream stream);
 
 /* ---- autotuner (launch configuration of the sweeps; the paper has no
  * counterpart) ------------------------------------------------------------ */

@@ -26,11 +26,11 @@ EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aa
            "aafwi_plan_set_stall",
            "aafwi_model_forward", "aafwi_born_forward", "aafwi_misfit", "aafwi_adjoint_gradient",
            "aafwi_born_adjoint", "aafwi_fwi_adjoint", "aafwi_read_misfit", "aafwi_aa_create", "aafwi_aa_destroy",
-           "aafwi_aa_set_eta", "aafwi_aa_step", "aafwi_aa_combine", "aafwi_absmax",
+           "aafwi_aa_set_eta", "aafwi_aa_set_beta", "aafwi_aa_set_weights", "aafwi_aa_step", "aafwi_aa_combine", "aafwi_absmax",
            "aafwi_launch_count", "aafwi_misfit_noalloc", "aafwi_unet_create", "aafwi_unet_destroy",
            "aafwi_unet_param_count", "aafwi_unet_set_params", "aafwi_unet_get_params", "aafwi_unet_forward",
            "aafwi_unet_loss_grad", "aafwi_unet_train_step", "aafwi_learned_features", "aafwi_learned_apply",
-           "aafwi_autotune")
+           "aafwi_autotune", "aafwi_dot", "aafwi_axpby")
 
 
 class AafwiError(RuntimeError):
@@ -101,6 +101,8 @@ def load(path=LIB_PATH):
         "aafwi_aa_create": ([Z, I, D, P], I),
         "aafwi_aa_destroy": ([P], None),
         "aafwi_aa_set_eta": ([P, D], I),
+        "aafwi_aa_set_beta": ([P, D], I),
+        "aafwi_aa_set_weights": ([P, P, P], I),
         "aafwi_aa_step": ([P, P, P, P, P, P, P, P], I),
         "aafwi_aa_combine": ([P, D, P, P, P, ctypes.c_float, ctypes.c_float, P, P], I),
         "aafwi_absmax": ([P, Z, P, P], I),
@@ -117,6 +119,8 @@ def load(path=LIB_PATH):
         "aafwi_learned_features": ([P, P, I, I, I, I, P, P, P], I),
         "aafwi_learned_apply": ([P, P, I, I, I, P, ctypes.c_float, ctypes.c_float, P, P], I),
         "aafwi_autotune": ([P, P, P, P, I, I, P, P, I, P, P], I),
+        "aafwi_dot": ([P, P, Z, P, P], I),
+        "aafwi_axpby": ([D, P, D, P, Z, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -330,6 +334,19 @@ class Plan:
         return J.value
 
 
+def dot(x, y, stream=None):
+    """<x, y> (FP64 accumulation) of two contiguous device float32 tensors."""
+    out = ctypes.c_double()
+    _check(load().aafwi_dot(_f32(x), _f32(y), x.numel(), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def axpby(a, x, b, y, stream=None):
+    """y <- a x + b y in place (device float32)."""
+    _check(load().aafwi_axpby(float(a), _f32(x), float(b), _f32(y), y.numel(), _stream(stream)))
+    return y
+
+
 class AA:
     """Owns an aafwi_aa: the AA(M) history ring and its FP64 Gram matrix."""
 
@@ -351,6 +368,14 @@ class AA:
 
     def set_eta(self, eta):
         _check(load().aafwi_aa_set_eta(self.h, float(eta)))
+
+    def set_weights(self, w, stream=None):
+        """Weighted l2 norm of the AA least squares (None: plain l2); before the first step."""
+        _check(load().aafwi_aa_set_weights(self.h, _f32(w) if w is not None else None, _stream(stream)))
+
+    def set_beta(self, beta):
+        """Damping of the AA point (Alg. 1 eq. AAupdate0); 1 = Alg. 2."""
+        _check(load().aafwi_aa_set_beta(self.h, float(beta)))
 
     def step(self, p_k, grad_k, p_tilde, p_bar, want_gamma=False, stream=None):
         gam = (ctypes.c_double * max(self.M, 1))()

@@ -86,6 +86,7 @@ struct aafwi_plan {
 
 struct aafwi_aa {
     AAState s{};
+    float *wbuf = nullptr;          // copy of the weighted-l2 weights
     int device = 0;
     std::vector<Buf> bufs;
 };
@@ -906,6 +907,7 @@ int aafwi_aa_create(size_t n, int M, double eta, aafwi_aa **out)
     s.n = (long long)n;
     s.M = M;
     s.eta = eta;
+    s.beta = 1.0;
     const int M1 = M + 1;
     bool ok = dalloc(a->bufs, &s.ring_p, (size_t)M1 * n) && dalloc(a->bufs, &s.ring_g, (size_t)M1 * n) &&
               dalloc(a->bufs, &s.gram, (size_t)M1 * M1) &&
@@ -936,6 +938,30 @@ int aafwi_aa_set_eta(aafwi_aa *a, double eta)
 {
     if (!a || !(eta > 0)) return AAFWI_ERR_ARG;
     a->s.eta = eta;
+    return AAFWI_OK;
+}
+
+int aafwi_aa_set_weights(aafwi_aa *a, const float *w, aafwi_stream stream)
+{
+    if (!a) return AAFWI_ERR_ARG;
+    if (a->s.count > 0) return fail(nullptr, AAFWI_ERR_STATE, "aa_set_weights after the first aa_step");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!w) {
+        a->s.weights = nullptr;
+        return AAFWI_OK;
+    }
+    if (!a->wbuf && !dalloc(a->bufs, &a->wbuf, (size_t)a->s.n))
+        return fail(nullptr, AAFWI_ERR_NOMEM, "cudaMalloc failed for the AA weights");
+    cudaError_t e = cudaMemcpyAsync(a->wbuf, w, (size_t)a->s.n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "aa_set_weights copy");
+    a->s.weights = a->wbuf;
+    return AAFWI_OK;
+}
+
+int aafwi_aa_set_beta(aafwi_aa *a, double beta)
+{
+    if (!a || !(beta >= 0.0) || beta > 1.0) return AAFWI_ERR_ARG;
+    a->s.beta = beta;
     return AAFWI_OK;
 }
 
@@ -991,6 +1017,30 @@ int aafwi_absmax(const float *x, size_t n, double *host_out, aafwi_stream stream
     cudaFreeAsync(buf, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "absmax");
+    return AAFWI_OK;
+}
+
+int aafwi_dot(const float *x, const float *y, size_t n, double *host_out, aafwi_stream stream)
+{
+    if (!x || !y || !host_out || n == 0) return fail(nullptr, AAFWI_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    double *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, (RED_BLOCKS + 1) * sizeof(double), st) != cudaSuccess)
+        return fail(nullptr, AAFWI_ERR_NOMEM, "dot scratch");
+    launch_dot(x, y, (long long)n, buf, buf + RED_BLOCKS, st);
+    cudaError_t e = cudaMemcpyAsync(host_out, buf + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(buf, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "dot");
+    return AAFWI_OK;
+}
+
+int aafwi_axpby(double a, const float *x, double b, float *y, size_t n, aafwi_stream stream)
+{
+    if (!x || !y || n == 0) return fail(nullptr, AAFWI_ERR_ARG, "NULL argument");
+    launch_axpby((float)a, x, (float)b, y, (long long)n, (cudaStream_t)stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "axpby");
     return AAFWI_OK;
 }
 

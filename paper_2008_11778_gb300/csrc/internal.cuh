@@ -190,6 +190,8 @@ constexpr int RED_BLOCKS = 608;    // 4 x 152 SMs
 void launch_misfit(const float *d_syn, const float *d_obs, float *resid, long long n,
                    double *partials, double *J_dev, cudaStream_t st);
 void launch_absmax(const float *x, long long n, double *partials, double *out_dev, cudaStream_t st);
+void launch_dot(const float *x, const float *y, long long n, double *partials, double *out_dev, cudaStream_t st);
+void launch_axpby(float a, const float *x, float b, float *y, long long n, cudaStream_t st);
 
 // Anderson acceleration.
 constexpr int AA_MAXM = 20;
@@ -203,6 +205,8 @@ struct AAState {
     int *meta;                     // [0] Mk used, [1] first dropped column
     double *dot;                   // [1] armijo dot
     double eta;
+    double beta;                   // damping of the AA point (1: Alg. 2)
+    float *weights;                // [n] diagonal weights of a weighted l2 norm, or null
     int count, head;               // entries in the ring, slot of the newest
 };
 void launch_aa_step(AAState &s, const float *p_k, const float *g_k, float *p_tilde,

@@ -87,6 +87,37 @@ void launch_misfit(const float *d_syn, const float *d_obs, float *resid, long lo
     k_finish_sum<<<1, RT, 0, st>>>(partials, RED_BLOCKS, 0.5, J_dev);
 }
 
+// <x, y> accumulated in FP64: block partials (grid-stride, fixed grid).
+__global__ void __launch_bounds__(RT) k_dot(const float *x, const float *y, long long n, double *partials)
+{
+    __shared__ double sh[RT / 32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
+        acc += (double)x[i] * (double)y[i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+void launch_dot(const float *x, const float *y, long long n, double *partials, double *out_dev, cudaStream_t st)
+{
+    count_launch(2);
+    k_dot<<<RED_BLOCKS, RT, 0, st>>>(x, y, n, partials);
+    k_finish_sum<<<1, RT, 0, st>>>(partials, RED_BLOCKS, 1.0, out_dev);
+}
+
+// y = a x + b y
+__global__ void __launch_bounds__(RT) k_axpby(float a, const float *x, float b, float *y, long long n)
+{
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
+        y[i] = fmaf(a, x[i], b * y[i]);
+}
+
+void launch_axpby(float a, const float *x, float b, float *y, long long n, cudaStream_t st)
+{
+    count_launch();
+    k_axpby<<<RED_BLOCKS, RT, 0, st>>>(a, x, b, y, n);
+}
+
 __global__ void __launch_bounds__(RT) k_absmax(const float *x, long long n, double *partials)
 {
     __shared__ double sh[RT / 32];
@@ -123,8 +154,9 @@ void launch_absmax(const float *x, long long n, double *partials, double *out_de
 // Anderson acceleration
 // ---------------------------------------------------------------------------
 
-// Copy (p_k, G_k) into ring slot `head` and accumulate <G_k, G_slot> for the
-// c history slots (chronological slot list `slots`, the newest last).
+// Copy (p_k, G_k) into ring slot `head` and accumulate <G_k, G_slot>_w for the
+// c history slots (chronological slot list `slots`, the newest last); w: the
+// diagonal weight of a weighted l2 norm (Sec. 2.1), or null for the l2 norm.
 struct AASlots {
     int slot[AA_MAXM + 1];
     int c;
@@ -132,7 +164,7 @@ struct AASlots {
 
 __global__ void __launch_bounds__(RT) k_aa_append(const float *p_k, const float *g_k, float *ring_p,
                                                   float *ring_g, long long n, int head, AASlots sl,
-                                                  double *partials)
+                                                  const float *w, double *partials)
 {
     __shared__ double sh[RT / 32];
     double acc[AA_MAXM + 1];
@@ -142,11 +174,12 @@ __global__ void __launch_bounds__(RT) k_aa_append(const float *p_k, const float 
         const float gv = g_k[i];
         ring_p[(long long)head * n + i] = p_k[i];
         ring_g[(long long)head * n + i] = gv;
+        const double gw = w ? (double)w[i] * (double)gv : (double)gv;
 #pragma unroll
         for (int j = 0; j <= AA_MAXM; ++j) {
             if (j < sl.c) {
                 const float o = sl.slot[j] == head ? gv : ring_g[(long long)sl.slot[j] * n + i];
-                acc[j] += (double)gv * (double)o;
+                acc[j] += gw * (double)o;
             }
         }
     }
@@ -221,10 +254,11 @@ __global__ void k_aa_solve(double *gram, const double *partials, int nblocks, in
     meta[1] = first;
 }
 
-// p_bar = p_k - eta G_k;  p_tilde = p_bar - sum_a gamma_a (Gp_{a+1} - Gp_a),
-// Gp_i = p_i - eta G_i, over the columns kept by the solve.
+// p_bar = p_k - eta G_k;  p_tilde = Gb_k - sum_a gamma_a (Gb_{a+1} - Gb_a),
+// Gb_i = p_i - beta eta G_i (the damped update of Alg. 1 eq. AAupdate0 in the
+// gamma form; beta = 1: Alg. 2 step 3), over the columns kept by the solve.
 __global__ void __launch_bounds__(RT) k_aa_mix(const float *ring_p, const float *ring_g, long long n,
-                                               AASlots sl, float eta, const double *gamma,
+                                               AASlots sl, float eta, float beta_eta, const double *gamma,
                                                const int *meta, float *p_tilde, float *p_bar)
 {
     __shared__ float gsh[AA_MAXM];
@@ -239,11 +273,11 @@ __global__ void __launch_bounds__(RT) k_aa_mix(const float *ring_p, const float 
     const int newest = sl.slot[sl.c - 1];
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
         const float pb = ring_p[(long long)newest * n + i] - eta * ring_g[(long long)newest * n + i];
-        float pt = pb;
-        float prev = ring_p[(long long)sl.slot[first] * n + i] - eta * ring_g[(long long)sl.slot[first] * n + i];
+        float pt = ring_p[(long long)newest * n + i] - beta_eta * ring_g[(long long)newest * n + i];
+        float prev = ring_p[(long long)sl.slot[first] * n + i] - beta_eta * ring_g[(long long)sl.slot[first] * n + i];
         for (int a = 0; a < mk; ++a) {
             const int sn = sl.slot[first + a + 1];
-            const float cur = ring_p[(long long)sn * n + i] - eta * ring_g[(long long)sn * n + i];
+            const float cur = ring_p[(long long)sn * n + i] - beta_eta * ring_g[(long long)sn * n + i];
             pt -= gsh[a] * (cur - prev);
             prev = cur;
         }
@@ -262,10 +296,10 @@ void launch_aa_step(AAState &s, const float *p_k, const float *g_k, float *p_til
     sl.c = s.count;
     for (int t = 0; t < sl.c; ++t) sl.slot[t] = ((s.head - (sl.c - 1) + t) % M1 + M1) % M1;
     count_launch(3);
-    k_aa_append<<<RED_BLOCKS, RT, 0, st>>>(p_k, g_k, s.ring_p, s.ring_g, s.n, s.head, sl, s.partials);
+    k_aa_append<<<RED_BLOCKS, RT, 0, st>>>(p_k, g_k, s.ring_p, s.ring_g, s.n, s.head, sl, s.weights, s.partials);
     k_aa_solve<<<1, 32, 0, st>>>(s.gram, s.partials, RED_BLOCKS, M1, s.head, sl, 1e-6, s.gamma, s.meta);
-    k_aa_mix<<<RED_BLOCKS, RT, 0, st>>>(s.ring_p, s.ring_g, s.n, sl, (float)s.eta, s.gamma, s.meta,
-                                        p_tilde, p_bar);
+    k_aa_mix<<<RED_BLOCKS, RT, 0, st>>>(s.ring_p, s.ring_g, s.n, sl, (float)s.eta, (float)(s.beta * s.eta),
+                                        s.gamma, s.meta, p_tilde, p_bar);
 }
 
 // p_next = clip(lam p_tilde + (1 - lam) p_bar); partial <G_k, p_next - p_k>.

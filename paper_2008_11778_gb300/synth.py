@@ -303,3 +303,13 @@ def small_problem(nz=30, nx=40, nb=8, nt=160, S=2, dx=10.0, dt=1e-3, f=15.0, see
     g = surface_geometry(nz, nx, nb, dx, dt, f, nt, S)
     return Problem("small-%dx%d" % (nx, nz), g, c, np.full_like(c, c.mean()), M=5, iters=10,
                    c_bounds=(1500.0, 3000.0))
+
+
+def uniform_noise(d, snr_db, seed):
+    """Mean-zero uniform noise for traces d at the given signal-to-noise ratio
+    (10 log10 of mean signal power over noise power): U(-a, a) with
+    a^2 / 3 = mean(d^2) / 10^(snr_db / 10).  Seeded; returns the noise only."""
+    d = np.asarray(d, dtype=np.float64)
+    p_noise = float(np.mean(d * d)) / 10.0 ** (snr_db / 10.0)
+    a = np.sqrt(3.0 * p_noise)
+    return np.random.default_rng(seed).uniform(-a, a, d.shape)

@@ -1,0 +1,215 @@
+"""The comparison solvers of Sec. 5 on the library's kernels against the
+oracle: L-BFGS(M) with the Alg. 2 line search (quadratic objective and an
+FWI problem with a data-sized residual) and restarted GMRES(M) (quadratic
+system and the LSRTM normal equations L^T L x = L^T d)."""
+import numpy as np
+import pytest
+
+from paper_2008_11778_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+HIST_TOL = 1e-3
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    from paper_2008_11778_gb300 import aafwi, build
+    build.build()
+    aafwi.load()
+    assert torch.cuda.is_available()
+    return torch
+
+
+def dev(torch, a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def quadratic(gpu, n, cond, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(np.linspace(1.0, cond, n)) @ Q.T
+    b = rng.standard_normal(n)
+    return A, b, gpu.as_tensor(A, dtype=gpu.float64, device="cuda"), gpu.as_tensor(b, dtype=gpu.float64, device="cuda")
+
+
+def test_dot_and_axpby(gpu):
+    from paper_2008_11778_gb300 import aafwi
+    rng = np.random.default_rng(0)
+    x, y = rng.standard_normal(100003).astype(np.float32), rng.standard_normal(100003).astype(np.float32)
+    X, Y = dev(gpu, x), dev(gpu, y)
+    ref = float(np.dot(x.astype(np.float64), y.astype(np.float64)))
+    assert abs(aafwi.dot(X, Y) - ref) <= 1e-12 * np.abs(x.astype(np.float64) * y).sum()
+    aafwi.axpby(0.5, X, -2.0, Y)
+    np.testing.assert_allclose(host(Y), 0.5 * x.astype(np.float64) - 2.0 * y, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("curvature", [False, True], ids=["armijo", "wolfe"])
+def test_lbfgs_quadratic_history_matches_oracle(gpu, curvature):
+    from oracle import aa as oaa
+    from paper_2008_11778_gb300 import solve
+    n = 300
+    A, b, At, bt = quadratic(gpu, n, 200.0, 5)
+
+    def grad_fn(x, g_out, reuse):
+        xd = x.double()
+        g_out.copy_((At @ xd - bt).float())
+        return float(0.5 * xd @ (At @ xd) - bt @ xd)
+
+    def misfit_fn(x):
+        xd = x.double()
+        return float(0.5 * xd @ (At @ xd) - bt @ xd)
+
+    out = solve.lbfgs_fwi(None, None, gpu.zeros(n, device="cuda"), M=5, iters=25, eta=1.0 / 200.0,
+                          grad_fn=grad_fn, misfit_fn=misfit_fn, curvature=curvature)
+
+    def ogf(x):
+        x32 = x.astype(np.float32).astype(np.float64)
+        return 0.5 * x32 @ A @ x32 - b @ x32, (A @ x32 - b).astype(np.float32).astype(np.float64)
+    ref = oaa.lbfgs(ogf, np.zeros(n), M=5, eta=1.0 / 200.0, iters=25, misfit_fn=lambda x: ogf(x)[0],
+                    curvature=curvature)
+    assert out["lam"] == ref["lam"]
+    Jstar = -0.5 * b @ np.linalg.solve(A, b)
+    assert rel(np.array(out["J"]) - Jstar, np.array(ref["J"]) - Jstar) < HIST_TOL
+    assert rel(host(out["p"]), ref["p"][-1]) < 1e-4
+
+
+def test_lbfgs_fwi_history_large_residual(gpu, orc):
+    """L-BFGS(5) with the weak-Wolfe search, 8 iterations, on the data-sized-
+    residual problem of the AA history test: the misfit history matches the
+    oracle's to the 1e-3 target."""
+    from oracle import aa as oaa
+    from paper_2008_11778_gb300 import aafwi, solve
+    p = synth.small_problem(nz=48, nx=120, nb=12, nt=300, S=3)
+    g = p.geom
+    d_obs = orc.forward(g, p.m_true).astype(np.float32)
+    lo, hi = p.m_bounds
+    plan = aafwi.Plan(g, max(float(p.c_true.max()), p.c_bounds[1]))
+    out = solve.lbfgs_fwi(plan, dev(gpu, d_obs), dev(gpu, p.m_start), M=5, iters=8, eta_factor=1e-3,
+                          bounds=(lo, hi), curvature=True)
+    ref = oaa.lbfgs(lambda m: orc.fwi_gradient(g, m.astype(np.float32), d_obs),
+                    p.m_start.astype(np.float32).astype(np.float64), M=5, eta=out["eta"], iters=8,
+                    bounds=(lo, hi), curvature=True)
+    assert out["lam"] == ref["lam"]
+    assert rel(out["J"], ref["J"]) < HIST_TOL
+    assert ref["J"][-1] < 0.9 * ref["J"][0]
+
+
+def test_gmres_quadratic_matches_oracle(gpu):
+    from oracle import aa as oaa
+    from paper_2008_11778_gb300 import solve
+    n = 300
+    A, b, At, bt = quadratic(gpu, n, 50.0, 6)
+
+    def residual_fn(x, out):
+        out.copy_((At @ x.double() - bt).float())
+
+    x0 = np.zeros(n, dtype=np.float32)
+    out = solve.gmres_restarted(residual_fn, dev(gpu, x0), M=4, iters=16)
+    xs, res = oaa.gmres_restarted(lambda v: A @ v, b, x0.astype(np.float64), M=4, iters=16)
+    assert rel(out["res"], res) < HIST_TOL
+    assert rel(host(out["x"]), xs[-1]) < 1e-4
+    assert out["applications"] == 1 + 16 + 4          # b, one per step, one per restart
+
+
+def test_gmres_lsrtm_normal_equations_vs_oracle(gpu, orc):
+    """GMRES(3) on L^T L x = L^T d (eq. LSRTM3), 6 steps from the RTM image,
+    with the library's LSRTM gradient as the residual map, against the oracle
+    GMRES on the oracle's Born operators."""
+    from oracle import aa as oaa
+    from paper_2008_11778_gb300 import aafwi, solve
+    p = synth.small_problem(nz=40, nx=64, nb=8, nt=180, S=2)
+    g = p.geom
+    rng = np.random.default_rng(7)
+    m0 = p.m_true.astype(np.float32)
+    rho_true = (0.1 * rng.standard_normal(m0.shape)).astype(np.float32)
+    d = orc.born_forward(g, m0, rho_true).astype(np.float32)
+    plan = aafwi.Plan(g, float(p.c_true.max()))
+    M0, D = dev(gpu, m0), dev(gpu, d)
+    rtm = gpu.empty_like(M0)
+    plan.born_adjoint(M0, D, rtm)
+    x0 = host(rtm)
+
+    def residual_fn(x, out):
+        plan.adjoint_gradient(aafwi.MODE_LSRTM, M0, x, D, out, sync=False)
+
+    out = solve.gmres_restarted(residual_fn, rtm, M=3, iters=6)
+    b = orc.born_adjoint(g, m0, d)
+    xs, res = oaa.gmres_restarted(lambda v: orc.born_adjoint(g, m0, orc.born_forward(g, m0, v)), b,
+                                  x0, M=3, iters=6)
+    assert rel(out["res"], res) < HIST_TOL
+    assert rel(host(out["x"]), xs[-1]) < 1e-3
+    assert res[-1] < 0.5 * res[0]
+
+
+@pytest.mark.parametrize("beta", [0.5, 0.0])
+def test_damped_aa_quadratic_history_matches_oracle(gpu, beta):
+    """Alg. 2 with the damped AA point (Alg. 1 eq. AAupdate0, beta < 1) on a
+    quadratic: line-search decisions, misfit gap and iterate against the oracle."""
+    from oracle import aa as oaa
+    from paper_2008_11778_gb300 import solve
+    n = 300
+    A, b, At, bt = quadratic(gpu, n, 200.0, 8)
+
+    def grad_fn(x, g_out, reuse):
+        xd = x.double()
+        g_out.copy_((At @ xd - bt).float())
+        return float(0.5 * xd @ (At @ xd) - bt @ xd)
+
+    def misfit_fn(x):
+        xd = x.double()
+        return float(0.5 * xd @ (At @ xd) - bt @ xd)
+
+    out = solve.aa_fwi(None, None, gpu.zeros(n, device="cuda"), M=5, iters=20, eta=1.0 / 200.0,
+                       grad_fn=grad_fn, misfit_fn=misfit_fn, beta=beta)
+
+    def ogf(x):
+        x32 = x.astype(np.float32).astype(np.float64)
+        return 0.5 * x32 @ A @ x32 - b @ x32, (A @ x32 - b).astype(np.float32).astype(np.float64)
+    ref = oaa.aa_gd(ogf, np.zeros(n), M=5, eta=1.0 / 200.0, iters=20, misfit_fn=lambda x: ogf(x)[0], beta=beta)
+    assert out["lam"] == ref["lam"]
+    Jstar = -0.5 * b @ np.linalg.solve(A, b)
+    assert rel(np.array(out["J"]) - Jstar, np.array(ref["J"]) - Jstar) < HIST_TOL
+    assert rel(host(out["p"]), ref["p"][-1]) < 1e-4
+
+
+def test_weighted_aa_quadratic_history_matches_oracle(gpu):
+    """Alg. 2 with a weighted l2 norm in the AA least squares (diagonal
+    weights 0.1..10) against the oracle."""
+    from oracle import aa as oaa
+    from paper_2008_11778_gb300 import solve
+    n = 300
+    A, b, At, bt = quadratic(gpu, n, 200.0, 9)
+    w = np.exp(np.random.default_rng(10).uniform(np.log(0.1), np.log(10.0), n)).astype(np.float32)
+
+    def grad_fn(x, g_out, reuse):
+        xd = x.double()
+        g_out.copy_((At @ xd - bt).float())
+        return float(0.5 * xd @ (At @ xd) - bt @ xd)
+
+    def misfit_fn(x):
+        xd = x.double()
+        return float(0.5 * xd @ (At @ xd) - bt @ xd)
+
+    out = solve.aa_fwi(None, None, gpu.zeros(n, device="cuda"), M=5, iters=20, eta=1.0 / 200.0,
+                       grad_fn=grad_fn, misfit_fn=misfit_fn, weights=dev(gpu, w))
+
+    def ogf(x):
+        x32 = x.astype(np.float32).astype(np.float64)
+        return 0.5 * x32 @ A @ x32 - b @ x32, (A @ x32 - b).astype(np.float32).astype(np.float64)
+    ref = oaa.aa_gd(ogf, np.zeros(n), M=5, eta=1.0 / 200.0, iters=20, misfit_fn=lambda x: ogf(x)[0],
+                    weights=w.astype(np.float64))
+    assert out["lam"] == ref["lam"]
+    Jstar = -0.5 * b @ np.linalg.solve(A, b)
+    assert rel(np.array(out["J"]) - Jstar, np.array(ref["J"]) - Jstar) < HIST_TOL
+    assert rel(host(out["p"]), ref["p"][-1]) < 1e-4
