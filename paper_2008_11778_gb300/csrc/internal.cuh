@@ -127,6 +127,9 @@ struct PlanLayout {
     size_t bytes, budget;
     bool fits;
 };
+// U-Net kernels' error word (bit 0: a tensor-core wait ran out), read and cleared; -1 if unreadable.
+int unet_take_error();
+
 PlanLayout plan_layout(long long field, long long cells, int S, int nt_max, long long trace_count,
                        const aafwi_plan_opts &o);
 

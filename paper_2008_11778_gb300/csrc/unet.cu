@@ -24,7 +24,7 @@
 namespace aafwi {
 
 int unet_conv3_fwd(const __nv_bfloat16 *x, const __nv_bfloat16 *w, int B, int H, int W, int Cin, int Cout,
-                   float *out, cudaStream_t st);
+                   float *out, long long out_cap, cudaStream_t st);
 int unet_conv3_dgrad(const __nv_bfloat16 *dz, const __nv_bfloat16 *wt, int B, int H, int W, int Cin, int Cout,
                      float *out, cudaStream_t st);
 int unet_conv3_wgrad(const __nv_bfloat16 *dz, const __nv_bfloat16 *x, int B, int H, int W, int Cin, int Cout,
@@ -414,7 +414,7 @@ const bf16 *wb(const aafwi_unet *u, const Conv &c) { return u->Pb + c.w; }
 // forward of one 3x3 conv + bias + ReLU into y
 void conv_fwd(aafwi_unet *u, const Conv &c, const bf16 *x, int B, int H, int W, bf16 *y, cudaStream_t st)
 {
-    const int s = unet_conv3_fwd(x, wb(u, c), B, H, W, c.Cin, c.Cout, u->gemm, st);
+    const int s = unet_conv3_fwd(x, wb(u, c), B, H, W, c.Cin, c.Cout, u->gemm, u->gemm_size, st);
     const long long MN = (long long)B * H * W * c.Cout;
     count_launch();
     k_epi<<<nblk(MN), ET, 0, st>>>(u->gemm, s, MN, c.Cout, u->P + c.b, 1, y);
@@ -679,6 +679,8 @@ int aafwi_unet_loss_grad(aafwi_unet *u, const float *x, const float *target, int
     if (e == cudaSuccess && loss_host) {
         e = cudaMemcpyAsync(loss_host, u->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && unet_take_error())
+            return uerr(u, AAFWI_ERR_TIMEOUT, "unet_loss_grad: a tensor-core wait ran out");
     }
     if (e != cudaSuccess) return uerr(u, AAFWI_ERR_CUDA, std::string("unet_loss_grad: ") + cudaGetErrorString(e));
     return AAFWI_OK;
@@ -726,6 +728,8 @@ int aafwi_unet_train_step(aafwi_unet *u, const float *x, const float *target, in
     if (e == cudaSuccess && loss_host) {
         e = cudaMemcpyAsync(loss_host, u->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && unet_take_error())
+            return uerr(u, AAFWI_ERR_TIMEOUT, "unet_train_step: a tensor-core wait ran out");
     }
     if (e != cudaSuccess) return uerr(u, AAFWI_ERR_CUDA, std::string("unet_train_step: ") + cudaGetErrorString(e));
     return AAFWI_OK;

@@ -4,16 +4,14 @@
 //
 // Every convolution-like operation is an implicit GEMM  C[M][N] = sum_k
 // A(m, k) B(k, n)  on BF16 operands with FP32 accumulation, computed with
-// mma.sync.m16n8k16 tensor-core instructions.  Activations are NHWC BF16.
+// tcgen05.mma (accumulator in tensor memory).  Activations are NHWC BF16.
 //   conv3x3 forward   M = pixels, N = Cout, K = 9 Cin   A = im2col(x), B = w[Cout][9][Cin]
 //   conv3x3 dgrad     M = pixels, N = Cin,  K = 9 Cout  A = im2col(dz) flipped, B = wt[Cin][9][Cout]
 //   conv3x3 wgrad     M = Cout,   N = 9 Cin, K = pixels A = dz^T, B = im2col(x)   (split over pixels)
 //   upconv2x2 forward M = pixels_in, N = 4 Cout, K = Cin      (output scattered to the 2x2 children)
 //   upconv2x2 dgrad   M = pixels_in, N = Cin,    K = 4 Cout   (gathers the 2x2 children)
 //   upconv2x2 wgrad   M = Cin,       N = 4 Cout, K = pixels_in
-// CTA tile 64 x 64 x 32, 4 warps each owning 32 x 32 (2 x 4 mma tiles);
-// operands are staged K-contiguous in shared memory and fed to the
-// fragments with 32-bit loads.
+// CTA tile 128 x 64, K chunks of 32; see k_gemm_tc.
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -21,15 +19,7 @@
 namespace aafwi {
 namespace unet {
 
-constexpr int BM = 64, BN = 64, BK = 32, KP = BK + 8;   // KP: padded row (bank spread)
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
+constexpr int BK = 32;   // K granularity of the splits
 
 // Operand gathers, one per GEMM mode.  fillA / fillB write 16 consecutive K
 // elements of one row of the A (M x K) or B^T (N x K) tile as raw BF16 bits,
@@ -64,11 +54,39 @@ __device__ __forceinline__ Pix pix(const ConvGeom &g, int p)
     return q;
 }
 
+// 16 consecutive BF16 values, as two 16-byte loads from a 32-byte aligned
+// address (element by element otherwise).
+__device__ __forceinline__ void load16(const unsigned short *p, unsigned short *dst)
+{
+    if (reinterpret_cast<uintptr_t>(p) & 31) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) dst[i] = p[i];
+        return;
+    }
+    const uint4 lo = __ldg(reinterpret_cast<const uint4 *>(p)), hi = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+    const unsigned w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        dst[2 * i] = (unsigned short)(w[i] & 0xFFFFu);
+        dst[2 * i + 1] = (unsigned short)(w[i] >> 16);
+    }
+}
+
 // im2col segment: element k = tap * C + c of pixel q, tap offsets (sign * (ky-1, kx-1))
 __device__ __forceinline__ void im2col16(const unsigned short *t, const ConvGeom &g, int C, Pix q, int k0, int ke,
                                          int sign, unsigned short *dst)
 {
     int tap = k0 / C, c = k0 - tap * C;
+    if ((C & 15) == 0 && k0 + 16 <= ke) {   // one tap, 16 consecutive channels (k0 is a multiple of 16)
+        const int yy = q.y + sign * (tap / 3 - 1), xx = q.x + sign * (tap % 3 - 1);
+        if (yy >= 0 && yy < g.H && xx >= 0 && xx < g.W) {
+            load16(t + (((long long)q.b * g.H + yy) * g.W + xx) * C + c, dst);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) dst[i] = 0;
+        }
+        return;
+    }
     for (int i = 0; i < 16; ++i) {
         const int k = k0 + i;
         unsigned short v = 0;
@@ -98,7 +116,9 @@ __device__ __forceinline__ void fillA(const Op<MODE> &o, int m, int k0, int ke, 
         for (int i = 0; i < 16; ++i) dst[i] = k0 + i < ke ? o.a[(long long)(k0 + i) * C + m] : 0;
     } else if (MODE == UP_FWD) {
         // m = input pixel, k = cin: x [Pin][Cin]
-        for (int i = 0; i < 16; ++i) dst[i] = k0 + i < ke ? o.a[(long long)m * g.Cin + k0 + i] : 0;
+        if ((g.Cin & 15) == 0 && k0 + 16 <= ke) load16(o.a + (long long)m * g.Cin + k0, dst);
+        else
+            for (int i = 0; i < 16; ++i) dst[i] = k0 + i < ke ? o.a[(long long)m * g.Cin + k0 + i] : 0;
     } else {  // UP_DGRAD: m = coarse pixel, k = q * Cout + co; dy [B][2H][2W][Cout]
         const Pix q0 = pix(g, m);
         int q = k0 / g.Cout, co = k0 - q * g.Cout;
@@ -123,7 +143,9 @@ __device__ __forceinline__ void fillB(const Op<MODE> &o, int n, int k0, int ke, 
     const ConvGeom &g = o.g;
     if (MODE == CONV_FWD || MODE == CONV_DGRAD || MODE == UP_DGRAD) {
         // weights stored N-major with K contiguous: w[n][k]
-        for (int i = 0; i < 16; ++i) dst[i] = k0 + i < ke ? o.b[(long long)n * o.K + k0 + i] : 0;
+        if ((o.K & 15) == 0 && k0 + 16 <= ke) load16(o.b + (long long)n * o.K + k0, dst);
+        else
+            for (int i = 0; i < 16; ++i) dst[i] = k0 + i < ke ? o.b[(long long)n * o.K + k0 + i] : 0;
     } else if (MODE == UP_FWD) {  // w [Cin][4 Cout]: B(k = cin, n)
         for (int i = 0; i < 16; ++i) dst[i] = k0 + i < ke ? o.b[(long long)(k0 + i) * o.N + n] : 0;
     } else if (MODE == CONV_WGRAD) {  // n = tap * Cin + cin, k = pixel: x [B][H][W][Cin]
@@ -153,76 +175,190 @@ __device__ __forceinline__ void fillB(const Op<MODE> &o, int n, int k0, int ke, 
     }
 }
 
-// One CTA: a BM x BN tile of C over its K split [kb, kb + klen).  The FP32
-// result goes to out[(split * M + m) * N + n] (split = blockIdx.z).
-template <int MODE>
-__global__ void __launch_bounds__(128) k_gemm(const Op<MODE> o, float *out)
+// ---------------------------------------------------------------------------
+// 5th-generation tensor cores (tcgen05): the same implicit GEMMs with the
+// accumulator in tensor memory.  CTA tile TM x TN, K in chunks of TK: the 128
+// threads gather the chunk's A (TM x TK) and B (TN x TK) operands into shared
+// memory in the K-major, unswizzled operand layout (8 x 8 BF16 core matrices,
+// 8 rows x 16 bytes); one thread issues TK/16 MMAs (128 x 64 x 16 each) and
+// commits them to an mbarrier, which every thread waits for (bounded) before
+// the next chunk overwrites the operands.  The epilogue reads the FP32
+// accumulator from tensor memory (warp w: lanes 32w .. 32w+31 = tile rows).
+// ---------------------------------------------------------------------------
+
+constexpr int TM = 128, TN = 64, TK = 32;
+static_assert(TK == BK, "K splits are laid out in multiples of BK");
+
+// Error word of the U-Net kernels (bit 0: a tensor-core commit wait ran out).
+__device__ int g_unet_err;
+int *unet_error_word()
 {
-    __shared__ __align__(16) unsigned short As[BM][KP];
-    __shared__ __align__(16) unsigned short Bs[BN][KP];
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    static int *p = nullptr;
+    if (!p) cudaGetSymbolAddress((void **)&p, g_unet_err);
+    return p;
+}
+
+}  // namespace unet
+
+// Host: the U-Net error word (then cleared); call after the work has been synchronised.
+int unet_take_error()
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, unet::g_unet_err, sizeof(int)) != cudaSuccess) return -1;
+    if (v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(unet::g_unet_err, &z, sizeof(int));
+    }
+    return v;
+}
+
+namespace unet {
+constexpr int T_LBO = 128;                  // bytes between core matrices adjacent along K
+constexpr int T_SBO = TK / 8 * 128;         // bytes between 8-row groups
+constexpr long long T_WAIT_LIMIT = 1LL << 22;
+
+__device__ __forceinline__ unsigned tc_off(int r, int k)
+{
+    return (unsigned)((r >> 3) * T_SBO + (k >> 3) * T_LBO + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ unsigned tc_smem(const void *p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (8-row group) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr)
+{
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((T_LBO >> 4) & 0x3FFF) << 16) |
+           ((unsigned long long)((T_SBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N = TN, M = TM.
+constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TN >> 3) << 17) |
+                              ((unsigned)(TM >> 4) << 24);
+
+__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned parity)
+{
+    for (long long i = 0; i < T_WAIT_LIMIT; ++i) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_store16(unsigned char *tile, int r, int k, const unsigned short (&seg)[16])
+{
+    uint4 lo, hi;
+    lo.x = seg[0] | ((unsigned)seg[1] << 16); lo.y = seg[2] | ((unsigned)seg[3] << 16);
+    lo.z = seg[4] | ((unsigned)seg[5] << 16); lo.w = seg[6] | ((unsigned)seg[7] << 16);
+    hi.x = seg[8] | ((unsigned)seg[9] << 16); hi.y = seg[10] | ((unsigned)seg[11] << 16);
+    hi.z = seg[12] | ((unsigned)seg[13] << 16); hi.w = seg[14] | ((unsigned)seg[15] << 16);
+    *reinterpret_cast<uint4 *>(tile + tc_off(r, k)) = lo;
+    *reinterpret_cast<uint4 *>(tile + tc_off(r, k + 8)) = hi;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_gemm_tc(const Op<MODE> o, float *out, int *err)
+{
+    __shared__ __align__(1024) unsigned char As[TM * TK * 2];
+    __shared__ __align__(1024) unsigned char Bs[TN * TK * 2];
+    __shared__ unsigned long long bar;
+    __shared__ unsigned tmem_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
     const int kb = blockIdx.z * o.klen;
     const int ke = min(kb + o.klen, o.K);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int grp = lane >> 2, tig = lane & 3;
-    const int fr = tid >> 1, fk = (tid & 1) * 16;     // staging: row fr, 16 K from fk
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-        unsigned short seg[16];
-        if (m0 + fr < o.M) fillA<MODE>(o, m0 + fr, k0 + fk, ke, seg);
-        else
-            for (int i = 0; i < 16; ++i) seg[i] = 0;
-        for (int i = 0; i < 16; i += 2)
-            *reinterpret_cast<uint32_t *>(&As[fr][fk + i]) = seg[i] | ((uint32_t)seg[i + 1] << 16);
-        if (n0 + fr < o.N) fillB<MODE>(o, n0 + fr, k0 + fk, ke, seg);
-        else
-            for (int i = 0; i < 16; ++i) seg[i] = 0;
-        for (int i = 0; i < 16; i += 2)
-            *reinterpret_cast<uint32_t *>(&Bs[fr][fk + i]) = seg[i] | ((uint32_t)seg[i + 1] << 16);
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < BK; ks += 16) {
-            uint32_t af[2][4], bf[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + 16 * i + grp;
-                af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][ks + 2 * tig]);
-                af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + 2 * tig]);
-                af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][ks + 8 + 2 * tig]);
-                af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + 8 + 2 * tig]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn + 8 * j + grp;
-                bf[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][ks + 2 * tig]);
-                bf[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][ks + 8 + 2 * tig]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
-        }
-        __syncthreads();
+    const unsigned b = tc_smem(&bar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&tmem_sh)),
+                     "r"(TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    float *dst = out + (long long)blockIdx.z * o.M * o.N;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_sh;
+    bool ok = true;
+    int chunk = 0;
+    for (int k0 = kb; k0 < ke && ok; k0 += TK, ++chunk) {
+        unsigned short seg[16];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+        for (int h = 0; h < 2; ++h) {          // A: row tid, K halves
+            if (m0 + tid < o.M) fillA<MODE>(o, m0 + tid, k0 + 16 * h, ke, seg);
+            else
+                for (int i = 0; i < 16; ++i) seg[i] = 0;
+            tc_store16(As, tid, 16 * h, seg);
+        }
+        {                                      // B: row tid % 64, K half tid / 64
+            const int r = tid & (TN - 1), h = tid / TN;
+            if (n0 + r < o.N) fillB<MODE>(o, n0 + r, k0 + 16 * h, ke, seg);
+            else
+                for (int i = 0; i < 16; ++i) seg[i] = 0;
+            tc_store16(Bs, r, 16 * h, seg);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operands visible to the tensor cores
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int r = m0 + wm + 16 * i + grp, c = n0 + wn + 8 * j + 2 * tig;
+            for (int ks = 0; ks < TK / 16; ++ks) {
+                const unsigned long long ad = tc_desc(tc_smem(As) + ks * 2 * T_LBO);
+                const unsigned long long bd = tc_desc(tc_smem(Bs) + ks * 2 * T_LBO);
+                const unsigned accum = (chunk > 0 || ks > 0) ? 1u : 0u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                             "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(accum)
+                             : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b)
+                         : "memory");
+        }
+        ok = __syncthreads_and(tc_wait(b, chunk & 1)) != 0;   // the MMAs have read the operands
+    }
+    if (!ok) {   // give the outstanding MMAs one more bounded wait before the tensor memory is freed
+        if (tid == 0) atomicOr(err, 1);
+        tc_wait(b, (chunk - 1) & 1);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float *dst = out + (long long)blockIdx.z * o.M * o.N;
+        const int row = m0 + warp * 32 + lane;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int rr = r + (e >> 1) * 8, cc = c + (e & 1);
-                if (rr < o.M && cc < o.N) dst[(long long)rr * o.N + cc] = acc[i][j][e];
+        for (int c = 0; c < TN; c += 16) {
+            unsigned v[16];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                         "%12, %13, %14, %15}, [%16];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                           "=r"(v[14]), "=r"(v[15])
+                         : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < o.M) {
+                float *rp = dst + (long long)row * o.N + n0 + c;
+                if (n0 + c + 16 <= o.N && (o.N & 3) == 0) {   // 16-byte stores
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4 *>(rp + j) =
+                            chunk > 0 ? make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                    __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (n0 + c + j < o.N) rp[j] = chunk > 0 ? __uint_as_float(v[j]) : 0.f;
+                }
             }
         }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
 }
 
 template <int MODE>
@@ -235,9 +371,9 @@ int gemm(const __nv_bfloat16 *a, const __nv_bfloat16 *b, ConvGeom g, int M, int 
     splits = max(1, min(splits, kchunks));
     o.klen = ((kchunks + splits - 1) / splits) * BK;
     splits = (K + o.klen - 1) / o.klen;
-    dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, splits);
+    dim3 grid((M + TM - 1) / TM, (N + TN - 1) / TN, splits);
     count_launch();
-    k_gemm<MODE><<<grid, 128, 0, st>>>(o, out);
+    k_gemm_tc<MODE><<<grid, 128, 0, st>>>(o, out, unet_error_word());
     return splits;
 }
 
@@ -252,10 +388,21 @@ using namespace unet;
 // FP32 GEMM results for one operation, [splits][M][N]; `splits` > 1 only for
 // the weight gradients (K = pixels); each returns the number of splits used.
 int unet_conv3_fwd(const __nv_bfloat16 *x, const __nv_bfloat16 *w, int B, int H, int W, int Cin, int Cout,
-                    float *out, cudaStream_t st)
+                    float *out, long long out_cap, cudaStream_t st)
 {
     ConvGeom g{B, H, W, Cin, Cout};
-    return gemm<CONV_FWD>(x, w, g, B * H * W, Cout, 9 * Cin, 1, out, st);
+    // split K when the output tiles alone leave SMs idle (deep levels, small batches)
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const long long M = (long long)B * H * W, N = Cout;
+    const long long tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+    long long splits = (2LL * sms + tiles - 1) / tiles;
+    splits = std::max(1LL, std::min(splits, out_cap / (M * N)));
+    return gemm<CONV_FWD>(x, w, g, (int)M, Cout, 9 * Cin, (int)splits, out, st);
 }
 
 int unet_conv3_dgrad(const __nv_bfloat16 *dz, const __nv_bfloat16 *wt, int B, int H, int W, int Cin, int Cout,
