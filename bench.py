@@ -47,6 +47,24 @@ def dist_env():
     return ws, rank, local
 
 
+def job_time_ms(ms_local, ws, device):
+    """Whole-job time of N independent replicas: the maximum over ranks of the
+    per-rank timed region (all-reduce MAX; no data-path collective)."""
+    if ws <= 1:
+        return ms_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(updates_per_rank, ws, ms_job):
+    """Weak scaling: every rank processes the same workload, so the job's
+    throughput is ws x the per-rank updates over the slowest rank's time."""
+    return ws * updates_per_rank / (ms_job / 1e3)
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -249,14 +267,10 @@ def run_ours(args):
     wall = time.perf_counter() - t0
     launches = aafwi.launch_count() - l0
     clk = clocks.stop()
-    ms_total = e_start.elapsed_time(e_end)
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = job_time_ms(e_start.elapsed_time(e_end), ws, dev)
     nf, na = run.n_forward - nf0, run.n_adjoint - na0
     upd = (nf + na) * upd_pass
-    value = ws * upd / (ms_total / 1e3)
+    value = job_value(upd, ws, ms_total)
 
     # dominant kernel: the adjoint sweep timed alone (reusing a stored forward)
     kt = time_sweeps(plan, run, dev, args.kernel_reps)
@@ -431,6 +445,23 @@ def ncu_case(args):
                       "launches": aafwi.launch_count()}))
 
 
+def ncu_unet_case():
+    """A small case of the learned preconditioner's kernels for ncu: the
+    U-Net (C = 32) forward and one training step on a 16 x 96 x 256 batch."""
+    import torch
+    from paper_2008_11778_gb300 import aafwi
+    net = aafwi.UNet(16, 96, 256, 32)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((16, 2, 96, 256), device="cuda", generator=g)
+    t = 0.1 * torch.randn((16, 96, 256), device="cuda", generator=g)
+    y = torch.empty((16, 96, 256), device="cuda")
+    net.forward(x, y)
+    loss = net.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_unet_case": "unet-c32-16x96x256", "loss": loss, "launches": aafwi.launch_count()}))
+    net.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,6 +472,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="small case for ncu captures")
+    ap.add_argument("--ncu-unet-case", action="store_true", help="small U-Net case for ncu captures")
     ap.add_argument("--engine", default="tuned", choices=["tuned"] + list(ENGINES),
                     help="sweep engine: the library's autotuner (default) or a fixed one")
     ap.add_argument("--tile-z", type=int, default=0, help="per-step tile rows with a fixed engine")
@@ -449,7 +481,9 @@ def main():
     ap.add_argument("--learned-target", type=float, default=1e-2)
     ap.add_argument("--learned-max-iters", type=int, default=120)
     args = ap.parse_args()
-    if args.ncu_case:
+    if args.ncu_unet_case:
+        ncu_unet_case()
+    elif args.ncu_case:
         ncu_case(args)
     elif args.impl == "reference":
         run_reference(args)
