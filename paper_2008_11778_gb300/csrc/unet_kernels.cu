@@ -235,6 +235,8 @@ __device__ __forceinline__ unsigned long long tc_desc(unsigned addr)
 // Instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N = TN, M = TM.
 constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TN >> 3) << 17) |
                               ((unsigned)(TM >> 4) << 24);
+// The same with A and B MN-major (bits 15, 16).
+constexpr unsigned TC_IDESC_MN = TC_IDESC | (1u << 15) | (1u << 16);
 
 __device__ __forceinline__ bool tc_wait(unsigned bar, unsigned parity)
 {
@@ -256,6 +258,78 @@ __device__ __forceinline__ void tc_store16(unsigned char *tile, int r, int k, co
     hi.z = seg[12] | ((unsigned)seg[13] << 16); hi.w = seg[14] | ((unsigned)seg[15] << 16);
     *reinterpret_cast<uint4 *>(tile + tc_off(r, k)) = lo;
     *reinterpret_cast<uint4 *>(tile + tc_off(r, k + 8)) = hi;
+}
+
+// Weight gradients (K = pixels) keep their operands MN-major: in NHWC the
+// channels of one pixel are contiguous, so a chunk's A (M = channels) and B
+// (N = tap x channel or child x channel) are gathered as 8-element (16-byte)
+// runs along M / N for each of the chunk's TK pixels.  MN-major core matrix:
+// 8 K-rows x 16 bytes (8 MN elements); same LBO (K groups) / SBO (MN groups).
+__device__ __forceinline__ unsigned tc_off_mn(int mn, int k)
+{
+    return (unsigned)((mn >> 3) * T_SBO + (k >> 3) * T_LBO + (k & 7) * 16 + (mn & 7) * 2);
+}
+
+__device__ __forceinline__ uint4 ld8(const unsigned short *p)
+{
+    if (reinterpret_cast<uintptr_t>(p) & 15) {
+        unsigned w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = p[2 * i] | ((unsigned)p[2 * i + 1] << 16);
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// A (M = channel of dz or x, K = pixel) run: channels mg*8 .. +7 of pixel k.
+template <int MODE>
+__device__ __forceinline__ uint4 wgrad_a8(const Op<MODE> &o, int m, int k, int ke)
+{
+    const int C = MODE == CONV_WGRAD ? o.g.Cout : o.g.Cin;
+    if (k >= ke || m >= o.M) return make_uint4(0, 0, 0, 0);
+    if (m + 8 <= o.M && (C & 7) == 0) return ld8(o.a + (long long)k * C + m);
+    unsigned short v[8];
+    for (int i = 0; i < 8; ++i) v[i] = m + i < o.M ? o.a[(long long)k * C + m + i] : 0;
+    return make_uint4(v[0] | ((unsigned)v[1] << 16), v[2] | ((unsigned)v[3] << 16), v[4] | ((unsigned)v[5] << 16),
+                      v[6] | ((unsigned)v[7] << 16));
+}
+
+// B (N = tap x Cin for conv, child x Cout for upconv; K = pixel) run: n .. n+7 at pixel k.
+template <int MODE>
+__device__ __forceinline__ uint4 wgrad_b8(const Op<MODE> &o, int n, int k, int ke)
+{
+    const ConvGeom &g = o.g;
+    if (k >= ke || n >= o.N) return make_uint4(0, 0, 0, 0);
+    const Pix p = pix(g, k);
+    unsigned short v[8];
+    const int C = MODE == CONV_WGRAD ? g.Cin : g.Cout;
+    const int grp = n / C, c = n - grp * C;
+    long long base = -1;
+    if (MODE == CONV_WGRAD) {
+        const int yy = p.y + grp / 3 - 1, xx = p.x + grp % 3 - 1;
+        if (yy >= 0 && yy < g.H && xx >= 0 && xx < g.W) base = (((long long)p.b * g.H + yy) * g.W + xx) * C;
+    } else {
+        const int Y = 2 * p.y + grp / 2, X = 2 * p.x + (grp & 1);
+        base = (((long long)p.b * 2 * g.H + Y) * 2 * g.W + X) * C;
+    }
+    if ((C & 7) == 0 && n + 8 <= o.N) return base < 0 ? make_uint4(0, 0, 0, 0) : ld8(o.b + base + c);
+    for (int i = 0; i < 8; ++i) {   // a run crossing a tap / child boundary or the end of N
+        const int ni = n + i;
+        v[i] = 0;
+        if (ni < o.N) {
+            const int gi = ni / C, ci = ni - gi * C;
+            long long bi = -1;
+            if (MODE == CONV_WGRAD) {
+                const int yy = p.y + gi / 3 - 1, xx = p.x + gi % 3 - 1;
+                if (yy >= 0 && yy < g.H && xx >= 0 && xx < g.W) bi = (((long long)p.b * g.H + yy) * g.W + xx) * C;
+            } else {
+                bi = (((long long)p.b * 2 * g.H + 2 * p.y + gi / 2) * 2 * g.W + 2 * p.x + (gi & 1)) * C;
+            }
+            if (bi >= 0) v[i] = o.b[bi + ci];
+        }
+    }
+    return make_uint4(v[0] | ((unsigned)v[1] << 16), v[2] | ((unsigned)v[3] << 16), v[4] | ((unsigned)v[5] << 16),
+                      v[6] | ((unsigned)v[7] << 16));
 }
 
 template <int MODE>
@@ -286,21 +360,36 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const Op<MODE> o, float *out, i
     const unsigned tmem = tmem_sh;
     bool ok = true;
     int chunk = 0;
+    constexpr bool MN = MODE == CONV_WGRAD || MODE == UP_WGRAD;
     for (int k0 = kb; k0 < ke && ok; k0 += TK, ++chunk) {
-        unsigned short seg[16];
+        if (MN) {
+            // A: TK pixels x TM/8 runs (4 per thread); B: TK pixels x TN/8 runs (2 per thread)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {          // A: row tid, K halves
-            if (m0 + tid < o.M) fillA<MODE>(o, m0 + tid, k0 + 16 * h, ke, seg);
-            else
-                for (int i = 0; i < 16; ++i) seg[i] = 0;
-            tc_store16(As, tid, 16 * h, seg);
-        }
-        {                                      // B: row tid % 64, K half tid / 64
-            const int r = tid & (TN - 1), h = tid / TN;
-            if (n0 + r < o.N) fillB<MODE>(o, n0 + r, k0 + 16 * h, ke, seg);
-            else
-                for (int i = 0; i < 16; ++i) seg[i] = 0;
-            tc_store16(Bs, r, 16 * h, seg);
+            for (int i = 0; i < TK * TM / 8 / 128; ++i) {
+                const int t = tid + 128 * i, k = t / (TM / 8), mg = t - k * (TM / 8);
+                *reinterpret_cast<uint4 *>(As + tc_off_mn(8 * mg, k)) = wgrad_a8<MODE>(o, m0 + 8 * mg, k0 + k, ke);
+            }
+#pragma unroll
+            for (int i = 0; i < TK * TN / 8 / 128; ++i) {
+                const int t = tid + 128 * i, k = t / (TN / 8), ng = t - k * (TN / 8);
+                *reinterpret_cast<uint4 *>(Bs + tc_off_mn(8 * ng, k)) = wgrad_b8<MODE>(o, n0 + 8 * ng, k0 + k, ke);
+            }
+        } else {
+            unsigned short seg[16];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {          // A: row tid, K halves
+                if (m0 + tid < o.M) fillA<MODE>(o, m0 + tid, k0 + 16 * h, ke, seg);
+                else
+                    for (int i = 0; i < 16; ++i) seg[i] = 0;
+                tc_store16(As, tid, 16 * h, seg);
+            }
+            {                                      // B: row tid % 64, K half tid / 64
+                const int r = tid & (TN - 1), h = tid / TN;
+                if (n0 + r < o.N) fillB<MODE>(o, n0 + r, k0 + 16 * h, ke, seg);
+                else
+                    for (int i = 0; i < 16; ++i) seg[i] = 0;
+                tc_store16(Bs, r, 16 * h, seg);
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operands visible to the tensor cores
         __syncthreads();
@@ -313,7 +402,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const Op<MODE> o, float *out, i
                 const unsigned accum = (chunk > 0 || ks > 0) ? 1u : 0u;
                 asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
                              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                             "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(accum)
+                             "l"(ad), "l"(bd), "r"(MN ? TC_IDESC_MN : TC_IDESC), "r"(accum)
                              : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b)
