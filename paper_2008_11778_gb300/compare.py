@@ -116,11 +116,44 @@ def fwi(grads=40, M=10, snr_db=None, log=None):
             "gradient_budget": grads, "runs": rows}
 
 
+def large_aa(iters=3, M=10, log=None):
+    """AA(M) on the large workload (2001 x 601, 200 shots, 6000 steps; the
+    planner's shot batches): J/J0 and wall seconds per iteration."""
+    log = log or _log
+    p = synth.large()
+    g = p.geom
+    plan = aafwi.Plan(g, p.c_bounds[1])
+    lo, hi = p.m_bounds
+    d = torch.empty(plan.trace_count, device="cuda")
+    plan.model_forward(_dev(p.m_true), d)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run = solve.AAInversion(plan, d, _dev(p.m_start), M, bounds=(lo, hi))
+    ts = [time.perf_counter() - t0]
+    for _ in range(iters):
+        run.step()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    out = {"workload": "large-2001x601-200shots-6000steps", "M": M, "shots_per_batch": plan.info.shots_per_batch,
+           "batches": plan.info.n_batches, "checkpoint_every": plan.info.checkpoint_every,
+           "J_over_J0": [j / run.J0 for j in run.history["J"]], "gradients": run.n_adjoint,
+           "forward_passes": run.n_forward, "seconds": ts}
+    log("large", out["J_over_J0"][-1], ts[-1])
+    run.close()
+    return out
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser(description="solver comparisons of the paper on this library")
     ap.add_argument("--lsrtm-iters", type=int, default=20)
     ap.add_argument("--fwi-grads", type=int, default=40)
     ap.add_argument("--snr-db", type=float, default=0.55)
+    ap.add_argument("--large-iters", type=int, default=0, help="AA iterations on the large workload (0: skip)")
+    ap.add_argument("--only-large", action="store_true")
     a = ap.parse_args()
-    res = {"lsrtm": lsrtm(a.lsrtm_iters), "fwi": fwi(a.fwi_grads), "fwi_noisy": fwi(a.fwi_grads, snr_db=a.snr_db)}
+    res = {}
+    if not a.only_large:
+        res = {"lsrtm": lsrtm(a.lsrtm_iters), "fwi": fwi(a.fwi_grads), "fwi_noisy": fwi(a.fwi_grads, snr_db=a.snr_db)}
+    if a.large_iters > 0:
+        res["large"] = large_aa(a.large_iters)
     print(json.dumps(res))
