@@ -21,9 +21,10 @@ namespace unet {
 
 constexpr int BK = 32;   // K granularity of the splits
 
-// Operand gathers, one per GEMM mode.  fillA / fillB write 16 consecutive K
-// elements of one row of the A (M x K) or B^T (N x K) tile as raw BF16 bits,
-// 0 outside the tensor, the zero padding or the K range.
+// Operand gathers of the K-major modes (forward and data gradients).  fillA /
+// fillB write 16 consecutive K elements of one row of the A (M x K) or B^T
+// (N x K) tile as raw BF16 bits, 0 outside the tensor, the zero padding or the
+// K range.  The weight gradients gather MN-major (wgrad_a8 / wgrad_b8).
 struct ConvGeom {
     int B, H, W;       // batch and spatial size of the GEMM's pixel grid
     int Cin, Cout;
@@ -110,10 +111,6 @@ __device__ __forceinline__ void fillA(const Op<MODE> &o, int m, int k0, int ke, 
     if (MODE == CONV_FWD || MODE == CONV_DGRAD) {
         // m = pixel; x or dz in NHWC [B][H][W][C]
         im2col16(o.a, g, MODE == CONV_FWD ? g.Cin : g.Cout, pix(g, m), k0, ke, MODE == CONV_FWD ? 1 : -1, dst);
-    } else if (MODE == CONV_WGRAD || MODE == UP_WGRAD) {
-        // m = channel, k = pixel: t [P][C]
-        const int C = MODE == CONV_WGRAD ? g.Cout : g.Cin;
-        for (int i = 0; i < 16; ++i) dst[i] = k0 + i < ke ? o.a[(long long)(k0 + i) * C + m] : 0;
     } else if (MODE == UP_FWD) {
         // m = input pixel, k = cin: x [Pin][Cin]
         if ((g.Cin & 15) == 0 && k0 + 16 <= ke) load16(o.a + (long long)m * g.Cin + k0, dst);
@@ -148,30 +145,6 @@ __device__ __forceinline__ void fillB(const Op<MODE> &o, int n, int k0, int ke, 
             for (int i = 0; i < 16; ++i) dst[i] = k0 + i < ke ? o.b[(long long)n * o.K + k0 + i] : 0;
     } else if (MODE == UP_FWD) {  // w [Cin][4 Cout]: B(k = cin, n)
         for (int i = 0; i < 16; ++i) dst[i] = k0 + i < ke ? o.b[(long long)(k0 + i) * o.N + n] : 0;
-    } else if (MODE == CONV_WGRAD) {  // n = tap * Cin + cin, k = pixel: x [B][H][W][Cin]
-        const int tap = n / g.Cin, c = n - tap * g.Cin;
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        for (int i = 0; i < 16; ++i) {
-            unsigned short v = 0;
-            if (k0 + i < ke) {
-                const Pix q = pix(g, k0 + i);
-                const int yy = q.y + dy, xx = q.x + dx;
-                if (yy >= 0 && yy < g.H && xx >= 0 && xx < g.W)
-                    v = o.b[(((long long)q.b * g.H + yy) * g.W + xx) * g.Cin + c];
-            }
-            dst[i] = v;
-        }
-    } else {  // UP_WGRAD: n = q * Cout + co, k = coarse pixel: dy [B][2H][2W][Cout]
-        const int q = n / g.Cout, co = n - q * g.Cout;
-        for (int i = 0; i < 16; ++i) {
-            unsigned short v = 0;
-            if (k0 + i < ke) {
-                const Pix p = pix(g, k0 + i);
-                const int Y = 2 * p.y + q / 2, X = 2 * p.x + (q & 1);
-                v = o.b[(((long long)p.b * 2 * g.H + Y) * 2 * g.W + X) * g.Cout + co];
-            }
-            dst[i] = v;
-        }
     }
 }
 
