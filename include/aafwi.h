@@ -102,7 +102,8 @@ typedef struct {
 } aafwi_plan_opts;
 
 /* plan engines */
-#define AAFWI_ENGINE_AUTO       0   /* persistent when the plan qualifies, else per step */
+#define AAFWI_ENGINE_AUTO       0   /* per step (the fastest on the workloads measured;
+                                       aafwi_autotune chooses per geometry) */
 #define AAFWI_ENGINE_PER_STEP   1   /* one launch per time step (all shots) */
 #define AAFWI_ENGINE_PERSISTENT 2   /* one cooperative launch per sweep; ARG if the
                                        plan does not qualify (full history, strips of

@@ -353,7 +353,9 @@ int finish_sync(aafwi_plan *p, double *J_host, cudaStream_t st)
 int setup_persist(aafwi_plan *p, int engine, const aafwi_shots *sh, std::string *why)
 {
     p->persist_fwd = p->persist_adj = false;
-    if (engine == AAFWI_ENGINE_PER_STEP) return AAFWI_OK;
+    // AUTO takes the per-step engine: on every workload measured here it is the
+    // fastest (aafwi_autotune decides per geometry when asked)
+    if (engine == AAFWI_ENGINE_PER_STEP || engine == AAFWI_ENGINE_AUTO) return AAFWI_OK;
     auto no = [&](const char *m) {
         if (engine == AAFWI_ENGINE_PERSISTENT || engine == AAFWI_ENGINE_HYBRID) {
             *why = std::string("persistent engine not available: ") + m;

@@ -19,7 +19,7 @@ namespace aafwi {
 // 8th-order Laplacian.
 constexpr int HALO = 4;
 constexpr int TX = 128;
-constexpr int TZ_DEFAULT = 32;
+constexpr int TZ_DEFAULT = 16;
 constexpr int BX = 32;
 constexpr int BY = 8;
 constexpr int SW = TX + 2 * HALO;      // shared tile row length (floats)

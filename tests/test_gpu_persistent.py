@@ -67,12 +67,14 @@ def test_persistent_equals_per_step_bitwise(A, orc, make):
             assert (torch.equal(a, b) if torch.is_tensor(a) else a == b)
 
 
-def test_batched_plan_runs_persistent(A):
+def test_batched_plan_qualifies_for_the_persistent_engine(A):
     p = synth.batched()
-    plan = A.Plan(p.geom, c_max=p.c_bounds[1])
+    plan = A.Plan(p.geom, c_max=p.c_bounds[1], engine=A.ENGINE_PERSISTENT)
     assert plan.info.engine == A.ENGINE_PERSISTENT
     assert plan.info.persist_ctas >= 100
     assert plan.info.checkpoint_every == 1
+    auto = A.Plan(p.geom, c_max=p.c_bounds[1])
+    assert auto.info.engine == A.ENGINE_PER_STEP and auto.info.tile_z == 16
 
 
 def test_bounded_wait_reports_timeout_and_context_survives(A, orc):
