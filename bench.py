@@ -208,9 +208,10 @@ def make_plan(aafwi, prob, g, m_tune, args):
     """The benchmark's plan: the library's autotuned launch configuration
     (timed on short sweeps of this geometry before the timed region), or the
     engine / tile height given on the command line."""
+    pdl = not args.no_pdl
     if args.engine == "tuned":
-        return aafwi.Plan(g, c_max=prob.c_bounds[1], tune_model=m_tune, tune_cache=args.tune_cache)
-    return aafwi.Plan(g, c_max=prob.c_bounds[1], engine=ENGINES[args.engine], tile_z=args.tile_z)
+        return aafwi.Plan(g, c_max=prob.c_bounds[1], tune_model=m_tune, tune_cache=args.tune_cache, pdl=pdl)
+    return aafwi.Plan(g, c_max=prob.c_bounds[1], engine=ENGINES[args.engine], tile_z=args.tile_z, pdl=pdl)
 
 
 def run_ours(args):
@@ -315,7 +316,7 @@ def run_ours(args):
                            "shots": g.S, "nt": int(g.nt.max()), "M": prob.M,
                            "checkpoint_every": plan.info.checkpoint_every,
                            "engine": ENGINE_NAMES.get(plan.info.engine, plan.info.engine),
-                           "tile_z": plan.info.tile_z,
+                           "tile_z": plan.info.tile_z, "pdl": not args.no_pdl,
                            "autotune": None if tuning is None else {
                                "steps": tuning.get("steps"), "cached": tuning.get("cached"),
                                "table_ms": [[ENGINE_NAMES.get(e, e), t, ms] for e, t, ms in tuning["table"]]},
@@ -433,7 +434,8 @@ def ncu_case(args):
     from paper_2008_11778_gb300 import aafwi, synth
     prob = synth.batched()
     g = prob.geom.with_nt(64)
-    plan = aafwi.Plan(g, c_max=prob.c_bounds[1], engine=ENGINES.get(args.engine, 0), tile_z=args.tile_z)
+    plan = aafwi.Plan(g, c_max=prob.c_bounds[1], engine=ENGINES.get(args.engine, 0), tile_z=args.tile_z,
+                      pdl=not args.no_pdl)
     m = torch.as_tensor(prob.m_start.astype(np.float32), device="cuda")
     d_obs = torch.zeros(plan.trace_count, device="cuda")
     grad = torch.empty_like(m)
@@ -476,6 +478,7 @@ def main():
     ap.add_argument("--engine", default="tuned", choices=["tuned"] + list(ENGINES),
                     help="sweep engine: the library's autotuner (default) or a fixed one")
     ap.add_argument("--tile-z", type=int, default=0, help="per-step tile rows with a fixed engine")
+    ap.add_argument("--no-pdl", action="store_true", help="plain launches instead of programmatic dependents")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (default: the library's)")
     ap.add_argument("--learned-eval", type=int, default=3, help="held-out models for learned vs plain AA")
     ap.add_argument("--learned-target", type=float, default=1e-2)

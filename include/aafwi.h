@@ -99,6 +99,9 @@ typedef struct {
     int shots_per_batch;         /* 0: planner picks -- all shots if their workspace fits, else
                                     batches of shots run one after another (full history while a
                                     batch still fills the GPU, else checkpoints); > 0: this many */
+    int no_pdl;                  /* 0: each per-step launch after the first of a sweep is a
+                                    programmatic dependent launch (it becomes resident while the
+                                    previous step drains; same results); 1: plain launches */
 } aafwi_plan_opts;
 
 /* plan engines */

@@ -56,6 +56,7 @@ struct aafwi_plan {
     // zbuf, the checkpoints and the T history / replay buffer
     CUtensorMap tm_f{}, tm_d{}, tm_z{}, tm_ck{};
     CUtensorMap tm_fi{}, tm_zi{}, tm_cki{}, tm_t{};
+    CUtensorMap tm_w{};             // (Wh, Wl) as slots 0, 1 of a one-shot map
     float *dsyn = nullptr, *resid = nullptr;
     double *partials = nullptr, *J = nullptr;
     double *rowsum = nullptr;       // [NZ][nx] FP64 partial sums of the shot sum
@@ -73,6 +74,7 @@ struct aafwi_plan {
     // CUDA graphs of the per-step sweeps (one launch per time step): each
     // (sweep kind, caller buffer) is captured once and then replayed
     bool graphs = true;
+    bool pdl = true;   // per-step launches after a sweep's first: programmatic dependents
     struct SweepGraph {
         int kind;                   // SWEEP_*
         const void *ptr;            // the caller buffer the sweep reads or writes
@@ -242,10 +244,10 @@ int sweep_forward(aafwi_plan *p, const Geo &g, bool born, float *traces, cudaStr
             BornArgs a{p->W, p->rho_pad, cur, prev, next, n & 1,
                        slot(p->dbuf, ps, (n + 1) & 1), slot(p->dbuf, ps, (n + 1) & 1), ckc, ckp,
                        traces, tout, n};
-            launch_born(g, a, p->tm_f, p->tm_d, st);
+            launch_born(g, a, p->tm_f, p->tm_d, st, p->pdl && n > 0);
         } else {
             FwdArgs a{p->W, cur, (n + 1) & 1, next, ckc, ckp, traces, tout, n};
-            launch_fwd(g, a, p->tm_f, p->tm_fi, st);
+            launch_fwd(g, a, p->tm_f, p->tm_fi, p->tm_w, st, p->pdl && n > 0);
         }
     }
     return check_launch(p);
@@ -275,9 +277,16 @@ int sweep_adjoint(aafwi_plan *p, const Geo &g, bool born, const float *resid, cu
         return cuda_fail(p, cudaGetLastError(), "memset");
     if (cudaMemsetAsync(p->zbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
+    // The first launch of the sweep follows the memsets and runs as a plain
+    // launch; every later step kernel follows a step kernel and is launched
+    // as a programmatic dependent of it.  With the full history no launch of
+    // the sweep writes T, so the adjoint copies T^n before its grid wait.
+    bool first = true;
     auto adj = [&](int n, int t_slot) {   // T^n in slot t_slot of the T map
-        AdjArgs a{p->W, (n + 1) & 1, n & 1, slot(p->zbuf, ps, n & 1), t_slot, resid, p->img, n, born ? 1 : 0};
-        launch_adj(g, a, p->tm_z, p->tm_zi, p->tm_t, st);
+        AdjArgs a{p->W, (n + 1) & 1, n & 1, slot(p->zbuf, ps, n & 1), t_slot, resid, p->img, n, born ? 1 : 0,
+                  p->full && !first ? 1 : 0};
+        launch_adj(g, a, p->tm_z, p->tm_zi, p->tm_t, st, p->pdl && !first);
+        first = false;
     };
     if (p->full) {
         for (int n = p->nt_max - 1; n >= 0; --n) adj(n, n + 1);
@@ -293,7 +302,9 @@ int sweep_adjoint(aafwi_plan *p, const Geo &g, bool born, const float *resid, cu
             for (int n = a; n < e; ++n) {
                 FwdArgs f{p->W, uslot(n), uslot(n - 1), slot(p->fbuf, ps, (n + 1) & 1), nullptr,
                           nullptr, nullptr, slot(p->rbuf, ps, n - a), n};
-                launch_fwd(g, f, ck(n) ? p->tm_ck : p->tm_f, ck(n - 1) ? p->tm_cki : p->tm_fi, st);
+                launch_fwd(g, f, ck(n) ? p->tm_ck : p->tm_f, ck(n - 1) ? p->tm_cki : p->tm_fi, p->tm_w,
+                           st, p->pdl && !first);
+                first = false;
             }
             for (int n = e - 1; n >= a; --n) adj(n, n - a);
         }
@@ -541,6 +552,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     auto *p = new aafwi_plan();
     cudaGetDevice(&p->device);
     p->graphs = o.no_graphs == 0;
+    p->pdl = o.no_pdl == 0;
     p->nx = g->nx; p->nz = g->nz; p->nb = g->nb;
     p->dx = g->dx; p->dz = g->dz; p->dt = g->dt;
     p->NZ = g->nz + 2 * g->nb;
@@ -691,7 +703,8 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
         };
         bool mk = map(&p->tm_f, p->fbuf, 2, true) && map(&p->tm_fi, p->fbuf, 2, false) &&
                   map(&p->tm_d, p->dbuf, 2, true) && map(&p->tm_z, p->zbuf, 2, true) &&
-                  map(&p->tm_zi, p->zbuf, 2, false);
+                  map(&p->tm_zi, p->zbuf, 2, false) &&
+                  encode_tile_map(&p->tm_w, p->W, p->NX, p->NZ, p->pitch, p->field, 1, 2, TZ, false, &why);
         if (mk && p->full) mk = map(&p->tm_t, p->hist, p->nt_max + 1, false);
         if (mk && !p->full)
             mk = map(&p->tm_ck, p->hist, 2 * p->nck, true) && map(&p->tm_cki, p->hist, 2 * p->nck, false) &&

@@ -102,6 +102,7 @@ struct AdjArgs {
     float *img;                    // per-shot accumulators [S][field]
     int n;
     int born;
+    int t_early;                   // T^n is not written by the preceding launches: copy it before the grid wait
 };
 
 // Number of kernels this library has launched (host-side count).
@@ -136,11 +137,16 @@ PlanLayout plan_layout(long long field, long long cells, int S, int nt_max, long
 cudaError_t init_kernels();  // per-device kernel attributes (dynamic shared memory)
 void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho, float mcfl,
                  double K, float *W, float *rho_pad, int *err, cudaStream_t st);
-void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_p, cudaStream_t st);
+// Step launches with pdl = true may become resident while the previous
+// kernel in the stream drains (programmatic dependent launch); they touch no
+// memory written by earlier launches before their grid-dependency wait.
+// tm_w: the model pair (Wh, Wl) as slots 0 and 1 of a one-shot interior map.
+void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_p,
+                const CUtensorMap &tm_w, cudaStream_t st, bool pdl = false);
 void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d,
-                 cudaStream_t st);
+                 cudaStream_t st, bool pdl = false);
 void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, const CUtensorMap &tm_z2,
-                const CUtensorMap &tm_t, cudaStream_t st);
+                const CUtensorMap &tm_t, cudaStream_t st, bool pdl = false);
 // Shot sum and E^T of the batch's images: rowsum (FP64 [NZ][nx]) = or +=
 // (accumulate) the sum over the batch's shots; the second pass, when out is
 // not null, folds rowsum over z into out [nz][nx].

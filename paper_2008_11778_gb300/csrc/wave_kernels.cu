@@ -81,26 +81,55 @@ struct Copy4 {
     int x, z, s, slot;
 };
 
-// Thread (0, 0) arms the CTA's mbarrier for `bytes` and issues the copies;
-// every thread then waits for them.  Returns false (and raises bit 2 of the
-// error word) if they do not land within the wait limit; the whole CTA
-// returns the same value.
+// Programmatic dependent launch: wait until the launches before this one
+// have completed and their writes are visible, then let the next launch in
+// the stream become resident while this grid runs.  Every thread of every
+// CTA waits before it touches memory that earlier launches write (so each
+// launch completes after its predecessor, including CTAs that return early).
+// Without the launch attribute the wait returns at once.
+__device__ __forceinline__ void grid_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ void issue(const Copy4 &cp, unsigned b)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(cp.dst)),
+                 "l"(reinterpret_cast<unsigned long long>(cp.map)), "r"(cp.x), "r"(cp.z), "r"(cp.s), "r"(cp.slot),
+                 "r"(b)
+                 : "memory");
+}
+
+// Thread (0, 0) arms the CTA's mbarrier for `bytes` and issues the copies:
+// the first n_early (sources no earlier launch of the stream writes) before
+// the grid-dependency wait, the rest after it; every thread then waits for
+// them.  Returns false (and raises bit 2 of the error word) if they do not
+// land within the wait limit; the whole CTA returns the same value.
 template <int N>
-__device__ __forceinline__ bool stage(unsigned long long *bar, const Copy4 (&cp)[N], unsigned bytes, int *err)
+__device__ __forceinline__ bool stage(unsigned long long *bar, const Copy4 (&cp)[N], unsigned bytes, int *err,
+                                      int n_early = 0)
 {
     const unsigned b = smem_addr(bar);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    if (lead) {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(cp[i].map)) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
 #pragma unroll
         for (int i = 0; i < N; ++i)
-            asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                         " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(cp[i].dst)),
-                         "l"(reinterpret_cast<unsigned long long>(cp[i].map)), "r"(cp[i].x), "r"(cp[i].z),
-                         "r"(cp[i].s), "r"(cp[i].slot), "r"(b)
-                         : "memory");
+            if (i < n_early) issue(cp[i], b);
+    }
+    grid_wait();
+    if (lead) {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i >= n_early) issue(cp[i], b);
     }
     __syncthreads();   // the barrier is initialised before anyone waits on it
     bool ok = false;
@@ -192,11 +221,15 @@ __device__ __forceinline__ void gather(const Geo &g, int s, int tile, int n, con
 
 template <int RZ>
 __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a, const __grid_constant__ CUtensorMap tm_u,
-                                                const __grid_constant__ CUtensorMap tm_p)
+                                                const __grid_constant__ CUtensorMap tm_p,
+                                                const __grid_constant__ CUtensorMap tm_w)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
-    if (a.n >= g.nt[sg]) return;
+    if (a.n >= g.nt[sg]) {
+        grid_wait();
+        return;
+    }
     const int tile = blockIdx.x;
     const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
     const int z0 = tzi * TZ, x0 = txi * TX;
@@ -204,9 +237,13 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
     __shared__ unsigned long long bar;
     Tile *su = reinterpret_cast<Tile *>(smem);                              // u^n with halo
     float(*sp)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW);        // u^{n-1}
+    float(*swh)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW + TZ * TX);      // Wh
+    float(*swl)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW + 2 * TZ * TX);  // Wl
     const long long base = (long long)s * g.field;
-    const Copy4 cp[2] = {{su, &tm_u, x0 - HALO, z0 - HALO, s, a.cur_slot}, {sp, &tm_p, x0, z0, s, a.prev_slot}};
-    if (!stage(&bar, cp, (unsigned)((SH * SW + TZ * TX) * sizeof(float)), g.err)) return;
+    // W is written only before a sweep's first launch: copied before the grid wait
+    const Copy4 cp[4] = {{swh, &tm_w, x0, z0, 0, 0}, {swl, &tm_w, x0, z0, 0, 1},
+                         {su, &tm_u, x0 - HALO, z0 - HALO, s, a.cur_slot}, {sp, &tm_p, x0, z0, s, a.prev_slot}};
+    if (!stage(&bar, cp, (unsigned)((SH * SW + 3 * TZ * TX) * sizeof(float)), g.err, 2)) return;
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {
         const float4 dgx = ld4g(g.dGx + x);
@@ -223,7 +260,8 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
             const float4 dG = sponge4(g.dGz[z], dgx);
             const float4 uc = ld4s(su, zl + HALO, xl + HALO);
             const float4 up = *reinterpret_cast<const float4 *>(&sp[zl][xl]);
-            const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
+            const float4 wh = *reinterpret_cast<const float4 *>(&swh[zl][xl]);
+            const float4 wl = *reinterpret_cast<const float4 *>(&swl[zl][xl]);
             st4g(a.u_next + base + cell, leapfrog(dG, uc, up, T, wh, wl));
             if (a.ck_cur) {
                 st4g(a.ck_cur + base + cell, uc);
@@ -240,7 +278,10 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
-    if (a.n >= g.nt[sg]) return;
+    if (a.n >= g.nt[sg]) {
+        grid_wait();
+        return;
+    }
     const int tile = blockIdx.x;
     const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
     const int z0 = tzi * TZ, x0 = txi * TX;
@@ -295,7 +336,10 @@ __global__ void __launch_bounds__(BX *BY, 5) k_adj(const Geo g, const AdjArgs a,
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
-    if (a.n >= g.nt[sg]) return;
+    if (a.n >= g.nt[sg]) {
+        grid_wait();
+        return;
+    }
     const int tile = blockIdx.x;
     const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
     const int z0 = tzi * TZ, x0 = txi * TX;
@@ -306,9 +350,9 @@ __global__ void __launch_bounds__(BX *BY, 5) k_adj(const Geo g, const AdjArgs a,
     float(*sz2)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW + TZ * TX);  // z^{n+2}
     float(*st)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW + 2 * TZ * TX);  // T^n
     const long long base = (long long)s * g.field;
-    const Copy4 cp[3] = {{sz, &tm_z, x0 - HALO, z0 - HALO, s, a.z1_slot}, {sz2, &tm_z2, x0, z0, s, a.z2_slot},
-                         {st, &tm_t, x0, z0, s, a.t_slot}};
-    if (!stage(&bar, cp, (unsigned)((SH * SW + 2 * TZ * TX) * sizeof(float)), g.err)) return;
+    const Copy4 cp[3] = {{st, &tm_t, x0, z0, s, a.t_slot}, {sz, &tm_z, x0 - HALO, z0 - HALO, s, a.z1_slot},
+                         {sz2, &tm_z2, x0, z0, s, a.z2_slot}};
+    if (!stage(&bar, cp, (unsigned)((SH * SW + 2 * TZ * TX) * sizeof(float)), g.err, a.t_early ? 1 : 0)) return;
     const int t = sg * g.ntiles + tile;
     const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
     const bool has_rec = r1 > r0;
@@ -425,7 +469,7 @@ __global__ void k_shot_sum_z(const Geo g, int nz, int nx, const double *rowsum, 
 }
 
 template <int RZ>
-static size_t fwd_smem() { return ((RZ * BY + 2 * HALO) * SW + RZ * BY * TX) * sizeof(float); }
+static size_t fwd_smem() { return ((RZ * BY + 2 * HALO) * SW + 3 * RZ * BY * TX) * sizeof(float); }
 template <int RZ>
 static size_t born_smem() { return 2 * (RZ * BY + 2 * HALO) * SW * sizeof(float); }
 template <int RZ>
@@ -486,32 +530,46 @@ bool encode_tile_map(CUtensorMap *m, const float *base, int NX, int NZ, int pitc
     return true;
 }
 
-void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_p, cudaStream_t st)
+// Launch a step kernel, with the programmatic-serialisation attribute when pdl.
+template <typename... P, typename... A>
+static void launch_step(void (*k)(P...), size_t smem, const Geo &g, cudaStream_t st, bool pdl, A &&...args)
 {
     count_launch();
-    const dim3 grid(g.ntiles, g.S), block(BX, BY);
-    if (g.tz == 16) k_fwd<2><<<grid, block, fwd_smem<2>(), st>>>(g, a, tm_u, tm_p);
-    else if (g.tz == 64) k_fwd<8><<<grid, block, fwd_smem<8>(), st>>>(g, a, tm_u, tm_p);
-    else k_fwd<4><<<grid, block, fwd_smem<4>(), st>>>(g, a, tm_u, tm_p);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g.ntiles, g.S);
+    cfg.blockDim = dim3(BX, BY);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);   // errors: cudaGetLastError
 }
 
-void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d, cudaStream_t st)
+void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_p,
+                const CUtensorMap &tm_w, cudaStream_t st, bool pdl)
 {
-    count_launch();
-    const dim3 grid(g.ntiles, g.S), block(BX, BY);
-    if (g.tz == 16) k_born<2><<<grid, block, born_smem<2>(), st>>>(g, a, tm_u, tm_d);
-    else if (g.tz == 64) k_born<8><<<grid, block, born_smem<8>(), st>>>(g, a, tm_u, tm_d);
-    else k_born<4><<<grid, block, born_smem<4>(), st>>>(g, a, tm_u, tm_d);
+    if (g.tz == 16) launch_step(k_fwd<2>, fwd_smem<2>(), g, st, pdl, g, a, tm_u, tm_p, tm_w);
+    else if (g.tz == 64) launch_step(k_fwd<8>, fwd_smem<8>(), g, st, pdl, g, a, tm_u, tm_p, tm_w);
+    else launch_step(k_fwd<4>, fwd_smem<4>(), g, st, pdl, g, a, tm_u, tm_p, tm_w);
+}
+
+void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d, cudaStream_t st,
+                 bool pdl)
+{
+    if (g.tz == 16) launch_step(k_born<2>, born_smem<2>(), g, st, pdl, g, a, tm_u, tm_d);
+    else if (g.tz == 64) launch_step(k_born<8>, born_smem<8>(), g, st, pdl, g, a, tm_u, tm_d);
+    else launch_step(k_born<4>, born_smem<4>(), g, st, pdl, g, a, tm_u, tm_d);
 }
 
 void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, const CUtensorMap &tm_z2,
-                const CUtensorMap &tm_t, cudaStream_t st)
+                const CUtensorMap &tm_t, cudaStream_t st, bool pdl)
 {
-    count_launch();
-    const dim3 grid(g.ntiles, g.S), block(BX, BY);
-    if (g.tz == 16) k_adj<2><<<grid, block, adj_smem<2>(), st>>>(g, a, tm_z, tm_z2, tm_t);
-    else if (g.tz == 64) k_adj<8><<<grid, block, adj_smem<8>(), st>>>(g, a, tm_z, tm_z2, tm_t);
-    else k_adj<4><<<grid, block, adj_smem<4>(), st>>>(g, a, tm_z, tm_z2, tm_t);
+    if (g.tz == 16) launch_step(k_adj<2>, adj_smem<2>(), g, st, pdl, g, a, tm_z, tm_z2, tm_t);
+    else if (g.tz == 64) launch_step(k_adj<8>, adj_smem<8>(), g, st, pdl, g, a, tm_z, tm_z2, tm_t);
+    else launch_step(k_adj<4>, adj_smem<4>(), g, st, pdl, g, a, tm_z, tm_z2, tm_t);
 }
 
 void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *rowsum, bool accumulate, float *out,

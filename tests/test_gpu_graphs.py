@@ -85,3 +85,31 @@ def test_graph_cache_reuses_and_recaptures(A):
     for d in outs[1:]:
         assert torch.equal(d, outs[0])
     assert torch.isfinite(outs[0]).all() and outs[0].abs().max() > 0
+
+
+@pytest.mark.parametrize("checkpoint_every", [1, 7], ids=["full", "checkpoints"])
+@pytest.mark.parametrize("graphs", [False, True], ids=["launches", "graphs"])
+def test_dependent_launches_equal_plain_launches(A, orc, checkpoint_every, graphs):
+    """Programmatic dependent launches (each step kernel resident while the
+    previous one drains, the adjoint's T^n copy issued before the grid wait)
+    give bitwise the results of plain launches, with the same launch count;
+    the records are uneven, so in the one-shot batches of the third plan
+    whole launches have no active CTA."""
+    import torch
+    p = synth.tiny()
+    g = p.geom
+    g.nt = np.array([600, 410, 520], dtype=np.int32)
+    d_obs = torch.as_tensor(orc.forward(g, p.m_true).astype(np.float32), device="cuda")
+    rho = torch.as_tensor(np.random.default_rng(6).uniform(-0.1, 0.1, (g.nz, g.nx)).astype(np.float32),
+                          device="cuda")
+    kw = dict(engine=A.ENGINE_PER_STEP, checkpoint_every=checkpoint_every, graphs=graphs)
+    o1, l1 = run_all(A, A.Plan(g, 3000.0, pdl=False, **kw), p, d_obs, rho)
+    o2, l2 = run_all(A, A.Plan(g, 3000.0, pdl=True, **kw), p, d_obs, rho)
+    o3, l3 = run_all(A, A.Plan(g, 3000.0, pdl=True, shots_per_batch=1, **kw), p, d_obs, rho)
+    for k in o1:
+        a, b, c = o1[k], o2[k], o3[k]
+        if isinstance(a, tuple):
+            assert a[0] == b[0] == c[0], k
+            a, b, c = a[1], b[1], c[1]
+        assert torch.equal(a, b) and torch.equal(a, c), k
+    assert l1 == l2
