@@ -102,6 +102,13 @@ typedef struct {
     int no_pdl;                  /* 0: each per-step launch after the first of a sweep is a
                                     programmatic dependent launch (it becomes resident while the
                                     previous step drains; same results); 1: plain launches */
+    int steps_per_launch;        /* FWI forward sweeps with the full history on the per-step
+                                    engine: 0 or 1 = one time step per launch; 2 = two (the tile
+                                    and a 4-cell ring advanced to n+1 on chip, then the tile to
+                                    n+2; bitwise the one-step results, fewer launches and L2
+                                    reads but 1.6x the stencil work of the first step: slower
+                                    on the workloads measured).  Born sweeps and checkpoint
+                                    plans always take one. */
 } aafwi_plan_opts;
 
 /* plan engines */
@@ -128,6 +135,7 @@ typedef struct {
     int shots_per_batch, n_batches;   /* the plan's shot batches (1 batch: all shots at once;
                                          more: the stored forward is not kept between calls,
                                          AAFWI_REUSE_FORWARD returns STATE) */
+    int steps_per_launch;        /* time steps per launch of the per-step FWI forward sweeps */
 } aafwi_plan_info;
 
 /* ---- plan -------------------------------------------------------------- */

@@ -46,7 +46,8 @@ struct aafwi_plan {
     float *W = nullptr, *rho_pad = nullptr;   // W: Wh then Wl, each [NZ][pitch]
     double K = 0.0;                 // dt^2 / (5040 dx^2)
     float *hist = nullptr;          // full: T^n in slot n+1 (nt_max+1 slots); else 2*nck checkpoint slots
-    float *fbuf = nullptr;          // 2 rotating forward slots (u^n, u^{n-1}; in place)
+    float *fbuf = nullptr;          // 4 forward slots: one-step sweeps rotate u^n, u^{n-1} in slots 0, 1
+                                    // (in place); two-step sweeps alternate pairs (0, 1) and (2, 3)
     float *rbuf = nullptr;          // k replay slots of T (checkpoint mode)
     float *dbuf = nullptr;          // 2 rotating Born slots
     float *zbuf = nullptr;          // 2 rotating adjoint slots
@@ -57,6 +58,7 @@ struct aafwi_plan {
     CUtensorMap tm_f{}, tm_d{}, tm_z{}, tm_ck{};
     CUtensorMap tm_fi{}, tm_zi{}, tm_cki{}, tm_t{};
     CUtensorMap tm_w{};             // (Wh, Wl) as slots 0, 1 of a one-shot map
+    CUtensorMap tm_f8{};            // fbuf with an 8-cell halo (two-step forward)
     float *dsyn = nullptr, *resid = nullptr;
     double *partials = nullptr, *J = nullptr;
     double *rowsum = nullptr;       // [NZ][nx] FP64 partial sums of the shot sum
@@ -75,6 +77,7 @@ struct aafwi_plan {
     // (sweep kind, caller buffer) is captured once and then replayed
     bool graphs = true;
     bool pdl = true;   // per-step launches after a sweep's first: programmatic dependents
+    int steps_per_launch = 1;       // full-history FWI forward sweeps: 1 or 2 (k_fwd2)
     struct SweepGraph {
         int kind;                   // SWEEP_*
         const void *ptr;            // the caller buffer the sweep reads or writes
@@ -230,9 +233,21 @@ int sweep_forward(aafwi_plan *p, const Geo &g, bool born, float *traces, cudaStr
         return cuda_fail(p, cudaGetLastError(), "memset");
     if (born && cudaMemsetAsync(p->dbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
-    for (int n = 0; n < p->nt_max; ++n) {
-        const int cur = n & 1;     // u^n in fbuf slot n&1; u^{n-1} and u^{n+1} in the other
-        float *prev = slot(p->fbuf, ps, (n + 1) & 1), *next = prev;
+    int n0 = 0, cur = 0, prv = 1;   // after the two-step part: u^n in slot cur, u^{n-1} in slot prv
+    if (!born && p->full && p->steps_per_launch == 2) {
+        // (u^{n-1}, u^n) in slots (2q, 2q+1); (u^{n+1}, u^{n+2}) to the other pair
+        int q = 0;
+        for (; n0 + 1 < p->nt_max; n0 += 2, q ^= 1) {
+            Fwd2Args a{p->W, 2 * q, 2 * q + 1, slot(p->fbuf, ps, 2 * (q ^ 1)), slot(p->fbuf, ps, 2 * (q ^ 1) + 1),
+                       traces, slot(p->hist, ps, n0 + 1), slot(p->hist, ps, n0 + 2), n0};
+            launch_fwd2(g, a, p->tm_f8, p->tm_f, st, p->pdl && n0 > 0);
+        }
+        cur = 2 * q + 1;
+        prv = 2 * q;
+    }
+    for (int n = n0; n < p->nt_max; ++n) {
+        // one step: u^{n+1} overwrites u^{n-1} in place, then the slots swap roles
+        float *prev = slot(p->fbuf, ps, prv), *next = prev;
         float *ckc = nullptr, *ckp = nullptr, *tout = nullptr;
         if (p->full) {
             tout = slot(p->hist, ps, n + 1);
@@ -246,9 +261,10 @@ int sweep_forward(aafwi_plan *p, const Geo &g, bool born, float *traces, cudaStr
                        traces, tout, n};
             launch_born(g, a, p->tm_f, p->tm_d, st, p->pdl && n > 0);
         } else {
-            FwdArgs a{p->W, cur, (n + 1) & 1, next, ckc, ckp, traces, tout, n};
+            FwdArgs a{p->W, cur, prv, next, ckc, ckp, traces, tout, n};
             launch_fwd(g, a, p->tm_f, p->tm_fi, p->tm_w, st, p->pdl && n > 0);
         }
+        std::swap(cur, prv);
     }
     return check_launch(p);
 }
@@ -483,8 +499,8 @@ PlanLayout aafwi::plan_layout(long long field, long long cells, int S, int nt_ma
     }
     L.budget = budget;
     const size_t F = (size_t)field * sizeof(float);
-    auto fixed = [&](int Sb) {   // W pair + rho; fbuf, dbuf, zbuf (2 slots each) + img; dsyn + resid
-        return 3 * F + (2 + 2 + 2 + 1) * F * Sb + 2 * (size_t)trace_count * sizeof(float) + (1 << 20);
+    auto fixed = [&](int Sb) {   // W pair + rho; fbuf (4 slots), dbuf, zbuf (2 each) + img; dsyn + resid
+        return 3 * F + (4 + 2 + 2 + 1) * F * Sb + 2 * (size_t)trace_count * sizeof(float) + (1 << 20);
     };
     const int k = o.checkpoint_every >= 2 ? o.checkpoint_every
                                           : std::max(2, (int)std::lround(std::sqrt(2.0 * nt_max)));
@@ -553,6 +569,11 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     cudaGetDevice(&p->device);
     p->graphs = o.no_graphs == 0;
     p->pdl = o.no_pdl == 0;
+    if (o.steps_per_launch < 0 || o.steps_per_launch > 2) {
+        delete p;
+        return fail(nullptr, AAFWI_ERR_ARG, "steps_per_launch must be 0, 1 or 2");
+    }
+    p->steps_per_launch = o.steps_per_launch == 2 ? 2 : 1;
     p->nx = g->nx; p->nz = g->nz; p->nb = g->nb;
     p->dx = g->dx; p->dz = g->dz; p->dt = g->dt;
     p->NZ = g->nz + 2 * g->nb;
@@ -662,7 +683,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
               upload(p->bufs, &d_troff, p->tr_off);
     const long long ps = (long long)p->Sb * p->field;   // one slot: the batch's shots
     ok = ok && dalloc(p->bufs, &p->W, 2 * p->field) && dalloc(p->bufs, &p->rho_pad, p->field) &&
-         dalloc(p->bufs, &p->dbuf, 2 * ps) && dalloc(p->bufs, &p->zbuf, 2 * ps) && dalloc(p->bufs, &p->fbuf, 2 * ps) &&
+         dalloc(p->bufs, &p->dbuf, 2 * ps) && dalloc(p->bufs, &p->zbuf, 2 * ps) && dalloc(p->bufs, &p->fbuf, 4 * ps) &&
          dalloc(p->bufs, &p->img, ps) && dalloc(p->bufs, &p->dsyn, p->trace_count) &&
          dalloc(p->bufs, &p->resid, p->trace_count) && dalloc(p->bufs, &p->partials, RED_BLOCKS) &&
          dalloc(p->bufs, &p->J, 1) && dalloc(p->bufs, &p->err, 1) &&
@@ -699,12 +720,15 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     {
         std::string why;
         auto map = [&](CUtensorMap *m, const float *buf, int slots, bool halo) {
-            return encode_tile_map(m, buf, p->NX, p->NZ, p->pitch, p->field, p->Sb, slots, TZ, halo, &why);
+            return encode_tile_map(m, buf, p->NX, p->NZ, p->pitch, p->field, p->Sb, slots, TZ, halo ? HALO : 0,
+                                   &why);
         };
-        bool mk = map(&p->tm_f, p->fbuf, 2, true) && map(&p->tm_fi, p->fbuf, 2, false) &&
+        bool mk = map(&p->tm_f, p->fbuf, 4, true) && map(&p->tm_fi, p->fbuf, 4, false) &&
+                  encode_tile_map(&p->tm_f8, p->fbuf, p->NX, p->NZ, p->pitch, p->field, p->Sb, 4, TZ, 2 * HALO,
+                                  &why) &&
                   map(&p->tm_d, p->dbuf, 2, true) && map(&p->tm_z, p->zbuf, 2, true) &&
                   map(&p->tm_zi, p->zbuf, 2, false) &&
-                  encode_tile_map(&p->tm_w, p->W, p->NX, p->NZ, p->pitch, p->field, 1, 2, TZ, false, &why);
+                  encode_tile_map(&p->tm_w, p->W, p->NX, p->NZ, p->pitch, p->field, 1, 2, TZ, 0, &why);
         if (mk && p->full) mk = map(&p->tm_t, p->hist, p->nt_max + 1, false);
         if (mk && !p->full)
             mk = map(&p->tm_ck, p->hist, 2 * p->nck, true) && map(&p->tm_cki, p->hist, 2 * p->nck, false) &&
@@ -760,6 +784,7 @@ int aafwi_plan_get_info(const aafwi_plan *p, aafwi_plan_info *info)
     info->persist_ctas = p->persist_adj ? p->pgeo.P : 0;
     info->shots_per_batch = p->Sb;
     info->n_batches = p->nbatch;
+    info->steps_per_launch = (p->full && p->steps_per_launch == 2 && !p->persist_fwd) ? 2 : 1;
     return AAFWI_OK;
 }
 

@@ -23,15 +23,17 @@ constexpr int TZ_DEFAULT = 16;
 constexpr int BX = 32;
 constexpr int BY = 8;
 constexpr int SW = TX + 2 * HALO;      // shared tile row length (floats)
+constexpr int SW8 = TX + 4 * HALO;     // the same with an 8-cell halo (two-step forward)
 inline bool tile_z_supported(int tz) { return tz == 16 || tz == 32 || tz == 64; }
 
 // The per-step kernels stage their inputs with TMA copies from 4D tensor
 // maps of the field buffers: (x < NX, z < NZ, shot, slot) with row pitch
-// `pitch`.  A halo map's box is a tile with its 4-cell halo (tz + 8 rows x SW
-// columns), an interior map's box the tile alone (tz x TX); cells outside the
+// `pitch`.  The box is a tile with a halo of `halo` cells on every side:
+// 0 (interior map, tz x TX), HALO (tz + 8 rows x SW columns) or 2 HALO (the
+// two-step forward's u^n, tz + 16 rows x SW8 columns); cells outside the
 // padded grid (negative or beyond NX / NZ) arrive as zeros.
 bool encode_tile_map(CUtensorMap *m, const float *base, int NX, int NZ, int pitch, long long field, int S,
-                     int slots, int tile_rows, bool halo, std::string *why);
+                     int slots, int tile_rows, int halo, std::string *why);
 
 // Per-plan geometry, all pointers device.
 struct Geo {
@@ -75,6 +77,18 @@ struct FwdArgs {
 };
 
 // Born step: background u and scattered du together (eq. Born).
+// Two forward steps n, n+1 in one launch (full history): reads u^{n-1},
+// u^n from fbuf slots, writes u^{n+1}, u^{n+2} to the other two (out of
+// place: neighbouring CTAs read u^{n-1} and u^n around their own tiles).
+struct Fwd2Args {
+    const float *W;
+    int prev_slot, cur_slot;       // u^{n-1} (4-cell halo map), u^n (8-cell halo map)
+    float *u1, *u2;                // out: u^{n+1}, u^{n+2}
+    float *traces;                 // CSR traces or null
+    float *t1, *t2;                // out: T^n, T^{n+1} (history slots n+1, n+2)
+    int n;
+};
+
 struct BornArgs {
     const float *W, *rho;
     int u_slot;                    // slot of u^n in the u tile map
@@ -143,6 +157,8 @@ void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho,
 // tm_w: the model pair (Wh, Wl) as slots 0 and 1 of a one-shot interior map.
 void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_p,
                 const CUtensorMap &tm_w, cudaStream_t st, bool pdl = false);
+void launch_fwd2(const Geo &g, const Fwd2Args &a, const CUtensorMap &tm_u8, const CUtensorMap &tm_u4, cudaStream_t st,
+                 bool pdl = false);
 void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d,
                  cudaStream_t st, bool pdl = false);
 void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, const CUtensorMap &tm_z2,

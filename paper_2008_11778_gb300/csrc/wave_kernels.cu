@@ -47,8 +47,10 @@ constexpr float A3 = 128.f;
 constexpr float A4 = -9.f;
 
 typedef float Tile[SW];
+typedef float Tile8[SW8];   // row of a tile with an 8-cell halo (two-step forward)
 
-__device__ __forceinline__ float4 ld4s(const Tile *s, int r, int c)
+template <int W>
+__device__ __forceinline__ float4 ld4s(const float (*s)[W], int r, int c)
 {
     return *reinterpret_cast<const float4 *>(&s[r][c]);
 }
@@ -147,7 +149,8 @@ __device__ __forceinline__ float d2(float c, float a, float b) { return (a - c) 
 
 // T = rz * S_z + S_x at the four cells (rr, cc..cc+3) of a staged tile, where
 // S is the integer-weight second difference along each axis (L = T/(5040 dx^2)).
-__device__ __forceinline__ float4 stencil4(const Tile *s, int rr, int cc, float rz)
+template <int W>
+__device__ __forceinline__ float4 stencil4(const float (*s)[W], int rr, int cc, float rz)
 {
     const float4 L = ld4s(s, rr, cc - 4), M = ld4s(s, rr, cc), R = ld4s(s, rr, cc + 4);
     const float v[12] = {L.x, L.y, L.z, L.w, M.x, M.y, M.z, M.w, R.x, R.y, R.z, R.w};
@@ -270,6 +273,90 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
         }
     }
     if (a.traces) gather(g, sg, tile, a.n, a.u_next + base, a.traces);
+}
+
+// Steps n and n+1 in one launch (full-history forward sweeps).  The CTA
+// stages u^n with an 8-cell halo and u^{n-1} with a 4-cell halo, advances
+// its tile and the 4-cell ring around it to u^{n+1} (in shared memory, over
+// u^{n-1}), then the tile to u^{n+2}.  Ring cells belong to neighbouring
+// tiles, which compute them with the same operations in the same order, so
+// every cell gets bitwise the value of the one-step kernel; ring cells
+// outside the grid columns [0, pitch) or rows [0, NZ) are zero, as the
+// one-step kernel's zero-filled halo.  T^n, T^{n+1} and u^{n+1}, u^{n+2} of
+// the tile go to HBM, the traces of both steps are gathered.  A shot whose
+// record ends after step n stops there.
+template <int RZ>
+__global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args a,
+                                                 const __grid_constant__ CUtensorMap tm_u8,
+                                                 const __grid_constant__ CUtensorMap tm_u4)
+{
+    constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO, SH8 = TZ + 4 * HALO;
+    constexpr int GR = SW / 4;   // float4 groups per row of tile + ring
+    const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
+    if (a.n >= g.nt[sg]) {
+        grid_wait();
+        return;
+    }
+    const bool second = a.n + 1 < g.nt[sg];
+    const int tile = blockIdx.x;
+    const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
+    const int z0 = tzi * TZ, x0 = txi * TX;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ unsigned long long bar;
+    Tile8 *sa = reinterpret_cast<Tile8 *>(smem);                // u^n, 8-cell halo
+    Tile *sb = reinterpret_cast<Tile *>(smem + SH8 * SW8);      // u^{n-1}, then u^{n+1}; 4-cell halo
+    const long long base = (long long)s * g.field;
+    const Copy4 cp[2] = {{sa, &tm_u8, x0 - 2 * HALO, z0 - 2 * HALO, s, a.cur_slot},
+                         {sb, &tm_u4, x0 - HALO, z0 - HALO, s, a.prev_slot}};
+    if (!stage(&bar, cp, (unsigned)((SH8 * SW8 + SH * SW) * sizeof(float)), g.err)) return;
+    const int src = g.src_pt[sg];
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    {   // step n on tile + ring; (rr, xr) in sb coordinates (origin z0 - 4, x0 - 4)
+        const float wsn = g.ws[a.n];
+        for (int i = tid; i < SH * GR; i += BX * BY) {
+            const int rr = i / GR, xr = (i - rr * GR) * 4;
+            const int z = z0 - HALO + rr, x = x0 - HALO + xr;
+            float4 un = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (z >= 0 && z < g.NZ && x >= 0 && x < g.pitch) {
+                const long long cell = (long long)z * g.pitch + x;
+                const bool inner = rr >= HALO && rr < HALO + TZ && xr >= HALO && xr < HALO + TX;
+                float4 T = stencil4(sa, rr + HALO, xr + HALO, g.rz);
+                add_source(T, src, (int)cell, wsn);
+                if (inner && a.t1) __stcs(reinterpret_cast<float4 *>(a.t1 + base + cell), T);
+                const float4 dG = sponge4(g.dGz[z], ld4g(g.dGx + x));
+                const float4 uc = ld4s(sa, rr + HALO, xr + HALO);
+                const float4 up = ld4s(sb, rr, xr);
+                const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
+                un = leapfrog(dG, uc, up, T, wh, wl);
+                if (inner) st4g(a.u1 + base + cell, un);
+            }
+            // only this thread reads this group of u^{n-1}
+            *reinterpret_cast<float4 *>(&sb[rr][xr]) = un;
+        }
+    }
+    __syncthreads();   // u^{n+1} of tile + ring in sb, the tile's stores visible to the block
+    if (a.traces) gather(g, sg, tile, a.n, a.u1 + base, a.traces);
+    if (!second) return;
+    const int xl = threadIdx.x * 4, x = x0 + xl;
+    if (x < g.pitch) {   // step n+1 on the tile
+        const float4 dgx = ld4g(g.dGx + x);
+        const float wsn = g.ws[a.n + 1];
+#pragma unroll
+        for (int r = 0; r < RZ; ++r) {
+            const int zl = threadIdx.y + r * BY, z = z0 + zl;
+            if (z >= g.NZ) break;
+            const long long cell = (long long)z * g.pitch + x;
+            float4 T = stencil4(sb, zl + HALO, xl + HALO, g.rz);
+            add_source(T, src, (int)cell, wsn);
+            if (a.t2) __stcs(reinterpret_cast<float4 *>(a.t2 + base + cell), T);
+            const float4 dG = sponge4(g.dGz[z], dgx);
+            const float4 uc = ld4s(sb, zl + HALO, xl + HALO);
+            const float4 up = ld4s(sa, zl + 2 * HALO, xl + 2 * HALO);
+            const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
+            st4g(a.u2 + base + cell, leapfrog(dG, uc, up, T, wh, wl));
+        }
+    }
+    if (a.traces) gather(g, sg, tile, a.n + 1, a.u2 + base, a.traces);
 }
 
 template <int RZ>
@@ -471,6 +558,8 @@ __global__ void k_shot_sum_z(const Geo g, int nz, int nx, const double *rowsum, 
 template <int RZ>
 static size_t fwd_smem() { return ((RZ * BY + 2 * HALO) * SW + 3 * RZ * BY * TX) * sizeof(float); }
 template <int RZ>
+static size_t fwd2_smem() { return ((RZ * BY + 4 * HALO) * SW8 + (RZ * BY + 2 * HALO) * SW) * sizeof(float); }
+template <int RZ>
 static size_t born_smem() { return 2 * (RZ * BY + 2 * HALO) * SW * sizeof(float); }
 template <int RZ>
 static size_t adj_smem() { return ((RZ * BY + 2 * HALO) * SW + 3 * RZ * BY * TX) * sizeof(float); }
@@ -479,6 +568,8 @@ template <int RZ>
 static cudaError_t init_tile_kernels()
 {
     cudaError_t e = cudaFuncSetAttribute(k_fwd<RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<RZ>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fwd2<RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd2_smem<RZ>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_born<RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)born_smem<RZ>());
     if (e == cudaSuccess)
@@ -502,7 +593,7 @@ void launch_prep(const Geo &g, int nz, int nx, const float *m, const float *rho,
 }
 
 bool encode_tile_map(CUtensorMap *m, const float *base, int NX, int NZ, int pitch, long long field, int S,
-                     int slots, int tile_rows, bool halo, std::string *why)
+                     int slots, int tile_rows, int halo, std::string *why)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -518,7 +609,7 @@ bool encode_tile_map(CUtensorMap *m, const float *base, int NX, int NZ, int pitc
     }
     const cuuint64_t dims[4] = {(cuuint64_t)NX, (cuuint64_t)NZ, (cuuint64_t)S, (cuuint64_t)slots};
     const cuuint64_t strides[3] = {(cuuint64_t)pitch * 4, (cuuint64_t)field * 4, (cuuint64_t)field * S * 4};
-    const cuuint32_t box[4] = {(cuuint32_t)(halo ? SW : TX), (cuuint32_t)(halo ? tile_rows + 2 * HALO : tile_rows), 1, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)(TX + 2 * halo), (cuuint32_t)(tile_rows + 2 * halo), 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dims, strides, box,
                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -554,6 +645,14 @@ void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, const C
     if (g.tz == 16) launch_step(k_fwd<2>, fwd_smem<2>(), g, st, pdl, g, a, tm_u, tm_p, tm_w);
     else if (g.tz == 64) launch_step(k_fwd<8>, fwd_smem<8>(), g, st, pdl, g, a, tm_u, tm_p, tm_w);
     else launch_step(k_fwd<4>, fwd_smem<4>(), g, st, pdl, g, a, tm_u, tm_p, tm_w);
+}
+
+void launch_fwd2(const Geo &g, const Fwd2Args &a, const CUtensorMap &tm_u8, const CUtensorMap &tm_u4, cudaStream_t st,
+                 bool pdl)
+{
+    if (g.tz == 16) launch_step(k_fwd2<2>, fwd2_smem<2>(), g, st, pdl, g, a, tm_u8, tm_u4);
+    else if (g.tz == 64) launch_step(k_fwd2<8>, fwd2_smem<8>(), g, st, pdl, g, a, tm_u8, tm_u4);
+    else launch_step(k_fwd2<4>, fwd2_smem<4>(), g, st, pdl, g, a, tm_u8, tm_u4);
 }
 
 void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d, cudaStream_t st,

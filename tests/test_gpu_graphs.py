@@ -113,3 +113,33 @@ def test_dependent_launches_equal_plain_launches(A, orc, checkpoint_every, graph
             a, b, c = a[1], b[1], c[1]
         assert torch.equal(a, b) and torch.equal(a, c), k
     assert l1 == l2
+
+
+@pytest.mark.parametrize("nt", [[600, 600, 600], [599, 410, 523]], ids=["even", "odd-uneven"])
+@pytest.mark.parametrize("spb", [0, 1], ids=["one-batch", "one-shot-batches"])
+def test_two_step_forward_equals_one_step(A, orc, nt, spb):
+    """The two-step forward kernel (tile + 4-cell ring advanced to n+1 in
+    shared memory, then the tile to n+2) gives bitwise the traces, the stored
+    T^n (through the FWI gradient) and the misfit of one step per launch;
+    odd record lengths end with a one-step launch, shots whose record ends
+    after the first of a launch's two steps stop there."""
+    import torch
+    p = synth.tiny()
+    g = p.geom
+    g.nt = np.array(nt, dtype=np.int32)
+    d_obs = torch.as_tensor(orc.forward(g, p.m_true).astype(np.float32), device="cuda")
+    rho = torch.as_tensor(np.random.default_rng(7).uniform(-0.1, 0.1, (g.nz, g.nx)).astype(np.float32),
+                          device="cuda")
+    one = A.Plan(g, 3000.0, engine=A.ENGINE_PER_STEP, steps_per_launch=1, shots_per_batch=spb)
+    two = A.Plan(g, 3000.0, engine=A.ENGINE_PER_STEP, steps_per_launch=2, shots_per_batch=spb)
+    assert one.info.steps_per_launch == 1 and two.info.steps_per_launch == 2
+    o1, l1 = run_all(A, one, p, d_obs, rho)
+    o2, l2 = run_all(A, two, p, d_obs, rho)
+    for k in o1:
+        a, b = o1[k], o2[k]
+        if isinstance(a, tuple):
+            assert a[0] == b[0], k
+            a, b = a[1], b[1]
+        assert torch.equal(a, b), k
+    nb = two.info.n_batches
+    assert l2["forward"] == l1["forward"] - nb * (max(nt) // 2)
