@@ -14,16 +14,13 @@
 // exchange their 4 edge rows each step through a double-buffered global
 // buffer and per-CTA step counters (release / acquire); every wait is bounded
 // and reports AAFWI_ERR_TIMEOUT through the plan's error word instead of
-// hanging.  The arithmetic per cell is that of wave_kernels.cu, in the same
-// order, so results are bitwise equal to the one-launch-per-step path.
+// hanging.  The arithmetic per cell is stencil_math.cuh's, as in the per-step
+// kernels, so results are bitwise equal to the one-launch-per-step path.
 #include "internal.cuh"
+#include "stencil_math.cuh"
 
 namespace aafwi {
 
-constexpr float PA1 = 8064.f;
-constexpr float PA2 = -1008.f;
-constexpr float PA3 = 128.f;
-constexpr float PA4 = -9.f;
 constexpr long long SPIN_LIMIT = 1LL << 22;   // x >= 64 ns sleep: about a second
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -37,8 +34,6 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-
-__device__ __forceinline__ float pd2(float c, float a, float b) { return (a - c) + (b - c); }
 
 // Thread 0 waits until both neighbours have completed `target` steps; the
 // whole CTA learns the outcome.  Returns false on timeout or a raised error.
@@ -109,20 +104,11 @@ __device__ void store_edges(const Geo &g, const PGeo &pg, const float *tile, int
 
 // T = rz S_z + S_x for the float4 group at the centre of the register column
 // w[0..8] (rows z-4..z+4 of the tile) with left / right neighbour groups L, R;
-// z neighbours outside [0, NZ) of the cell's own shot read as zero.  Same
-// arithmetic, in the same order, as pstencil and the per-step kernels.
+// z neighbours outside [0, NZ) of the cell's own shot read as zero.  The
+// arithmetic is stencil_math.cuh's, shared with the per-step kernels.
 template <bool MASK>
 __device__ __forceinline__ float4 col_stencil(const Geo &g, const float4 (&w)[9], float4 L, float4 R, int z)
 {
-    const float4 M = w[4];
-    const float v[12] = {L.x, L.y, L.z, L.w, M.x, M.y, M.z, M.w, R.x, R.y, R.z, R.w};
-    float sx[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float c = v[4 + i];
-        sx[i] = PA1 * pd2(c, v[3 + i], v[5 + i]) + PA2 * pd2(c, v[2 + i], v[6 + i])
-              + PA3 * pd2(c, v[1 + i], v[7 + i]) + PA4 * pd2(c, v[i], v[8 + i]);
-    }
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 up[4], dn[4];
 #pragma unroll
@@ -130,37 +116,7 @@ __device__ __forceinline__ float4 col_stencil(const Geo &g, const float4 (&w)[9]
         up[k - 1] = !MASK || z - k >= 0 ? w[4 - k] : zero;
         dn[k - 1] = !MASK || z + k < g.NZ ? w[4 + k] : zero;
     }
-    float4 o;
-    o.x = g.rz * (PA1 * pd2(M.x, up[0].x, dn[0].x) + PA2 * pd2(M.x, up[1].x, dn[1].x) + PA3 * pd2(M.x, up[2].x, dn[2].x) + PA4 * pd2(M.x, up[3].x, dn[3].x)) + sx[0];
-    o.y = g.rz * (PA1 * pd2(M.y, up[0].y, dn[0].y) + PA2 * pd2(M.y, up[1].y, dn[1].y) + PA3 * pd2(M.y, up[2].y, dn[2].y) + PA4 * pd2(M.y, up[3].y, dn[3].y)) + sx[1];
-    o.z = g.rz * (PA1 * pd2(M.z, up[0].z, dn[0].z) + PA2 * pd2(M.z, up[1].z, dn[1].z) + PA3 * pd2(M.z, up[2].z, dn[2].z) + PA4 * pd2(M.z, up[3].z, dn[3].z)) + sx[2];
-    o.w = g.rz * (PA1 * pd2(M.w, up[0].w, dn[0].w) + PA2 * pd2(M.w, up[1].w, dn[1].w) + PA3 * pd2(M.w, up[2].w, dn[2].w) + PA4 * pd2(M.w, up[3].w, dn[3].w)) + sx[3];
-    return o;
-}
-
-__device__ __forceinline__ float pstep1(float dG, float cur, float prev, float T, float wh, float wl)
-{
-    const float wq = fmaf(wh, T, wl * T);
-    const float gp = prev - dG * prev;
-    const float t = ((cur - gp) + cur) + wq;
-    return t - dG * t;
-}
-
-__device__ __forceinline__ float4 pleap(float4 dG, float4 cur, float4 prev, float4 T, float4 wh, float4 wl)
-{
-    return make_float4(pstep1(dG.x, cur.x, prev.x, T.x, wh.x, wl.x), pstep1(dG.y, cur.y, prev.y, T.y, wh.y, wl.y),
-                       pstep1(dG.z, cur.z, prev.z, T.z, wh.z, wl.z), pstep1(dG.w, cur.w, prev.w, T.w, wh.w, wl.w));
-}
-
-__device__ __forceinline__ void padd_source(float4 &q, int src, int pt, float w)
-{
-    const int d = src - pt;
-    if (d >= 0 && d < 4) {
-        if (d == 0) q.x += w;
-        else if (d == 1) q.y += w;
-        else if (d == 2) q.z += w;
-        else q.w += w;
-    }
+    return stencil_T(L, w[4], R, up, dn, g.rz);
 }
 
 // Shared layout: two tiles of (rows_max + 8) x pitch floats, then
@@ -256,12 +212,6 @@ __device__ __forceinline__ RowW load_roww(const Geo &g, const float *W, int z, i
     return q;
 }
 
-__device__ __forceinline__ float4 sponge_of(float dz, float4 dgx)
-{
-    return make_float4(dz + dgx.x - dz * dgx.x, dz + dgx.y - dz * dgx.y, dz + dgx.z - dz * dgx.z,
-                       dz + dgx.w - dz * dgx.w);
-}
-
 // L2 prefetch of `bytes` (a multiple of 16, 16-byte aligned) starting at p.
 __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
 {
@@ -281,10 +231,10 @@ __device__ __forceinline__ void fwd_cell(const Geo &g, const PGeo &pg, const PFw
         const float4 L = x4 > 0 ? A4[ti - 1] : zero;
         const float4 R = x4 + 1 < W4 ? A4[ti + 1] : zero;
         float4 T = (z >= 4 && z < g.NZ - 4) ? col_stencil<false>(g, w, L, R, z) : col_stencil<true>(g, w, L, R, z);
-        padd_source(T, srcpt, z * g.pitch + x, wsn);
+        add_source(T, srcpt, z * g.pitch + x, wsn);
         const long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
         __stcs(reinterpret_cast<float4 *>(a.hist + (long long)(n + 1) * pg.slot + cell), T);
-        out = pleap(sponge_of(q.dz, dgx), w[4], B4[ti], T, q.wh, q.wl);
+        out = leapfrog(neg_sponge4(q.dz, dgx, neg4(dgx)), w[4], B4[ti], T, q.wh, q.wl);
     }
     B4[ti] = out;
 }
@@ -308,32 +258,23 @@ __device__ __forceinline__ void adj_cell(const Geo &g, const PGeo &pg, const PAd
         const float4 R = x4 + 1 < W4 ? A4[ti + 1] : zero;
         float4 Tz = (z >= 4 && z < g.NZ - 4) ? col_stencil<false>(g, w, L, R, z) : col_stencil<true>(g, w, L, R, z);
         if (sl >= 0) {
-            const float4 inj = rin[sl - s0];
-            Tz.x += inj.x; Tz.y += inj.y; Tz.z += inj.z; Tz.w += inj.w;
+            Tz = add4(Tz, rin[sl - s0]);
         }
         const long long cell = (long long)s * g.field + (long long)z * g.pitch + x;
         const float4 wh = q.wh;
-        const float4 zn = pleap(sponge_of(q.dz, dgx), w[4], B4[ti], Tz, q.wh, q.wl);
+        const float4 zn = leapfrog(neg_sponge4(q.dz, dgx, neg4(dgx)), w[4], B4[ti], Tz, q.wh, q.wl);
         float4 sc;
         if (a.born) {
             sc = make_float4(-g.tscale, -g.tscale, -g.tscale, -g.tscale);
         } else {
-            sc = make_float4(g.iscale * wh.x, g.iscale * wh.y, g.iscale * wh.z, g.iscale * wh.w);
+            sc = make_float4(__fmul_rn(g.iscale, wh.x), __fmul_rn(g.iscale, wh.y), __fmul_rn(g.iscale, wh.z),
+                             __fmul_rn(g.iscale, wh.w));
         }
         if (imode != 0) {
             float4 *ip = reinterpret_cast<float4 *>(a.img + cell);
             float4 im = *ip;
-            if (imode == 2 && n + 1 < nts) {
-                const float4 z1 = w[4];
-                im.x = fmaf(sc.x * z1.x, Tu1.x, im.x);
-                im.y = fmaf(sc.y * z1.y, Tu1.y, im.y);
-                im.z = fmaf(sc.z * z1.z, Tu1.z, im.z);
-                im.w = fmaf(sc.w * z1.w, Tu1.w, im.w);
-            }
-            im.x = fmaf(sc.x * zn.x, Tu.x, im.x);
-            im.y = fmaf(sc.y * zn.y, Tu.y, im.y);
-            im.z = fmaf(sc.z * zn.z, Tu.z, im.z);
-            im.w = fmaf(sc.w * zn.w, Tu.w, im.w);
+            if (imode == 2 && n + 1 < nts) im = image_acc(im, sc, w[4], Tu1);
+            im = image_acc(im, sc, zn, Tu);
             *ip = im;
         }
         out = zn;

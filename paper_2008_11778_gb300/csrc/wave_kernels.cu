@@ -12,19 +12,13 @@
 // stencil result it computes anyway; the adjoint step reads T^n back for the
 // imaging condition, so it stages only z^{n+1} and evaluates one stencil.
 //
-// FP32 evaluation chosen to keep the rounding error of long runs small
-// (the residual of an inversion is often < 1 % of the data, so trace errors
-// are amplified in the misfit and the gradient):
-//   * L is evaluated as differences to the centre cell with the integer
-//     weights 5040 x (8/5, -1/5, 8/315, -1/560) = (8064, -1008, 128, -9):
-//     T = sum_k a_k [(u_{+k} - u) + (u_{-k} - u)]  (the centre weight is
-//     -2 sum a_k exactly), so no weight carries a rounding error and the
-//     large-magnitude cancellation of c0 u against the neighbours is avoided;
-//   * W (L u + s) = Wt T with Wt = dt^2/(5040 dx^2 m) per cell held as the
-//     FP32 pair Wh + Wl derived in FP64 (no rounding of W repeats coherently
-//     over a constant-velocity layer);
-//   * G x is applied as x - (1 - G) x with 1 - G tabulated, which is exact
-//     (G = 1) in the interior and accurate to |1-G| eps in the sponge.
+// FP32 evaluation (stencil_math.cuh, shared with the persistent kernels)
+// keeps the rounding error of long runs small, since the residual of an
+// inversion is often < 1 % of the data and trace errors are amplified in the
+// misfit and the gradient: L as differences to the centre cell with integer
+// weights, W as the FP64-derived pair Wh + Wl, G x as x - (1 - G) x; every
+// rounding explicit, pairs of cells on packed FP32x2 instructions.
+//
 // One launch advances every shot by one step: grid (tiles per shot, shots).
 // A CTA stages its tz x TX tile plus a 4-cell halo of each stencil input in
 // shared memory with 128-bit loads; each thread owns one float4 column group
@@ -33,18 +27,13 @@
 #include <cudaTypedefs.h>   // PFN_cuTensorMapEncodeTiled
 
 #include "internal.cuh"
+#include "stencil_math.cuh"
 
 namespace aafwi {
 
 std::atomic<unsigned long long> g_launch_count{0};
 thread_local unsigned long long *g_capture_count = nullptr;
 
-// 5040 x Fornberg's 8th-order central weights for the second derivative at
-// offsets 1..4 (the centre weight is -2 x their sum).
-constexpr float A1 = 8064.f;
-constexpr float A2 = -1008.f;
-constexpr float A3 = 128.f;
-constexpr float A4 = -9.f;
 
 typedef float Tile[SW];
 typedef float Tile8[SW8];   // row of a tile with an 8-cell halo (two-step forward)
@@ -145,67 +134,17 @@ __device__ __forceinline__ bool stage(unsigned long long *bar, const Copy4 (&cp)
     return __syncthreads_and(ok) != 0;   // the whole CTA takes the same branch
 }
 
-__device__ __forceinline__ float d2(float c, float a, float b) { return (a - c) + (b - c); }
-
-// T = rz * S_z + S_x at the four cells (rr, cc..cc+3) of a staged tile, where
-// S is the integer-weight second difference along each axis (L = T/(5040 dx^2)).
+// T at the four cells (rr, cc..cc+3) of a staged tile of row width W.
 template <int W>
 __device__ __forceinline__ float4 stencil4(const float (*s)[W], int rr, int cc, float rz)
 {
-    const float4 L = ld4s(s, rr, cc - 4), M = ld4s(s, rr, cc), R = ld4s(s, rr, cc + 4);
-    const float v[12] = {L.x, L.y, L.z, L.w, M.x, M.y, M.z, M.w, R.x, R.y, R.z, R.w};
-    float sx[4];
+    float4 up[4], dn[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float c = v[4 + i];
-        sx[i] = A1 * d2(c, v[3 + i], v[5 + i]) + A2 * d2(c, v[2 + i], v[6 + i])
-              + A3 * d2(c, v[1 + i], v[7 + i]) + A4 * d2(c, v[i], v[8 + i]);
+    for (int k = 1; k <= 4; ++k) {
+        up[k - 1] = ld4s(s, rr - k, cc);
+        dn[k - 1] = ld4s(s, rr + k, cc);
     }
-    const float4 a1 = ld4s(s, rr - 1, cc), b1 = ld4s(s, rr + 1, cc);
-    const float4 a2 = ld4s(s, rr - 2, cc), b2 = ld4s(s, rr + 2, cc);
-    const float4 a3 = ld4s(s, rr - 3, cc), b3 = ld4s(s, rr + 3, cc);
-    const float4 a4 = ld4s(s, rr - 4, cc), b4 = ld4s(s, rr + 4, cc);
-    float4 o;
-    o.x = rz * (A1 * d2(M.x, a1.x, b1.x) + A2 * d2(M.x, a2.x, b2.x) + A3 * d2(M.x, a3.x, b3.x) + A4 * d2(M.x, a4.x, b4.x)) + sx[0];
-    o.y = rz * (A1 * d2(M.y, a1.y, b1.y) + A2 * d2(M.y, a2.y, b2.y) + A3 * d2(M.y, a3.y, b3.y) + A4 * d2(M.y, a4.y, b4.y)) + sx[1];
-    o.z = rz * (A1 * d2(M.z, a1.z, b1.z) + A2 * d2(M.z, a2.z, b2.z) + A3 * d2(M.z, a3.z, b3.z) + A4 * d2(M.z, a4.z, b4.z)) + sx[2];
-    o.w = rz * (A1 * d2(M.w, a1.w, b1.w) + A2 * d2(M.w, a2.w, b2.w) + A3 * d2(M.w, a3.w, b3.w) + A4 * d2(M.w, a4.w, b4.w)) + sx[3];
-    return o;
-}
-
-// Add w to the component of q whose cell is the source cell.
-__device__ __forceinline__ void add_source(float4 &q, int src, int pt, float w)
-{
-    const int d = src - pt;
-    if (d >= 0 && d < 4) {
-        if (d == 0) q.x += w;
-        else if (d == 1) q.y += w;
-        else if (d == 2) q.z += w;
-        else q.w += w;
-    }
-}
-
-// G (2 cur - G prev + (Wh + Wl) T) with G x = x - dG x.
-__device__ __forceinline__ float step1(float dG, float cur, float prev, float T, float wh, float wl)
-{
-    const float wq = fmaf(wh, T, wl * T);
-    const float gp = prev - dG * prev;
-    const float t = ((cur - gp) + cur) + wq;
-    return t - dG * t;
-}
-
-__device__ __forceinline__ float4 leapfrog(float4 dG, float4 cur, float4 prev, float4 T, float4 wh,
-                                           float4 wl)
-{
-    return make_float4(step1(dG.x, cur.x, prev.x, T.x, wh.x, wl.x), step1(dG.y, cur.y, prev.y, T.y, wh.y, wl.y),
-                       step1(dG.z, cur.z, prev.z, T.z, wh.z, wl.z), step1(dG.w, cur.w, prev.w, T.w, wh.w, wl.w));
-}
-
-// 1 - G(z, x) = dz + dx - dz dx for the four cells of a float4 group.
-__device__ __forceinline__ float4 sponge4(float dz, float4 dx)
-{
-    return make_float4(dz + dx.x - dz * dx.x, dz + dx.y - dz * dx.y, dz + dx.z - dz * dx.z,
-                       dz + dx.w - dz * dx.w);
+    return stencil_T(ld4s(s, rr, cc - 4), ld4s(s, rr, cc), ld4s(s, rr, cc + 4), up, dn, rz);
 }
 
 // Write f at this tile's receivers into the CSR traces (sample n).
@@ -249,7 +188,7 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
     if (!stage(&bar, cp, (unsigned)((SH * SW + 3 * TZ * TX) * sizeof(float)), g.err, 2)) return;
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {
-        const float4 dgx = ld4g(g.dGx + x);
+        const float4 dgx = ld4g(g.dGx + x), ndgx = neg4(dgx);
         const int src = g.src_pt[sg];
         const float wsn = g.ws[a.n];
 #pragma unroll
@@ -260,12 +199,12 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
             float4 T = stencil4(su, zl + HALO, xl + HALO, g.rz);
             add_source(T, src, (int)cell, wsn);
             if (a.t_out) __stcs(reinterpret_cast<float4 *>(a.t_out + base + cell), T);
-            const float4 dG = sponge4(g.dGz[z], dgx);
+            const float4 ndG = neg_sponge4(g.dGz[z], dgx, ndgx);
             const float4 uc = ld4s(su, zl + HALO, xl + HALO);
             const float4 up = *reinterpret_cast<const float4 *>(&sp[zl][xl]);
             const float4 wh = *reinterpret_cast<const float4 *>(&swh[zl][xl]);
             const float4 wl = *reinterpret_cast<const float4 *>(&swl[zl][xl]);
-            st4g(a.u_next + base + cell, leapfrog(dG, uc, up, T, wh, wl));
+            st4g(a.u_next + base + cell, leapfrog(ndG, uc, up, T, wh, wl));
             if (a.ck_cur) {
                 st4g(a.ck_cur + base + cell, uc);
                 st4g(a.ck_prev + base + cell, up);
@@ -323,11 +262,12 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args 
                 float4 T = stencil4(sa, rr + HALO, xr + HALO, g.rz);
                 add_source(T, src, (int)cell, wsn);
                 if (inner && a.t1) __stcs(reinterpret_cast<float4 *>(a.t1 + base + cell), T);
-                const float4 dG = sponge4(g.dGz[z], ld4g(g.dGx + x));
+                const float4 dgx = ld4g(g.dGx + x);
+                const float4 ndG = neg_sponge4(g.dGz[z], dgx, neg4(dgx));
                 const float4 uc = ld4s(sa, rr + HALO, xr + HALO);
                 const float4 up = ld4s(sb, rr, xr);
                 const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
-                un = leapfrog(dG, uc, up, T, wh, wl);
+                un = leapfrog(ndG, uc, up, T, wh, wl);
                 if (inner) st4g(a.u1 + base + cell, un);
             }
             // only this thread reads this group of u^{n-1}
@@ -339,7 +279,7 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args 
     if (!second) return;
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {   // step n+1 on the tile
-        const float4 dgx = ld4g(g.dGx + x);
+        const float4 dgx = ld4g(g.dGx + x), ndgx = neg4(dgx);
         const float wsn = g.ws[a.n + 1];
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
@@ -349,11 +289,11 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args 
             float4 T = stencil4(sb, zl + HALO, xl + HALO, g.rz);
             add_source(T, src, (int)cell, wsn);
             if (a.t2) __stcs(reinterpret_cast<float4 *>(a.t2 + base + cell), T);
-            const float4 dG = sponge4(g.dGz[z], dgx);
+            const float4 ndG = neg_sponge4(g.dGz[z], dgx, ndgx);
             const float4 uc = ld4s(sb, zl + HALO, xl + HALO);
             const float4 up = ld4s(sa, zl + 2 * HALO, xl + 2 * HALO);
             const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
-            st4g(a.u2 + base + cell, leapfrog(dG, uc, up, T, wh, wl));
+            st4g(a.u2 + base + cell, leapfrog(ndG, uc, up, T, wh, wl));
         }
     }
     if (a.traces) gather(g, sg, tile, a.n + 1, a.u2 + base, a.traces);
@@ -381,7 +321,7 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
     if (!stage(&bar, cp, (unsigned)(2 * SH * SW * sizeof(float)), g.err)) return;
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {
-        const float4 dgx = ld4g(g.dGx + x);
+        const float4 dgx = ld4g(g.dGx + x), ndgx = neg4(dgx);
         const int src = g.src_pt[sg];
         const float wsn = g.ws[a.n];
 #pragma unroll
@@ -395,18 +335,15 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
             float4 Td = stencil4(sd, zl + HALO, xl + HALO, g.rz);
             const float4 rho = ld4g(a.rho + cell);
             // scattered source: W L du - W rho (L u + s)  ->  Wt (T_d - rho T)
-            Td.x -= rho.x * T.x;
-            Td.y -= rho.y * T.y;
-            Td.z -= rho.z * T.z;
-            Td.w -= rho.w * T.w;
-            const float4 dG = sponge4(g.dGz[z], dgx);
+            Td = born_src(Td, rho, T);
+            const float4 ndG = neg_sponge4(g.dGz[z], dgx, ndgx);
             const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
             const float4 uc = ld4s(su, zl + HALO, xl + HALO);
             const float4 up = ld4g(a.u_prev + base + cell);
             const float4 dc = ld4s(sd, zl + HALO, xl + HALO);
             const float4 dp = ld4g(a.d_prev + base + cell);
-            st4g(a.u_next + base + cell, leapfrog(dG, uc, up, T, wh, wl));
-            st4g(a.d_next + base + cell, leapfrog(dG, dc, dp, Td, wh, wl));
+            st4g(a.u_next + base + cell, leapfrog(ndG, uc, up, T, wh, wl));
+            st4g(a.d_next + base + cell, leapfrog(ndG, dc, dp, Td, wh, wl));
             if (a.ck_cur) {
                 st4g(a.ck_cur + base + cell, uc);
                 st4g(a.ck_prev + base + cell, up);
@@ -458,7 +395,7 @@ __global__ void __launch_bounds__(BX *BY, 5) k_adj(const Geo g, const AdjArgs a,
     __syncthreads();
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x >= g.pitch) return;
-    const float4 dgx = ld4g(g.dGx + x);
+    const float4 dgx = ld4g(g.dGx + x), ndgx = neg4(dgx);
 #pragma unroll
     for (int r = 0; r < RZ; ++r) {
         const int zl = threadIdx.y + r * BY, z = z0 + zl;
@@ -468,26 +405,22 @@ __global__ void __launch_bounds__(BX *BY, 5) k_adj(const Geo g, const AdjArgs a,
         float4 Tz = stencil4(sz, zl + HALO, xl + HALO, g.rz);
         if (has_rec) {
             const float4 inj = *reinterpret_cast<const float4 *>(&sinj[zl][xl]);
-            Tz.x += inj.x; Tz.y += inj.y; Tz.z += inj.z; Tz.w += inj.w;
+            Tz = add4(Tz, inj);
         }
-        const float4 dG = sponge4(g.dGz[z], dgx);
+        const float4 ndG = neg_sponge4(g.dGz[z], dgx, ndgx);
         const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
         const float4 z1 = ld4s(sz, zl + HALO, xl + HALO);
         const float4 z2 = *reinterpret_cast<const float4 *>(&sz2[zl][xl]);
-        const float4 zn = leapfrog(dG, z1, z2, Tz, wh, wl);
+        const float4 zn = leapfrog(ndG, z1, z2, Tz, wh, wl);
         // L u + s = Tu * tscale; FWI scale -1/m (= -tscale Tu 5040 dx^2 Wt/dt^2), Born -1
         float4 sc;
         if (a.born) {
             sc = make_float4(-g.tscale, -g.tscale, -g.tscale, -g.tscale);
         } else {
-            sc = make_float4(g.iscale * wh.x, g.iscale * wh.y, g.iscale * wh.z, g.iscale * wh.w);
+            sc = make_float4(__fmul_rn(g.iscale, wh.x), __fmul_rn(g.iscale, wh.y), __fmul_rn(g.iscale, wh.z),
+                             __fmul_rn(g.iscale, wh.w));
         }
-        float4 im = ld4g(a.img + base + cell);
-        im.x = fmaf(sc.x * zn.x, Tu.x, im.x);
-        im.y = fmaf(sc.y * zn.y, Tu.y, im.y);
-        im.z = fmaf(sc.z * zn.z, Tu.z, im.z);
-        im.w = fmaf(sc.w * zn.w, Tu.w, im.w);
-        st4g(a.img + base + cell, im);
+        st4g(a.img + base + cell, image_acc(ld4g(a.img + base + cell), sc, zn, Tu));
         st4g(a.z2n + base + cell, zn);
     }
 }
