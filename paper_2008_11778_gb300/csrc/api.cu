@@ -219,6 +219,7 @@ Geo batch_geo(const aafwi_plan *p, int b)
     Geo g = p->geo;
     g.shot0 = b * p->Sb;
     g.S = std::min(p->Sb, p->S - g.shot0);
+    g.nt_min = *std::min_element(p->nt.begin() + g.shot0, p->nt.begin() + g.shot0 + g.S);
     return g;
 }
 
@@ -716,6 +717,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     G.tscale = (float)(1.0 / t5040);
     G.inj_scale = (float)t5040;
     G.nt = d_nt; G.src_pt = d_src; G.ws = d_ws; G.dGz = d_Gz; G.dGx = d_Gx;
+    G.nt_min = *std::min_element(p->nt.begin(), p->nt.end());
     G.trec_off = d_toff; G.trec_pt = d_tpt; G.trec_col = d_tcol; G.tr_off = d_troff; G.nrec = d_nrec;
     {
         std::string why;

@@ -41,6 +41,7 @@ struct Geo {
     int S;                         // shots of this launch (a batch); field buffers hold them at s * field
     int shot0;                     // global index of the batch's first shot (per-shot tables are global)
     int tz;                        // tile rows of the per-step kernels
+    int nt_min;                    // shortest record of the batch: every shot is active below it
     int *err;                      // error word (bit 2: a bounded wait ran out)
     int ntz, ntx, ntiles;          // tiles per shot along z, x; total
     long long field;               // floats per shot field (NZ * pitch)

@@ -95,12 +95,11 @@ __device__ __forceinline__ void issue(const Copy4 &cp, unsigned b)
 
 // Thread (0, 0) arms the CTA's mbarrier for `bytes` and issues the copies:
 // the first n_early (sources no earlier launch of the stream writes) before
-// the grid-dependency wait, the rest after it; every thread then waits for
-// them.  Returns false (and raises bit 2 of the error word) if they do not
-// land within the wait limit; the whole CTA returns the same value.
+// the grid-dependency wait, the rest after it.  The CTA can then load what
+// it needs besides the tiles while the copies are in flight.
 template <int N>
-__device__ __forceinline__ bool stage(unsigned long long *bar, const Copy4 (&cp)[N], unsigned bytes, int *err,
-                                      int n_early = 0)
+__device__ __forceinline__ void stage_issue(unsigned long long *bar, const Copy4 (&cp)[N], unsigned bytes,
+                                            int n_early = 0)
 {
     const unsigned b = smem_addr(bar);
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
@@ -122,6 +121,14 @@ __device__ __forceinline__ bool stage(unsigned long long *bar, const Copy4 (&cp)
         for (int i = 0; i < N; ++i)
             if (i >= n_early) issue(cp[i], b);
     }
+}
+
+// Every thread waits for the copies of stage_issue.  Returns false (and
+// raises bit 2 of the error word) if they do not land within the wait
+// limit; the whole CTA returns the same value.
+__device__ __forceinline__ bool stage_wait(unsigned long long *bar, int *err)
+{
+    const unsigned b = smem_addr(bar);
     __syncthreads();   // the barrier is initialised before anyone waits on it
     bool ok = false;
     for (long long i = 0; i < TMA_WAIT_LIMIT && !ok; ++i) {
@@ -132,6 +139,13 @@ __device__ __forceinline__ bool stage(unsigned long long *bar, const Copy4 (&cp)
     }
     if (!ok) atomicOr(err, 4);
     return __syncthreads_and(ok) != 0;   // the whole CTA takes the same branch
+}
+
+// Shot sg has no step n: every shot of the batch is active below nt_min, so
+// the record length is read only near the end of the sweep.
+__device__ __forceinline__ bool shot_done(const Geo &g, int sg, int n)
+{
+    return n >= g.nt_min && n >= g.nt[sg];
 }
 
 // T at the four cells (rr, cc..cc+3) of a staged tile of row width W.
@@ -147,18 +161,38 @@ __device__ __forceinline__ float4 stencil4(const float (*s)[W], int rr, int cc, 
     return stencil_T(ld4s(s, rr, cc - 4), ld4s(s, rr, cc), ld4s(s, rr, cc + 4), up, dn, rz);
 }
 
-// Write f at this tile's receivers into the CSR traces (sample n).
-__device__ __forceinline__ void gather(const Geo &g, int s, int tile, int n, const float *f,
-                                       float *traces)
+// Write f at this tile's receivers [r0, r1) (of the per-(shot, tile)
+// lists) into the CSR traces of shot s, sample n.
+__device__ __forceinline__ void gather(const Geo &g, int s, int r0, int r1, int n, const float *f, float *traces)
 {
-    const int t = s * g.ntiles + tile;
-    const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
     if (r1 <= r0) return;
     __syncthreads();  // the tile's stores above are now visible to the block
     const long long tb = g.tr_off[s] + (long long)n * g.nrec[s];
     const int tid = threadIdx.y * BX + threadIdx.x;
     for (int i = r0 + tid; i < r1; i += BX * BY)
         traces[tb + g.trec_col[i]] = f[g.trec_pt[i]];
+}
+
+// Sponge factors of a thread's float4 column group (dgx and its negative)
+// and of its RZ rows, read while the CTA's tile copies are in flight.
+template <int RZ>
+struct Sponge {
+    float4 dgx, ndgx;
+    float dz[RZ];
+};
+
+template <int RZ>
+__device__ __forceinline__ Sponge<RZ> load_sponge(const Geo &g, int z0, int x)
+{
+    Sponge<RZ> q;
+    q.dgx = x < g.pitch ? ld4g(g.dGx + x) : make_float4(0.f, 0.f, 0.f, 0.f);
+    q.ndgx = neg4(q.dgx);
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        const int z = z0 + threadIdx.y + r * BY;
+        q.dz[r] = z < g.NZ ? g.dGz[z] : 0.f;
+    }
+    return q;
 }
 
 template <int RZ>
@@ -168,7 +202,7 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
-    if (a.n >= g.nt[sg]) {
+    if (shot_done(g, sg, a.n)) {
         grid_wait();
         return;
     }
@@ -185,12 +219,15 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
     // W is written only before a sweep's first launch: copied before the grid wait
     const Copy4 cp[4] = {{swh, &tm_w, x0, z0, 0, 0}, {swl, &tm_w, x0, z0, 0, 1},
                          {su, &tm_u, x0 - HALO, z0 - HALO, s, a.cur_slot}, {sp, &tm_p, x0, z0, s, a.prev_slot}};
-    if (!stage(&bar, cp, (unsigned)((SH * SW + 3 * TZ * TX) * sizeof(float)), g.err, 2)) return;
+    stage_issue(&bar, cp, (unsigned)((SH * SW + 3 * TZ * TX) * sizeof(float)), 2);
     const int xl = threadIdx.x * 4, x = x0 + xl;
+    const Sponge<RZ> sp_ = load_sponge<RZ>(g, z0, x);
+    const int src = g.src_pt[sg];
+    const float wsn = g.ws[a.n];
+    const int t = sg * g.ntiles + tile;
+    const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
+    if (!stage_wait(&bar, g.err)) return;
     if (x < g.pitch) {
-        const float4 dgx = ld4g(g.dGx + x), ndgx = neg4(dgx);
-        const int src = g.src_pt[sg];
-        const float wsn = g.ws[a.n];
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
             const int zl = threadIdx.y + r * BY, z = z0 + zl;
@@ -199,7 +236,7 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
             float4 T = stencil4(su, zl + HALO, xl + HALO, g.rz);
             add_source(T, src, (int)cell, wsn);
             if (a.t_out) __stcs(reinterpret_cast<float4 *>(a.t_out + base + cell), T);
-            const float4 ndG = neg_sponge4(g.dGz[z], dgx, ndgx);
+            const float4 ndG = neg_sponge4(sp_.dz[r], sp_.dgx, sp_.ndgx);
             const float4 uc = ld4s(su, zl + HALO, xl + HALO);
             const float4 up = *reinterpret_cast<const float4 *>(&sp[zl][xl]);
             const float4 wh = *reinterpret_cast<const float4 *>(&swh[zl][xl]);
@@ -211,7 +248,7 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
             }
         }
     }
-    if (a.traces) gather(g, sg, tile, a.n, a.u_next + base, a.traces);
+    if (a.traces) gather(g, sg, r0, r1, a.n, a.u_next + base, a.traces);
 }
 
 // Steps n and n+1 in one launch (full-history forward sweeps).  The CTA
@@ -232,11 +269,11 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args 
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO, SH8 = TZ + 4 * HALO;
     constexpr int GR = SW / 4;   // float4 groups per row of tile + ring
     const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
-    if (a.n >= g.nt[sg]) {
+    if (shot_done(g, sg, a.n)) {
         grid_wait();
         return;
     }
-    const bool second = a.n + 1 < g.nt[sg];
+    const bool second = !shot_done(g, sg, a.n + 1);
     const int tile = blockIdx.x;
     const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
     const int z0 = tzi * TZ, x0 = txi * TX;
@@ -247,11 +284,15 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args 
     const long long base = (long long)s * g.field;
     const Copy4 cp[2] = {{sa, &tm_u8, x0 - 2 * HALO, z0 - 2 * HALO, s, a.cur_slot},
                          {sb, &tm_u4, x0 - HALO, z0 - HALO, s, a.prev_slot}};
-    if (!stage(&bar, cp, (unsigned)((SH8 * SW8 + SH * SW) * sizeof(float)), g.err)) return;
+    stage_issue(&bar, cp, (unsigned)((SH8 * SW8 + SH * SW) * sizeof(float)));
     const int src = g.src_pt[sg];
+    const float ws0 = g.ws[a.n], ws1 = second ? g.ws[a.n + 1] : 0.f;
+    const int t = sg * g.ntiles + tile;
+    const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
+    if (!stage_wait(&bar, g.err)) return;
     const int tid = threadIdx.y * BX + threadIdx.x;
     {   // step n on tile + ring; (rr, xr) in sb coordinates (origin z0 - 4, x0 - 4)
-        const float wsn = g.ws[a.n];
+        const float wsn = ws0;
         for (int i = tid; i < SH * GR; i += BX * BY) {
             const int rr = i / GR, xr = (i - rr * GR) * 4;
             const int z = z0 - HALO + rr, x = x0 - HALO + xr;
@@ -275,12 +316,12 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args 
         }
     }
     __syncthreads();   // u^{n+1} of tile + ring in sb, the tile's stores visible to the block
-    if (a.traces) gather(g, sg, tile, a.n, a.u1 + base, a.traces);
+    if (a.traces) gather(g, sg, r0, r1, a.n, a.u1 + base, a.traces);
     if (!second) return;
     const int xl = threadIdx.x * 4, x = x0 + xl;
     if (x < g.pitch) {   // step n+1 on the tile
         const float4 dgx = ld4g(g.dGx + x), ndgx = neg4(dgx);
-        const float wsn = g.ws[a.n + 1];
+        const float wsn = ws1;
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
             const int zl = threadIdx.y + r * BY, z = z0 + zl;
@@ -296,7 +337,7 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args 
             st4g(a.u2 + base + cell, leapfrog(ndG, uc, up, T, wh, wl));
         }
     }
-    if (a.traces) gather(g, sg, tile, a.n + 1, a.u2 + base, a.traces);
+    if (a.traces) gather(g, sg, r0, r1, a.n + 1, a.u2 + base, a.traces);
 }
 
 template <int RZ>
@@ -305,7 +346,7 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
-    if (a.n >= g.nt[sg]) {
+    if (shot_done(g, sg, a.n)) {
         grid_wait();
         return;
     }
@@ -318,12 +359,15 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
     Tile *sd = su + SH;      // SH * SW * 4 bytes on: a multiple of 128
     const long long base = (long long)s * g.field;
     const Copy4 cp[2] = {{su, &tm_u, x0 - HALO, z0 - HALO, s, a.u_slot}, {sd, &tm_d, x0 - HALO, z0 - HALO, s, a.d_slot}};
-    if (!stage(&bar, cp, (unsigned)(2 * SH * SW * sizeof(float)), g.err)) return;
+    stage_issue(&bar, cp, (unsigned)(2 * SH * SW * sizeof(float)));
     const int xl = threadIdx.x * 4, x = x0 + xl;
+    const Sponge<RZ> sp_ = load_sponge<RZ>(g, z0, x);
+    const int src = g.src_pt[sg];
+    const float wsn = g.ws[a.n];
+    const int t = sg * g.ntiles + tile;
+    const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
+    if (!stage_wait(&bar, g.err)) return;
     if (x < g.pitch) {
-        const float4 dgx = ld4g(g.dGx + x), ndgx = neg4(dgx);
-        const int src = g.src_pt[sg];
-        const float wsn = g.ws[a.n];
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
             const int zl = threadIdx.y + r * BY, z = z0 + zl;
@@ -336,7 +380,7 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
             const float4 rho = ld4g(a.rho + cell);
             // scattered source: W L du - W rho (L u + s)  ->  Wt (T_d - rho T)
             Td = born_src(Td, rho, T);
-            const float4 ndG = neg_sponge4(g.dGz[z], dgx, ndgx);
+            const float4 ndG = neg_sponge4(sp_.dz[r], sp_.dgx, sp_.ndgx);
             const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
             const float4 uc = ld4s(su, zl + HALO, xl + HALO);
             const float4 up = ld4g(a.u_prev + base + cell);
@@ -350,17 +394,17 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
             }
         }
     }
-    if (a.traces) gather(g, sg, tile, a.n, a.d_next + base, a.traces);
+    if (a.traces) gather(g, sg, r0, r1, a.n, a.d_next + base, a.traces);
 }
 
 template <int RZ>
-__global__ void __launch_bounds__(BX *BY, 5) k_adj(const Geo g, const AdjArgs a, const __grid_constant__ CUtensorMap tm_z,
+__global__ void __launch_bounds__(BX *BY, 4) k_adj(const Geo g, const AdjArgs a, const __grid_constant__ CUtensorMap tm_z,
                                                 const __grid_constant__ CUtensorMap tm_z2,
                                                 const __grid_constant__ CUtensorMap tm_t)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
-    if (a.n >= g.nt[sg]) {
+    if (shot_done(g, sg, a.n)) {
         grid_wait();
         return;
     }
@@ -376,7 +420,18 @@ __global__ void __launch_bounds__(BX *BY, 5) k_adj(const Geo g, const AdjArgs a,
     const long long base = (long long)s * g.field;
     const Copy4 cp[3] = {{st, &tm_t, x0, z0, s, a.t_slot}, {sz, &tm_z, x0 - HALO, z0 - HALO, s, a.z1_slot},
                          {sz2, &tm_z2, x0, z0, s, a.z2_slot}};
-    if (!stage(&bar, cp, (unsigned)((SH * SW + 2 * TZ * TX) * sizeof(float)), g.err, a.t_early ? 1 : 0)) return;
+    stage_issue(&bar, cp, (unsigned)((SH * SW + 2 * TZ * TX) * sizeof(float)), a.t_early ? 1 : 0);
+    // while the copies are in flight (past the grid wait): the image cells
+    // this thread updates, the sponge, the residual injection
+    const int xl = threadIdx.x * 4, x = x0 + xl;
+    const bool xin = x < g.pitch;
+    float4 im[RZ];
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        const int z = z0 + threadIdx.y + r * BY;
+        if (xin && z < g.NZ) im[r] = ld4g(a.img + base + (long long)z * g.pitch + x);
+    }
+    const Sponge<RZ> sp_ = load_sponge<RZ>(g, z0, x);
     const int t = sg * g.ntiles + tile;
     const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
     const bool has_rec = r1 > r0;
@@ -392,10 +447,8 @@ __global__ void __launch_bounds__(BX *BY, 5) k_adj(const Geo g, const AdjArgs a,
             sinj[zz - z0][xx - x0] = g.inj_scale * a.resid[tb + g.trec_col[i]];
         }
     }
-    __syncthreads();
-    const int xl = threadIdx.x * 4, x = x0 + xl;
-    if (x >= g.pitch) return;
-    const float4 dgx = ld4g(g.dGx + x), ndgx = neg4(dgx);
+    if (!stage_wait(&bar, g.err)) return;   // also orders the injection tile
+    if (!xin) return;
 #pragma unroll
     for (int r = 0; r < RZ; ++r) {
         const int zl = threadIdx.y + r * BY, z = z0 + zl;
@@ -407,10 +460,10 @@ __global__ void __launch_bounds__(BX *BY, 5) k_adj(const Geo g, const AdjArgs a,
             const float4 inj = *reinterpret_cast<const float4 *>(&sinj[zl][xl]);
             Tz = add4(Tz, inj);
         }
-        const float4 ndG = neg_sponge4(g.dGz[z], dgx, ndgx);
-        const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
+        const float4 ndG = neg_sponge4(sp_.dz[r], sp_.dgx, sp_.ndgx);
         const float4 z1 = ld4s(sz, zl + HALO, xl + HALO);
         const float4 z2 = *reinterpret_cast<const float4 *>(&sz2[zl][xl]);
+        const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
         const float4 zn = leapfrog(ndG, z1, z2, Tz, wh, wl);
         // L u + s = Tu * tscale; FWI scale -1/m (= -tscale Tu 5040 dx^2 Wt/dt^2), Born -1
         float4 sc;
@@ -420,7 +473,7 @@ __global__ void __launch_bounds__(BX *BY, 5) k_adj(const Geo g, const AdjArgs a,
             sc = make_float4(__fmul_rn(g.iscale, wh.x), __fmul_rn(g.iscale, wh.y), __fmul_rn(g.iscale, wh.z),
                              __fmul_rn(g.iscale, wh.w));
         }
-        st4g(a.img + base + cell, image_acc(ld4g(a.img + base + cell), sc, zn, Tu));
+        st4g(a.img + base + cell, image_acc(im[r], sc, zn, Tu));
         st4g(a.z2n + base + cell, zn);
     }
 }
