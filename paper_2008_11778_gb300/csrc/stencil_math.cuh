@@ -74,12 +74,15 @@ __device__ __forceinline__ float4 stencil_T(float4 L, float4 M, float4 R, const 
                                             const float4 (&dn)[4], float rz)
 {
     const float v[12] = {L.x, L.y, L.z, L.w, M.x, M.y, M.z, M.w, R.x, R.y, R.z, R.w};
-    float sx[4];
+    float2 sx[2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float c = v[4 + i];
-        sx[i] = wsum1(dd1(c, v[3 + i], v[5 + i]), dd1(c, v[2 + i], v[6 + i]), dd1(c, v[1 + i], v[7 + i]),
-                      dd1(c, v[i], v[8 + i]));
+    for (int p = 0; p < 2; ++p) {   // cells (2p, 2p+1)
+        const int i = 4 + 2 * p;
+        const float2 c = make_float2(v[i], v[i + 1]);
+        sx[p] = wsum2(dd2(c, make_float2(v[i - 1], v[i]), make_float2(v[i + 1], v[i + 2])),
+                      dd2(c, make_float2(v[i - 2], v[i - 1]), make_float2(v[i + 2], v[i + 3])),
+                      dd2(c, make_float2(v[i - 3], v[i - 2]), make_float2(v[i + 3], v[i + 4])),
+                      dd2(c, make_float2(v[i - 4], v[i - 3]), make_float2(v[i + 4], v[i + 5])));
     }
     const float2 r2 = bc2(rz);
     const float2 c0 = lo2(M), c1 = hi2(M);
@@ -87,7 +90,7 @@ __device__ __forceinline__ float4 stencil_T(float4 L, float4 M, float4 R, const 
                             dd2(c0, lo2(up[2]), lo2(dn[2])), dd2(c0, lo2(up[3]), lo2(dn[3])));
     const float2 s1 = wsum2(dd2(c1, hi2(up[0]), hi2(dn[0])), dd2(c1, hi2(up[1]), hi2(dn[1])),
                             dd2(c1, hi2(up[2]), hi2(dn[2])), dd2(c1, hi2(up[3]), hi2(dn[3])));
-    return cat2(__ffma2_rn(r2, s0, make_float2(sx[0], sx[1])), __ffma2_rn(r2, s1, make_float2(sx[2], sx[3])));
+    return cat2(__ffma2_rn(r2, s0, sx[0]), __ffma2_rn(r2, s1, sx[1]));
 }
 
 // -(1 - G) = dz dx - (dz + dx) for the four cells of a group: dz of the row,
