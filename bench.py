@@ -208,7 +208,7 @@ def make_plan(aafwi, prob, g, m_tune, args):
     """The benchmark's plan: the library's autotuned launch configuration
     (timed on short sweeps of this geometry before the timed region), or the
     engine / tile height given on the command line."""
-    kw = dict(pdl=not args.no_pdl, steps_per_launch=args.steps_per_launch)
+    kw = dict(pdl=not args.no_pdl, steps_per_launch=args.steps_per_launch, lanes=args.lanes)
     if args.engine == "tuned":
         return aafwi.Plan(g, c_max=prob.c_bounds[1], tune_model=m_tune, tune_cache=args.tune_cache, **kw)
     return aafwi.Plan(g, c_max=prob.c_bounds[1], engine=ENGINES[args.engine], tile_z=args.tile_z, **kw)
@@ -280,8 +280,11 @@ def run_ours(args):
     pts_sweep = sum(active_points(g, n) for n in range(nt))
     eng = plan.info.engine
     spl = plan.info.steps_per_launch
-    adj_per_sweep = 1 if eng in (aafwi.ENGINE_PERSISTENT, aafwi.ENGINE_HYBRID) else nt
-    fwd_per_sweep = 1 if eng == aafwi.ENGINE_PERSISTENT else (nt + 1) // 2 if spl == 2 else nt
+    adj_per_sweep = 1 if eng in (aafwi.ENGINE_PERSISTENT, aafwi.ENGINE_HYBRID) else nt * plan.info.lanes
+    lanes = plan.info.lanes
+    # per-step sweeps: nt (or nt/2) launches per lane; lanes run concurrently,
+    # so a launch's duration is the sweep's event time over all its launches
+    fwd_per_sweep = 1 if eng == aafwi.ENGINE_PERSISTENT else lanes * ((nt + 1) // 2 if spl == 2 else nt)
     adj_name = "k_adj_persist" if adj_per_sweep == 1 else "k_adj"
     fwd_name = "k_fwd_persist" if fwd_per_sweep == 1 else "k_fwd2" if spl == 2 else "k_fwd"
     # the kernel with the larger share of the timed steps is the dominant one
@@ -296,7 +299,7 @@ def run_ours(args):
                 "bytes_per_launch": b, "ms_per_launch": ms, "launches_per_sweep": per_sweep,
                 "us_per_time_step": 1e3 * sweep_ms / nt, "share_of_step": share}
 
-    fwd_roof = kernel_roof(fwd_name, "forward sweep, %d step(s) per launch" % (1 if fwd_per_sweep == nt else 2),
+    fwd_roof = kernel_roof(fwd_name, "forward sweep, %d step(s) per launch" % (2 if spl == 2 else 1),
                            BYTES_FWD, fwd_per_sweep, kt["fwd_ms"], t_fwd / ms_total)
     adj_roof = kernel_roof(adj_name, "adjoint sweep + imaging", BYTES_ADJ, adj_per_sweep, kt["adj_ms"],
                            t_adj / ms_total)
@@ -323,7 +326,7 @@ def run_ours(args):
                            "checkpoint_every": plan.info.checkpoint_every,
                            "engine": ENGINE_NAMES.get(plan.info.engine, plan.info.engine),
                            "tile_z": plan.info.tile_z, "pdl": not args.no_pdl,
-                           "steps_per_launch": plan.info.steps_per_launch,
+                           "steps_per_launch": plan.info.steps_per_launch, "lanes": plan.info.lanes,
                            "autotune": None if tuning is None else {
                                "steps": tuning.get("steps"), "cached": tuning.get("cached"),
                                "table_ms": [[ENGINE_NAMES.get(e, e), t, ms] for e, t, ms in tuning["table"]]},
@@ -442,7 +445,7 @@ def ncu_case(args):
     prob = synth.batched()
     g = prob.geom.with_nt(64)
     plan = aafwi.Plan(g, c_max=prob.c_bounds[1], engine=ENGINES.get(args.engine, 0), tile_z=args.tile_z,
-                      pdl=not args.no_pdl, steps_per_launch=args.steps_per_launch)
+                      pdl=not args.no_pdl, steps_per_launch=args.steps_per_launch, lanes=args.lanes)
     m = torch.as_tensor(prob.m_start.astype(np.float32), device="cuda")
     d_obs = torch.zeros(plan.trace_count, device="cuda")
     grad = torch.empty_like(m)
@@ -487,6 +490,8 @@ def main():
                     help="sweep engine: the library's autotuner (default) or a fixed one")
     ap.add_argument("--tile-z", type=int, default=0, help="per-step tile rows with a fixed engine")
     ap.add_argument("--no-pdl", action="store_true", help="plain launches instead of programmatic dependents")
+    ap.add_argument("--lanes", type=int, default=0, choices=(0, 1, 2, 3, 4),
+                    help="shot lanes of the per-step sweeps (0: the library's default)")
     ap.add_argument("--steps-per-launch", type=int, default=0, choices=(0, 1, 2),
                     help="forward time steps per launch (0: the library's default)")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (default: the library's)")

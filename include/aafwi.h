@@ -109,6 +109,11 @@ typedef struct {
                                     reads but 1.6x the stencil work of the first step: slower
                                     on the workloads measured).  Born sweeps and checkpoint
                                     plans always take one. */
+    int lanes;                   /* per-step sweeps: the batch's shots in this many groups (0 = 4,
+                                    the most; fewer if the batch has fewer shots) whose launch
+                                    chains run on forked streams, so that one group's step
+                                    boundary (grid drain, dependency wait, refill) overlaps the
+                                    others' work; same results for any value */
 } aafwi_plan_opts;
 
 /* plan engines */
@@ -136,6 +141,7 @@ typedef struct {
                                          more: the stored forward is not kept between calls,
                                          AAFWI_REUSE_FORWARD returns STATE) */
     int steps_per_launch;        /* time steps per launch of the per-step FWI forward sweeps */
+    int lanes;                   /* shot lanes of the per-step sweeps */
 } aafwi_plan_info;
 
 /* ---- plan -------------------------------------------------------------- */

@@ -86,6 +86,11 @@ struct aafwi_plan {
     };
     std::vector<SweepGraph> sweep_graphs;   // most recently used last
     cudaStream_t cap = nullptr;     // capture stream
+    // shot lanes: the per-step sweeps of a batch run as `lanes` independent
+    // launch chains over consecutive shot groups, on forked streams
+    int lanes = 4;
+    cudaStream_t lane_st[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
     std::string msg;
 };
 
@@ -149,6 +154,60 @@ void drop_graphs(aafwi_plan *p)
     p->sweep_graphs.clear();
     if (p->cap) cudaStreamDestroy(p->cap);
     p->cap = nullptr;
+}
+
+constexpr int kMaxLanes = 4;
+
+void destroy_lanes(aafwi_plan *p)
+{
+    for (int l = 0; l + 1 < kMaxLanes; ++l) {
+        if (p->lane_st[l]) cudaStreamDestroy(p->lane_st[l]);
+        if (p->ev_join[l]) cudaEventDestroy(p->ev_join[l]);
+        p->lane_st[l] = nullptr;
+        p->ev_join[l] = nullptr;
+    }
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    p->ev_fork = nullptr;
+}
+
+// The batch's shots split into p->lanes consecutive groups (fewer if the
+// batch has fewer shots), each with its launch geometry and stream: lane 0
+// on st, the others on the plan's lane streams forked from st.  One lane's
+// step boundary (grid drain, dependency, refill) then overlaps the other
+// lanes' work.  Lanes touch disjoint shots, so results do not depend on
+// how their launches interleave.
+struct Lanes {
+    int L = 1;
+    Geo g[kMaxLanes];
+    cudaStream_t st[kMaxLanes];
+};
+
+int fork_lanes(aafwi_plan *p, const Geo &g, cudaStream_t st, Lanes &ln)
+{
+    ln.L = std::max(1, std::min(p->lanes, g.S));
+    int off = 0;
+    for (int l = 0; l < ln.L; ++l) {
+        const int cnt = g.S / ln.L + (l < g.S % ln.L ? 1 : 0);
+        ln.g[l] = g;
+        ln.g[l].s_off = g.s_off + off;
+        ln.g[l].S = cnt;
+        ln.st[l] = l == 0 ? st : p->lane_st[l - 1];
+        off += cnt;
+    }
+    if (ln.L == 1) return AAFWI_OK;
+    cudaError_t e = cudaEventRecord(p->ev_fork, st);
+    for (int l = 1; l < ln.L && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(ln.st[l], p->ev_fork, 0);
+    return e == cudaSuccess ? AAFWI_OK : cuda_fail(p, e, "lane fork");
+}
+
+int join_lanes(aafwi_plan *p, const Lanes &ln)
+{
+    cudaError_t e = cudaSuccess;
+    for (int l = 1; l < ln.L && e == cudaSuccess; ++l) {
+        e = cudaEventRecord(p->ev_join[l - 1], ln.st[l]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ln.st[0], p->ev_join[l - 1], 0);
+    }
+    return e == cudaSuccess ? AAFWI_OK : cuda_fail(p, e, "lane join");
 }
 
 // Run body(stream) -- a sweep of per-step launches -- through the plan's
@@ -234,6 +293,9 @@ int sweep_forward(aafwi_plan *p, const Geo &g, bool born, float *traces, cudaStr
         return cuda_fail(p, cudaGetLastError(), "memset");
     if (born && cudaMemsetAsync(p->dbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
+    Lanes ln;
+    int rc = fork_lanes(p, g, st, ln);
+    if (rc) return rc;
     int n0 = 0, cur = 0, prv = 1;   // after the two-step part: u^n in slot cur, u^{n-1} in slot prv
     if (!born && p->full && p->steps_per_launch == 2) {
         // (u^{n-1}, u^n) in slots (2q, 2q+1); (u^{n+1}, u^{n+2}) to the other pair
@@ -241,7 +303,7 @@ int sweep_forward(aafwi_plan *p, const Geo &g, bool born, float *traces, cudaStr
         for (; n0 + 1 < p->nt_max; n0 += 2, q ^= 1) {
             Fwd2Args a{p->W, 2 * q, 2 * q + 1, slot(p->fbuf, ps, 2 * (q ^ 1)), slot(p->fbuf, ps, 2 * (q ^ 1) + 1),
                        traces, slot(p->hist, ps, n0 + 1), slot(p->hist, ps, n0 + 2), n0};
-            launch_fwd2(g, a, p->tm_f8, p->tm_f, st, p->pdl && n0 > 0);
+            for (int l = 0; l < ln.L; ++l) launch_fwd2(ln.g[l], a, p->tm_f8, p->tm_f, ln.st[l], p->pdl && n0 > 0);
         }
         cur = 2 * q + 1;
         prv = 2 * q;
@@ -256,17 +318,21 @@ int sweep_forward(aafwi_plan *p, const Geo &g, bool born, float *traces, cudaStr
             ckc = slot(p->hist, ps, 2LL * (n / p->k));
             ckp = slot(p->hist, ps, 2LL * (n / p->k) + 1);
         }
-        if (born) {
-            BornArgs a{p->W, p->rho_pad, cur, prev, next, n & 1,
-                       slot(p->dbuf, ps, (n + 1) & 1), slot(p->dbuf, ps, (n + 1) & 1), ckc, ckp,
-                       traces, tout, n};
-            launch_born(g, a, p->tm_f, p->tm_d, st, p->pdl && n > 0);
-        } else {
-            FwdArgs a{p->W, cur, prv, next, ckc, ckp, traces, tout, n};
-            launch_fwd(g, a, p->tm_f, p->tm_fi, p->tm_w, st, p->pdl && n > 0);
+        for (int l = 0; l < ln.L; ++l) {
+            if (born) {
+                BornArgs a{p->W, p->rho_pad, cur, prev, next, n & 1,
+                           slot(p->dbuf, ps, (n + 1) & 1), slot(p->dbuf, ps, (n + 1) & 1), ckc, ckp,
+                           traces, tout, n};
+                launch_born(ln.g[l], a, p->tm_f, p->tm_d, ln.st[l], p->pdl && n > 0);
+            } else {
+                FwdArgs a{p->W, cur, prv, next, ckc, ckp, traces, tout, n};
+                launch_fwd(ln.g[l], a, p->tm_f, p->tm_fi, p->tm_w, ln.st[l], p->pdl && n > 0);
+            }
         }
         std::swap(cur, prv);
     }
+    rc = join_lanes(p, ln);
+    if (rc) return rc;
     return check_launch(p);
 }
 
@@ -294,15 +360,18 @@ int sweep_adjoint(aafwi_plan *p, const Geo &g, bool born, const float *resid, cu
         return cuda_fail(p, cudaGetLastError(), "memset");
     if (cudaMemsetAsync(p->zbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "memset");
-    // The first launch of the sweep follows the memsets and runs as a plain
+    // The first launch of each lane follows the memsets and runs as a plain
     // launch; every later step kernel follows a step kernel and is launched
     // as a programmatic dependent of it.  With the full history no launch of
     // the sweep writes T, so the adjoint copies T^n before its grid wait.
+    Lanes ln;
+    int rc = fork_lanes(p, g, st, ln);
+    if (rc) return rc;
     bool first = true;
     auto adj = [&](int n, int t_slot) {   // T^n in slot t_slot of the T map
         AdjArgs a{p->W, (n + 1) & 1, n & 1, slot(p->zbuf, ps, n & 1), t_slot, resid, p->img, n, born ? 1 : 0,
                   p->full && !first ? 1 : 0};
-        launch_adj(g, a, p->tm_z, p->tm_zi, p->tm_t, st, p->pdl && !first);
+        for (int l = 0; l < ln.L; ++l) launch_adj(ln.g[l], a, p->tm_z, p->tm_zi, p->tm_t, ln.st[l], p->pdl && !first);
         first = false;
     };
     if (p->full) {
@@ -319,13 +388,16 @@ int sweep_adjoint(aafwi_plan *p, const Geo &g, bool born, const float *resid, cu
             for (int n = a; n < e; ++n) {
                 FwdArgs f{p->W, uslot(n), uslot(n - 1), slot(p->fbuf, ps, (n + 1) & 1), nullptr,
                           nullptr, nullptr, slot(p->rbuf, ps, n - a), n};
-                launch_fwd(g, f, ck(n) ? p->tm_ck : p->tm_f, ck(n - 1) ? p->tm_cki : p->tm_fi, p->tm_w,
-                           st, p->pdl && !first);
+                for (int l = 0; l < ln.L; ++l)
+                    launch_fwd(ln.g[l], f, ck(n) ? p->tm_ck : p->tm_f, ck(n - 1) ? p->tm_cki : p->tm_fi, p->tm_w,
+                               ln.st[l], p->pdl && !first);
                 first = false;
             }
             for (int n = e - 1; n >= a; --n) adj(n, n - a);
         }
     }
+    rc = join_lanes(p, ln);
+    if (rc) return rc;
     return check_launch(p);
 }
 
@@ -575,6 +647,22 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
         return fail(nullptr, AAFWI_ERR_ARG, "steps_per_launch must be 0, 1 or 2");
     }
     p->steps_per_launch = o.steps_per_launch == 2 ? 2 : 1;
+    if (o.lanes < 0 || o.lanes > kMaxLanes) {
+        delete p;
+        return fail(nullptr, AAFWI_ERR_ARG, "lanes must be 0 .. 4");
+    }
+    p->lanes = o.lanes == 0 ? kMaxLanes : o.lanes;
+    if (p->lanes > 1) {
+        bool ok = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int l = 0; ok && l + 1 < p->lanes; ++l)
+            ok = cudaStreamCreateWithFlags(&p->lane_st[l], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&p->ev_join[l], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            destroy_lanes(p);
+            delete p;
+            return cuda_fail(nullptr, cudaGetLastError(), "lane streams");
+        }
+    }
     p->nx = g->nx; p->nz = g->nz; p->nb = g->nb;
     p->dx = g->dx; p->dz = g->dz; p->dt = g->dt;
     p->NZ = g->nz + 2 * g->nb;
@@ -582,6 +670,10 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     p->pitch = (p->NX + 31) / 32 * 32;
     p->S = sh->S;
     p->field = (long long)p->NZ * p->pitch;
+    if (p->field >= (1LL << 31)) {   // the step kernels address a shot's cells with 32-bit offsets
+        delete p;
+        return fail(nullptr, AAFWI_ERR_ARG, "padded grid of 2^31 cells or more");
+    }
     const int S = sh->S;
     p->nt.assign(sh->nt, sh->nt + S);
     p->nt_max = *std::max_element(p->nt.begin(), p->nt.end());
@@ -758,6 +850,7 @@ void aafwi_plan_destroy(aafwi_plan *p)
 {
     if (!p) return;
     drop_graphs(p);
+    destroy_lanes(p);
     free_bufs(p->bufs);
     delete p;
 }
@@ -787,6 +880,7 @@ int aafwi_plan_get_info(const aafwi_plan *p, aafwi_plan_info *info)
     info->shots_per_batch = p->Sb;
     info->n_batches = p->nbatch;
     info->steps_per_launch = (p->full && p->steps_per_launch == 2 && !p->persist_fwd) ? 2 : 1;
+    info->lanes = std::min(p->lanes, p->Sb);
     return AAFWI_OK;
 }
 

@@ -40,6 +40,7 @@ struct Geo {
     int NZ, NX, pitch, nb;
     int S;                         // shots of this launch (a batch); field buffers hold them at s * field
     int shot0;                     // global index of the batch's first shot (per-shot tables are global)
+    int s_off;                     // batch-local index of this launch's first shot (a lane of the batch)
     int tz;                        // tile rows of the per-step kernels
     int nt_min;                    // shortest record of the batch: every shot is active below it
     int *err;                      // error word (bit 2: a bounded wait ran out)

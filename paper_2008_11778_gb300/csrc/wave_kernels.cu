@@ -19,7 +19,8 @@
 // weights, W as the FP64-derived pair Wh + Wl, G x as x - (1 - G) x; every
 // rounding explicit, pairs of cells on packed FP32x2 instructions.
 //
-// One launch advances every shot by one step: grid (tiles per shot, shots).
+// One launch advances every shot of a lane (a set of consecutive shots of
+// the batch) by one step: grid (x tiles, z tiles, shots of the lane).
 // A CTA stages its tz x TX tile plus a 4-cell halo of each stencil input in
 // shared memory with 128-bit loads; each thread owns one float4 column group
 // on tz/8 rows.  Source injection, receiver gather and residual injection are
@@ -56,7 +57,11 @@ __device__ __forceinline__ void st4g(float *p, float4 v)
 
 // ---- TMA staging of a tile ------------------------------------------------
 
-constexpr long long TMA_WAIT_LIMIT = 1LL << 20;   // try_wait rounds before giving up
+// A waiting thread is suspended in try_wait until the copies land or
+// TMA_SUSPEND_NS pass (so it does not spin through issue slots); after
+// TMA_WAIT_LIMIT rounds (about a second) it gives up.
+constexpr long long TMA_WAIT_LIMIT = 1LL << 20;
+constexpr unsigned TMA_SUSPEND_NS = 1000;
 
 __device__ __forceinline__ unsigned smem_addr(const void *p)
 {
@@ -133,8 +138,8 @@ __device__ __forceinline__ bool stage_wait(unsigned long long *bar, int *err)
     bool ok = false;
     for (long long i = 0; i < TMA_WAIT_LIMIT && !ok; ++i) {
         unsigned done;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
-                     " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(b) : "memory");
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(b), "r"(TMA_SUSPEND_NS) : "memory");
         ok = done != 0;
     }
     if (!ok) atomicOr(err, 4);
@@ -201,13 +206,12 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
                                                 const __grid_constant__ CUtensorMap tm_w)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
-    const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
+    const int s = g.s_off + blockIdx.z, sg = g.shot0 + s;   // batch-local, global shot
     if (shot_done(g, sg, a.n)) {
         grid_wait();
         return;
     }
-    const int tile = blockIdx.x;
-    const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
+    const int txi = blockIdx.x, tzi = blockIdx.y, tile = tzi * g.ntx + txi;
     const int z0 = tzi * TZ, x0 = txi * TX;
     extern __shared__ __align__(128) float smem[];
     __shared__ unsigned long long bar;
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
         for (int r = 0; r < RZ; ++r) {
             const int zl = threadIdx.y + r * BY, z = z0 + zl;
             if (z >= g.NZ) break;
-            const long long cell = (long long)z * g.pitch + x;
+            const int cell = z * g.pitch + x;
             float4 T = stencil4(su, zl + HALO, xl + HALO, g.rz);
             add_source(T, src, (int)cell, wsn);
             if (a.t_out) __stcs(reinterpret_cast<float4 *>(a.t_out + base + cell), T);
@@ -268,14 +272,13 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args 
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO, SH8 = TZ + 4 * HALO;
     constexpr int GR = SW / 4;   // float4 groups per row of tile + ring
-    const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
+    const int s = g.s_off + blockIdx.z, sg = g.shot0 + s;   // batch-local, global shot
     if (shot_done(g, sg, a.n)) {
         grid_wait();
         return;
     }
     const bool second = !shot_done(g, sg, a.n + 1);
-    const int tile = blockIdx.x;
-    const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
+    const int txi = blockIdx.x, tzi = blockIdx.y, tile = tzi * g.ntx + txi;
     const int z0 = tzi * TZ, x0 = txi * TX;
     extern __shared__ __align__(128) float smem[];
     __shared__ unsigned long long bar;
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args 
             const int z = z0 - HALO + rr, x = x0 - HALO + xr;
             float4 un = make_float4(0.f, 0.f, 0.f, 0.f);
             if (z >= 0 && z < g.NZ && x >= 0 && x < g.pitch) {
-                const long long cell = (long long)z * g.pitch + x;
+                const int cell = z * g.pitch + x;
                 const bool inner = rr >= HALO && rr < HALO + TZ && xr >= HALO && xr < HALO + TX;
                 float4 T = stencil4(sa, rr + HALO, xr + HALO, g.rz);
                 add_source(T, src, (int)cell, wsn);
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args 
         for (int r = 0; r < RZ; ++r) {
             const int zl = threadIdx.y + r * BY, z = z0 + zl;
             if (z >= g.NZ) break;
-            const long long cell = (long long)z * g.pitch + x;
+            const int cell = z * g.pitch + x;
             float4 T = stencil4(sb, zl + HALO, xl + HALO, g.rz);
             add_source(T, src, (int)cell, wsn);
             if (a.t2) __stcs(reinterpret_cast<float4 *>(a.t2 + base + cell), T);
@@ -345,13 +348,12 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
                                                  const __grid_constant__ CUtensorMap tm_d)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
-    const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
+    const int s = g.s_off + blockIdx.z, sg = g.shot0 + s;   // batch-local, global shot
     if (shot_done(g, sg, a.n)) {
         grid_wait();
         return;
     }
-    const int tile = blockIdx.x;
-    const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
+    const int txi = blockIdx.x, tzi = blockIdx.y, tile = tzi * g.ntx + txi;
     const int z0 = tzi * TZ, x0 = txi * TX;
     extern __shared__ __align__(128) float smem[];
     __shared__ unsigned long long bar;
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
         for (int r = 0; r < RZ; ++r) {
             const int zl = threadIdx.y + r * BY, z = z0 + zl;
             if (z >= g.NZ) break;
-            const long long cell = (long long)z * g.pitch + x;
+            const int cell = z * g.pitch + x;
             float4 T = stencil4(su, zl + HALO, xl + HALO, g.rz);
             add_source(T, src, (int)cell, wsn);
             if (a.t_out) __stcs(reinterpret_cast<float4 *>(a.t_out + base + cell), T);
@@ -403,13 +405,12 @@ __global__ void __launch_bounds__(BX *BY, 4) k_adj(const Geo g, const AdjArgs a,
                                                 const __grid_constant__ CUtensorMap tm_t)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
-    const int s = blockIdx.y, sg = g.shot0 + s;   // batch-local, global shot
+    const int s = g.s_off + blockIdx.z, sg = g.shot0 + s;   // batch-local, global shot
     if (shot_done(g, sg, a.n)) {
         grid_wait();
         return;
     }
-    const int tile = blockIdx.x;
-    const int tzi = tile / g.ntx, txi = tile - tzi * g.ntx;
+    const int txi = blockIdx.x, tzi = blockIdx.y, tile = tzi * g.ntx + txi;
     const int z0 = tzi * TZ, x0 = txi * TX;
     extern __shared__ __align__(128) float smem[];
     __shared__ unsigned long long bar;
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(BX *BY, 4) k_adj(const Geo g, const AdjArgs a,
 #pragma unroll
     for (int r = 0; r < RZ; ++r) {
         const int z = z0 + threadIdx.y + r * BY;
-        if (xin && z < g.NZ) im[r] = ld4g(a.img + base + (long long)z * g.pitch + x);
+        if (xin && z < g.NZ) im[r] = ld4g(a.img + base + z * g.pitch + x);
     }
     const Sponge<RZ> sp_ = load_sponge<RZ>(g, z0, x);
     const int t = sg * g.ntiles + tile;
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(BX *BY, 4) k_adj(const Geo g, const AdjArgs a,
     for (int r = 0; r < RZ; ++r) {
         const int zl = threadIdx.y + r * BY, z = z0 + zl;
         if (z >= g.NZ) break;
-        const long long cell = (long long)z * g.pitch + x;
+        const int cell = z * g.pitch + x;
         const float4 Tu = *reinterpret_cast<const float4 *>(&st[zl][xl]);
         float4 Tz = stencil4(sz, zl + HALO, xl + HALO, g.rz);
         if (has_rec) {
@@ -613,7 +614,7 @@ static void launch_step(void (*k)(P...), size_t smem, const Geo &g, cudaStream_t
 {
     count_launch();
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(g.ntiles, g.S);
+    cfg.gridDim = dim3(g.ntx, g.ntz, g.S);   // (x tiles, z tiles, shots): CTAs in tile order per shot
     cfg.blockDim = dim3(BX, BY);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;

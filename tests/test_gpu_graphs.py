@@ -141,5 +141,34 @@ def test_two_step_forward_equals_one_step(A, orc, nt, spb):
             assert a[0] == b[0], k
             a, b = a[1], b[1]
         assert torch.equal(a, b), k
-    nb = two.info.n_batches
-    assert l2["forward"] == l1["forward"] - nb * (max(nt) // 2)
+    nb, lanes = two.info.n_batches, two.info.lanes
+    assert l2["forward"] == l1["forward"] - nb * lanes * (max(nt) // 2)
+
+
+@pytest.mark.parametrize("graphs", [False, True], ids=["launches", "graphs"])
+@pytest.mark.parametrize("checkpoint_every", [1, 7], ids=["full", "checkpoints"])
+def test_shot_lanes_equal_one_lane(A, orc, graphs, checkpoint_every):
+    """Shot lanes (the batch's shots in groups whose launch chains run on
+    forked streams) give bitwise the results of one chain, for every
+    operator, uneven records included."""
+    import torch
+    p = synth.small_problem(nz=40, nx=70, nb=10, nt=200, S=5)
+    g = p.geom
+    g.nt = np.array([200, 131, 200, 77, 163], dtype=np.int32)
+    d_obs = torch.as_tensor(orc.forward(g, p.m_true).astype(np.float32), device="cuda")
+    rho = torch.as_tensor(np.random.default_rng(8).uniform(-0.1, 0.1, (g.nz, g.nx)).astype(np.float32),
+                          device="cuda")
+    kw = dict(engine=A.ENGINE_PER_STEP, checkpoint_every=checkpoint_every, graphs=graphs)
+    outs = []
+    for lanes in (1, 2, 4):
+        plan = A.Plan(g, 3000.0, lanes=lanes, **kw)
+        assert plan.info.lanes == lanes
+        outs.append(run_all(A, plan, p, d_obs, rho))
+    (o1, l1) = outs[0]
+    for o, l in outs[1:]:
+        for k in o1:
+            a, b = o1[k], o[k]
+            if isinstance(a, tuple):
+                assert a[0] == b[0], k
+                a, b = a[1], b[1]
+            assert torch.equal(a, b), k
