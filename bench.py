@@ -125,7 +125,7 @@ class ClockSampler:
 def kernel_source_hash():
     """Hash of the sources the wave-equation kernels are built from."""
     h = hashlib.sha256()
-    for name in ("internal.cuh", "wave_kernels.cu", "persist_kernels.cu"):
+    for name in ("internal.cuh", "stencil_math.cuh", "wave_kernels.cu", "persist_kernels.cu"):
         with open(os.path.join(ROOT, "paper_2008_11778_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
