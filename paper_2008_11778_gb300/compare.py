@@ -143,6 +143,39 @@ def large_aa(iters=3, M=10, log=None):
     return out
 
 
+def lsrtm_gradient_rate(reps=3, log=None):
+    """Wall time of one LSRTM gradient on the LSRTM workload (737 x 240,
+    64 shots, 4000 steps): Born pair forward + adjoint with the background
+    replayed from the stored history, timed with CUDA events on the launching
+    stream; the rate counts the four wavefield passes per gradient."""
+    log = log or _log
+    p = synth.lsrtm()
+    g = p.geom
+    plan = aafwi.Plan(g, 4700.0)
+    m0 = _dev(p.m_true)
+    rho = _dev(p.extra["rho_true"])
+    d = torch.empty(plan.trace_count, device="cuda")
+    plan.born_forward(m0, rho, d)
+    rho0 = torch.zeros_like(rho)
+    grad = torch.empty_like(rho)
+    plan.adjoint_gradient(aafwi.MODE_LSRTM, m0, rho0, d, grad)
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.adjoint_gradient(aafwi.MODE_LSRTM, m0, rho0, d, grad, sync=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    upd = 4 * g.updates_per_pass()
+    out = {"workload": "lsrtm-737x240-64shots-4000steps", "ms_per_gradient": min(ms),
+           "updates_per_s": upd / (min(ms) * 1e-3), "lanes": plan.info.lanes,
+           "checkpoint_every": plan.info.checkpoint_every}
+    log("lsrtm gradient", out["ms_per_gradient"], "ms")
+    plan.close()
+    return out
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser(description="solver comparisons of the paper on this library")
     ap.add_argument("--lsrtm-iters", type=int, default=20)
@@ -150,8 +183,12 @@ if __name__ == "__main__":
     ap.add_argument("--snr-db", type=float, default=0.55)
     ap.add_argument("--large-iters", type=int, default=0, help="AA iterations on the large workload (0: skip)")
     ap.add_argument("--only-large", action="store_true")
+    ap.add_argument("--lsrtm-rate", action="store_true", help="time one LSRTM gradient and stop")
     a = ap.parse_args()
     res = {}
+    if a.lsrtm_rate:
+        print(json.dumps({"lsrtm_gradient": lsrtm_gradient_rate()}))
+        raise SystemExit(0)
     if not a.only_large:
         res = {"lsrtm": lsrtm(a.lsrtm_iters), "fwi": fwi(a.fwi_grads), "fwi_noisy": fwi(a.fwi_grads, snr_db=a.snr_db)}
     if a.large_iters > 0:
