@@ -55,3 +55,30 @@ def test_create_errors_need_no_gpu(lib):
     rc = lib.aafwi_plan_create(None, None, None, None, None)
     assert rc == 1
     assert b"NULL" in lib.aafwi_last_error(None)
+
+
+def header_struct_fields(name):
+    """Field names, in order, of `typedef struct { ... } name;` in include/aafwi.h."""
+    src = open(os.path.join(ROOT, "include", "aafwi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct\s*\{([^{}]*)\}\s*" + name + r"\s*;", src)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = re.sub(r"\bconst\b", "", decl).strip()
+        if not decl:
+            continue
+        t = re.match(r"(?:long\s+long|unsigned\s+\w+|\w+)\s+(.*)$", decl, flags=re.S)
+        assert t, decl
+        fields += [n.replace("*", "").strip() for n in t.group(1).split(",")]
+    return fields
+
+
+@pytest.mark.parametrize("c_name, py_name", [("aafwi_plan_opts", "PlanOpts"), ("aafwi_plan_info", "PlanInfo"),
+                                             ("aafwi_grid", "Grid"), ("aafwi_shots", "Shots")])
+def test_binding_structs_match_the_header(c_name, py_name):
+    """The ctypes mirrors of the ABI structs list the header's fields in the
+    header's order (a field added on one side only would shift the rest)."""
+    from paper_2008_11778_gb300 import aafwi
+    py = [f[0] for f in getattr(aafwi, py_name)._fields_]
+    assert py == header_struct_fields(c_name)
