@@ -14,7 +14,8 @@ namespace aafwi {
 
 // Tile of one CTA of the per-step kernels: tz rows x TX columns of one shot,
 // 256 threads laid out 32 (x) x 8 (z); a thread owns 4 consecutive columns
-// (one float4) on tz/8 rows.  tz is a plan parameter (16, 32 or 64; the
+// (one float4) on tz/8 rows (the forward: adjacent rows; the others: rows
+// 8 apart).  tz is a plan parameter (16, 32 or 64; the
 // kernels are instantiated for each).  HALO = stencil radius of the
 // 8th-order Laplacian.
 constexpr int HALO = 4;

@@ -200,8 +200,11 @@ __device__ __forceinline__ Sponge<RZ> load_sponge(const Geo &g, int z0, int x)
     return q;
 }
 
+// Forward step.  A thread owns RZ adjacent rows of its float4 column group
+// and keeps their z window (RZ + 8 rows) in registers, so the rows share
+// their z-neighbour loads (64 registers, 4 CTAs per SM).
 template <int RZ>
-__global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a, const __grid_constant__ CUtensorMap tm_u,
+__global__ void __launch_bounds__(BX *BY, 4) k_fwd(const Geo g, const FwdArgs a, const __grid_constant__ CUtensorMap tm_u,
                                                 const __grid_constant__ CUtensorMap tm_p,
                                                 const __grid_constant__ CUtensorMap tm_w)
 {
@@ -225,27 +228,47 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd(const Geo g, const FwdArgs a,
                          {su, &tm_u, x0 - HALO, z0 - HALO, s, a.cur_slot}, {sp, &tm_p, x0, z0, s, a.prev_slot}};
     stage_issue(&bar, cp, (unsigned)((SH * SW + 3 * TZ * TX) * sizeof(float)), 2);
     const int xl = threadIdx.x * 4, x = x0 + xl;
-    const Sponge<RZ> sp_ = load_sponge<RZ>(g, z0, x);
+    const int zb = threadIdx.y * RZ;   // this thread's RZ adjacent rows zb .. zb+RZ-1 of the tile
+    Sponge<RZ> sp_;
+    sp_.dgx = x < g.pitch ? ld4g(g.dGx + x) : make_float4(0.f, 0.f, 0.f, 0.f);
+    sp_.ndgx = neg4(sp_.dgx);
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) sp_.dz[r] = z0 + zb + r < g.NZ ? g.dGz[z0 + zb + r] : 0.f;
     const int src = g.src_pt[sg];
     const float wsn = g.ws[a.n];
     const int t = sg * g.ntiles + tile;
     const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
     if (!stage_wait(&bar, g.err)) return;
     if (x < g.pitch) {
+        // the z window of the thread's column group: tile rows zb-4 .. zb+RZ+3
+        float4 wz[RZ + 8];
+#pragma unroll
+        for (int k = 0; k < RZ + 8; ++k) wz[k] = ld4s(su, zb + k, xl + HALO);
+        float4 T[RZ];
 #pragma unroll
         for (int r = 0; r < RZ; ++r) {
-            const int zl = threadIdx.y + r * BY, z = z0 + zl;
+            float4 up[4], dn[4];
+#pragma unroll
+            for (int k = 1; k <= 4; ++k) {
+                up[k - 1] = wz[r + 4 - k];
+                dn[k - 1] = wz[r + 4 + k];
+            }
+            T[r] = stencil_T(ld4s(su, zb + r + HALO, xl), wz[r + 4], ld4s(su, zb + r + HALO, xl + 2 * HALO), up, dn,
+                             g.rz);
+        }
+#pragma unroll
+        for (int r = 0; r < RZ; ++r) {
+            const int zl = zb + r, z = z0 + zl;
             if (z >= g.NZ) break;
             const int cell = z * g.pitch + x;
-            float4 T = stencil4(su, zl + HALO, xl + HALO, g.rz);
-            add_source(T, src, (int)cell, wsn);
-            if (a.t_out) __stcs(reinterpret_cast<float4 *>(a.t_out + base + cell), T);
+            add_source(T[r], src, (int)cell, wsn);
+            if (a.t_out) __stcs(reinterpret_cast<float4 *>(a.t_out + base + cell), T[r]);
             const float4 ndG = neg_sponge4(sp_.dz[r], sp_.dgx, sp_.ndgx);
-            const float4 uc = ld4s(su, zl + HALO, xl + HALO);
+            const float4 uc = wz[r + 4];
             const float4 up = *reinterpret_cast<const float4 *>(&sp[zl][xl]);
             const float4 wh = *reinterpret_cast<const float4 *>(&swh[zl][xl]);
             const float4 wl = *reinterpret_cast<const float4 *>(&swl[zl][xl]);
-            st4g(a.u_next + base + cell, leapfrog(ndG, uc, up, T, wh, wl));
+            st4g(a.u_next + base + cell, leapfrog(ndG, uc, up, T[r], wh, wl));
             if (a.ck_cur) {
                 st4g(a.ck_cur + base + cell, uc);
                 st4g(a.ck_prev + base + cell, up);
