@@ -371,7 +371,8 @@ int sweep_adjoint(aafwi_plan *p, const Geo &g, bool born, const float *resid, cu
     auto adj = [&](int n, int t_slot) {   // T^n in slot t_slot of the T map
         AdjArgs a{p->W, (n + 1) & 1, n & 1, slot(p->zbuf, ps, n & 1), t_slot, resid, p->img, n, born ? 1 : 0,
                   p->full && !first ? 1 : 0};
-        for (int l = 0; l < ln.L; ++l) launch_adj(ln.g[l], a, p->tm_z, p->tm_zi, p->tm_t, ln.st[l], p->pdl && !first);
+        for (int l = 0; l < ln.L; ++l)
+            launch_adj(ln.g[l], a, p->tm_z, p->tm_zi, p->tm_t, p->tm_w, ln.st[l], p->pdl && !first);
         first = false;
     };
     if (p->full) {

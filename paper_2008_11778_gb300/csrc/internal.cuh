@@ -165,7 +165,7 @@ void launch_fwd2(const Geo &g, const Fwd2Args &a, const CUtensorMap &tm_u8, cons
 void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d,
                  cudaStream_t st, bool pdl = false);
 void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, const CUtensorMap &tm_z2,
-                const CUtensorMap &tm_t, cudaStream_t st, bool pdl = false);
+                const CUtensorMap &tm_t, const CUtensorMap &tm_w, cudaStream_t st, bool pdl = false);
 // Shot sum and E^T of the batch's images: rowsum (FP64 [NZ][nx]) = or +=
 // (accumulate) the sum over the batch's shots; the second pass, when out is
 // not null, folds rowsum over z into out [nz][nx].

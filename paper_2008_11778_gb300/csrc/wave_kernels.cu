@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
 template <int RZ>
 __global__ void __launch_bounds__(BX *BY, 4) k_adj(const Geo g, const AdjArgs a, const __grid_constant__ CUtensorMap tm_z,
                                                 const __grid_constant__ CUtensorMap tm_z2,
-                                                const __grid_constant__ CUtensorMap tm_t)
+                                                const __grid_constant__ CUtensorMap tm_t,
+                                                const __grid_constant__ CUtensorMap tm_w)
 {
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = g.s_off + blockIdx.z, sg = g.shot0 + s;   // batch-local, global shot
@@ -441,10 +442,13 @@ __global__ void __launch_bounds__(BX *BY, 4) k_adj(const Geo g, const AdjArgs a,
     float(*sinj)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW);           // residual injection
     float(*sz2)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW + TZ * TX);  // z^{n+2}
     float(*st)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW + 2 * TZ * TX);  // T^n
+    float(*swh)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW + 3 * TZ * TX);  // Wh
+    float(*swl)[TX] = reinterpret_cast<float(*)[TX]>(smem + SH * SW + 4 * TZ * TX);  // Wl
     const long long base = (long long)s * g.field;
-    const Copy4 cp[3] = {{st, &tm_t, x0, z0, s, a.t_slot}, {sz, &tm_z, x0 - HALO, z0 - HALO, s, a.z1_slot},
-                         {sz2, &tm_z2, x0, z0, s, a.z2_slot}};
-    stage_issue(&bar, cp, (unsigned)((SH * SW + 2 * TZ * TX) * sizeof(float)), a.t_early ? 1 : 0);
+    // before the grid wait: W always, T^n when no launch of the sweep writes it
+    const Copy4 cp[5] = {{swh, &tm_w, x0, z0, 0, 0}, {swl, &tm_w, x0, z0, 0, 1}, {st, &tm_t, x0, z0, s, a.t_slot},
+                         {sz, &tm_z, x0 - HALO, z0 - HALO, s, a.z1_slot}, {sz2, &tm_z2, x0, z0, s, a.z2_slot}};
+    stage_issue(&bar, cp, (unsigned)((SH * SW + 4 * TZ * TX) * sizeof(float)), a.t_early ? 3 : 2);
     // while the copies are in flight (past the grid wait): the image cells
     // this thread updates, the sponge, the residual injection
     const int xl = threadIdx.x * 4, x = x0 + xl;
@@ -487,7 +491,8 @@ __global__ void __launch_bounds__(BX *BY, 4) k_adj(const Geo g, const AdjArgs a,
         const float4 ndG = neg_sponge4(sp_.dz[r], sp_.dgx, sp_.ndgx);
         const float4 z1 = ld4s(sz, zl + HALO, xl + HALO);
         const float4 z2 = *reinterpret_cast<const float4 *>(&sz2[zl][xl]);
-        const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
+        const float4 wh = *reinterpret_cast<const float4 *>(&swh[zl][xl]);
+        const float4 wl = *reinterpret_cast<const float4 *>(&swl[zl][xl]);
         const float4 zn = leapfrog(ndG, z1, z2, Tz, wh, wl);
         // L u + s = Tu * tscale; FWI scale -1/m (= -tscale Tu 5040 dx^2 Wt/dt^2), Born -1
         float4 sc;
@@ -572,7 +577,7 @@ static size_t fwd2_smem() { return ((RZ * BY + 4 * HALO) * SW8 + (RZ * BY + 2 * 
 template <int RZ>
 static size_t born_smem() { return 2 * (RZ * BY + 2 * HALO) * SW * sizeof(float); }
 template <int RZ>
-static size_t adj_smem() { return ((RZ * BY + 2 * HALO) * SW + 3 * RZ * BY * TX) * sizeof(float); }
+static size_t adj_smem() { return ((RZ * BY + 2 * HALO) * SW + 5 * RZ * BY * TX) * sizeof(float); }
 
 template <int RZ>
 static cudaError_t init_tile_kernels()
@@ -674,11 +679,11 @@ void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const
 }
 
 void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, const CUtensorMap &tm_z2,
-                const CUtensorMap &tm_t, cudaStream_t st, bool pdl)
+                const CUtensorMap &tm_t, const CUtensorMap &tm_w, cudaStream_t st, bool pdl)
 {
-    if (g.tz == 16) launch_step(k_adj<2>, adj_smem<2>(), g, st, pdl, g, a, tm_z, tm_z2, tm_t);
-    else if (g.tz == 64) launch_step(k_adj<8>, adj_smem<8>(), g, st, pdl, g, a, tm_z, tm_z2, tm_t);
-    else launch_step(k_adj<4>, adj_smem<4>(), g, st, pdl, g, a, tm_z, tm_z2, tm_t);
+    if (g.tz == 16) launch_step(k_adj<2>, adj_smem<2>(), g, st, pdl, g, a, tm_z, tm_z2, tm_t, tm_w);
+    else if (g.tz == 64) launch_step(k_adj<8>, adj_smem<8>(), g, st, pdl, g, a, tm_z, tm_z2, tm_t, tm_w);
+    else launch_step(k_adj<4>, adj_smem<4>(), g, st, pdl, g, a, tm_z, tm_z2, tm_t, tm_w);
 }
 
 void launch_shot_sum(const Geo &g, int nz, int nx, const float *img, double *rowsum, bool accumulate, float *out,
