@@ -201,8 +201,8 @@ __device__ __forceinline__ Sponge<RZ> load_sponge(const Geo &g, int z0, int x)
 }
 
 // Forward step.  A thread owns RZ adjacent rows of its float4 column group
-// and keeps their z window (RZ + 8 rows) in registers, so the rows share
-// their z-neighbour loads (64 registers, 4 CTAs per SM).
+// and keeps the z window of each pair of them (10 rows) in registers, so
+// the pair shares its z-neighbour loads (64 registers, 4 CTAs per SM).
 template <int RZ>
 __global__ void __launch_bounds__(BX *BY, 4) k_fwd(const Geo g, const FwdArgs a, const __grid_constant__ CUtensorMap tm_u,
                                                 const __grid_constant__ CUtensorMap tm_p,
@@ -240,38 +240,43 @@ __global__ void __launch_bounds__(BX *BY, 4) k_fwd(const Geo g, const FwdArgs a,
     const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
     if (!stage_wait(&bar, g.err)) return;
     if (x < g.pitch) {
-        // the z window of the thread's column group: tile rows zb-4 .. zb+RZ+3
-        float4 wz[RZ + 8];
+        // rows in chunks of RC; the z window of a chunk (tile rows zc-4 ..
+        // zc+RC+3 of the thread's column group) sits in registers
+        constexpr int RC = RZ < 2 ? RZ : 2;
 #pragma unroll
-        for (int k = 0; k < RZ + 8; ++k) wz[k] = ld4s(su, zb + k, xl + HALO);
-        float4 T[RZ];
+        for (int c = 0; c < RZ; c += RC) {
+            float4 wz[RC + 8];
 #pragma unroll
-        for (int r = 0; r < RZ; ++r) {
-            float4 up[4], dn[4];
+            for (int k = 0; k < RC + 8; ++k) wz[k] = ld4s(su, zb + c + k, xl + HALO);
+            float4 T[RC];
 #pragma unroll
-            for (int k = 1; k <= 4; ++k) {
-                up[k - 1] = wz[r + 4 - k];
-                dn[k - 1] = wz[r + 4 + k];
+            for (int r = 0; r < RC; ++r) {
+                float4 up[4], dn[4];
+#pragma unroll
+                for (int k = 1; k <= 4; ++k) {
+                    up[k - 1] = wz[r + 4 - k];
+                    dn[k - 1] = wz[r + 4 + k];
+                }
+                T[r] = stencil_T(ld4s(su, zb + c + r + HALO, xl), wz[r + 4], ld4s(su, zb + c + r + HALO, xl + 2 * HALO),
+                                 up, dn, g.rz);
             }
-            T[r] = stencil_T(ld4s(su, zb + r + HALO, xl), wz[r + 4], ld4s(su, zb + r + HALO, xl + 2 * HALO), up, dn,
-                             g.rz);
-        }
 #pragma unroll
-        for (int r = 0; r < RZ; ++r) {
-            const int zl = zb + r, z = z0 + zl;
-            if (z >= g.NZ) break;
-            const int cell = z * g.pitch + x;
-            add_source(T[r], src, (int)cell, wsn);
-            if (a.t_out) __stcs(reinterpret_cast<float4 *>(a.t_out + base + cell), T[r]);
-            const float4 ndG = neg_sponge4(sp_.dz[r], sp_.dgx, sp_.ndgx);
-            const float4 uc = wz[r + 4];
-            const float4 up = *reinterpret_cast<const float4 *>(&sp[zl][xl]);
-            const float4 wh = *reinterpret_cast<const float4 *>(&swh[zl][xl]);
-            const float4 wl = *reinterpret_cast<const float4 *>(&swl[zl][xl]);
-            st4g(a.u_next + base + cell, leapfrog(ndG, uc, up, T[r], wh, wl));
-            if (a.ck_cur) {
-                st4g(a.ck_cur + base + cell, uc);
-                st4g(a.ck_prev + base + cell, up);
+            for (int r = 0; r < RC; ++r) {
+                const int zl = zb + c + r, z = z0 + zl;
+                if (z >= g.NZ) break;
+                const int cell = z * g.pitch + x;
+                add_source(T[r], src, (int)cell, wsn);
+                if (a.t_out) __stcs(reinterpret_cast<float4 *>(a.t_out + base + cell), T[r]);
+                const float4 ndG = neg_sponge4(sp_.dz[c + r], sp_.dgx, sp_.ndgx);
+                const float4 uc = wz[r + 4];
+                const float4 up = *reinterpret_cast<const float4 *>(&sp[zl][xl]);
+                const float4 wh = *reinterpret_cast<const float4 *>(&swh[zl][xl]);
+                const float4 wl = *reinterpret_cast<const float4 *>(&swl[zl][xl]);
+                st4g(a.u_next + base + cell, leapfrog(ndG, uc, up, T[r], wh, wl));
+                if (a.ck_cur) {
+                    st4g(a.ck_cur + base + cell, uc);
+                    st4g(a.ck_prev + base + cell, up);
+                }
             }
         }
     }
@@ -453,9 +458,10 @@ __global__ void __launch_bounds__(BX *BY, 4) k_adj(const Geo g, const AdjArgs a,
     // this thread updates, the sponge, the residual injection
     const int xl = threadIdx.x * 4, x = x0 + xl;
     const bool xin = x < g.pitch;
-    float4 im[RZ];
+    constexpr bool PRE = RZ <= 4;   // prefetch the image cells (64-row tiles: too many registers)
+    float4 im[PRE ? RZ : 1];
 #pragma unroll
-    for (int r = 0; r < RZ; ++r) {
+    for (int r = 0; r < (PRE ? RZ : 0); ++r) {
         const int z = z0 + threadIdx.y + r * BY;
         if (xin && z < g.NZ) im[r] = ld4g(a.img + base + z * g.pitch + x);
     }
@@ -502,7 +508,8 @@ __global__ void __launch_bounds__(BX *BY, 4) k_adj(const Geo g, const AdjArgs a,
             sc = make_float4(__fmul_rn(g.iscale, wh.x), __fmul_rn(g.iscale, wh.y), __fmul_rn(g.iscale, wh.z),
                              __fmul_rn(g.iscale, wh.w));
         }
-        st4g(a.img + base + cell, image_acc(im[r], sc, zn, Tu));
+        const float4 imr = PRE ? im[PRE ? r : 0] : ld4g(a.img + base + cell);
+        st4g(a.img + base + cell, image_acc(imr, sc, zn, Tu));
         st4g(a.z2n + base + cell, zn);
     }
 }
