@@ -368,9 +368,10 @@ def time_sweeps(plan, run, dev, reps):
 
 
 def run_e2e(plan, prob, dev, steps):
-    """The FWI gradient through the public call with host buffers: each step
-    copies m and d_obs from pinned host memory, runs adjoint_gradient (forward
-    + adjoint), and reads the gradient and J back."""
+    """The FWI gradient through the C-ABI call with host buffers
+    (aafwi_adjoint_gradient_host): each step copies m and d_obs from pinned
+    host memory into the plan's device staging, runs forward + adjoint, and
+    copies the gradient and J back, all inside the one call."""
     import torch
     g = prob.geom
     m_h = torch.as_tensor(prob.m_start.astype(np.float32)).pin_memory()
@@ -378,17 +379,10 @@ def run_e2e(plan, prob, dev, steps):
     plan.model_forward(torch.as_tensor(prob.m_true.astype(np.float32), device=dev), d_dev)
     d_h = d_dev.cpu().pin_memory()
     g_h = torch.empty_like(m_h).pin_memory()
-    m_d = torch.empty_like(m_h, device=dev)
-    o_d = torch.empty_like(d_h, device=dev)
-    gr_d = torch.empty_like(m_d)
     stream = torch.cuda.current_stream()
 
     def one():
-        m_d.copy_(m_h, non_blocking=True)
-        o_d.copy_(d_h, non_blocking=True)
-        plan.adjoint_gradient(0, m_d, None, o_d, gr_d, sync=False)
-        g_h.copy_(gr_d, non_blocking=True)
-        return plan.read_misfit()          # D2H of J, synchronises
+        return plan.adjoint_gradient_host(0, m_h, None, d_h, g_h)   # synchronises
 
     one()
     torch.cuda.synchronize()
@@ -403,7 +397,7 @@ def run_e2e(plan, prob, dev, steps):
     h2d = m_h.numel() * 4 + d_h.numel() * 4
     d2h = g_h.numel() * 4 + 8
     return {"value": upd / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": ms, "call": "aafwi_adjoint_gradient (FWI) with host-resident m and d_obs"}
+            "ms_per_step": ms, "call": "aafwi_adjoint_gradient_host (FWI): host m and d_obs in, host gradient and J out"}
 
 
 def learned_vs_plain(n_eval, target, max_iters):

@@ -192,6 +192,19 @@ int aafwi_adjoint_gradient(aafwi_plan *plan, int mode, const float *m, const flo
                            const float *d_obs, float *grad, double *J_host, int flags,
                            aafwi_stream stream);
 
+/* The same gradient with host buffers: the whole round trip in one call.
+ * m, rho: host [nz][nx] (rho NULL for FWI); d_obs: host CSR traces; grad:
+ * host [nz][nx] (out); J_host required.  The call copies m, rho and d_obs
+ * into plan-owned device staging buffers (allocated on first use), runs
+ * aafwi_adjoint_gradient on them, copies grad back and returns after the
+ * stream has synchronised.  Pinned host memory makes the copies DMA on the
+ * stream; pageable memory also works.  The stored forward belongs to the
+ * staging buffer, so AAFWI_REUSE_FORWARD is not offered here.
+ * Errors: as aafwi_adjoint_gradient; NOMEM if the staging buffers cannot be
+ * allocated. */
+int aafwi_adjoint_gradient_host(aafwi_plan *plan, int mode, const float *m, const float *rho,
+                                const float *d_obs, float *grad, double *J_host, aafwi_stream stream);
+
 /* Adjoint-state gradient for an arbitrary adjoint source (the data-space
  * derivative dJ/df of any misfit, Sec. 2.2 eq. FWI_adj): grad = (dF/dm)^T adj_src.
  * m: device [nz][nx]; adj_src: device CSR traces; grad: device [nz][nx].

@@ -25,6 +25,7 @@ REUSE_FORWARD = 1
 EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aafwi_last_error",
            "aafwi_plan_set_stall",
            "aafwi_model_forward", "aafwi_born_forward", "aafwi_misfit", "aafwi_adjoint_gradient",
+           "aafwi_adjoint_gradient_host",
            "aafwi_born_adjoint", "aafwi_fwi_adjoint", "aafwi_read_misfit", "aafwi_aa_create", "aafwi_aa_destroy",
            "aafwi_aa_set_eta", "aafwi_aa_set_beta", "aafwi_aa_set_weights", "aafwi_aa_step", "aafwi_aa_combine", "aafwi_absmax",
            "aafwi_launch_count", "aafwi_misfit_noalloc", "aafwi_unet_create", "aafwi_unet_destroy",
@@ -97,6 +98,7 @@ def load(path=LIB_PATH):
         "aafwi_born_forward": ([P, P, P, P, P], I),
         "aafwi_misfit": ([P, P, P, P, P, P], I),
         "aafwi_adjoint_gradient": ([P, I, P, P, P, P, P, I, P], I),
+        "aafwi_adjoint_gradient_host": ([P, I, P, P, P, P, P, P], I),
         "aafwi_born_adjoint": ([P, P, P, P, P], I),
         "aafwi_fwi_adjoint": ([P, P, P, P, I, P], I),
         "aafwi_read_misfit": ([P, P, P], I),
@@ -158,6 +160,16 @@ def _f32(t):
     if t.dtype != torch.float32:
         raise TypeError("expected float32, got %s" % t.dtype)
     return _ptr(t)
+
+
+def _host_f32(t):
+    """Host pointer of a contiguous CPU float32 tensor (None -> NULL)."""
+    import torch
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous() or t.dtype != torch.float32:
+        raise ValueError("expected a contiguous CPU float32 tensor")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _np_ptr(a):
@@ -322,6 +334,14 @@ class Plan:
                                              REUSE_FORWARD if reuse_forward else 0, _stream(stream)),
                self.h)
         return J.value if sync else None
+
+    def adjoint_gradient_host(self, mode, m, rho, d_obs, grad, stream=None):
+        """adjoint_gradient with host (CPU) tensors, copies included; returns J."""
+        J = ctypes.c_double()
+        _check(load().aafwi_adjoint_gradient_host(self.h, int(mode), _host_f32(m), _host_f32(rho),
+                                                  _host_f32(d_obs), _host_f32(grad), ctypes.byref(J),
+                                                  _stream(stream)), self.h)
+        return J.value
 
     def fwi_adjoint(self, m, adj_src, grad, reuse_forward=False, stream=None):
         _check(load().aafwi_fwi_adjoint(self.h, _f32(m), _f32(adj_src), _f32(grad),

@@ -60,6 +60,8 @@ struct aafwi_plan {
     CUtensorMap tm_w{};             // (Wh, Wl) as slots 0, 1 of a one-shot map
     CUtensorMap tm_f8{};            // fbuf with an 8-cell halo (two-step forward)
     float *dsyn = nullptr, *resid = nullptr;
+    // device staging of aafwi_adjoint_gradient_host (allocated on first use)
+    float *stage_m = nullptr, *stage_rho = nullptr, *stage_d = nullptr, *stage_g = nullptr;
     double *partials = nullptr, *J = nullptr;
     double *rowsum = nullptr;       // [NZ][nx] FP64 partial sums of the shot sum
     int *err = nullptr;
@@ -996,6 +998,32 @@ int aafwi_adjoint_gradient(aafwi_plan *p, int mode, const float *m, const float 
         p->fwd_valid = p->nbatch == 1;
         p->fwd_model = m;
     }
+    return finish_sync(p, J_host, st);
+}
+
+int aafwi_adjoint_gradient_host(aafwi_plan *p, int mode, const float *m, const float *rho, const float *d_obs,
+                                float *grad, double *J_host, aafwi_stream stream)
+{
+    if (!p || !m || !d_obs || !grad || !J_host) return fail(p, AAFWI_ERR_ARG, "NULL argument");
+    if (mode != AAFWI_MODE_FWI && mode != AAFWI_MODE_LSRTM) return fail(p, AAFWI_ERR_ARG, "unknown mode");
+    if (mode == AAFWI_MODE_LSRTM && !rho) return fail(p, AAFWI_ERR_ARG, "LSRTM needs rho");
+    const size_t n = (size_t)p->nz * p->nx;
+    bool ok = (p->stage_m || dalloc(p->bufs, &p->stage_m, n)) && (p->stage_rho || dalloc(p->bufs, &p->stage_rho, n)) &&
+              (p->stage_d || dalloc(p->bufs, &p->stage_d, (size_t)p->trace_count)) &&
+              (p->stage_g || dalloc(p->bufs, &p->stage_g, n));
+    if (!ok) return fail(p, AAFWI_ERR_NOMEM, "device staging buffers for host arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool born = mode == AAFWI_MODE_LSRTM;
+    cudaError_t e = cudaMemcpyAsync(p->stage_m, m, n * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && born) e = cudaMemcpyAsync(p->stage_rho, rho, n * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->stage_d, d_obs, (size_t)p->trace_count * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "host to device copy");
+    const int rc = aafwi_adjoint_gradient(p, mode, p->stage_m, born ? p->stage_rho : nullptr, p->stage_d, p->stage_g,
+                                          nullptr, 0, stream);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(grad, p->stage_g, n * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "device to host copy");
     return finish_sync(p, J_host, st);
 }
 
