@@ -484,7 +484,7 @@ def main():
                     help="sweep engine: the library's autotuner (default) or a fixed one")
     ap.add_argument("--tile-z", type=int, default=0, help="per-step tile rows with a fixed engine")
     ap.add_argument("--no-pdl", action="store_true", help="plain launches instead of programmatic dependents")
-    ap.add_argument("--lanes", type=int, default=0, choices=(0, 1, 2, 3, 4),
+    ap.add_argument("--lanes", type=int, default=0, choices=range(9),
                     help="shot lanes of the per-step sweeps (0: the library's default)")
     ap.add_argument("--steps-per-launch", type=int, default=0, choices=(0, 1, 2),
                     help="forward time steps per launch (0: the library's default)")

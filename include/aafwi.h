@@ -110,7 +110,7 @@ typedef struct {
                                     on the workloads measured).  Born sweeps and checkpoint
                                     plans always take one. */
     int lanes;                   /* per-step sweeps: the batch's shots in this many groups (0 = 4,
-                                    the most; fewer if the batch has fewer shots) whose launch
+                                    at most 8; fewer if the batch has fewer shots) whose launch
                                     chains run on forked streams, so that one group's step
                                     boundary (grid drain, dependency wait, refill) overlaps the
                                     others' work; same results for any value */

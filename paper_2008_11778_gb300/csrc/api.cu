@@ -29,6 +29,8 @@ struct Buf {
 
 }  // namespace
 
+constexpr int kMaxLanes = 8;   // shot lanes of a per-step sweep: the caller's stream + 7 lane streams
+
 struct aafwi_plan {
     int device = 0;
     int nx = 0, nz = 0, nb = 0, NZ = 0, NX = 0, pitch = 0, S = 0, nt_max = 0;
@@ -91,8 +93,8 @@ struct aafwi_plan {
     // shot lanes: the per-step sweeps of a batch run as `lanes` independent
     // launch chains over consecutive shot groups, on forked streams
     int lanes = 4;
-    cudaStream_t lane_st[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t lane_st[kMaxLanes - 1] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kMaxLanes - 1] = {};
     std::string msg;
 };
 
@@ -158,7 +160,7 @@ void drop_graphs(aafwi_plan *p)
     p->cap = nullptr;
 }
 
-constexpr int kMaxLanes = 4;
+constexpr int kDefaultLanes = 4;
 
 void destroy_lanes(aafwi_plan *p)
 {
@@ -652,9 +654,9 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     p->steps_per_launch = o.steps_per_launch == 2 ? 2 : 1;
     if (o.lanes < 0 || o.lanes > kMaxLanes) {
         delete p;
-        return fail(nullptr, AAFWI_ERR_ARG, "lanes must be 0 .. 4");
+        return fail(nullptr, AAFWI_ERR_ARG, "lanes must be 0 .. 8");
     }
-    p->lanes = o.lanes == 0 ? kMaxLanes : o.lanes;
+    p->lanes = o.lanes == 0 ? kDefaultLanes : o.lanes;
     if (p->lanes > 1) {
         bool ok = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) == cudaSuccess;
         for (int l = 0; ok && l + 1 < p->lanes; ++l)
