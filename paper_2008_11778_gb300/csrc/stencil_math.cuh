@@ -55,21 +55,10 @@ __device__ __forceinline__ float2 wsum2(float2 d1, float2 d2, float2 d3, float2 
     return __ffma2_rn(bc2(A1), d1, s);
 }
 
-// The same for one cell (x neighbours, whose pairs do not sit in adjacent
-// registers).
-__device__ __forceinline__ float dd1(float c, float a, float b) { return __fadd_rn(__fsub_rn(a, c), __fsub_rn(b, c)); }
-
-__device__ __forceinline__ float wsum1(float d1, float d2, float d3, float d4)
-{
-    float s = __fmul_rn(A4, d4);
-    s = __fmaf_rn(A3, d3, s);
-    s = __fmaf_rn(A2, d2, s);
-    return __fmaf_rn(A1, d1, s);
-}
-
 // T = rz S_z + S_x for the float4 group M (4 adjacent cells of a row); L, R
 // the groups to its left and right, up[k-1] / dn[k-1] the groups k rows
-// above / below (zeros outside the grid).
+// above / below (zeros outside the grid).  The x neighbours of a cell pair
+// do not all sit in adjacent registers: the compiler pairs them by moves.
 __device__ __forceinline__ float4 stencil_T(float4 L, float4 M, float4 R, const float4 (&up)[4],
                                             const float4 (&dn)[4], float rz)
 {
