@@ -329,7 +329,8 @@ def run_ours(args):
                            "steps_per_launch": plan.info.steps_per_launch, "lanes": plan.info.lanes,
                            "autotune": None if tuning is None else {
                                "steps": tuning.get("steps"), "cached": tuning.get("cached"),
-                               "table_ms": [[ENGINE_NAMES.get(e, e), t, ms] for e, t, ms in tuning["table"]]},
+                               "lanes": tuning.get("lanes"),
+                               "table_ms": [[ENGINE_NAMES.get(r[0], r[0])] + list(r[1:]) for r in tuning["table"]]},
                            "l2": "inputs larger than L2 (wavefield history %.1f GB)" % (
                                plan.info.workspace_bytes / 1e9),
                            "passes": {"forward": nf, "adjoint": na},

@@ -359,6 +359,7 @@ int aafwi_axpby(double a, const float *x, double b, float *y, size_t n, aafwi_st
 typedef struct {
     int engine;      /* AAFWI_ENGINE_PER_STEP, _PERSISTENT or _HYBRID */
     int tile_z;      /* tile rows of the per-step forward (16, 32 or 64); 0 for PERSISTENT */
+    int lanes;       /* shot lanes of the per-step sweeps (aafwi_plan_info.lanes of the plan) */
     double ms;       /* median CUDA-event time of one forward sweep plus one FWI
                         adjoint sweep reusing it, over the first `steps` steps */
 } aafwi_tune_entry;
@@ -368,7 +369,8 @@ typedef struct {
  * height, and, when a plan with these options keeps the full history and its
  * strips fit on chip, the persistent engine and the hybrid engine with each
  * tile height (base->engine, when not AUTO, restricts the candidates to that
- * engine).  Each candidate is a temporary
+ * engine); all with the default shot lanes, then, unless base->lanes fixes
+ * them, the winner with 1, 2 and 8 lanes.  Each candidate is a temporary
  * plan over the same shots with every record length cut to `steps` (the
  * sweeps' time grows in proportion to the steps), timed `reps` times after one
  * warm-up on the device model m [nz][nx] (FP32, m = 1/c^2) with zero observed

@@ -63,7 +63,8 @@ class PlanOpts(ctypes.Structure):
 
 
 class TuneEntry(ctypes.Structure):
-    _fields_ = [("engine", ctypes.c_int), ("tile_z", ctypes.c_int), ("ms", ctypes.c_double)]
+    _fields_ = [("engine", ctypes.c_int), ("tile_z", ctypes.c_int), ("lanes", ctypes.c_int),
+                ("ms", ctypes.c_double)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -231,7 +232,7 @@ def cache_store(path, key, value):
 
 
 def run_autotune(geom, c_max, m, steps=64, reps=3, engine=ENGINE_AUTO, max_workspace_bytes=0):
-    """aafwi_autotune: {"engine", "tile_z", "table": [(engine, tile_z, ms), ...]}."""
+    """aafwi_autotune: {"engine", "tile_z", "lanes", "table": [(engine, tile_z, lanes, ms), ...]}."""
     L = load()
     g, s, keep = _geom_structs(geom, c_max)
     base = PlanOpts(int(max_workspace_bytes), 0, 0, 0, int(engine), 0, 0)
@@ -240,8 +241,9 @@ def run_autotune(geom, c_max, m, steps=64, reps=3, engine=ENGINE_AUTO, max_works
     n = ctypes.c_int()
     _check(L.aafwi_autotune(ctypes.byref(g), ctypes.byref(s), _np_ptr(keep[6]), _f32(m), int(steps),
                             int(reps), ctypes.byref(base), table, 16, ctypes.byref(n), ctypes.byref(best)))
-    return {"engine": int(best.engine), "tile_z": int(best.tile_z), "steps": int(steps),
-            "table": [(int(table[i].engine), int(table[i].tile_z), float(table[i].ms)) for i in range(n.value)]}
+    return {"engine": int(best.engine), "tile_z": int(best.tile_z), "lanes": int(best.lanes), "steps": int(steps),
+            "table": [(int(table[i].engine), int(table[i].tile_z), int(table[i].lanes), float(table[i].ms))
+                      for i in range(n.value)]}
 
 
 def autotune(geom, c_max, m, steps=64, reps=3, engine=ENGINE_AUTO, max_workspace_bytes=0, cache_path=None,
@@ -271,7 +273,7 @@ class Plan:
                  graphs=True, tile_z=0, tune_model=None, tune_cache=None, shots_per_batch=0, pdl=True,
                  steps_per_launch=0, lanes=0):
         """tune_model: a device model m [nz][nx]; when given, the engine and
-        tile height come from autotune() (cached in tune_cache, default
+        tile height (and the shot lanes, unless given) come from autotune() (cached in tune_cache, default
         $AAFWI_TUNE_CACHE or ~/.cache/aafwi/tune.json)."""
         L = load()
         self.geom = geom
@@ -279,6 +281,7 @@ class Plan:
             t = autotune(geom, c_max, tune_model, engine=engine, max_workspace_bytes=max_workspace_bytes,
                          cache_path=tune_cache)
             engine, tile_z = t["engine"], t["tile_z"]
+            lanes = lanes or t.get("lanes", 0)
             self.tuning = t
         g, s, self._keep = _geom_structs(geom, c_max)
         o = PlanOpts(int(max_workspace_bytes), int(checkpoint_every), int(tile_z), 0, int(engine),

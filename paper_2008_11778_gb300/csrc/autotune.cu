@@ -1,6 +1,7 @@
 // autotune.cu -- choice of the sweeps' launch configuration (engine: per
-// step, persistent or hybrid; tile height of the per-step kernels) by timing short sweeps of temporary plans
-// of the same geometry.  Host code over the public entry points only.
+// step, persistent or hybrid; tile height and shot lanes of the per-step
+// kernels) by timing short sweeps of temporary plans of the same geometry.
+// Host code over the public entry points only.
 #include <algorithm>
 #include <vector>
 
@@ -11,7 +12,7 @@ using namespace aafwi;
 namespace {
 
 struct Candidate {
-    int engine, tile_z;
+    int engine, tile_z, lanes;   // lanes 0: the plan default
 };
 
 struct Scratch {
@@ -86,10 +87,10 @@ extern "C" int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, 
     std::vector<Candidate> cands;
     auto allowed = [&](int e) { return o.engine == AAFWI_ENGINE_AUTO || o.engine == e; };
     if (allowed(AAFWI_ENGINE_PER_STEP))
-        for (int tz : {16, 32, 64}) cands.push_back({AAFWI_ENGINE_PER_STEP, tz});
-    if (full && allowed(AAFWI_ENGINE_PERSISTENT)) cands.push_back({AAFWI_ENGINE_PERSISTENT, 0});
+        for (int tz : {16, 32, 64}) cands.push_back({AAFWI_ENGINE_PER_STEP, tz, o.lanes});
+    if (full && allowed(AAFWI_ENGINE_PERSISTENT)) cands.push_back({AAFWI_ENGINE_PERSISTENT, 0, o.lanes});
     if (full && allowed(AAFWI_ENGINE_HYBRID))
-        for (int tz : {16, 32, 64}) cands.push_back({AAFWI_ENGINE_HYBRID, tz});
+        for (int tz : {16, 32, 64}) cands.push_back({AAFWI_ENGINE_HYBRID, tz, o.lanes});
     if (cands.empty())
         return tune_fail(AAFWI_ERR_ARG, "autotune: the persistent engines need the full history of all shots at once");
     aafwi_shots sh = *shots;
@@ -101,15 +102,21 @@ extern "C" int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, 
     int ntimed = 0;
     double best_ms = -1.0;
     Candidate win{};
-    for (const Candidate &c : cands) {
+    // one candidate: a temporary plan timed on the cut records; false if it
+    // does not qualify (persistent strips), rc set on an error
+    auto try_one = [&](const Candidate &c, int *rc) -> bool {
         aafwi_plan_opts co = o;
         co.engine = c.engine;
         co.tile_z = c.tile_z;
+        co.lanes = c.lanes;
         co.checkpoint_every = 1;
         aafwi_plan *p = nullptr;
-        int rc = aafwi_plan_create(grid, &sh, wavelet, &co, &p);
-        if (rc == AAFWI_ERR_ARG && c.engine != AAFWI_ENGINE_PER_STEP) continue;   // strips do not qualify
-        if (rc) return rc;
+        *rc = aafwi_plan_create(grid, &sh, wavelet, &co, &p);
+        if (*rc == AAFWI_ERR_ARG && c.engine != AAFWI_ENGINE_PER_STEP) {   // strips do not qualify
+            *rc = AAFWI_OK;
+            return false;
+        }
+        if (*rc) return false;
         aafwi_plan_info info{};
         aafwi_plan_get_info(p, &info);
         if (!sc.d_obs) {
@@ -119,22 +126,39 @@ extern "C" int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, 
                 cudaMemset(sc.d_obs, 0, nt_bytes) != cudaSuccess) {
                 cudaGetLastError();
                 aafwi_plan_destroy(p);
-                return tune_fail(AAFWI_ERR_NOMEM, "autotune: scratch buffers");
+                *rc = tune_fail(AAFWI_ERR_NOMEM, "autotune: scratch buffers");
+                return false;
             }
         }
         double ms = 0.0;
-        rc = time_plan(p, m, sc, reps, &ms);
-        if (rc) {
+        *rc = time_plan(p, m, sc, reps, &ms);
+        if (*rc) {
             set_call_error(aafwi_last_error(p));
             aafwi_plan_destroy(p);
-            return rc;
+            return false;
         }
         aafwi_plan_destroy(p);
-        if (ntimed < table_cap) table[ntimed] = {c.engine, c.tile_z, ms};
+        if (ntimed < table_cap) table[ntimed] = {c.engine, c.tile_z, info.lanes, ms};
         ++ntimed;
         if (best_ms < 0 || ms < best_ms) {
             best_ms = ms;
             win = c;
+        }
+        return true;
+    };
+    for (const Candidate &c : cands) {
+        int rc = AAFWI_OK;
+        try_one(c, &rc);
+        if (rc) return rc;
+    }
+    // shot lanes of the winner's per-step sweeps (more than the shots: the same plan)
+    if (ntimed > 0 && o.lanes == 0 && win.engine != AAFWI_ENGINE_PERSISTENT) {
+        const Candidate w = win;
+        for (int l : {1, 2, 8}) {
+            if (l > S) continue;
+            int rc = AAFWI_OK;
+            try_one({w.engine, w.tile_z, l}, &rc);
+            if (rc) return rc;
         }
     }
     if (n_entries) *n_entries = ntimed;
@@ -142,5 +166,6 @@ extern "C" int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, 
     *best = o;
     best->engine = win.engine;
     best->tile_z = win.tile_z;
+    best->lanes = win.lanes;
     return AAFWI_OK;
 }

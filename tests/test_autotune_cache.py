@@ -12,8 +12,8 @@ class FakeTuner:
 
     def __call__(self, geom, c_max, m, steps, reps, engine, max_workspace_bytes):
         self.calls += 1
-        return {"engine": aafwi.ENGINE_PER_STEP, "tile_z": 64, "steps": steps,
-                "table": [(1, 16, 3.0), (1, 32, 2.5), (1, 64, 2.0)]}
+        return {"engine": aafwi.ENGINE_PER_STEP, "tile_z": 64, "lanes": 0, "steps": steps,
+                "table": [(1, 16, 4, 3.0), (1, 32, 4, 2.5), (1, 64, 4, 2.0)]}
 
 
 def test_key_tracks_geometry_and_device():

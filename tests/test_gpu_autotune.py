@@ -54,21 +54,25 @@ def test_autotune_picks_the_fastest_and_plans_follow_it(A, orc, tmp_path):
     g = p.geom
     m = torch.as_tensor(p.m_start.astype(np.float32), device="cuda")
     res = A.run_autotune(g, 3000.0, m, steps=40, reps=2)
-    kinds = {(e, t) for e, t, _ in res["table"]}
+    kinds = {(e, t) for e, t, _, _ in res["table"]}
     assert {(A.ENGINE_PER_STEP, 16), (A.ENGINE_PER_STEP, 32), (A.ENGINE_PER_STEP, 64)} <= kinds
     assert (A.ENGINE_PERSISTENT, 0) in kinds                      # the tiny plan keeps its full history
     assert {(A.ENGINE_HYBRID, 16), (A.ENGINE_HYBRID, 32), (A.ENGINE_HYBRID, 64)} <= kinds
-    assert all(ms > 0 for _, _, ms in res["table"])
-    best = min(res["table"], key=lambda e: e[2])
+    assert all(ms > 0 for _, _, _, ms in res["table"])
+    best = min(res["table"], key=lambda e: e[3])
     assert (res["engine"], res["tile_z"]) == (best[0], best[1])
+    assert res["lanes"] in (0, best[2])                  # 0: the default lanes won
+    if res["engine"] != A.ENGINE_PERSISTENT:            # the winner re-timed with 1 and 2 lanes (3 shots)
+        assert {l for e, t, l, _ in res["table"] if (e, t) == (res["engine"], res["tile_z"])} >= {1, 2, 3}
     only = A.run_autotune(g, 3000.0, m, steps=40, reps=1, engine=A.ENGINE_PER_STEP)
-    assert {e for e, _, _ in only["table"]} == {A.ENGINE_PER_STEP}
+    assert {e for e, _, _, _ in only["table"]} == {A.ENGINE_PER_STEP}
 
     cache = str(tmp_path / "tune.json")
     tuned = A.Plan(g, 3000.0, tune_model=m, tune_cache=cache)
     again = A.Plan(g, 3000.0, tune_model=m, tune_cache=cache)
     assert not tuned.tuning["cached"] and again.tuning["cached"]
     assert (again.info.engine, again.tuning["tile_z"]) == (tuned.info.engine, tuned.tuning["tile_z"])
+    assert again.info.lanes == tuned.info.lanes
     manual = A.Plan(g, 3000.0, engine=tuned.tuning["engine"], tile_z=tuned.tuning["tile_z"])
     d_obs = torch.as_tensor(orc.forward(g, p.m_true).astype(np.float32), device="cuda")
     a, b = outputs(A, tuned, p, d_obs), outputs(A, manual, p, d_obs)
