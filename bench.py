@@ -131,9 +131,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_record(kernel):
+def traffic_record(kernel, shots_per_launch=None):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None if absent or taken on a different kernel source."""
+    None if absent or taken on a different kernel source.  Per-step kernels'
+    records hold one launch of `shots_per_launch` shots; the bytes scale with
+    the shots of the benchmark's launches (a lane of the batch)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -142,7 +144,10 @@ def traffic_record(kernel):
     rec = d.get(kernel)
     if not rec or rec.get("source_hash") != kernel_source_hash():
         return None
-    return rec.get("bytes_per_launch_full")
+    b = rec.get("bytes_per_launch_full")
+    if b is not None and shots_per_launch and rec.get("shots_per_launch"):
+        b = b * shots_per_launch / rec["shots_per_launch"]
+    return b
 
 
 # ---------------------------------------------------------------------------
@@ -294,8 +299,10 @@ def run_ours(args):
         b = bpu * pts_sweep / per_sweep
         ms = sweep_ms / per_sweep
         gbs = b / (ms * 1e-3) / 1e9
+        launch_shots = g.S / lanes if per_sweep > 1 else None
         return {"bound": "hbm", "kernel": name + " (" + what + ")", "achieved": gbs, "peak": peak,
-                "unit": "GB/s", "frac": gbs / peak, "peak_kind": peak_kind, "traffic": traffic_record(name),
+                "unit": "GB/s", "frac": gbs / peak, "peak_kind": peak_kind,
+                "traffic": traffic_record(name, launch_shots),
                 "bytes_per_launch": b, "ms_per_launch": ms, "launches_per_sweep": per_sweep,
                 "us_per_time_step": 1e3 * sweep_ms / nt, "share_of_step": share}
 
