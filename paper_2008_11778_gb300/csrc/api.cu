@@ -95,6 +95,14 @@ struct aafwi_plan {
     int lanes = 4;
     cudaStream_t lane_st[kMaxLanes - 1] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[kMaxLanes - 1] = {};
+    ~aafwi_plan()
+    {
+        for (cudaStream_t s : lane_st)
+            if (s) cudaStreamDestroy(s);
+        for (cudaEvent_t e : ev_join)
+            if (e) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+    }
     std::string msg;
 };
 
@@ -161,18 +169,6 @@ void drop_graphs(aafwi_plan *p)
 }
 
 constexpr int kDefaultLanes = 4;
-
-void destroy_lanes(aafwi_plan *p)
-{
-    for (int l = 0; l + 1 < kMaxLanes; ++l) {
-        if (p->lane_st[l]) cudaStreamDestroy(p->lane_st[l]);
-        if (p->ev_join[l]) cudaEventDestroy(p->ev_join[l]);
-        p->lane_st[l] = nullptr;
-        p->ev_join[l] = nullptr;
-    }
-    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
-    p->ev_fork = nullptr;
-}
 
 // The batch's shots split into p->lanes consecutive groups (fewer if the
 // batch has fewer shots), each with its launch geometry and stream: lane 0
@@ -639,6 +635,17 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     }
     aafwi_plan_opts o{};
     if (opts) o = *opts;
+    // options and shapes are checked before any device call
+    if (o.steps_per_launch < 0 || o.steps_per_launch > 2)
+        return fail(nullptr, AAFWI_ERR_ARG, "steps_per_launch must be 0, 1 or 2");
+    if (o.lanes < 0 || o.lanes > kMaxLanes) return fail(nullptr, AAFWI_ERR_ARG, "lanes must be 0 .. 8");
+    if (o.tile_z != 0 && !tile_z_supported(o.tile_z))
+        return fail(nullptr, AAFWI_ERR_ARG, "tile_z must be 0 (default), 16, 32 or 64");
+    if (o.tile_x != 0 && o.tile_x != TX) return fail(nullptr, AAFWI_ERR_ARG, "tile_x must be 0 (default) or 128");
+    if ((long long)(g->nz + 2 * g->nb) * ((g->nx + 2 * g->nb + 31) / 32 * 32) >= (1LL << 31))
+        return fail(nullptr, AAFWI_ERR_ARG, "padded grid of 2^31 cells or more");   // 32-bit cell offsets
+    if (*std::min_element(sh->nt, sh->nt + sh->S) < 1) return fail(nullptr, AAFWI_ERR_ARG, "record length must be >= 1");
+    if (sh->rec_off[0] != 0) return fail(nullptr, AAFWI_ERR_ARG, "rec_off[0] must be 0");
     {
         cudaError_t ie = init_kernels();
         if (ie != cudaSuccess) return cuda_fail(nullptr, ie, "kernel attributes");
@@ -647,15 +654,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     cudaGetDevice(&p->device);
     p->graphs = o.no_graphs == 0;
     p->pdl = o.no_pdl == 0;
-    if (o.steps_per_launch < 0 || o.steps_per_launch > 2) {
-        delete p;
-        return fail(nullptr, AAFWI_ERR_ARG, "steps_per_launch must be 0, 1 or 2");
-    }
     p->steps_per_launch = o.steps_per_launch == 2 ? 2 : 1;
-    if (o.lanes < 0 || o.lanes > kMaxLanes) {
-        delete p;
-        return fail(nullptr, AAFWI_ERR_ARG, "lanes must be 0 .. 8");
-    }
     p->lanes = o.lanes == 0 ? kDefaultLanes : o.lanes;
     if (p->lanes > 1) {
         bool ok = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) == cudaSuccess;
@@ -663,8 +662,7 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
             ok = cudaStreamCreateWithFlags(&p->lane_st[l], cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&p->ev_join[l], cudaEventDisableTiming) == cudaSuccess;
         if (!ok) {
-            destroy_lanes(p);
-            delete p;
+            delete p;   // the destructor releases the streams and events made so far
             return cuda_fail(nullptr, cudaGetLastError(), "lane streams");
         }
     }
@@ -675,30 +673,10 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
     p->pitch = (p->NX + 31) / 32 * 32;
     p->S = sh->S;
     p->field = (long long)p->NZ * p->pitch;
-    if (p->field >= (1LL << 31)) {   // the step kernels address a shot's cells with 32-bit offsets
-        delete p;
-        return fail(nullptr, AAFWI_ERR_ARG, "padded grid of 2^31 cells or more");
-    }
     const int S = sh->S;
     p->nt.assign(sh->nt, sh->nt + S);
     p->nt_max = *std::max_element(p->nt.begin(), p->nt.end());
-    if (*std::min_element(p->nt.begin(), p->nt.end()) < 1) {
-        delete p;
-        return fail(nullptr, AAFWI_ERR_ARG, "record length must be >= 1");
-    }
-    if (sh->rec_off[0] != 0) {
-        delete p;
-        return fail(nullptr, AAFWI_ERR_ARG, "rec_off[0] must be 0");
-    }
     // tiles
-    if (o.tile_z != 0 && !tile_z_supported(o.tile_z)) {
-        delete p;
-        return fail(nullptr, AAFWI_ERR_ARG, "tile_z must be 0 (default), 16, 32 or 64");
-    }
-    if (o.tile_x != 0 && o.tile_x != TX) {
-        delete p;
-        return fail(nullptr, AAFWI_ERR_ARG, "tile_x must be 0 (default) or 128");
-    }
     const int TZ = o.tile_z ? o.tile_z : TZ_DEFAULT;
     const int ntz = (p->NZ + TZ - 1) / TZ, ntx = (p->pitch + TX - 1) / TX, ntiles = ntz * ntx;
     // sources, receivers, per-tile receiver lists, trace offsets
@@ -855,7 +833,6 @@ void aafwi_plan_destroy(aafwi_plan *p)
 {
     if (!p) return;
     drop_graphs(p);
-    destroy_lanes(p);
     free_bufs(p->bufs);
     delete p;
 }

@@ -83,3 +83,20 @@ def test_binding_structs_match_the_header(c_name, py_name):
     from paper_2008_11778_gb300 import aafwi
     py = [f[0] for f in getattr(aafwi, py_name)._fields_]
     assert py == header_struct_fields(c_name)
+
+
+@pytest.mark.parametrize("field, value, words", [("lanes", 9, b"lanes"), ("steps_per_launch", 3, b"steps_per_launch"),
+                                                 ("tile_z", 24, b"tile_z"), ("tile_x", 64, b"tile_x")])
+def test_bad_plan_options_are_refused_before_any_device_call(lib, field, value, words):
+    """Plan options out of range come back as ARG with a message naming the
+    option; the checks run before the library touches the device."""
+    from paper_2008_11778_gb300 import aafwi, synth
+    L = aafwi.load()
+    g, s, keep = aafwi._geom_structs(synth.tiny().geom, 3000.0)
+    o = aafwi.PlanOpts()
+    setattr(o, field, value)
+    h = ctypes.c_void_p()
+    rc = L.aafwi_plan_create(ctypes.byref(g), ctypes.byref(s), aafwi._np_ptr(keep[6]), ctypes.byref(o),
+                             ctypes.byref(h))
+    assert rc == 1 and not h.value
+    assert words in L.aafwi_last_error(None)
