@@ -460,6 +460,26 @@ def ncu_case(args):
                       "launches": aafwi.launch_count()}))
 
 
+def ncu_lsrtm_case(args):
+    """A small case of the LSRTM kernels for ncu: the LSRTM geometry (64 shots,
+    737 x 240) cut to 64 time steps; one LSRTM gradient (Born pair forward
+    storing the background history, adjoint with the Born imaging)."""
+    import torch
+    from paper_2008_11778_gb300 import aafwi, synth
+    prob = synth.lsrtm()
+    g = prob.geom.with_nt(64)
+    plan = aafwi.Plan(g, c_max=4700.0, tile_z=args.tile_z, lanes=args.lanes)
+    m0 = torch.as_tensor(prob.m_true.astype(np.float32), device="cuda")
+    rho = torch.as_tensor(prob.extra["rho_true"].astype(np.float32), device="cuda")
+    d = torch.empty(plan.trace_count, device="cuda")
+    plan.born_forward(m0, rho, d)
+    grad = torch.empty_like(m0)
+    J = plan.adjoint_gradient(aafwi.MODE_LSRTM, m0, torch.zeros_like(rho), d, grad)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_lsrtm_case": "lsrtm-737x240-64shots-64steps", "J": J, "tile_z": plan.info.tile_z,
+                      "lanes": plan.info.lanes, "launches": aafwi.launch_count()}))
+
+
 def ncu_unet_case():
     """A small case of the learned preconditioner's kernels for ncu: the
     U-Net (C = 32) forward and one training step on a 16 x 96 x 256 batch."""
@@ -488,6 +508,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="small case for ncu captures")
     ap.add_argument("--ncu-unet-case", action="store_true", help="small U-Net case for ncu captures")
+    ap.add_argument("--ncu-lsrtm-case", action="store_true", help="small LSRTM case for ncu captures")
     ap.add_argument("--engine", default="tuned", choices=["tuned"] + list(ENGINES),
                     help="sweep engine: the library's autotuner (default) or a fixed one")
     ap.add_argument("--tile-z", type=int, default=0, help="per-step tile rows with a fixed engine")
@@ -503,6 +524,8 @@ def main():
     args = ap.parse_args()
     if args.ncu_unet_case:
         ncu_unet_case()
+    elif args.ncu_lsrtm_case:
+        ncu_lsrtm_case(args)
     elif args.ncu_case:
         ncu_case(args)
     elif args.impl == "reference":
