@@ -23,7 +23,13 @@
  *  * All arithmetic runs in this library's CUDA kernels; there is no CPU
  *    fallback.  Workspace (wavefield history or checkpoints, per-shot image
  *    accumulators, traces, reduction partials) belongs to the plan and is
- *    allocated once by aafwi_plan_create with cudaMalloc.
+ *    allocated once by aafwi_plan_create with cudaMalloc (the staging
+ *    buffers of aafwi_adjoint_gradient_host on its first call).
+ *  * A plan is used by one host thread at a time, and its calls run in the
+ *    order they are made on one stream: the workspace is shared by all of
+ *    them.  Internally a per-step sweep may fork onto the plan's own lane
+ *    streams and joins back to the caller's stream before the call returns
+ *    its work to it.
  *
  * Discretisation (the paper leaves it open; this library's reading):
  *   u^{n+1} = G (2 u^n - G u^{n-1} + W (L u^n + s^n)),  u^0 = u^{-1} = 0,
