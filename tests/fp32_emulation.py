@@ -1,9 +1,14 @@
 """numpy float32 emulation of the CUDA forward recurrence (test helper).
 
-Mirrors the FP32 evaluation order of the library's forward kernel (integer-
-weight differences for L, 1 - G tabulated, K split in hi + lo, division by m)
-so that the effect of FP32 wavefields alone can be measured on the CPU, with
-the FP64 oracle supplying everything else.  Used only to explain tolerances.
+Mirrors the FP32 evaluation of the library's step kernels, operation by
+operation: the Laplacian as integer-weight differences to the centre cell,
+accumulated from the smallest weight up through fused multiply-adds; the
+model as the FP64-derived pair Wh + Wl of Wt = dt^2 / (5040 dx^2 m); the
+sponge as x - (1 - G) x with 1 - G = dz + dx - dz dx from per-axis tables.
+A fused multiply-add fma(a, b, c) of float32 operands is emulated in float64
+(the product is exact there) with one rounding to float32.  Used only to explain tolerances
+and the choice of evaluation order: the FP64 oracle supplies everything
+else.
 """
 import numpy as np
 
@@ -13,27 +18,52 @@ f32, f64 = np.float32, np.float64
 A = [f32(8064), f32(-1008), f32(128), f32(-9)]
 
 
-def _stencil(u):
+def fma(a, b, c):
+    """float32 fma with a single rounding (float64 product is exact)."""
+    return (np.asarray(a, f64) * np.asarray(b, f64) + np.asarray(c, f64)).astype(f32)
+
+
+def weighted_sum(d, order="small_first"):
+    """sum_k A_k d_k: 'small_first' = the kernels' order (A4 d4 first, the
+    dominant A1 d1 last through an fma); 'large_first' = A1 d1 rounded first;
+    'plain' = separate roundings, left to right."""
+    if order == "small_first":
+        s = (A[3] * d[3]).astype(f32)
+        for k in (2, 1, 0):
+            s = fma(A[k], d[k], s)
+    elif order == "large_first":
+        s = (A[0] * d[0]).astype(f32)
+        for k in (1, 2, 3):
+            s = fma(A[k], d[k], s)
+    else:
+        s = (A[0] * d[0]).astype(f32)
+        for k in (1, 2, 3):
+            s = (s + (A[k] * d[k]).astype(f32)).astype(f32)
+    return s
+
+
+def stencil_T(u, rz=f32(1.0), order="small_first"):
+    """T = rz S_z + S_x with S the integer-weight differences to the centre."""
     NZ, NX = u.shape
     p = np.zeros((NZ + 8, NX + 8), f32)
     p[4:-4, 4:-4] = u
-    sz = np.zeros_like(u)
-    sx = np.zeros_like(u)
-    for k in range(1, 5):
-        sz = sz + A[k - 1] * ((p[4 - k:4 - k + NZ, 4:-4] - u) + (p[4 + k:4 + k + NZ, 4:-4] - u))
-        sx = sx + A[k - 1] * ((p[4:-4, 4 - k:4 - k + NX] - u) + (p[4:-4, 4 + k:4 + k + NX] - u))
-    return sz + sx
+    dz = [((p[4 - k:4 - k + NZ, 4:-4] - u) + (p[4 + k:4 + k + NZ, 4:-4] - u)).astype(f32) for k in range(1, 5)]
+    dx = [((p[4:-4, 4 - k:4 - k + NX] - u) + (p[4:-4, 4 + k:4 + k + NX] - u)).astype(f32) for k in range(1, 5)]
+    return fma(rz, weighted_sum(dz, order), weighted_sum(dx, order))
 
 
-def forward_fp32(g, m):
-    """Traces (float64 array, CSR layout) of the float32 recurrence; dz == dx."""
-    assert g.dz == g.dx
+def forward_fp32(g, m, order="small_first"):
+    """Traces (float64 array, CSR layout) of the float32 recurrence."""
     nb = g.nb
-    mp = oracle.extend(m, nb).astype(f32)
-    dl = (1.0 - oracle.sponge(g.nz, g.nx, nb)).astype(f32)
-    K = g.dt ** 2 / (5040.0 * g.dx ** 2)
-    Kh = f32(K)
-    Kl = f32(K - f64(Kh))
+    mp = oracle.extend(m, nb).astype(f64)
+    G = oracle.sponge(g.nz, g.nx, nb)              # g(d_z) g(d_x); an interior column / row gives each factor
+    dz = (1.0 - G[:, nb]).astype(f32)[:, None]     # the kernels' per-row and per-column tables of 1 - g
+    dx = (1.0 - G[nb, :]).astype(f32)[None, :]
+    ndG = fma(dz, dx, fma(dz, f32(-1.0), -dx))     # -(1 - G) = dz dx - (dz + dx), as the kernels form it
+    Wt = g.dt ** 2 / (5040.0 * g.dx ** 2 * mp)
+    wh = Wt.astype(f32)
+    wl = (Wt - wh.astype(f64)).astype(f32)
+    rz = f32(g.dx ** 2 / g.dz ** 2)
     wsp = (np.asarray(g.wavelet) * 5040.0 * g.dx / g.dz).astype(f32)
     out = []
     for s in range(g.S):
@@ -43,13 +73,12 @@ def forward_fp32(g, m):
         riz, rix = g.rec_iz[r0:r1] + nb, g.rec_ix[r0:r1] + nb
         tr = np.zeros((g.nt[s], r1 - r0))
         for n in range(g.nt[s]):
-            T = _stencil(u)
+            T = stencil_T(u, rz, order)
             T[g.src_iz[s] + nb, g.src_ix[s] + nb] += wsp[n]
-            y = T / mp
-            wq = Kh * y + Kl * y
-            gp = up - dl * up
-            t = ((u - gp) + u) + wq
-            up, u = u, t - dl * t
+            wq = fma(wh, T, (wl * T).astype(f32))
+            gp = fma(ndG, up, up)
+            t = (((u - gp).astype(f32) + u).astype(f32) + wq).astype(f32)
+            up, u = u, fma(ndG, t, t)
             tr[n] = u[riz, rix]
         out.append(tr.ravel())
     return np.concatenate(out)
