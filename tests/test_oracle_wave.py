@@ -78,6 +78,18 @@ def test_sponge_profile_is_one_inside_and_decays_outward(orc):
     assert G.max() == 1.0 and G.min() < 1.0
 
 
+def test_sponge_is_the_product_of_the_axis_profiles(orc):
+    """G = g(d_z) g(d_x) with g(d) = exp(-(0.015 d)^2), d = cells into the
+    sponge: the reading of the non-reflecting boundary, written out."""
+    nz, nx, nb = 7, 9, 6
+    G = orc.sponge(nz, nx, nb)
+    d = lambda i, n: max(nb - i, i - (nb + n - 1), 0)
+    g = lambda dd: np.exp(-(0.015 * dd) ** 2)
+    ref = np.array([[g(d(i, nz)) * g(d(j, nx)) for j in range(nx + 2 * nb)] for i in range(nz + 2 * nb)])
+    np.testing.assert_allclose(G, ref, rtol=1e-15, atol=0)
+    np.testing.assert_array_equal(G, np.outer(G[:, nb], G[nb, :]))   # separable, bitwise
+
+
 def _point_geometry(n_phys, nb, h, dt, f, nt, offsets):
     cz = n_phys // 2
     g = synth.surface_geometry(n_phys, n_phys, nb, h, dt, f, nt, 1)
