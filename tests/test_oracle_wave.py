@@ -305,3 +305,28 @@ def test_fwi_gradient_equals_born_adjoint_of_residual(orc):
     # E^T folds sponge cells of the same physical cell together; 1/m is uniform over them
     np.testing.assert_allclose(grad, img / p.m_start, rtol=1e-11, atol=1e-13 * np.abs(grad).max())
     assert J == pytest.approx(0.5 * float(r @ r), rel=1e-14)
+
+
+def test_ricker_wavelet_properties():
+    """The source time function (Sec. 4.1 names a Ricker wavelet by its centre
+    frequency): unit peak at t0 = 1.5/f, symmetric about it, zero crossings at
+    tau = +-1/(sqrt(2) pi f), zero mean, and an amplitude spectrum
+    proportional to nu^2 exp(-nu^2/f^2), whose maximum sits at nu = f."""
+    import math
+    f, dt = 15.0, 1e-4
+    n = 4000
+    w = synth.ricker(f, dt, n)
+    t0 = 1.5 / f
+    i0 = int(round(t0 / dt))
+    assert abs(w[i0] - 1.0) < 1e-12 and w.argmax() == i0
+    np.testing.assert_allclose(w[i0 - 500:i0], w[i0 + 500:i0:-1], atol=1e-12)
+    tz = t0 + 1.0 / (math.sqrt(2.0) * math.pi * f)
+    assert abs(synth.ricker(f, 1.0, 1, t0=-tz + t0)[0]) < 1e-12   # w at tau = tz - t0
+    assert abs(w.sum() * dt) < 1e-6
+    spec = np.abs(np.fft.rfft(w, 1 << 18)) * dt
+    nu = np.fft.rfftfreq(1 << 18, dt)
+    assert abs(nu[spec.argmax()] - f) < 0.05
+    ref = nu ** 2 * np.exp(-(nu / f) ** 2)
+    k = (nu > 2.0) & (nu < 60.0)
+    ratio = spec[k] / ref[k]
+    assert ratio.std() < 1e-3 * ratio.mean()
