@@ -13,7 +13,9 @@ A geometry object is anything with the attributes
   src_iz, src_ix                [S] int physical source cells
   nt                            [S] int record length per shot
   rec_off, rec_iz, rec_ix       CSR receivers per shot (physical cells)
-  wavelet                       [max nt] float64 source time function
+  freq                          Ricker centre frequency f (Hz)
+The source time function is the oracle's own: oracle.c evaluates the Ricker
+wavelet w(t_n), t_n = n dt, with delay 1.5/f (``ricker`` returns its samples).
 Traces are a flat float64 array: shot s at offset sum_{q<s} nt_q*nrec_q,
 time-major [nt_s][nrec_s].
 """
@@ -32,7 +34,7 @@ class _Geom(ctypes.Structure):
                 ("src_iz", ctypes.c_void_p), ("src_ix", ctypes.c_void_p),
                 ("nt", ctypes.c_void_p), ("rec_off", ctypes.c_void_p),
                 ("rec_iz", ctypes.c_void_p), ("rec_ix", ctypes.c_void_p),
-                ("wavelet", ctypes.c_void_p)]
+                ("freq", ctypes.c_double), ("amp", ctypes.c_double)]
 
 
 def lib():
@@ -56,6 +58,7 @@ def lib():
         L.og_born_forward.argtypes = [P, P, P, P]
         L.og_born_adjoint.argtypes = [P, P, P, P]
         L.og_num_threads.restype = ctypes.c_int
+        L.og_ricker.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, P]
         _lib = L
     return _lib
 
@@ -75,20 +78,19 @@ def _ptr(a):
 class _Bound:
     """Keeps the converted arrays alive while the C struct points at them."""
 
-    def __init__(self, g):
+    def __init__(self, g, amp=1.0):
         self.src_iz, self.src_ix = _i32(g.src_iz), _i32(g.src_ix)
         self.nt, self.rec_off = _i32(g.nt), _i32(g.rec_off)
         self.rec_iz, self.rec_ix = _i32(g.rec_iz), _i32(g.rec_ix)
-        self.wavelet = _f64(g.wavelet)
         S = len(self.src_iz)
         assert len(self.src_ix) == S and len(self.nt) == S and len(self.rec_off) == S + 1
-        assert self.wavelet.size >= int(self.nt.max())
+        assert float(g.freq) > 0.0, "the geometry must name the Ricker centre frequency"
         self.S = S
         self.nz, self.nx = int(g.nz), int(g.nx)
         self.st = _Geom(int(g.nz), int(g.nx), int(g.nb), float(g.dz), float(g.dx), float(g.dt), S,
                         _ptr(self.src_iz).value, _ptr(self.src_ix).value, _ptr(self.nt).value,
                         _ptr(self.rec_off).value, _ptr(self.rec_iz).value, _ptr(self.rec_ix).value,
-                        _ptr(self.wavelet).value)
+                        float(g.freq), float(amp))
 
     @property
     def ref(self):
@@ -109,6 +111,14 @@ def trace_offsets(g):
 
 def num_threads():
     return lib().og_num_threads()
+
+
+def ricker(f, dt, nt):
+    """The oracle's source time function: w(n dt), n < nt, Ricker wavelet of
+    centre frequency f delayed by 1.5/f (Sec. 4.1 reading)."""
+    out = np.empty(int(nt))
+    lib().og_ricker(float(f), float(dt), int(nt), _ptr(out))
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -174,9 +184,10 @@ def propagate_adjoint(W, G, dz, dx, r, riz, rix):
 # Shot-level operators
 # --------------------------------------------------------------------------
 
-def forward(g, m):
-    """F: m (physical, s^2/m^2) -> traces  (eq. FWD sampled by R, eq. FWI)."""
-    b = _Bound(g)
+def forward(g, m, amp=1.0):
+    """F: m (physical, s^2/m^2) -> traces  (eq. FWD sampled by R, eq. FWI);
+    ``amp`` scales the source (linearity pins)."""
+    b = _Bound(g, amp)
     m = _f64(m)
     assert m.shape == (b.nz, b.nx)
     out = np.empty(trace_count(g))

@@ -30,6 +30,12 @@
  *       du^{n+1} = G (2 du^n - G du^{n-1} + W L du^n) - G W rho (L u0^n + s^n)
  *   Born adjoint: z as above with the Born residual, and
  *       img_pad = -sum_n z^n (L u0^n + s^n),  img = E^T img_pad.
+ *   Source (Sec. 4.1 names a Ricker wavelet by its centre frequency f; delay
+ *     and amplitude are readings): s^n = a w(t_n) / (dx dz) at the source cell,
+ *       w(t) = (1 - 2 pi^2 f^2 tau^2) exp(-pi^2 f^2 tau^2),  tau = t - 1.5/f,
+ *       t_n = n dt, a = 1 unless a caller scales it (linearity pins).
+ *     The oracle evaluates w itself from (f, dt); it takes no samples from
+ *     its callers.
  *
  * Shots are independent; the per-shot loop may run in parallel (OpenMP) but
  * per-shot results are summed afterwards in shot order, so results do not
@@ -46,6 +52,7 @@
 static const double FD_C[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0,
                                8.0 / 315.0, -1.0 / 560.0};
 static const double SPONGE_A = 0.015;
+static const double OG_PI = 3.14159265358979323846;
 
 typedef struct {
     int nz, nx, nb;         /* physical grid and sponge width (cells) */
@@ -57,12 +64,28 @@ typedef struct {
     const int *rec_off;     /* [S+1] CSR offsets into rec_iz/rec_ix */
     const int *rec_iz;      /* physical receiver coordinates */
     const int *rec_ix;
-    const double *wavelet;  /* [max nt] source time function w(t_n) */
+    double freq;            /* Ricker centre frequency f (Hz), > 0 */
+    double amp;             /* source amplitude a */
 } og_geom;
 
 /* ------------------------------------------------------------------ */
 /* Building blocks                                                      */
 /* ------------------------------------------------------------------ */
+
+/* Ricker wavelet sample w(t) with centre frequency f and delay t0 = 1.5/f. */
+static double ricker_at(double f, double t)
+{
+    const double t0 = 1.5 / f;
+    double a = OG_PI * f * (t - t0);
+    a = a * a;
+    return (1.0 - 2.0 * a) * exp(-a);
+}
+
+/* out[n] = w(n dt), n = 0 .. nt-1 (the samples the shot operators inject). */
+void og_ricker(double f, double dt, int nt, double *out)
+{
+    for (int n = 0; n < nt; ++n) out[n] = ricker_at(f, n * dt);
+}
 
 /* out = L u on an NZ x NX grid (x fastest), u = 0 outside the grid. */
 void og_laplacian(int NZ, int NX, double dz, double dx, const double *u,
@@ -246,7 +269,7 @@ static void shot_forward(const og_geom *g, const og_medium *md, int s,
     for (int n = 0; n < nt; ++n) {
         /* q = L u^n + s^n */
         og_laplacian(NZ, NX, g->dz, g->dx, u0, q);
-        q[src] += g->wavelet[n] * inv_cell;
+        q[src] += g->amp * ricker_at(g->freq, n * g->dt) * inv_cell;
         if (lap_hist) memcpy(lap_hist + (size_t)n * N, q, N * sizeof(double));
         for (size_t p = 0; p < N; ++p)
             up[p] = md->G[p] * (2.0 * u0[p] - md->G[p] * um[p] + md->W[p] * q[p]);

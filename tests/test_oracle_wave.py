@@ -179,19 +179,51 @@ def test_forward_causality_exact_zero(orc):
 
 
 def test_forward_linear_in_source(orc):
+    """Scaling the source scales the traces (bitwise for a factor 2), and the
+    recurrence with a general source is additive in it."""
     p = synth.tiny()
     g = p.geom
     d1 = orc.forward(g, p.m_true)
-    g2 = g.subset(range(g.S))
-    g2.wavelet = 2.0 * g.wavelet
-    assert np.array_equal(orc.forward(g2, p.m_true), 2.0 * d1)
-    g3 = g.subset(range(g.S))
-    extra = synth.ricker(25.0, g.dt, len(g.wavelet))
-    g3.wavelet = g.wavelet + extra
-    g4 = g.subset(range(g.S))
-    g4.wavelet = extra
-    dsum = orc.forward(g3, p.m_true)
-    np.testing.assert_allclose(dsum, d1 + orc.forward(g4, p.m_true), rtol=0, atol=1e-12 * np.abs(dsum).max())
+    assert np.array_equal(orc.forward(g, p.m_true, amp=2.0), 2.0 * d1)
+    rng = np.random.default_rng(11)
+    NZ, NX, nt = 16, 19, 30
+    W = (1e-3 ** 2) * rng.uniform(1500, 2500, (NZ, NX)) ** 2
+    G = orc.sponge(NZ - 8, NX - 8, 4)
+    riz, rix = np.array([3, 8, 12]), np.array([4, 9, 15])
+    s1, s2 = rng.standard_normal((2, nt, NZ, NX))
+    t12 = orc.propagate(W, G, 10.0, 10.0, s1 + s2, riz, rix)
+    t1, t2 = (orc.propagate(W, G, 10.0, 10.0, s, riz, rix) for s in (s1, s2))
+    np.testing.assert_allclose(t12, t1 + t2, rtol=0, atol=1e-12 * np.abs(t12).max())
+
+
+def test_forward_is_the_propagator_with_a_point_ricker_source(orc):
+    """The shot operator injects w(t_n)/(dx dz) at the source cell, w being the
+    oracle's own Ricker samples: it equals the general recurrence driven by
+    that point source, bitwise."""
+    p = synth.small_problem()
+    g = p.geom.subset([1])
+    nt = int(g.nt[0])
+    m = p.m_true
+    d = orc.forward(g, m)
+    mp = orc.extend(m, g.nb)
+    W = g.dt ** 2 / mp
+    G = orc.sponge(g.nz, g.nx, g.nb)
+    s = np.zeros((nt,) + mp.shape)
+    s[:, g.src_iz[0] + g.nb, g.src_ix[0] + g.nb] = orc.ricker(g.freq, g.dt, nt) * (1.0 / (g.dx * g.dz))
+    tr = orc.propagate(W, G, g.dz, g.dx, s, g.rec_iz + g.nb, g.rec_ix + g.nb)
+    assert np.array_equal(tr.ravel(), d)
+
+
+def test_oracle_ricker_is_the_inputs_wavelet():
+    """The oracle evaluates its source time function itself; the wavelet the
+    input generator hands to the CUDA library (synth.ricker) must be the same
+    samples, element by element."""
+    import oracle as orc_mod
+    for f, dt, nt in ((10.0, 1e-3, 600), (8.0, 1.5e-3, 2500), (15.0, 1e-3, 4000), (12.0, 0.8e-3, 6000)):
+        a = orc_mod.ricker(f, dt, nt)
+        b = synth.ricker(f, dt, nt)
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-15)
+        assert a.max() <= 1.0 and a.argmax() == int(round(1.5 / f / dt))
 
 
 # -------------------------------------------------------------- adjoint ----
@@ -313,15 +345,17 @@ def test_ricker_wavelet_properties():
     tau = +-1/(sqrt(2) pi f), zero mean, and an amplitude spectrum
     proportional to nu^2 exp(-nu^2/f^2), whose maximum sits at nu = f."""
     import math
+    import oracle as orc_mod
     f, dt = 15.0, 1e-4
     n = 4000
-    w = synth.ricker(f, dt, n)
+    w = orc_mod.ricker(f, dt, n)
     t0 = 1.5 / f
     i0 = int(round(t0 / dt))
     assert abs(w[i0] - 1.0) < 1e-12 and w.argmax() == i0
     np.testing.assert_allclose(w[i0 - 500:i0], w[i0 + 500:i0:-1], atol=1e-12)
     tz = t0 + 1.0 / (math.sqrt(2.0) * math.pi * f)
     assert abs(synth.ricker(f, 1.0, 1, t0=-tz + t0)[0]) < 1e-12   # w at tau = tz - t0
+    assert abs(orc_mod.ricker(f, tz, 2)[1]) < 1e-12                 # w(t0 + tz - t0) = w(tz)
     assert abs(w.sum() * dt) < 1e-6
     spec = np.abs(np.fft.rfft(w, 1 << 18)) * dt
     nu = np.fft.rfftfreq(1 << 18, dt)
