@@ -86,17 +86,23 @@ def test_forward_ragged_uneven_shots(gpu, orc):
 
 # ----------------------------------------------------------------- gradient
 
-# FP32 conditioning of the end-to-end FWI gradient: the gradient is linear in
-# the residual r = F(m) - d, and on the tiny problem ||r|| is only ~0.17 % of
-# ||d|| (the direct wave is the same for the start and the true model).  A
-# forward trace error e relative to ||d|| is therefore amplified ~600x in r,
-# and (concentrated near the sources, where the gradient is largest) somewhat
-# more in the gradient.  FP32 leap-frog traces cannot be closer than ~1e-6 to
-# the FP64 recurrence after 600 steps, so the end-to-end gradient of this
-# problem is checked at 3e-3; the adjoint / imaging operator itself, given the
-# same residual, and the gradient of problems whose residual is not small
-# against the data, are checked at the 1e-4 target.
-E2E_SMALL_RESIDUAL_TOL = 3e-3
+# FP32 floor of the tiny problem's end-to-end parity.  Its residual
+# r = F(m) - d is only ~0.1 % of the data (the direct wave is the same for the
+# start and the true model), so an FP32 trace error e relative to the data is
+# ~1000 e relative to r, and the gradient is linear in r.  The stated targets
+# (gradient 1e-4, 10-iteration history 1e-3) are NOT met on this problem: a
+# float32 emulation shows that no FP32-field form of the recurrence reaches
+# them (tests/test_fp32_conditioning.py: the kernels' form gives a gradient
+# error of 1.3e-3 and a history departure of 2.3e-2; carrying the increment
+# and a compensated u, 2.0e-4 and 1.6e-2; the FP32 stencil alone leaves the
+# traces at 8e-8).  The *_stated_target tests assert the targets and are
+# expected to fail (strict xfail); the other tests bound the measured floor.
+# The adjoint / imaging operator given the same residual, and problems whose
+# residual is the size of the data, are checked at the targets.
+TINY_GRAD_FLOOR = 3e-3
+TINY_HIST_FLOOR = 1e-1
+TINY_UNMET = ("stated target unmet by FP32 wavefields on this small-residual problem: the float32 "
+              "emulation floor (tests/test_fp32_conditioning.py) lies above it")
 
 
 def test_fwi_adjoint_operator_tiny(gpu, orc):
@@ -115,7 +121,8 @@ def test_fwi_adjoint_operator_tiny(gpu, orc):
     assert rel(host(grad), ref) < GRAD_TOL
 
 
-def test_fwi_gradient_tiny(gpu, orc):
+@pytest.fixture(scope="module")
+def tiny_gradient(gpu, orc):
     p = synth.tiny()
     g = p.geom
     d_obs = orc.forward(g, p.m_true)
@@ -124,8 +131,19 @@ def test_fwi_gradient_tiny(gpu, orc):
     plan = plan_for(p)
     grad = gpu.empty(m.shape, device="cuda")
     J = plan.adjoint_gradient(0, dev(gpu, m), None, dev(gpu, d_obs), grad)
+    return J, J_ref, rel(host(grad), grad_ref)
+
+
+def test_fwi_gradient_tiny(tiny_gradient):
+    """The tiny problem's end-to-end gradient within its measured FP32 floor."""
+    J, J_ref, e = tiny_gradient
     assert abs(J - J_ref) / J_ref < HIST_TOL
-    assert rel(host(grad), grad_ref) < E2E_SMALL_RESIDUAL_TOL
+    assert e < TINY_GRAD_FLOOR
+
+
+@pytest.mark.xfail(strict=True, reason=TINY_UNMET)
+def test_fwi_gradient_tiny_stated_target(tiny_gradient):
+    assert tiny_gradient[2] < GRAD_TOL
 
 
 def test_fwi_gradient_large_residual(gpu, orc):
@@ -294,14 +312,8 @@ def test_aa_step_matches_oracle(gpu):
     assert dot == pytest.approx(float(gs[-1] @ (host(nxt) - ps[-1])), rel=1e-6)
 
 
-def test_aa_fwi_misfit_history_tiny(gpu, orc):
-    """Alg. 2 with AA(5), 10 iterations, on the tiny problem against the FP64
-    oracle (tests/golden/tiny_aa_history.json).  The line-search decisions and
-    the first iterations match to 1e-3; later iterations inherit the FP32
-    wavefield error amplified by the AA extrapolation (an FP32 forward alone,
-    with the oracle's FP64 adjoint and AA, moves the history by the same order:
-    tests/test_fp32_conditioning.py), so the whole history is held to 1e-1
-    and to the acceleration over steepest descent."""
+@pytest.fixture(scope="module")
+def tiny_history(gpu, orc):
     from paper_2008_11778_gb300 import solve
     with open(os.path.join(HERE, "golden", "tiny_aa_history.json")) as f:
         ref = json.load(f)
@@ -311,15 +323,31 @@ def test_aa_fwi_misfit_history_tiny(gpu, orc):
     lo, hi = p.m_bounds
     out = solve.aa_fwi(plan, dev(gpu, d_obs), dev(gpu, p.m_start), M=p.M, iters=p.iters,
                        eta_factor=ref["eta_factor"], bounds=(lo, hi))
+    return out, ref
+
+
+def test_aa_fwi_misfit_history_tiny(tiny_history):
+    """Alg. 2 with AA(5), 10 iterations, on the tiny problem against the FP64
+    oracle (tests/golden/tiny_aa_history.json): the line-search decisions,
+    the history lengths and the first iterations match (1e-3); the whole
+    history stays within its measured FP32 floor and accelerates over
+    steepest descent as the oracle's does."""
+    out, ref = tiny_history
     # eta = 1e-4 max|p0| / max|grad J(p0)|: the max sits at a source-adjacent
     # cell, where the end-to-end FP32 gradient error is largest
-    assert abs(out["eta"] - ref["eta"]) / ref["eta"] < E2E_SMALL_RESIDUAL_TOL
+    assert abs(out["eta"] - ref["eta"]) / ref["eta"] < TINY_GRAD_FLOOR
     assert out["lam"] == ref["lam"]
     assert out["Mk"] == ref["Mk"]
     assert rel(out["J"][:4], ref["J"][:4]) < HIST_TOL
-    assert rel(out["J"], ref["J"]) < 1e-1
+    assert rel(out["J"], ref["J"]) < TINY_HIST_FLOOR
     assert out["J"][-1] < 0.75 * ref["J_sd"][-1]
     assert all(b <= a for a, b in zip(out["J"][1:], out["J"][2:]))
+
+
+@pytest.mark.xfail(strict=True, reason=TINY_UNMET)
+def test_aa_fwi_misfit_history_tiny_stated_target(tiny_history):
+    out, ref = tiny_history
+    assert rel(out["J"], ref["J"]) < HIST_TOL
 
 
 def test_aa_fwi_misfit_history_large_residual(gpu, orc):
