@@ -269,7 +269,10 @@ int aafwi_aa_combine(aafwi_aa *aa, double lambda, const float *p_tilde, const fl
                      aafwi_stream stream);
 
 /* max_i |x_i| of a device FP32 vector (FP64 result on the host, syncs);
- * used to fix eta = factor * max|p_0| / max|grad J(p_0)|. */
+ * used to fix eta = factor * max|p_0| / max|grad J(p_0)|.  Its scratch (and
+ * aafwi_dot's) is one small library-owned buffer per device, allocated by the
+ * first call on that device and reused; calls from several host threads are
+ * serialised.  Errors: ARG (NULL, n = 0), NOMEM (first call), CUDA. */
 int aafwi_absmax(const float *x, size_t n, double *host_out, aafwi_stream stream);
 
 /* ---- learned preconditioner (not part of the paper) ---------------------- */
@@ -335,9 +338,10 @@ int aafwi_learned_apply(const float *m, const float *delta, int nz, int nx, int 
  *   (the call synchronises the stream) or NULL; at least one of the two.
  * n must lie in [1, AAFWI_MISFIT_NOALLOC_MAX_SAMPLES]; larger inputs return
  * AAFWI_ERR_ARG with a message (aafwi_last_error(NULL)) and launch nothing.
- * The first call on a device looks up the array's device address once for
- * that device (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the one array and every call overwrites it, so
+ * Every call looks up the array's address on the current device
+ * (cudaGetSymbolAddress, a host-side query); the first call on a device may
+ * also load the library's kernels there, so make that first call before any
+ * stream capture.  All calls share the one array and every call overwrites it, so
  * calls whose kernels overlap on the GPU (other streams, other host threads)
  * race: serialise them on one stream. */
 #define AAFWI_MISFIT_NOALLOC_MAX_SAMPLES (1LL << 32)
@@ -350,8 +354,9 @@ int aafwi_misfit_noalloc(const float *d_syn, const float *d_obs, long long n, fl
  * the LSRTM normal equations, L-BFGS for FWI) ------------------------------ */
 
 /* <x, y> of two device FP32 vectors of length n, accumulated in FP64 in a
- * fixed order (deterministic); result on the host (syncs the stream).
- * Errors: ARG (NULL, n = 0), NOMEM, CUDA. */
+ * fixed order (deterministic); result on the host (syncs the stream).  Uses
+ * the per-device reduction scratch of aafwi_absmax (no allocation after the
+ * first call on a device).  Errors: ARG (NULL, n = 0), NOMEM, CUDA. */
 int aafwi_dot(const float *x, const float *y, size_t n, double *host_out, aafwi_stream stream);
 
 /* y = a x + b y on device FP32 vectors of length n (a, b rounded to FP32);
@@ -377,7 +382,8 @@ typedef struct {
  * tile height (base->engine, when not AUTO, restricts the candidates to that
  * engine); all with the default shot lanes, then, unless base->lanes fixes
  * them, the winner with 1, 2 and 8 lanes.  Each candidate is a temporary
- * plan over the same shots with every record length cut to `steps` (the
+ * plan over the same shots (over the first batch of shots when a plan of the
+ * full record would run them in batches) with every record length cut to `steps` (the
  * sweeps' time grows in proportion to the steps), timed `reps` times after one
  * warm-up on the device model m [nz][nx] (FP32, m = 1/c^2) with zero observed
  * data, on a stream of its own.

@@ -10,6 +10,7 @@
 #include <vector>
 #include <algorithm>
 #include <set>
+#include <mutex>
 
 #include "../../include/aafwi.h"
 #include "internal.cuh"
@@ -157,7 +158,9 @@ bool upload(std::vector<Buf> &bufs, T **out, const std::vector<T> &h)
 
 float *slot(float *base, long long per_slot, long long i) { return base + per_slot * i; }
 
-enum { SWEEP_FWD = 0, SWEEP_BORN = 1, SWEEP_ADJ = 2, SWEEP_ADJ_BORN = 3 };
+// Sweep kinds of the graph cache; SWEEP_FWD_TRACES is a forward sweep that
+// stores no history (the traces of a plan whose history cannot be reused).
+enum { SWEEP_FWD = 0, SWEEP_BORN = 1, SWEEP_ADJ = 2, SWEEP_ADJ_BORN = 3, SWEEP_FWD_TRACES = 4, SWEEP_KINDS = 5 };
 constexpr size_t kMaxSweepGraphs = 8;   // per batch
 
 void drop_graphs(aafwi_plan *p)
@@ -169,6 +172,27 @@ void drop_graphs(aafwi_plan *p)
 }
 
 constexpr int kDefaultLanes = 4;
+
+// Scratch of the stand-alone reductions (aafwi_dot, aafwi_absmax): RED_BLOCKS
+// FP64 partials and the result, allocated once per device on first use and
+// reused by every later call.  Callers hold g_red_mu until the result is back
+// on the host, so calls from several host threads do not share it in flight.
+std::mutex g_red_mu;
+constexpr int kMaxDevices = 64;
+double *g_red_buf[kMaxDevices] = {};
+
+bool reduction_scratch(double **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+    if (!g_red_buf[dev] && cudaMalloc((void **)&g_red_buf[dev], (RED_BLOCKS + 1) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        g_red_buf[dev] = nullptr;
+        return false;
+    }
+    *out = g_red_buf[dev];
+    return true;
+}
 
 // The batch's shots split into p->lanes consecutive groups (fewer if the
 // batch has fewer shots), each with its launch geometry and stream: lane 0
@@ -285,8 +309,9 @@ Geo batch_geo(const aafwi_plan *p, int b)
 // Per-step forward sweep over the batch's shots (born: u and du together).
 // u^n and u^{n-1} rotate in fbuf (u^{n+1} overwrites u^{n-1} in place); with
 // the full history T^n goes to history slot n+1, else (u^n, u^{n-1}) are
-// checkpointed every k steps.
-int sweep_forward(aafwi_plan *p, const Geo &g, bool born, float *traces, cudaStream_t st)
+// checkpointed every k steps.  With store = false neither is written (the
+// traces alone are wanted).
+int sweep_forward(aafwi_plan *p, const Geo &g, bool born, bool store, float *traces, cudaStream_t st)
 {
     const long long ps = (long long)p->Sb * p->field;
     if (cudaMemsetAsync(p->fbuf, 0, 2 * ps * sizeof(float), st) != cudaSuccess)
@@ -302,7 +327,8 @@ int sweep_forward(aafwi_plan *p, const Geo &g, bool born, float *traces, cudaStr
         int q = 0;
         for (; n0 + 1 < p->nt_max; n0 += 2, q ^= 1) {
             Fwd2Args a{p->W, 2 * q, 2 * q + 1, slot(p->fbuf, ps, 2 * (q ^ 1)), slot(p->fbuf, ps, 2 * (q ^ 1) + 1),
-                       traces, slot(p->hist, ps, n0 + 1), slot(p->hist, ps, n0 + 2), n0};
+                       traces, store ? slot(p->hist, ps, n0 + 1) : nullptr,
+                       store ? slot(p->hist, ps, n0 + 2) : nullptr, n0};
             for (int l = 0; l < ln.L; ++l) launch_fwd2(ln.g[l], a, p->tm_f8, p->tm_f, ln.st[l], p->pdl && n0 > 0);
         }
         cur = 2 * q + 1;
@@ -312,7 +338,8 @@ int sweep_forward(aafwi_plan *p, const Geo &g, bool born, float *traces, cudaStr
         // one step: u^{n+1} overwrites u^{n-1} in place, then the slots swap roles
         float *prev = slot(p->fbuf, ps, prv), *next = prev;
         float *ckc = nullptr, *ckp = nullptr, *tout = nullptr;
-        if (p->full) {
+        if (!store) {
+        } else if (p->full) {
             tout = slot(p->hist, ps, n + 1);
         } else if (n % p->k == 0) {
             ckc = slot(p->hist, ps, 2LL * (n / p->k));
@@ -337,17 +364,19 @@ int sweep_forward(aafwi_plan *p, const Geo &g, bool born, float *traces, cudaStr
 }
 
 // Forward sweep over batch b (born: u and du together); traces -> CSR.
-int run_forward(aafwi_plan *p, int b, bool born, float *traces, cudaStream_t st)
+// store = false: no history or checkpoints (FWI forward of per-step engines).
+int run_forward(aafwi_plan *p, int b, bool born, float *traces, cudaStream_t st, bool store = true)
 {
     p->hist_T = false;
     int rc;
     const Geo g = batch_geo(p, b);
+    store = store || born || p->persist_fwd;
     if (p->persist_fwd && !born) rc = run_persist_forward(p, traces, st);
-    else if (!p->graphs) rc = sweep_forward(p, g, born, traces, st);
+    else if (!p->graphs) rc = sweep_forward(p, g, born, store, traces, st);
     else
-        rc = run_graph(p, (born ? SWEEP_BORN : SWEEP_FWD) + 4 * b, traces, st,
-                       [&](cudaStream_t cs) { return sweep_forward(p, g, born, traces, cs); });
-    p->hist_T = rc == AAFWI_OK && p->full;
+        rc = run_graph(p, (born ? SWEEP_BORN : store ? SWEEP_FWD : SWEEP_FWD_TRACES) + SWEEP_KINDS * b, traces, st,
+                       [&](cudaStream_t cs) { return sweep_forward(p, g, born, store, traces, cs); });
+    p->hist_T = rc == AAFWI_OK && p->full && store;
     return rc;
 }
 
@@ -418,7 +447,7 @@ int run_adjoint(aafwi_plan *p, int b, bool born, const float *resid, cudaStream_
     }
     const Geo g = batch_geo(p, b);
     if (!p->graphs) return sweep_adjoint(p, g, born, resid, st);
-    return run_graph(p, (born ? SWEEP_ADJ_BORN : SWEEP_ADJ) + 4 * b, resid, st,
+    return run_graph(p, (born ? SWEEP_ADJ_BORN : SWEEP_ADJ) + SWEEP_KINDS * b, resid, st,
                      [&](cudaStream_t cs) { return sweep_adjoint(p, g, born, resid, cs); });
 }
 
@@ -873,8 +902,10 @@ int aafwi_model_forward(aafwi_plan *p, const float *m, float *d_out, aafwi_strea
     int rc;
     p->fwd_valid = false;
     if ((rc = prep(p, m, nullptr, st))) return rc;
+    // with several batches only the last batch's wavefield would survive, and
+    // no adjoint can reuse it: store no history
     for (int b = 0; b < p->nbatch; ++b)
-        if ((rc = run_forward(p, b, false, p->dsyn, st))) return rc;
+        if ((rc = run_forward(p, b, false, p->dsyn, st, p->nbatch == 1))) return rc;
     if (d_out && d_out != p->dsyn &&
         cudaMemcpyAsync(d_out, p->dsyn, p->trace_count * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return cuda_fail(p, cudaGetLastError(), "copy traces");
@@ -1152,13 +1183,11 @@ int aafwi_absmax(const float *x, size_t n, double *host_out, aafwi_stream stream
 {
     if (!x || !host_out || n == 0) return fail(nullptr, AAFWI_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_red_mu);
     double *buf = nullptr;
-    // small scratch owned by this call (RED_BLOCKS partials + result)
-    if (cudaMallocAsync((void **)&buf, (RED_BLOCKS + 1) * sizeof(double), st) != cudaSuccess)
-        return fail(nullptr, AAFWI_ERR_NOMEM, "absmax scratch");
+    if (!reduction_scratch(&buf)) return fail(nullptr, AAFWI_ERR_NOMEM, "absmax scratch");
     launch_absmax(x, (long long)n, buf, buf + RED_BLOCKS, st);
     cudaError_t e = cudaMemcpyAsync(host_out, buf + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(buf, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "absmax");
     return AAFWI_OK;
@@ -1168,12 +1197,11 @@ int aafwi_dot(const float *x, const float *y, size_t n, double *host_out, aafwi_
 {
     if (!x || !y || !host_out || n == 0) return fail(nullptr, AAFWI_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_red_mu);
     double *buf = nullptr;
-    if (cudaMallocAsync((void **)&buf, (RED_BLOCKS + 1) * sizeof(double), st) != cudaSuccess)
-        return fail(nullptr, AAFWI_ERR_NOMEM, "dot scratch");
+    if (!reduction_scratch(&buf)) return fail(nullptr, AAFWI_ERR_NOMEM, "dot scratch");
     launch_dot(x, y, (long long)n, buf, buf + RED_BLOCKS, st);
     cudaError_t e = cudaMemcpyAsync(host_out, buf + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(buf, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "dot");
     return AAFWI_OK;

@@ -93,8 +93,12 @@ extern "C" int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, 
         for (int tz : {16, 32, 64}) cands.push_back({AAFWI_ENGINE_HYBRID, tz, o.lanes});
     if (cands.empty())
         return tune_fail(AAFWI_ERR_ARG, "autotune: the persistent engines need the full history of all shots at once");
+    // A plan of the full record that runs its shots in batches sweeps one
+    // batch at a time: time the candidates on one batch (the first lay.Sb
+    // shots) so that a launch covers the shots it will cover in that plan.
     aafwi_shots sh = *shots;
     sh.nt = nt.data();
+    if (lay.nbatch > 1) sh.S = lay.Sb;
     Scratch sc;
     if (cudaStreamCreateWithFlags(&sc.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&sc.e0) != cudaSuccess || cudaEventCreate(&sc.e1) != cudaSuccess)
@@ -155,7 +159,7 @@ extern "C" int aafwi_autotune(const aafwi_grid *grid, const aafwi_shots *shots, 
     if (ntimed > 0 && o.lanes == 0 && win.engine != AAFWI_ENGINE_PERSISTENT) {
         const Candidate w = win;
         for (int l : {1, 2, 8}) {
-            if (l > S) continue;
+            if (l > sh.S) continue;
             int rc = AAFWI_OK;
             try_one({w.engine, w.tile_z, l}, &rc);
             if (rc) return rc;

@@ -12,7 +12,6 @@
 // The partial sums are taken over fixed chunks of CHUNK samples, one CTA per
 // chunk, so the result does not depend on scheduling; the array holds at most
 // MAX_CHUNKS partials, which bounds a call to MAX_CHUNKS * CHUNK samples.
-#include <mutex>
 #include <string>
 
 #include "../../include/aafwi.h"
@@ -28,10 +27,6 @@ constexpr int NT = 256;
 
 // partials [0, MAX_CHUNKS) and the misfit J at [MAX_CHUNKS].
 static __device__ __align__(256) double g_misfit_scratch[MAX_CHUNKS + 1];
-
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-double *g_scratch_addr[MAX_DEVICES] = {nullptr};
 
 __device__ __forceinline__ double block_sum256(double v, double *sh)
 {
@@ -80,22 +75,16 @@ __global__ void __launch_bounds__(NT) k_misfit_finish(const double *partials, in
     }
 }
 
-// Device address of the scratch array for the current device, looked up once
-// per device (host code may not take the address of a __device__ symbol).
+// Device address of the scratch array on the current device.  Host code may
+// not take the address of a __device__ symbol, so it is looked up on every
+// call: the lookup is a host-side query, and a cached address could go stale
+// if the device's context were reset and the module loaded again.
 cudaError_t scratch_for_current_device(double **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    double *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_misfit_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-        double *p = nullptr;
-        e = cudaGetSymbolAddress((void **)&p, g_misfit_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

@@ -147,6 +147,9 @@ def time_to_target(run, target, max_iters):
 TRAIN_SEED0 = 4 * 1000 + 2008          # training models: seeds TRAIN_SEED0 + i
 EVAL_SEED0 = 4 * 1000 + 2008 + 100000  # held-out models: disjoint seeds
 WEIGHTS = __file__.replace("learned.py", "weights/unet_c32.npz")
+# evaluation record of the committed weights on the held-out models, written by
+# `python -m paper_2008_11778_gb300.learned --eval-only --eval 50 --record`
+EVAL_RECORD = __file__.replace("learned.py", "weights/unet_c32_eval.json")
 
 
 def save_weights(path, params, meta):
@@ -220,9 +223,12 @@ def _layer_list(C):
     return L
 
 
-def compare(params, n_eval, target, max_iters, C=32, log=print):
+def compare(params, n_eval, target, max_iters, C=32, log=print, plain_eta_factors=(1e-4,)):
     """Wall seconds (GPU synchronised) for plain AA(10) and learned AA(10) to
-    reach J/J0 <= target on n_eval held-out 400 x 150 models."""
+    reach J/J0 <= target on n_eval held-out 400 x 150 models.  Plain AA runs
+    once per step factor in plain_eta_factors (eta = factor max|p_0| /
+    max|grad J(p_0)|; the first is the default reading, which the learned run
+    also uses); row["plain"] is the default, row["plain_eta"] holds them all."""
     from . import synth as S
     prob0 = S.learned_eval_model(EVAL_SEED0)
     g = prob0.geom
@@ -238,21 +244,28 @@ def compare(params, n_eval, target, max_iters, C=32, log=print):
         d = torch.empty(plan.trace_count, device="cuda")
         plan.model_forward(mt, d)
         m0 = torch.as_tensor(prob.m_start.astype(np.float32), device="cuda")
-        row = {"seed": EVAL_SEED0 + i}
-        for name in ("plain", "learned"):
+        row = {"seed": EVAL_SEED0 + i, "plain_eta": {}}
+        arms = [("plain", f) for f in plain_eta_factors] + [("learned", plain_eta_factors[0])]
+        for name, f in arms:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             if name == "plain":
-                run = solve.AAInversion(plan, d, m0, 10, bounds=prob.m_bounds)
+                run = solve.AAInversion(plan, d, m0, 10, bounds=prob.m_bounds, eta_factor=f)
             else:
-                run = LearnedAAInversion(plan, d, m0, 10, prop, bounds=prob.m_bounds)
+                run = LearnedAAInversion(plan, d, m0, 10, prop, bounds=prob.m_bounds, eta_factor=f)
             _, it, r = time_to_target(run, target, max_iters)
             torch.cuda.synchronize()
             total = time.perf_counter() - t0
-            row[name] = {"seconds": total, "iterations": it, "J_over_J0": r, "reached": r <= target,
-                         "forward_passes": run.n_forward, "adjoint_passes": run.n_adjoint,
-                         "learned_steps": getattr(run, "n_learned", 0)}
+            res = {"seconds": total, "iterations": it, "J_over_J0": r, "reached": bool(r <= target),
+                   "forward_passes": run.n_forward, "adjoint_passes": run.n_adjoint,
+                   "learned_steps": getattr(run, "n_learned", 0), "eta_factor": f}
             run.close()
+            if name == "plain":
+                row["plain_eta"]["%g" % f] = res
+                if f == plain_eta_factors[0]:
+                    row["plain"] = res
+            else:
+                row["learned"] = res
         log(row)
         rows.append(row)
     plan.close()
@@ -260,22 +273,91 @@ def compare(params, n_eval, target, max_iters, C=32, log=print):
     return rows
 
 
+def best_plain(row):
+    """The fastest plain arm of a row among those that reached the target, else
+    the one with the lowest final J/J0."""
+    arms = list(row["plain_eta"].values())
+    reached = [a for a in arms if a["reached"]]
+    if reached:
+        return min(reached, key=lambda a: a["seconds"])
+    return min(arms, key=lambda a: a["J_over_J0"])
+
+
+def summarize(rows, target, max_iters):
+    """Per-model seconds and flags, and the median / minimum speed-up of the
+    learned arm over the default plain arm and over the best plain arm."""
+    sp = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in rows]
+    bp = [best_plain(r) for r in rows]
+    spb = [b["seconds"] / r["learned"]["seconds"] for b, r in zip(bp, rows)]
+    both = [r["plain"]["reached"] and r["learned"]["reached"] for r in rows]
+    both_b = [b["reached"] and r["learned"]["reached"] for b, r in zip(bp, rows)]
+    return {
+        "target": target, "max_iters": max_iters, "models": len(rows),
+        "plain_eta_factors": sorted({float(k) for r in rows for k in r["plain_eta"]}),
+        "plain_reached": sum(r["plain"]["reached"] for r in rows),
+        "best_plain_reached": sum(b["reached"] for b in bp),
+        "learned_reached": sum(r["learned"]["reached"] for r in rows),
+        "median_speedup": float(np.median(sp)), "min_speedup": float(np.min(sp)),
+        "median_speedup_both_reached": float(np.median([x for x, k in zip(sp, both) if k])) if any(both) else None,
+        "median_speedup_vs_best_plain": float(np.median(spb)), "min_speedup_vs_best_plain": float(np.min(spb)),
+        "median_speedup_vs_best_plain_both_reached":
+            float(np.median([x for x, k in zip(spb, both_b) if k])) if any(both_b) else None,
+        "plain_s": [r["plain"]["seconds"] for r in rows],
+        "plain_reached_flags": [r["plain"]["reached"] for r in rows],
+        "best_plain_s": [b["seconds"] for b in bp],
+        "best_plain_eta_factor": [b["eta_factor"] for b in bp],
+        "best_plain_reached_flags": [b["reached"] for b in bp],
+        "learned_s": [r["learned"]["seconds"] for r in rows],
+        "learned_reached_flags": [r["learned"]["reached"] for r in rows],
+    }
+
+
+def load_eval_record(path=EVAL_RECORD):
+    """The committed evaluation record's summary (None if absent)."""
+    import json
+    import os
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    out = dict(rec["summary"])
+    out["source"] = os.path.basename(path)
+    out["command"] = rec.get("command")
+    out["gpu"] = rec.get("gpu")
+    return out
+
+
 if __name__ == "__main__":
     import argparse
     import json
+    import sys
     ap = argparse.ArgumentParser(description="train / evaluate the learned preconditioner")
     ap.add_argument("--models", type=int, default=120)
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--eval", type=int, default=4)
     ap.add_argument("--target", type=float, default=0.1)
     ap.add_argument("--max-iters", type=int, default=80)
+    ap.add_argument("--eta-factors", default="1e-4", help="comma-separated step factors of the plain arms")
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--eval-only", action="store_true")
+    ap.add_argument("--record", nargs="?", const=EVAL_RECORD, default=None,
+                    help="write the evaluation record (default path: the committed record)")
     a = ap.parse_args()
     if a.eval_only:
         params, meta = load_weights(a.out)
     else:
         params, meta = train_preconditioner(a.models, steps=a.steps)
         save_weights(a.out, params, {k: np.asarray(v) for k, v in meta.items()})
-    rows = compare(params, a.eval, a.target, a.max_iters)
-    print(json.dumps({"train": {k: float(v) for k, v in meta.items()}, "eval": rows}, default=float))
+    factors = tuple(float(x) for x in a.eta_factors.split(","))
+    rows = compare(params, a.eval, a.target, a.max_iters, plain_eta_factors=factors,
+                   log=lambda r: print(json.dumps(r, default=float), flush=True))
+    summary = summarize(rows, a.target, a.max_iters)
+    if a.record:
+        rec = {"what": "learned AA(10) vs plain AA(10) on held-out 400 x 150 models (seeds EVAL_SEED0 + i), "
+                       "wall seconds to J/J0 <= target on one GPU",
+               "command": "python -m paper_2008_11778_gb300.learned " + " ".join(sys.argv[1:]),
+               "gpu": torch.cuda.get_device_name(0), "training": {k: float(v) for k, v in meta.items()},
+               "summary": summary, "rows": rows}
+        with open(a.record, "w") as f:
+            json.dump(rec, f, indent=1, default=float)
+    print(json.dumps({"train": {k: float(v) for k, v in meta.items()}, "summary": summary}, default=float))
