@@ -54,7 +54,13 @@ extern "C" {
 #define AAFWI_ERR_CFL       2   /* c_max*dt/min(dx,dz) above the stability limit 0.55 */
 #define AAFWI_ERR_OOB       3   /* source / receiver outside the physical grid */
 #define AAFWI_ERR_NAN       4   /* model has a non-finite or non-positive value */
-#define AAFWI_ERR_TIMEOUT   5   /* a bounded device-side wait ran out (persistent sweeps) */
+#define AAFWI_ERR_TIMEOUT   5   /* a bounded device-side wait ran out.  A persistent sweep's
+                                   neighbour wait: the call fails, the plan stays usable.  A
+                                   per-step kernel's tile-copy (TMA) wait or a U-Net tensor-core
+                                   wait: a copy or an MMA may still have been in flight when the
+                                   CTA returned, so the plan / network is retired -- every later
+                                   call on it returns AAFWI_ERR_TIMEOUT; destroy it and reset the
+                                   device context (cudaDeviceReset) before going on */
 #define AAFWI_ERR_CUDA      6   /* a CUDA runtime call failed */
 #define AAFWI_ERR_NOMEM     7   /* workspace does not fit the budget / device */
 #define AAFWI_ERR_STATE     8   /* call out of order (e.g. reuse without a stored forward) */

@@ -71,6 +71,7 @@ struct aafwi_plan {
     size_t ws_bytes = 0;
     bool fwd_valid = false;
     const float *fwd_model = nullptr;
+    bool retired = false;           // a TMA wait ran out: every later call is refused
     // persistent engine
     bool persist_fwd = false;       // FWI forward sweeps: one cooperative launch each
     bool persist_adj = false;       // adjoint sweeps: one cooperative launch each
@@ -460,6 +461,16 @@ int prep(aafwi_plan *p, const float *m, const float *rho, cudaStream_t st)
     return check_launch(p);
 }
 
+constexpr const char *kRetired =
+    "a tile copy (TMA) did not complete within its bounded wait; the plan is retired and refuses every "
+    "later call: destroy it and reset the device context (cudaDeviceReset) before continuing";
+
+// The first check of every plan entry point: a retired plan runs nothing.
+int refuse_retired(aafwi_plan *p)
+{
+    return p && p->retired ? fail(p, AAFWI_ERR_TIMEOUT, kRetired) : AAFWI_OK;
+}
+
 int finish_sync(aafwi_plan *p, double *J_host, cudaStream_t st)
 {
     if (!J_host) return AAFWI_OK;
@@ -470,6 +481,10 @@ int finish_sync(aafwi_plan *p, double *J_host, cudaStream_t st)
     if (e != cudaSuccess) return cuda_fail(p, e, "synchronise");
     if (err) {
         p->fwd_valid = false;
+        if (err & 8) {
+            p->retired = true;
+            return fail(p, AAFWI_ERR_TIMEOUT, kRetired);
+        }
         cudaMemsetAsync(p->err, 0, sizeof(int), st);
         if (err & 1) return fail(p, AAFWI_ERR_NAN, "model has a non-finite or non-positive value");
         if (err & 4) return fail(p, AAFWI_ERR_TIMEOUT, "a persistent sweep's bounded wait ran out");
@@ -897,6 +912,7 @@ int aafwi_plan_get_info(const aafwi_plan *p, aafwi_plan_info *info)
 
 int aafwi_model_forward(aafwi_plan *p, const float *m, float *d_out, aafwi_stream stream)
 {
+    if (int rc0 = refuse_retired(p)) return rc0;
     if (!p || !m) return fail(p, AAFWI_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
@@ -916,6 +932,7 @@ int aafwi_model_forward(aafwi_plan *p, const float *m, float *d_out, aafwi_strea
 
 int aafwi_born_forward(aafwi_plan *p, const float *m0, const float *rho, float *d_out, aafwi_stream stream)
 {
+    if (int rc0 = refuse_retired(p)) return rc0;
     if (!p || !m0 || !rho || !d_out) return fail(p, AAFWI_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
@@ -929,6 +946,7 @@ int aafwi_born_forward(aafwi_plan *p, const float *m0, const float *rho, float *
 int aafwi_misfit(aafwi_plan *p, const float *d_syn, const float *d_obs, float *resid, double *J_host,
                  aafwi_stream stream)
 {
+    if (int rc0 = refuse_retired(p)) return rc0;
     if (!p || !d_syn || !d_obs) return fail(p, AAFWI_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     launch_misfit(d_syn, d_obs, resid, p->trace_count, p->partials, p->J, st);
@@ -939,6 +957,7 @@ int aafwi_misfit(aafwi_plan *p, const float *d_syn, const float *d_obs, float *r
 
 int aafwi_read_misfit(aafwi_plan *p, double *J_host, aafwi_stream stream)
 {
+    if (int rc0 = refuse_retired(p)) return rc0;
     if (!p || !J_host) return fail(p, AAFWI_ERR_ARG, "NULL argument");
     return finish_sync(p, J_host, (cudaStream_t)stream);
 }
@@ -989,6 +1008,7 @@ int gradient_pass(aafwi_plan *p, bool fwd_born, bool adj_born, bool reuse, const
 int aafwi_adjoint_gradient(aafwi_plan *p, int mode, const float *m, const float *rho, const float *d_obs,
                            float *grad, double *J_host, int flags, aafwi_stream stream)
 {
+    if (int rc0 = refuse_retired(p)) return rc0;
     if (!p || !m || !d_obs || !grad) return fail(p, AAFWI_ERR_ARG, "NULL argument");
     if (mode != AAFWI_MODE_FWI && mode != AAFWI_MODE_LSRTM) return fail(p, AAFWI_ERR_ARG, "unknown mode");
     if (mode == AAFWI_MODE_LSRTM && !rho) return fail(p, AAFWI_ERR_ARG, "LSRTM needs rho");
@@ -1014,6 +1034,7 @@ int aafwi_adjoint_gradient(aafwi_plan *p, int mode, const float *m, const float 
 int aafwi_adjoint_gradient_host(aafwi_plan *p, int mode, const float *m, const float *rho, const float *d_obs,
                                 float *grad, double *J_host, aafwi_stream stream)
 {
+    if (int rc0 = refuse_retired(p)) return rc0;
     if (!p || !m || !d_obs || !grad || !J_host) return fail(p, AAFWI_ERR_ARG, "NULL argument");
     if (mode != AAFWI_MODE_FWI && mode != AAFWI_MODE_LSRTM) return fail(p, AAFWI_ERR_ARG, "unknown mode");
     if (mode == AAFWI_MODE_LSRTM && !rho) return fail(p, AAFWI_ERR_ARG, "LSRTM needs rho");
@@ -1040,6 +1061,7 @@ int aafwi_adjoint_gradient_host(aafwi_plan *p, int mode, const float *m, const f
 int aafwi_fwi_adjoint(aafwi_plan *p, const float *m, const float *adj_src, float *grad, int flags,
                       aafwi_stream stream)
 {
+    if (int rc0 = refuse_retired(p)) return rc0;
     if (!p || !m || !adj_src || !grad) return fail(p, AAFWI_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
@@ -1059,6 +1081,7 @@ int aafwi_fwi_adjoint(aafwi_plan *p, const float *m, const float *adj_src, float
 
 int aafwi_born_adjoint(aafwi_plan *p, const float *m0, const float *resid, float *img, aafwi_stream stream)
 {
+    if (int rc0 = refuse_retired(p)) return rc0;
     if (!p || !m0 || !resid || !img) return fail(p, AAFWI_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
@@ -1086,7 +1109,7 @@ int aafwi_aa_create(size_t n, int M, double eta, aafwi_aa **out)
     const int M1 = M + 1;
     bool ok = dalloc(a->bufs, &s.ring_p, (size_t)M1 * n) && dalloc(a->bufs, &s.ring_g, (size_t)M1 * n) &&
               dalloc(a->bufs, &s.gram, (size_t)M1 * M1) &&
-              dalloc(a->bufs, &s.partials, (size_t)RED_BLOCKS * (AA_MAXM + 2)) &&
+              dalloc(a->bufs, &s.partials, (size_t)RED_BLOCKS * (2 * AA_MAXM)) &&
               dalloc(a->bufs, &s.gamma, AA_MAXM) && dalloc(a->bufs, &s.meta, 4) && dalloc(a->bufs, &s.dot, 1);
     if (!ok) {
         free_bufs(a->bufs);

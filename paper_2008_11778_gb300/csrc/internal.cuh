@@ -227,8 +227,8 @@ struct AAState {
     long long n;
     int M;
     float *ring_p, *ring_g;        // [M+1][n]
-    double *gram;                  // [(M+1)*(M+1)] by slot
-    double *partials;              // [RED_BLOCKS][M+2]
+    double *gram;                  // [(M+1)*(M+1)]: H = dG^T dG by the slots naming the differences
+    double *partials;              // [RED_BLOCKS][2 * AA_MAXM] (aa_step), [RED_BLOCKS] (combine)
     double *gamma;                 // [M]
     int *meta;                     // [0] Mk used, [1] first dropped column
     double *dot;                   // [1] armijo dot

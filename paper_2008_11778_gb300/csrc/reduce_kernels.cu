@@ -154,68 +154,94 @@ void launch_absmax(const float *x, long long n, double *partials, double *out_de
 // Anderson acceleration
 // ---------------------------------------------------------------------------
 
-// Copy (p_k, G_k) into ring slot `head` and accumulate <G_k, G_slot>_w for the
-// c history slots (chronological slot list `slots`, the newest last); w: the
-// diagonal weight of a weighted l2 norm (Sec. 2.1), or null for the l2 norm.
+// The least squares of Alg. 2 step 2 (eqs. Ak, solveGamma) in the gamma
+// form: gamma = argmin || dG gamma - G_k ||, dG_j = G_{j+1} - G_j over the
+// window.  Its normal matrix and right-hand side are accumulated from the
+// differences themselves: dG_j is formed per element in FP64 from the FP32
+// ring (exact), so near convergence, when ||dG|| << ||G||, nothing cancels
+// (differences of Gram entries of the G_i would lose log10(||G||^2/||dG||^2)
+// digits).  The matrix H = dG^T dG is kept by difference across iterations:
+// difference j is named by the ring slot of its newer end, and each step adds
+// the inner products of the newest difference with all of them.
 struct AASlots {
     int slot[AA_MAXM + 1];
     int c;
 };
 
+// Copy (p_k, G_k) into ring slot `head` (the newest of the c chronological
+// slots) and accumulate per block, w the diagonal weight of a weighted l2
+// norm (Sec. 2.1) or null:
+//   partials[b][j]           = <dG_new, dG_j>_w   (dG_new = dG_{c-2})
+//   partials[b][AA_MAXM + j] = <dG_j, G_k>_w      for j < c - 1.
 __global__ void __launch_bounds__(RT) k_aa_append(const float *p_k, const float *g_k, float *ring_p,
                                                   float *ring_g, long long n, int head, AASlots sl,
                                                   const float *w, double *partials)
 {
     __shared__ double sh[RT / 32];
-    double acc[AA_MAXM + 1];
+    const int nd = sl.c - 1;
+    double accH[AA_MAXM], accB[AA_MAXM];
 #pragma unroll
-    for (int j = 0; j <= AA_MAXM; ++j) acc[j] = 0.0;
+    for (int j = 0; j < AA_MAXM; ++j) accH[j] = accB[j] = 0.0;
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
         const float gv = g_k[i];
         ring_p[(long long)head * n + i] = p_k[i];
         ring_g[(long long)head * n + i] = gv;
-        const double gw = w ? (double)w[i] * (double)gv : (double)gv;
+        if (nd < 1) continue;
+        const double wi = w ? (double)w[i] : 1.0;
+        const double gk = (double)gv;
+        const double dnew = gk - (double)ring_g[(long long)sl.slot[nd - 1] * n + i];
+        double ga = (double)ring_g[(long long)sl.slot[0] * n + i];
 #pragma unroll
-        for (int j = 0; j <= AA_MAXM; ++j) {
-            if (j < sl.c) {
-                const float o = sl.slot[j] == head ? gv : ring_g[(long long)sl.slot[j] * n + i];
-                acc[j] += gw * (double)o;
+        for (int j = 0; j < AA_MAXM; ++j) {
+            if (j < nd) {
+                const double gb = j + 1 == nd ? gk : (double)ring_g[(long long)sl.slot[j + 1] * n + i];
+                const double d = gb - ga;
+                accH[j] += wi * dnew * d;
+                accB[j] += wi * d * gk;
+                ga = gb;
             }
         }
     }
-    for (int j = 0; j < sl.c; ++j) {
-        const double v = block_sum(acc[j], sh);
-        if (threadIdx.x == 0) partials[(long long)blockIdx.x * (AA_MAXM + 2) + j] = v;
+#pragma unroll
+    for (int j = 0; j < AA_MAXM; ++j) {   // unrolled: the accumulators stay in registers
+        if (j < nd) {
+            const double h = block_sum(accH[j], sh);
+            const double b = block_sum(accB[j], sh);
+            if (threadIdx.x == 0) {
+                partials[(long long)blockIdx.x * (2 * AA_MAXM) + j] = h;
+                partials[(long long)blockIdx.x * (2 * AA_MAXM) + AA_MAXM + j] = b;
+            }
+        }
     }
 }
 
-// Finish the new Gram row, then solve the small least-squares problem
-// gamma = argmin || dG gamma - G_k || through the normal equations in FP64:
-// H = dG^T dG from the Gram matrix of the history gradients, Cholesky
-// H = R^T R; while min R_jj < tol * max R_jj drop the oldest column.
-__global__ void k_aa_solve(double *gram, const double *partials, int nblocks, int M1, int head,
-                           AASlots sl, double tol, double *gamma, int *meta)
+// Finish the new row of H and the right-hand side, then solve the normal
+// equations H gamma = dG^T G_k in FP64 by Cholesky H = R^T R; while
+// min R_jj < tol * max R_jj drop the oldest column and refactor.
+// dgram[(M+1) x (M+1)]: H by the slot naming each difference.
+__global__ void k_aa_solve(double *dgram, const double *partials, int nblocks, int M1, AASlots sl, double tol,
+                           double *gamma, int *meta)
 {
-    __shared__ double row[AA_MAXM + 1];
-    const int c = sl.c;
-    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+    __shared__ double hrow[AA_MAXM], rhs[AA_MAXM];
+    const int Mk = sl.c - 1;
+    for (int j = threadIdx.x; j < 2 * Mk; j += blockDim.x) {
+        const int col = j < Mk ? j : AA_MAXM + (j - Mk);
         double acc = 0.0;
-        for (int b = 0; b < nblocks; ++b) acc += partials[(long long)b * (AA_MAXM + 2) + j];
-        row[j] = acc;
+        for (int b = 0; b < nblocks; ++b) acc += partials[(long long)b * (2 * AA_MAXM) + col];
+        if (j < Mk) hrow[j] = acc;
+        else rhs[j - Mk] = acc;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    for (int j = 0; j < c; ++j) {
-        gram[head * M1 + sl.slot[j]] = row[j];
-        gram[sl.slot[j] * M1 + head] = row[j];
+    auto key = [&](int j) { return sl.slot[j + 1]; };   // slot naming difference j
+    for (int j = 0; j < Mk; ++j) {
+        dgram[key(Mk - 1) * M1 + key(j)] = hrow[j];
+        dgram[key(j) * M1 + key(Mk - 1)] = hrow[j];
     }
-    const int Mk = c - 1;
     double H[AA_MAXM][AA_MAXM], R[AA_MAXM][AA_MAXM], b[AA_MAXM], y[AA_MAXM];
-    auto G = [&](int a, int bb) { return gram[sl.slot[a] * M1 + sl.slot[bb]]; };
     for (int a = 0; a < Mk; ++a) {
-        for (int q = 0; q < Mk; ++q)
-            H[a][q] = G(a + 1, q + 1) - G(a + 1, q) - G(a, q + 1) + G(a, q);
-        b[a] = G(a + 1, Mk) - G(a, Mk);
+        for (int q = 0; q < Mk; ++q) H[a][q] = dgram[key(a) * M1 + key(q)];
+        b[a] = rhs[a];
     }
     int first = 0;
     for (; first < Mk; ++first) {
@@ -256,33 +282,36 @@ __global__ void k_aa_solve(double *gram, const double *partials, int nblocks, in
 
 // p_bar = p_k - eta G_k;  p_tilde = Gb_k - sum_a gamma_a (Gb_{a+1} - Gb_a),
 // Gb_i = p_i - beta eta G_i (the damped update of Alg. 1 eq. AAupdate0 in the
-// gamma form; beta = 1: Alg. 2 step 3), over the columns kept by the solve.
+// gamma form; beta = 1: Alg. 2 step 3), over the columns kept by the solve;
+// per element in FP64 from the FP32 ring, rounded once.
 __global__ void __launch_bounds__(RT) k_aa_mix(const float *ring_p, const float *ring_g, long long n,
-                                               AASlots sl, float eta, float beta_eta, const double *gamma,
+                                               AASlots sl, double eta, double beta_eta, const double *gamma,
                                                const int *meta, float *p_tilde, float *p_bar)
 {
-    __shared__ float gsh[AA_MAXM];
+    __shared__ double gsh[AA_MAXM];
     __shared__ int first_sh, mk_sh;
     if (threadIdx.x == 0) {
         mk_sh = meta[0];
         first_sh = meta[1];
     }
-    if (threadIdx.x < AA_MAXM) gsh[threadIdx.x] = threadIdx.x < meta[0] ? (float)gamma[threadIdx.x] : 0.f;
+    if (threadIdx.x < AA_MAXM) gsh[threadIdx.x] = threadIdx.x < meta[0] ? gamma[threadIdx.x] : 0.0;
     __syncthreads();
     const int first = first_sh, mk = mk_sh;
     const int newest = sl.slot[sl.c - 1];
+    auto gb = [&](int s, long long i) {
+        return (double)ring_p[(long long)s * n + i] - beta_eta * (double)ring_g[(long long)s * n + i];
+    };
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
-        const float pb = ring_p[(long long)newest * n + i] - eta * ring_g[(long long)newest * n + i];
-        float pt = ring_p[(long long)newest * n + i] - beta_eta * ring_g[(long long)newest * n + i];
-        float prev = ring_p[(long long)sl.slot[first] * n + i] - beta_eta * ring_g[(long long)sl.slot[first] * n + i];
+        const double pb = (double)ring_p[(long long)newest * n + i] - eta * (double)ring_g[(long long)newest * n + i];
+        double pt = gb(newest, i);
+        double prev = gb(sl.slot[first], i);
         for (int a = 0; a < mk; ++a) {
-            const int sn = sl.slot[first + a + 1];
-            const float cur = ring_p[(long long)sn * n + i] - beta_eta * ring_g[(long long)sn * n + i];
+            const double cur = gb(sl.slot[first + a + 1], i);
             pt -= gsh[a] * (cur - prev);
             prev = cur;
         }
-        p_bar[i] = pb;
-        p_tilde[i] = pt;
+        p_bar[i] = (float)pb;
+        p_tilde[i] = (float)pt;
     }
 }
 
@@ -297,9 +326,9 @@ void launch_aa_step(AAState &s, const float *p_k, const float *g_k, float *p_til
     for (int t = 0; t < sl.c; ++t) sl.slot[t] = ((s.head - (sl.c - 1) + t) % M1 + M1) % M1;
     count_launch(3);
     k_aa_append<<<RED_BLOCKS, RT, 0, st>>>(p_k, g_k, s.ring_p, s.ring_g, s.n, s.head, sl, s.weights, s.partials);
-    k_aa_solve<<<1, 32, 0, st>>>(s.gram, s.partials, RED_BLOCKS, M1, s.head, sl, 1e-6, s.gamma, s.meta);
-    k_aa_mix<<<RED_BLOCKS, RT, 0, st>>>(s.ring_p, s.ring_g, s.n, sl, (float)s.eta, (float)(s.beta * s.eta),
-                                        s.gamma, s.meta, p_tilde, p_bar);
+    k_aa_solve<<<1, 64, 0, st>>>(s.gram, s.partials, RED_BLOCKS, M1, sl, 1e-6, s.gamma, s.meta);
+    k_aa_mix<<<RED_BLOCKS, RT, 0, st>>>(s.ring_p, s.ring_g, s.n, sl, s.eta, s.beta * s.eta, s.gamma, s.meta,
+                                        p_tilde, p_bar);
 }
 
 // p_next = clip(lam p_tilde + (1 - lam) p_bar); partial <G_k, p_next - p_k>.

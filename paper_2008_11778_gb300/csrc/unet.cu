@@ -378,6 +378,7 @@ struct aafwi_unet {
     float *gacc = nullptr, *gacc2 = nullptr;   // FP32 activation-gradient accumulators
     bf16 *gb1 = nullptr, *gb2 = nullptr;       // BF16 activation gradients
     double *lpart = nullptr, *loss = nullptr;
+    bool retired = false;   // a tensor-core wait ran out: every later call is refused
     std::string msg;
 };
 
@@ -388,6 +389,24 @@ int uerr(aafwi_unet *u, int code, const std::string &m)
     if (u) u->msg = m;
     set_call_error(m);
     return code;
+}
+
+// After a bounded tensor-core wait ran out, MMAs of the abandoned CTA may
+// still have been in flight when it freed its tensor memory: the network is
+// retired and refuses every later call.
+constexpr const char *kUnetRetired =
+    "a tensor-core wait ran out; the network is retired and refuses every later call: destroy it and "
+    "reset the device context (cudaDeviceReset) before continuing";
+
+int retire(aafwi_unet *u)
+{
+    u->retired = true;
+    return uerr(u, AAFWI_ERR_TIMEOUT, kUnetRetired);
+}
+
+int refuse_retired(aafwi_unet *u)
+{
+    return u && u->retired ? uerr(u, AAFWI_ERR_TIMEOUT, kUnetRetired) : AAFWI_OK;
 }
 
 template <class T>
@@ -634,6 +653,7 @@ long long aafwi_unet_param_count(const aafwi_unet *u) { return u ? u->nparam : 0
 
 int aafwi_unet_set_params(aafwi_unet *u, const float *host, long long n)
 {
+    if (int rc0 = refuse_retired(u)) return rc0;
     if (!u || !host || n != u->nparam) return uerr(u, AAFWI_ERR_ARG, "unet_set_params: size mismatch");
     cudaError_t e = cudaMemcpy(u->P, host, n * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
@@ -650,6 +670,7 @@ int aafwi_unet_set_params(aafwi_unet *u, const float *host, long long n)
 
 int aafwi_unet_get_params(aafwi_unet *u, float *host, long long n)
 {
+    if (int rc0 = refuse_retired(u)) return rc0;
     if (!u || !host || n != u->nparam) return uerr(u, AAFWI_ERR_ARG, "unet_get_params: size mismatch");
     cudaError_t e = cudaMemcpy(host, u->P, n * sizeof(float), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return uerr(u, AAFWI_ERR_CUDA, std::string("unet_get_params: ") + cudaGetErrorString(e));
@@ -658,6 +679,7 @@ int aafwi_unet_get_params(aafwi_unet *u, float *host, long long n)
 
 int aafwi_unet_forward(aafwi_unet *u, const float *x, int B, float *y, aafwi_stream stream)
 {
+    if (int rc0 = refuse_retired(u)) return rc0;
     if (!u || !x || !y || B < 1 || B > u->Bmax) return uerr(u, AAFWI_ERR_ARG, "unet_forward: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
     forward(u, x, B, st);
@@ -670,6 +692,7 @@ int aafwi_unet_forward(aafwi_unet *u, const float *x, int B, float *y, aafwi_str
 int aafwi_unet_loss_grad(aafwi_unet *u, const float *x, const float *target, int B, float *grad,
                          double *loss_host, aafwi_stream stream)
 {
+    if (int rc0 = refuse_retired(u)) return rc0;
     if (!u || !x || !target || B < 1 || B > u->Bmax) return uerr(u, AAFWI_ERR_ARG, "unet_loss_grad: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
     loss_and_grad(u, x, target, B, st);
@@ -679,8 +702,7 @@ int aafwi_unet_loss_grad(aafwi_unet *u, const float *x, const float *target, int
     if (e == cudaSuccess && loss_host) {
         e = cudaMemcpyAsync(loss_host, u->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess && unet_take_error())
-            return uerr(u, AAFWI_ERR_TIMEOUT, "unet_loss_grad: a tensor-core wait ran out");
+        if (e == cudaSuccess && unet_take_error()) return retire(u);
     }
     if (e != cudaSuccess) return uerr(u, AAFWI_ERR_CUDA, std::string("unet_loss_grad: ") + cudaGetErrorString(e));
     return AAFWI_OK;
@@ -716,6 +738,7 @@ int aafwi_learned_apply(const float *m, const float *delta, int nz, int nx, int 
 int aafwi_unet_train_step(aafwi_unet *u, const float *x, const float *target, int B, float lr,
                           double *loss_host, aafwi_stream stream)
 {
+    if (int rc0 = refuse_retired(u)) return rc0;
     int rc = aafwi_unet_loss_grad(u, x, target, B, nullptr, nullptr, stream);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
@@ -728,8 +751,7 @@ int aafwi_unet_train_step(aafwi_unet *u, const float *x, const float *target, in
     if (e == cudaSuccess && loss_host) {
         e = cudaMemcpyAsync(loss_host, u->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess && unet_take_error())
-            return uerr(u, AAFWI_ERR_TIMEOUT, "unet_train_step: a tensor-core wait ran out");
+        if (e == cudaSuccess && unet_take_error()) return retire(u);
     }
     if (e != cudaSuccess) return uerr(u, AAFWI_ERR_CUDA, std::string("unet_train_step: ") + cudaGetErrorString(e));
     return AAFWI_OK;

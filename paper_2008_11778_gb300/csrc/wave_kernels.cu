@@ -142,7 +142,9 @@ __device__ __forceinline__ bool stage_wait(unsigned long long *bar, int *err)
                      " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(b), "r"(TMA_SUSPEND_NS) : "memory");
         ok = done != 0;
     }
-    if (!ok) atomicOr(err, 4);
+    // bit 8: a tile copy may still be in flight into this CTA's shared memory
+    // after the CTA returns, so the host retires the plan (sticky)
+    if (!ok) atomicOr(err, 8);
     return __syncthreads_and(ok) != 0;   // the whole CTA takes the same branch
 }
 

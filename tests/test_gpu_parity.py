@@ -312,6 +312,44 @@ def test_aa_step_matches_oracle(gpu):
     assert dot == pytest.approx(float(gs[-1] @ (host(nxt) - ps[-1])), rel=1e-6)
 
 
+def test_aa_step_nearly_equal_gradients(gpu):
+    """Late-iteration regime (Alg. 2 step 2, eqs. Ak, solveGamma): gradients
+    that differ by ~1e-6 of their norm while the window slides over the ring.
+    The least squares is accumulated from the differences G_{i+1} - G_i
+    themselves (exact in FP64 from the FP32 ring), so gamma and the AA point
+    match the oracle's Householder solution on the same FP32 inputs; sums of
+    Gram entries of the G_i would cancel about 12 digits here."""
+    from oracle import aa as oaa
+    from paper_2008_11778_gb300 import aafwi
+    rng = np.random.default_rng(21)
+    n, M, eta = 200_003, 5, 0.01
+    g_base = rng.standard_normal(n)
+    p_base = rng.standard_normal(n)
+    st = aafwi.AA(n, M, eta)
+    pt, pb = gpu.empty(n, device="cuda"), gpu.empty(n, device="cuda")
+    ps, gs = [], []
+    g_cur, p_cur = g_base.copy(), p_base.copy()
+    worst_g, worst_p = 0.0, 0.0
+    for k in range(9):
+        g_cur = g_cur + 1e-6 * rng.standard_normal(n)
+        p_cur = p_cur + 1e-6 * rng.standard_normal(n)
+        g32, p32 = g_cur.astype(np.float32), p_cur.astype(np.float32)
+        ps.append(p32.astype(np.float64))
+        gs.append(g32.astype(np.float64))
+        gam, Mk = st.step(dev(gpu, p32), dev(gpu, g32), pt, pb, want_gamma=True)
+        ref_bar, ref_tilde, ref_gam, ref_Mk = oaa.anderson_point(ps[-(M + 1):], gs[-(M + 1):], eta)
+        assert Mk == ref_Mk == min(M, k)
+        if Mk:
+            d = np.diff(np.stack(gs[-(Mk + 1):]), axis=0)
+            assert np.linalg.norm(d) / np.linalg.norm(gs[-1]) < 5e-6   # the regime under test
+            worst_g = max(worst_g, float(np.abs(gam - ref_gam).max() / np.abs(ref_gam).max()))
+        worst_p = max(worst_p, rel(host(pt), ref_tilde))
+        assert rel(host(pb), ref_bar) < 1e-7
+    assert worst_g < 1e-8
+    assert worst_p < 1e-6
+    st.close()
+
+
 @pytest.fixture(scope="module")
 def tiny_history(gpu, orc):
     from paper_2008_11778_gb300 import solve

@@ -213,3 +213,31 @@ def test_weighted_aa_quadratic_history_matches_oracle(gpu):
     Jstar = -0.5 * b @ np.linalg.solve(A, b)
     assert rel(np.array(out["J"]) - Jstar, np.array(ref["J"]) - Jstar) < HIST_TOL
     assert rel(host(out["p"]), ref["p"][-1]) < 1e-4
+
+
+def test_noisy_data_aa_fwi_history_matches_oracle(gpu, orc):
+    """The noisy-data experiment (Sec. 4.2): observed data with mean-zero
+    uniform noise at SNR 0.55 dB, Alg. 2 with AA(5) for 10 iterations on the
+    GPU against the oracle's run on the same noisy data (misfit history and
+    line-search decisions at the 1e-3 target)."""
+    from oracle import aa as oaa
+    from paper_2008_11778_gb300 import aafwi, solve
+    p = synth.small_problem(nz=48, nx=120, nb=12, nt=300, S=3)
+    g = p.geom
+    clean = orc.forward(g, p.m_true)
+    noise = synth.uniform_noise(clean, 0.55, seed=4 * 1000 + 2008)
+    snr = 10.0 * np.log10(np.mean(clean ** 2) / np.mean(noise ** 2))
+    assert abs(snr - 0.55) < 0.05 and abs(noise.mean()) < 0.05 * noise.std()
+    d_obs = (clean + noise).astype(np.float32)
+    lo, hi = p.m_bounds
+    plan = aafwi.Plan(g, p.c_bounds[1])
+    out = solve.aa_fwi(plan, dev(gpu, d_obs), dev(gpu, p.m_start), M=5, iters=10, eta_factor=1e-3,
+                       bounds=(lo, hi))
+    ref = oaa.aa_gd(lambda m: orc.fwi_gradient(g, m.astype(np.float32), d_obs),
+                    p.m_start.astype(np.float32).astype(np.float64), M=5, eta=out["eta"], iters=10,
+                    bounds=(lo, hi),
+                    misfit_fn=lambda m: 0.5 * float(np.sum((orc.forward(g, m.astype(np.float32)) - d_obs) ** 2)))
+    assert out["lam"] == ref["lam"]
+    assert rel(out["J"], ref["J"]) < HIST_TOL
+    assert ref["J"][-1] < ref["J"][0]
+    plan.close()

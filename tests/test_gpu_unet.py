@@ -80,3 +80,61 @@ def test_unet_training_reduces_loss(A):
         L = net.train_step(xd, td, 2e-3)
     assert L < 0.3 * L0
     assert np.isfinite(net.get_params()).all()
+
+
+@pytest.fixture(scope="module")
+def production_case():
+    """The production network (C = 32) on a batch of the training shape
+    (2 x 96 x 256): split-K weight gradients and 16-byte channel gathers run
+    as in training.  Reference: the oracle in its BF16-rounding mode and in
+    FP64."""
+    from oracle import unet as U
+    C = 32
+    rng = np.random.default_rng(17)
+    p = U.init_params(C, 17)
+    x = rng.standard_normal((2, 2, 96, 256)).astype(np.float32)
+    t = (0.1 * rng.standard_normal((2, 96, 256))).astype(np.float32)
+    return C, p, x, t, U.loss_grad(p, x, t, C), U.loss_grad(p, x, t, C, exact=True)
+
+
+def test_unet_production_shape_forward(A, production_case):
+    """Forward of the C = 32 network on a 2 x 96 x 256 batch: the runtime sits
+    within a quarter of the BF16 quantisation error (the BF16 reference
+    against FP64) of the BF16 reference."""
+    import torch
+    from oracle import unet as U
+    C, p, x, _, _, _ = production_case
+    net = A.UNet(2, 96, 256, C)
+    net.set_params(p)
+    y = net.forward(torch.as_tensor(x, device="cuda")).cpu().numpy()
+    ref, exact = U.forward(p, x, C), U.forward(p, x, C, exact=True)
+    q = rel(ref, exact)                  # what BF16 activations cost
+    assert rel(y, ref) < 0.25 * q
+    net.close()
+
+
+def test_unet_production_shape_gradient_per_layer(A, production_case):
+    """Loss gradient of the C = 32 network on a 2 x 96 x 256 batch, layer by
+    layer: each weight and bias slice of the runtime lies within half of that
+    slice's BF16 quantisation error (BF16 reference against FP64) of the BF16
+    reference (the runtime accumulates in FP32 where the reference uses FP64,
+    so a BF16 rounding or a ReLU mask can flip where a value sits on the
+    boundary)."""
+    import torch
+    from oracle import unet as U
+    C, p, x, t, (Lr, gr), (Le, ge) = production_case
+    net = A.UNet(2, 96, 256, C)
+    net.set_params(p)
+    g = torch.empty(net.nparam, device="cuda")
+    L = net.loss_grad(torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda"), g)
+    g = g.cpu().numpy()
+    assert abs(L - Lr) <= 0.25 * abs(Lr - Le) + 1e-6 * abs(Lr)
+    o = 0
+    for kind, ci, co in U.layers(C):
+        nw = (9 if kind == "c3" else 4) * ci * co
+        for a, b in ((o, o + nw), (o + nw, o + nw + co)):
+            q = rel(gr[a:b], ge[a:b])
+            assert rel(g[a:b], gr[a:b]) < 0.5 * q, (kind, ci, co, a == o, rel(g[a:b], gr[a:b]), q)
+        o += nw + co
+    assert rel(g[o:], gr[o:]) < 0.5 * rel(gr[o:], ge[o:])      # the 1x1 head
+    net.close()
