@@ -247,6 +247,44 @@ int aafwi_aa_set_eta(aafwi_aa *aa, double eta);
  * beta is outside [0, 1]. */
 int aafwi_aa_set_beta(aafwi_aa *aa, double beta);
 
+/* Norm of the optimisation step (Sec. 2.1: eq. AAopt may use the l1, l2 or
+ * l-infinity norm; the first and the last need linear programming).
+ * AAFWI_NORM_L2 (default) is the least squares of Alg. 2 step 2.  With
+ * AAFWI_NORM_L1 / AAFWI_NORM_LINF, aa_step takes the columns the l2 rank
+ * safeguard keeps and solves gamma = argmin || W (dG gamma - G_k) ||_1 or _inf
+ * (W the diagonal of aa_set_weights, identity without): the n rows stay on
+ * the GPU, each round is one pass over the ring, and the host solves a linear
+ * programme in the Mk+1 unknowns -- l-infinity by an exact working-set method
+ * (rows above the current level are added until none is left), l1 by cutting
+ * planes on sum |r_i| until the best value and the lower bound agree to a
+ * relative gap of 1e-9.  Both are bounded by a box of 1e3 x max(1, |gamma_l2|)
+ * around zero; a solution on that box returns AAFWI_ERR_STATE.  These steps
+ * synchronise the stream.  May be changed between steps.  Errors: ARG, NOMEM
+ * (first switch to l1 / l-infinity allocates the round buffers). */
+#define AAFWI_NORM_L2   0
+#define AAFWI_NORM_L1   1
+#define AAFWI_NORM_LINF 2
+int aafwi_aa_set_norm(aafwi_aa *aa, int norm);
+
+/* Statistics of the last l1 / l-infinity step: the optimal value found
+ * (sum or max of |W (dG gamma - G_k)|), the LP lower bound, rounds (passes
+ * over the ring) and LP rows (cuts for l1, working-set rows for l-infinity). */
+typedef struct {
+    double objective;
+    double lower_bound;
+    int rounds;
+    int rows;
+} aafwi_aa_lp_info;
+int aafwi_aa_get_lp_info(const aafwi_aa *aa, aafwi_aa_lp_info *info);
+
+/* The host LP solver of the l1 / l-infinity steps, exposed for testing:
+ * x = argmin c^T x subject to A x <= b, x free; A row-major [m][nv]
+ * (1 <= nv <= 64), b [m], c [nv]; x [nv] and *obj (may be NULL) receive the
+ * optimum.  Revised simplex on the dual with Bland's rule.  Host memory
+ * only; no device call.  Errors: ARG, STATE (unbounded, infeasible or an
+ * iteration limit; aafwi_last_error(NULL) says which). */
+int aafwi_lp_min(int nv, int m, const double *A, const double *b, const double *c, double *x, double *obj);
+
 /* Weighted l2 norm for the AA least-squares problem (Sec. 2.1): gamma =
  * argmin sum_i w_i ((dG gamma - G_k)_i)^2 with the device FP32 weights w [n]
  * (w_i >= 0; copied, the caller keeps its buffer); NULL restores the plain l2

@@ -10,6 +10,8 @@ Contents, each following the paper's statement in its own order:
                    Householder QR of the explicit n x M_k matrix (the oracle
                    refactors every iteration; a rank-updated QR as in
                    Sec. 2.1 gives the same factors up to rounding).
+  aa_gamma_lp      eq. AAopt with the l1 or l-infinity norm (Sec. 2.1: linear
+                   programming), the LP written out on the explicit matrix.
   aa_gd            Alg. 2: l2-AA on the steepest-descent map G(p) = p - eta*grad J(p)
                    (eq. GD) with the backtracking line search between the AA
                    point p~ and the plain point p-bar.
@@ -34,6 +36,8 @@ Readings of points the paper leaves open (shared with the GPU drivers):
     [lo, hi] (physical velocity bounds mapped to m = 1/c^2), identically in
     every trial; the Armijo test is applied to the clipped point.
   * Alg. 2 input step p_1 = G(p_0) is taken without a line search.
+  * l1 / l-infinity AA: the columns are those the l2 rank safeguard keeps, and
+    the weights multiply |residual| (the l2 weights multiply its square).
   * L-BFGS (the paper gives eqs. secant / lbfgs_update, not an algorithm):
     the textbook two-loop recursion with initial matrix gamma_k I,
     gamma_k = <s, y> / <y, y> of the newest pair; a pair enters the memory
@@ -115,7 +119,43 @@ def aa_gamma(A, f, rank_tol=RANK_TOL):
     return np.zeros(0), first
 
 
-def anderson_point(P, Gr, eta, rank_tol=RANK_TOL, beta=1.0, weights=None):
+def aa_gamma_lp(A, f, norm, weights=None):
+    """gamma = argmin ||W (A gamma - f)||_p for p = 1 ("l1") or infinity
+    ("linf"), W = diag(weights) (identity if None): Sec. 2.1 notes that these
+    norms in eq. AAopt need linear programming.  The LP is written out on the
+    explicit matrix and solved by scipy's HiGHS (the definition, no
+    reformulation):
+      linf:  min t        s.t.  -t <= w_i (A_i gamma - f_i) <= t
+      l1:    min sum e_i  s.t.  -e_i <= w_i (A_i gamma - f_i) <= e_i
+    Returns (gamma, optimal value)."""
+    from scipy.optimize import linprog
+    from scipy.sparse import csr_matrix, hstack, identity, vstack
+    A = np.asarray(A, dtype=np.float64)
+    f = np.asarray(f, dtype=np.float64)
+    n, M = A.shape
+    w = np.ones(n) if weights is None else np.asarray(weights, dtype=np.float64)
+    Aw, fw = A * w[:, None], f * w
+    if norm == "linf":
+        one = np.ones((n, 1))
+        A_ub = np.block([[Aw, -one], [-Aw, -one]])
+        c = np.r_[np.zeros(M), 1.0]
+        bounds = [(None, None)] * M + [(0.0, None)]
+    elif norm == "l1":
+        I = identity(n, format="csr")
+        A_ub = vstack([hstack([csr_matrix(Aw), -I]), hstack([csr_matrix(-Aw), -I])]).tocsr()
+        c = np.r_[np.zeros(M), np.ones(n)]
+        bounds = [(None, None)] * M + [(0.0, None)] * n
+    else:
+        raise ValueError(norm)
+    res = linprog(c, A_ub=A_ub, b_ub=np.r_[fw, -fw], bounds=bounds, method="highs",
+                  options={"primal_feasibility_tolerance": 1e-10, "dual_feasibility_tolerance": 1e-10})
+    assert res.status == 0, res.message
+    gamma = res.x[:M]
+    r = np.abs(w * (A @ gamma - f))
+    return gamma, float(r.max() if norm == "linf" else r.sum())
+
+
+def anderson_point(P, Gr, eta, rank_tol=RANK_TOL, beta=1.0, weights=None, norm="l2"):
     """Alg. 2 steps 1-3 for the history P = [p_{k-Mk}..p_k], Gr = [G_{k-Mk}..G_k].
 
     With a damping beta != 1 the AA point is Alg. 1's eq. AAupdate0,
@@ -127,7 +167,8 @@ def anderson_point(P, Gr, eta, rank_tol=RANK_TOL, beta=1.0, weights=None):
     Returns (p_bar, p_tilde, gamma, Mk_used).
       p_bar   = G(p_k) = p_k - eta G_k                         (step 1, eq. GD)
       gamma   = argmin || [G_{i+1} - G_i] gamma - G_k ||        (step 2; the -eta of
-                 f_k = -eta G_k and A_k = -eta [dG] cancels)
+                 f_k = -eta G_k and A_k = -eta [dG] cancels; the l2 norm
+                 unless norm is "l1" or "linf", see aa_gamma_lp)
       p_tilde = G(p_k) - sum_i gamma_i [G(p_{i+1}) - G(p_i)]   (step 3, eq. AA2_update)
     """
     shape = np.shape(P[-1])
@@ -144,6 +185,9 @@ def anderson_point(P, Gr, eta, rank_tol=RANK_TOL, beta=1.0, weights=None):
     else:
         sw = np.sqrt(np.asarray(weights, dtype=np.float64).ravel())
         gamma, first = aa_gamma(dG * sw[:, None], gk * sw, rank_tol)
+    if norm != "l2" and len(gamma):
+        # l1 / l-infinity (Sec. 2.1) over the columns the l2 rank safeguard keeps
+        gamma, _ = aa_gamma_lp(dG[:, first:], gk, norm, weights)
     if beta != 1.0:
         Pk, Gk = P[first:], Gr[first:]
         alpha = gamma_to_alpha(gamma)
@@ -159,7 +203,8 @@ def anderson_point(P, Gr, eta, rank_tol=RANK_TOL, beta=1.0, weights=None):
 
 
 def aa_gd(grad_fn, p0, M, eta, iters, line_search=True, bounds=None,
-          lambdas=LAMBDAS, c1=ARMIJO_C1, rank_tol=RANK_TOL, misfit_fn=None, beta=1.0, weights=None):
+          lambdas=LAMBDAS, c1=ARMIJO_C1, rank_tol=RANK_TOL, misfit_fn=None, beta=1.0, weights=None,
+          norm="l2"):
     """Alg. 2: l2-based AA for gradient descent.
 
     grad_fn(p) -> (J, grad); misfit_fn(p) -> J (defaults to grad_fn(p)[0]).
@@ -180,7 +225,7 @@ def aa_gd(grad_fn, p0, M, eta, iters, line_search=True, bounds=None,
             p_next = clip(p - eta * g)       # Alg. 2 input: p_1 = G(p_0)
             lam, Mk, gamma = 0.0, 0, np.zeros(0)
         else:
-            p_bar, p_tilde, gamma, Mk = anderson_point(P, Gr, eta, rank_tol, beta, weights)
+            p_bar, p_tilde, gamma, Mk = anderson_point(P, Gr, eta, rank_tol, beta, weights, norm)
             lam = 0.0
             if line_search and Mk > 0:
                 for trial in lambdas:

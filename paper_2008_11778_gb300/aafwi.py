@@ -31,7 +31,10 @@ EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aa
            "aafwi_launch_count", "aafwi_misfit_noalloc", "aafwi_unet_create", "aafwi_unet_destroy",
            "aafwi_unet_param_count", "aafwi_unet_set_params", "aafwi_unet_get_params", "aafwi_unet_forward",
            "aafwi_unet_loss_grad", "aafwi_unet_train_step", "aafwi_learned_features", "aafwi_learned_apply",
-           "aafwi_autotune", "aafwi_dot", "aafwi_axpby")
+           "aafwi_autotune", "aafwi_dot", "aafwi_axpby", "aafwi_aa_set_norm", "aafwi_aa_get_lp_info",
+           "aafwi_lp_min")
+
+NORM_L2, NORM_L1, NORM_LINF = 0, 1, 2
 
 
 class AafwiError(RuntimeError):
@@ -126,6 +129,9 @@ def load(path=LIB_PATH):
         "aafwi_autotune": ([P, P, P, P, I, I, P, P, I, P, P], I),
         "aafwi_dot": ([P, P, Z, P, P], I),
         "aafwi_axpby": ([D, P, D, P, Z, P], I),
+        "aafwi_aa_set_norm": ([P, I], I),
+        "aafwi_aa_get_lp_info": ([P, P], I),
+        "aafwi_lp_min": ([I, I, P, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -404,6 +410,16 @@ class AA:
         """Damping of the AA point (Alg. 1 eq. AAupdate0); 1 = Alg. 2."""
         _check(load().aafwi_aa_set_beta(self.h, float(beta)))
 
+    def set_norm(self, norm):
+        """Norm of the optimisation step (Sec. 2.1): NORM_L2, NORM_L1 or NORM_LINF."""
+        _check(load().aafwi_aa_set_norm(self.h, int(norm)))
+
+    def lp_info(self):
+        """Statistics of the last l1 / l-infinity step (aafwi_aa_lp_info as a dict)."""
+        info = AALpInfo()
+        _check(load().aafwi_aa_get_lp_info(self.h, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in AALpInfo._fields_}
+
     def step(self, p_k, grad_k, p_tilde, p_bar, want_gamma=False, stream=None):
         gam = (ctypes.c_double * max(self.M, 1))()
         Mk = ctypes.c_int()
@@ -420,6 +436,25 @@ class AA:
                                        float(lo), float(hi), ctypes.byref(dot) if want_dot else None,
                                        _stream(stream)))
         return dot.value if want_dot else None
+
+
+class AALpInfo(ctypes.Structure):
+    _fields_ = [("objective", ctypes.c_double), ("lower_bound", ctypes.c_double),
+                ("rounds", ctypes.c_int), ("rows", ctypes.c_int)]
+
+
+def lp_min(A, b, c):
+    """aafwi_lp_min (host only): argmin c^T x s.t. A x <= b; returns (x, c^T x)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    m, nv = A.shape
+    x = np.empty(nv)
+    obj = ctypes.c_double()
+    _check(load().aafwi_lp_min(nv, m, A.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p),
+                               c.ctypes.data_as(ctypes.c_void_p), x.ctypes.data_as(ctypes.c_void_p),
+                               ctypes.byref(obj)))
+    return x, obj.value
 
 
 MISFIT_NOALLOC_MAX_SAMPLES = 1 << 32

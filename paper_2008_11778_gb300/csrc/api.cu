@@ -1106,6 +1106,7 @@ int aafwi_aa_create(size_t n, int M, double eta, aafwi_aa **out)
     s.M = M;
     s.eta = eta;
     s.beta = 1.0;
+    s.norm = AAFWI_NORM_L2;
     const int M1 = M + 1;
     bool ok = dalloc(a->bufs, &s.ring_p, (size_t)M1 * n) && dalloc(a->bufs, &s.ring_g, (size_t)M1 * n) &&
               dalloc(a->bufs, &s.gram, (size_t)M1 * M1) &&
@@ -1163,24 +1164,72 @@ int aafwi_aa_set_beta(aafwi_aa *a, double beta)
     return AAFWI_OK;
 }
 
+int aafwi_aa_set_norm(aafwi_aa *a, int norm)
+{
+    if (!a || (norm != AAFWI_NORM_L2 && norm != AAFWI_NORM_L1 && norm != AAFWI_NORM_LINF))
+        return fail(nullptr, AAFWI_ERR_ARG, "aa_set_norm: unknown norm");
+    AAState &s = a->s;
+    if (norm != AAFWI_NORM_L2 && !s.lp_rows) {
+        const bool ok = dalloc(a->bufs, &s.lp_rows, AA_LP_ROWS) && dalloc(a->bufs, &s.lp_cnt, 1) &&
+                        dalloc(a->bufs, &s.lp_part, (size_t)RED_BLOCKS * (AA_MAXM + 1)) &&
+                        dalloc(a->bufs, &s.lp_gat, (size_t)AA_LP_ROWS * (AA_MAXM + 2));
+        if (!ok) return fail(nullptr, AAFWI_ERR_NOMEM, "cudaMalloc failed for the l1 / l-infinity buffers");
+    }
+    s.norm = norm;
+    return AAFWI_OK;
+}
+
+int aafwi_aa_get_lp_info(const aafwi_aa *a, aafwi_aa_lp_info *info)
+{
+    if (!a || !info) return AAFWI_ERR_ARG;
+    info->objective = a->s.lp.objective;
+    info->lower_bound = a->s.lp.lower_bound;
+    info->rounds = a->s.lp.rounds;
+    info->rows = a->s.lp.rows;
+    return AAFWI_OK;
+}
+
 int aafwi_aa_step(aafwi_aa *a, const float *p_k, const float *grad_k, float *p_tilde, float *p_bar,
                   double *gamma_host, int *Mk_host, aafwi_stream stream)
 {
     if (!a || !p_k || !grad_k || !p_tilde || !p_bar) return fail(nullptr, AAFWI_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
-    launch_aa_step(a->s, p_k, grad_k, p_tilde, p_bar, st);
+    AAState &s = a->s;
+    launch_aa_step(s, p_k, grad_k, st);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "aa_step launch");
+    if (s.norm != AAFWI_NORM_L2 && s.count > 1) {
+        // l1 / l-infinity: the LP rounds start from the l2 solution over the
+        // columns its rank safeguard keeps
+        int meta[2] = {0, 0};
+        double gl2[AA_MAXM], glp[AA_MAXM];
+        e = cudaMemcpyAsync(meta, s.meta, sizeof meta, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(gl2, s.gamma, sizeof gl2, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "aa_step readback");
+        if (meta[0] > 0) {
+            std::string msg;
+            const int rc = aa_lp_gamma(s, s.slots + meta[1], meta[0], s.norm, gl2, glp, &s.lp, &msg, st);
+            if (rc) return fail(nullptr, rc, rc == AAFWI_ERR_CUDA ? std::string("aa_step: l1 / l-infinity pass failed")
+                                                                : msg);
+            e = cudaMemcpyAsync(s.gamma, glp, meta[0] * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // glp lives on this stack frame
+            if (e != cudaSuccess) return cuda_fail(nullptr, e, "aa_step gamma upload");
+        }
+    }
+    launch_aa_mix(s, p_tilde, p_bar, st);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "aa_step launch");
     if (gamma_host || Mk_host) {
         int meta[2] = {0, 0};
         double gam[AA_MAXM];
-        e = cudaMemcpyAsync(meta, a->s.meta, sizeof meta, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(gam, a->s.gamma, sizeof gam, cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(meta, s.meta, sizeof meta, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(gam, s.gamma, sizeof gam, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "aa_step readback");
         if (Mk_host) *Mk_host = meta[0];
         if (gamma_host)
-            for (int j = 0; j < a->s.M; ++j) gamma_host[j] = j < meta[0] ? gam[j] : 0.0;
+            for (int j = 0; j < s.M; ++j) gamma_host[j] = j < meta[0] ? gam[j] : 0.0;
     }
     return AAFWI_OK;
 }

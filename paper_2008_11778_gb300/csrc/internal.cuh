@@ -223,6 +223,13 @@ void launch_axpby(float a, const float *x, float b, float *y, long long n, cudaS
 
 // Anderson acceleration.
 constexpr int AA_MAXM = 20;
+constexpr int AA_LP_ROWS = 4096;        // rows one l-infinity round may add to its working set
+constexpr int AA_LP_MAX_ROUNDS = 3000;  // rounds of the l1 / l-infinity LP before giving up
+constexpr double AA_LP_GAP = 1e-9;      // relative optimality gap at which the LP rounds stop
+struct AALpStats {
+    double objective = 0.0, lower_bound = 0.0;
+    int rounds = 0, rows = 0;
+};
 struct AAState {
     long long n;
     int M;
@@ -236,10 +243,22 @@ struct AAState {
     double beta;                   // damping of the AA point (1: Alg. 2)
     float *weights;                // [n] diagonal weights of a weighted l2 norm, or null
     int count, head;               // entries in the ring, slot of the newest
+    int norm;                      // AAFWI_NORM_L2 / _L1 / _LINF
+    int *lp_rows, *lp_cnt;         // l1 / l-infinity rounds: rows above a level [AA_LP_ROWS], their count
+    double *lp_part, *lp_gat;      // per-block partials [RED_BLOCKS][AA_MAXM+1], gathered rows
+    AALpStats lp;                  // of the last l1 / l-infinity step
+    int slots[AA_MAXM + 1];        // chronological slots of the last step's window
 };
-void launch_aa_step(AAState &s, const float *p_k, const float *g_k, float *p_tilde,
-                    float *p_bar, cudaStream_t st);
+// Alg. 2 steps 1-3: append (p_k, G_k) and solve the l2 least squares for gamma
+// (the rank safeguard decides the kept columns)...
+void launch_aa_step(AAState &s, const float *p_k, const float *g_k, cudaStream_t st);
+// ...then form p_tilde, p_bar from the gamma in s.gamma.
+void launch_aa_mix(AAState &s, float *p_tilde, float *p_bar, cudaStream_t st);
 void launch_aa_combine(AAState &s, float lam, const float *p_tilde, const float *p_bar,
                        float *p_next, float lo, float hi, bool want_dot, cudaStream_t st);
+// l1 / l-infinity gamma over the kept window slots[0..mk] (host rounds over
+// device passes; gamma_in: the l2 solution); AAFWI_OK or an error (msg set).
+int aa_lp_gamma(AAState &s, const int *slots, int mk, int norm, const double *gamma_in, double *gamma,
+                AALpStats *stats, std::string *msg, cudaStream_t st);
 
 }  // namespace aafwi

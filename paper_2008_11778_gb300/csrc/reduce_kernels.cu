@@ -7,37 +7,9 @@
 // partials summed in block order by the second pass), so results do not depend
 // on scheduling.
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace aafwi {
-
-constexpr int RT = 256;  // threads per reduction block
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ double warp_max(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Block-wide sum; result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double *sh)
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    v = threadIdx.x < RT / 32 ? sh[threadIdx.x] : 0.0;
-    if (w == 0) v = warp_sum(v);
-    return v;
-}
 
 __global__ void __launch_bounds__(RT) k_misfit(const float *d, const float *o, float *r, long long n,
                                                double *partials)
@@ -315,8 +287,7 @@ __global__ void __launch_bounds__(RT) k_aa_mix(const float *ring_p, const float 
     }
 }
 
-void launch_aa_step(AAState &s, const float *p_k, const float *g_k, float *p_tilde, float *p_bar,
-                    cudaStream_t st)
+void launch_aa_step(AAState &s, const float *p_k, const float *g_k, cudaStream_t st)
 {
     const int M1 = s.M + 1;
     s.head = s.count == 0 ? 0 : (s.head + 1) % M1;
@@ -324,9 +295,18 @@ void launch_aa_step(AAState &s, const float *p_k, const float *g_k, float *p_til
     AASlots sl;
     sl.c = s.count;
     for (int t = 0; t < sl.c; ++t) sl.slot[t] = ((s.head - (sl.c - 1) + t) % M1 + M1) % M1;
-    count_launch(3);
+    for (int t = 0; t < sl.c; ++t) s.slots[t] = sl.slot[t];
+    count_launch(2);
     k_aa_append<<<RED_BLOCKS, RT, 0, st>>>(p_k, g_k, s.ring_p, s.ring_g, s.n, s.head, sl, s.weights, s.partials);
     k_aa_solve<<<1, 64, 0, st>>>(s.gram, s.partials, RED_BLOCKS, M1, sl, 1e-6, s.gamma, s.meta);
+}
+
+void launch_aa_mix(AAState &s, float *p_tilde, float *p_bar, cudaStream_t st)
+{
+    AASlots sl;
+    sl.c = s.count;
+    for (int t = 0; t < sl.c; ++t) sl.slot[t] = s.slots[t];
+    count_launch();
     k_aa_mix<<<RED_BLOCKS, RT, 0, st>>>(s.ring_p, s.ring_g, s.n, sl, s.eta, s.beta * s.eta, s.gamma, s.meta,
                                         p_tilde, p_bar);
 }

@@ -39,10 +39,11 @@ class AAInversion:
 
     def __init__(self, plan, d_obs, p0, M, eta=None, eta_factor=1e-4, bounds=None,
                  lambdas=LAMBDAS, c1=ARMIJO_C1, mode=aafwi.MODE_FWI, m0=None, line_search=True,
-                 grad_fn=None, misfit_fn=None, beta=1.0, weights=None):
+                 grad_fn=None, misfit_fn=None, beta=1.0, weights=None, norm=aafwi.NORM_L2):
         """grad_fn(x, g_out, reuse) -> J and misfit_fn(x) -> J replace the wave-
         equation objective (plan / d_obs unused then): Alg. 2 applies to any
-        fixed-point map G(p) = p - eta grad J(p)."""
+        fixed-point map G(p) = p - eta grad J(p).  norm: the norm of the
+        optimisation step (Sec. 2.1; aafwi.NORM_L2, NORM_L1 or NORM_LINF)."""
         self.plan, self.d_obs, self.M = plan, d_obs, M
         self.grad_fn, self.misfit_fn = grad_fn, misfit_fn
         self.mode, self.m0 = mode, m0
@@ -67,6 +68,8 @@ class AAInversion:
             self.aa.set_beta(beta)
         if weights is not None:
             self.aa.set_weights(weights.contiguous())
+        if norm != aafwi.NORM_L2:
+            self.aa.set_norm(norm)
         self.k = 0
         self.history = {"J": [self.J], "lam": [], "Mk": []}
 
@@ -124,7 +127,7 @@ class AAInversion:
 
 def aa_fwi(plan, d_obs, p0, M, iters, eta=None, eta_factor=1e-4, bounds=None, lambdas=LAMBDAS,
            c1=ARMIJO_C1, mode=aafwi.MODE_FWI, m0=None, line_search=True, target=None, callback=None,
-           grad_fn=None, misfit_fn=None, beta=1.0, weights=None):
+           grad_fn=None, misfit_fn=None, beta=1.0, weights=None, norm=aafwi.NORM_L2):
     """Run Alg. 2 for ``iters`` iterations (or until J/J_0 <= target).
 
     Returns a dict with J (J[k] = J(p_k)), lam, Mk, eta, the final p and grad
@@ -132,7 +135,7 @@ def aa_fwi(plan, d_obs, p0, M, iters, eta=None, eta_factor=1e-4, bounds=None, la
     """
     t0 = time.perf_counter()
     run = AAInversion(plan, d_obs, p0, M, eta, eta_factor, bounds, lambdas, c1, mode, m0, line_search,
-                      grad_fn, misfit_fn, beta, weights)
+                      grad_fn, misfit_fn, beta, weights, norm)
     ts = [time.perf_counter() - t0]
     for k in range(iters):
         J = run.step()

@@ -76,7 +76,7 @@ def header_struct_fields(name):
 
 @pytest.mark.parametrize("c_name, py_name", [("aafwi_plan_opts", "PlanOpts"), ("aafwi_plan_info", "PlanInfo"),
                                              ("aafwi_grid", "Grid"), ("aafwi_shots", "Shots"),
-                                             ("aafwi_tune_entry", "TuneEntry")])
+                                             ("aafwi_tune_entry", "TuneEntry"), ("aafwi_aa_lp_info", "AALpInfo")])
 def test_binding_structs_match_the_header(c_name, py_name):
     """The ctypes mirrors of the ABI structs list the header's fields in the
     header's order (a field added on one side only would shift the rest)."""

@@ -241,3 +241,83 @@ def test_noisy_data_aa_fwi_history_matches_oracle(gpu, orc):
     assert rel(out["J"], ref["J"]) < HIST_TOL
     assert ref["J"][-1] < ref["J"][0]
     plan.close()
+
+
+@pytest.mark.parametrize("norm, weighted", [("l1", False), ("linf", False), ("l1", True), ("linf", True)],
+                         ids=["l1", "linf", "l1-weighted", "linf-weighted"])
+def test_aa_lp_step_matches_oracle(gpu, norm, weighted):
+    """AA with the l1 / l-infinity norm in the optimisation step (Sec. 2.1):
+    over a sliding window the GPU rounds reach the oracle's LP optimum (the
+    optimal value is unique; gamma need not be), the GPU gamma attains it,
+    and the AA point is formed from that gamma."""
+    from oracle import aa as oaa
+    from paper_2008_11778_gb300 import aafwi
+    rng = np.random.default_rng(31 if norm == "l1" else 32)
+    n, M, eta = 6001, 4, 0.03
+    A = rng.standard_normal((40, n)) / 20.0
+    w = np.exp(rng.uniform(-1.0, 1.0, n)).astype(np.float32) if weighted else None
+    st = aafwi.AA(n, M, eta)
+    st.set_norm(aafwi.NORM_L1 if norm == "l1" else aafwi.NORM_LINF)
+    if weighted:
+        st.set_weights(dev(gpu, w))
+    pt, pb = gpu.empty(n, device="cuda"), gpu.empty(n, device="cuda")
+    x = rng.standard_normal(n).astype(np.float32)
+    ps, gs = [], []
+    w64 = None if w is None else w.astype(np.float64)
+    for k in range(8):
+        gk = (A.T @ (A @ x) + 0.1 * x + 0.05 * rng.laplace(size=n)).astype(np.float32)
+        ps.append(x.astype(np.float64))
+        gs.append(gk.astype(np.float64))
+        gam, Mk = st.step(dev(gpu, x), dev(gpu, gk), pt, pb, want_gamma=True)
+        P, G = ps[-(M + 1):], gs[-(M + 1):]
+        ref_bar, ref_tilde, ref_gam, ref_Mk = oaa.anderson_point(P, G, eta, weights=w64, norm=norm)
+        assert Mk == ref_Mk == min(M, k)
+        if Mk:
+            dG = np.stack([G[i + 1] - G[i] for i in range(len(G) - 1)], axis=1)[:, -Mk:]
+            _, opt = oaa.aa_gamma_lp(dG, G[-1], norm, w64)
+            wt = np.ones(n) if w64 is None else w64
+            r = np.abs(wt * (dG @ gam - G[-1]))
+            val = r.max() if norm == "linf" else r.sum()
+            info = st.lp_info()
+            assert val == pytest.approx(opt, rel=1e-7)                 # gamma attains the optimum
+            assert info["objective"] == pytest.approx(val, rel=1e-9)
+            assert info["lower_bound"] <= info["objective"] * (1 + 1e-9)
+            # the AA point of this gamma (eq. AA2_update), formed in FP64 here
+            tilde = P[-1] - eta * G[-1] - sum(g * ((P[-Mk + i] - eta * G[-Mk + i]) - (P[-Mk - 1 + i] - eta * G[-Mk - 1 + i]))
+                                              for i, g in enumerate(gam))
+            assert rel(host(pt), tilde) < 1e-6
+        assert rel(host(pb), ref_bar) < 1e-6
+        x = (0.5 * ref_tilde + 0.5 * ref_bar + 0.01 * rng.standard_normal(n)).astype(np.float32)
+    st.close()
+
+
+@pytest.mark.parametrize("norm", ["l1", "linf"])
+def test_aa_lp_quadratic_history_matches_oracle(gpu, norm):
+    """Alg. 2 with the l1 / l-infinity AA step on a quadratic: line-search
+    decisions, misfit gap and iterate against the oracle's Alg. 2."""
+    from oracle import aa as oaa
+    from paper_2008_11778_gb300 import aafwi, solve
+    n = 300
+    A, b, At, bt = quadratic(gpu, n, 200.0, 12)
+
+    def grad_fn(x, g_out, reuse):
+        xd = x.double()
+        g_out.copy_((At @ xd - bt).float())
+        return float(0.5 * xd @ (At @ xd) - bt @ xd)
+
+    def misfit_fn(x):
+        xd = x.double()
+        return float(0.5 * xd @ (At @ xd) - bt @ xd)
+
+    out = solve.aa_fwi(None, None, gpu.zeros(n, device="cuda"), M=5, iters=20, eta=1.0 / 200.0,
+                       grad_fn=grad_fn, misfit_fn=misfit_fn,
+                       norm=aafwi.NORM_L1 if norm == "l1" else aafwi.NORM_LINF)
+
+    def ogf(x):
+        x32 = x.astype(np.float32).astype(np.float64)
+        return 0.5 * x32 @ A @ x32 - b @ x32, (A @ x32 - b).astype(np.float32).astype(np.float64)
+    ref = oaa.aa_gd(ogf, np.zeros(n), M=5, eta=1.0 / 200.0, iters=20, misfit_fn=lambda x: ogf(x)[0], norm=norm)
+    assert out["lam"] == ref["lam"]
+    Jstar = -0.5 * b @ np.linalg.solve(A, b)
+    assert rel(np.array(out["J"]) - Jstar, np.array(ref["J"]) - Jstar) < HIST_TOL
+    assert (np.array(ref["J"]) - Jstar)[-1] < 0.5 * (np.array(ref["J"]) - Jstar)[1]

@@ -284,3 +284,137 @@ def test_weighted_l2_gamma():
     _, _, gs, _ = aa.anderson_point(P, Gr, eta, weights=sel.astype(float))
     _, _, gr, _ = aa.anderson_point([p[sel] for p in P], [g[sel] for g in Gr], eta)
     np.testing.assert_allclose(gs, gr, rtol=1e-10)
+
+
+# ------------------------------------------------- l1 / l-infinity AA (Sec. 2.1)
+
+def _lp_data(n, M, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, M))
+    f = A @ rng.standard_normal(M) + rng.laplace(size=n)
+    return A, f
+
+
+def test_l1_gamma_is_the_weighted_median_for_one_column():
+    """M = 1: argmin sum |a_i g - f_i| = sum |a_i| |g - f_i/a_i| is the median
+    of the ratios f_i/a_i weighted by |a_i| (closed form)."""
+    from oracle import aa
+    A, f = _lp_data(41, 1, 1)
+    a = A[:, 0]
+    ratio, wgt = f / a, np.abs(a)
+    order = np.argsort(ratio)
+    cw = np.cumsum(wgt[order])
+    g_med = ratio[order][np.searchsorted(cw, 0.5 * cw[-1])]
+    gamma, val = aa.aa_gamma_lp(A, f, "l1")
+    assert val == pytest.approx(np.abs(a * g_med - f).sum(), rel=1e-10)
+    assert gamma[0] == pytest.approx(g_med, rel=1e-8, abs=1e-10)
+
+
+def test_linf_gamma_by_brute_force_over_pairs_for_one_column():
+    """M = 1: max_i |a_i g - f_i| is convex piecewise linear in g; its minimum
+    lies where two of the lines |a_i g - f_i| cross (pairs and signs)."""
+    from oracle import aa
+    A, f = _lp_data(30, 1, 2)
+    a = A[:, 0]
+    best = np.inf
+    for i in range(len(a)):
+        for j in range(i + 1, len(a)):
+            for s in (1.0, -1.0):   # a_i g - f_i = s (a_j g - f_j)
+                den = a[i] - s * a[j]
+                if abs(den) < 1e-14:
+                    continue
+                g = (f[i] - s * f[j]) / den
+                best = min(best, np.abs(a * g - f).max())
+    _, val = aa.aa_gamma_lp(A, f, "linf")
+    assert val == pytest.approx(best, rel=1e-10)
+
+
+def test_l1_gamma_by_brute_force_over_interpolating_pairs():
+    """M = 2: an l1 optimum interpolates two rows (a vertex of the LP): the
+    minimum over all pairs of rows of the interpolant's objective."""
+    from oracle import aa
+    A, f = _lp_data(22, 2, 3)
+    best = np.inf
+    for i in range(len(f)):
+        for j in range(i + 1, len(f)):
+            B = A[[i, j]]
+            if abs(np.linalg.det(B)) < 1e-12:
+                continue
+            g = np.linalg.solve(B, f[[i, j]])
+            best = min(best, np.abs(A @ g - f).sum())
+    _, val = aa.aa_gamma_lp(A, f, "l1")
+    assert val == pytest.approx(best, rel=1e-10)
+
+
+def test_linf_gamma_by_brute_force_over_levelled_triples():
+    """M = 2: the minimax optimum levels three rows, s_i (A_i g - f_i) = t for
+    signs s: the minimum over triples and signs of the levelled solutions'
+    objective (t >= 0)."""
+    import itertools
+    from oracle import aa
+    A, f = _lp_data(13, 2, 4)
+    best = np.inf
+    for tri in itertools.combinations(range(len(f)), 3):
+        for sg in itertools.product((1.0, -1.0), repeat=3):
+            K = np.array([[sg[q] * A[i, 0], sg[q] * A[i, 1], -1.0] for q, i in enumerate(tri)])
+            if abs(np.linalg.det(K)) < 1e-12:
+                continue
+            sol = np.linalg.solve(K, np.array([sg[q] * f[i] for q, i in enumerate(tri)]))
+            if sol[2] < 0:
+                continue
+            best = min(best, np.abs(A @ sol[:2] - f).max())
+    _, val = aa.aa_gamma_lp(A, f, "linf")
+    assert val == pytest.approx(best, rel=1e-10)
+
+
+@pytest.mark.parametrize("norm", ["l1", "linf"])
+def test_lp_gamma_weights_equal_scaled_rows(norm):
+    """A weighted norm equals the plain norm of the rows scaled by the weights."""
+    from oracle import aa
+    A, f = _lp_data(200, 4, 5)
+    w = np.exp(np.random.default_rng(6).uniform(-1.0, 1.0, len(f)))
+    _, v1 = aa.aa_gamma_lp(A, f, norm, weights=w)
+    _, v2 = aa.aa_gamma_lp(A * w[:, None], f * w, norm)
+    assert v1 == pytest.approx(v2, rel=1e-10)
+
+
+def test_host_lp_solver_matches_highs():
+    """The library's host LP solver (aafwi_lp_min, no device call) against
+    scipy's HiGHS on random bounded LPs, on degenerate ones (many rows through
+    one vertex) and on the minimax fit of the l-infinity step."""
+    from scipy.optimize import linprog
+    from paper_2008_11778_gb300 import aafwi, build
+    build.build()
+    rng = np.random.default_rng(8)
+    for nv, m in ((2, 7), (5, 40), (11, 400), (21, 300)):
+        A = rng.standard_normal((m, nv))
+        x0 = rng.standard_normal(nv)
+        b = A @ x0 + rng.uniform(0.0, 1.0, m)
+        box = np.vstack([np.eye(nv), -np.eye(nv)])
+        A2, b2 = np.vstack([A, box]), np.r_[b, np.full(2 * nv, 50.0)]
+        c = rng.standard_normal(nv)
+        x, obj = aafwi.lp_min(A2, b2, c)
+        ref = linprog(c, A_ub=A2, b_ub=b2, bounds=[(None, None)] * nv, method="highs")
+        assert obj == pytest.approx(ref.fun, rel=1e-9, abs=1e-9)
+        assert (A2 @ x <= b2 + 1e-8 * (1 + np.abs(b2))).all()
+        # degenerate: 3 nv extra rows through the optimal vertex
+        D = rng.standard_normal((3 * nv, nv))
+        A3, b3 = np.vstack([A2, D]), np.r_[b2, D @ ref.x]
+        x, obj = aafwi.lp_min(A3, b3, c)
+        ref3 = linprog(c, A_ub=A3, b_ub=b3, bounds=[(None, None)] * nv, method="highs")
+        assert obj == pytest.approx(ref3.fun, rel=1e-9, abs=1e-9)
+    # minimax fit as the l-infinity step writes it
+    from oracle import aa
+    Af, f = _lp_data(300, 5, 9)
+    one = np.ones((300, 1))
+    A4 = np.block([[Af, -one], [-Af, -one]])
+    x, obj = aafwi.lp_min(A4, np.r_[f, -f], np.r_[np.zeros(5), 1.0])
+    assert obj == pytest.approx(aa.aa_gamma_lp(Af, f, "linf")[1], rel=1e-9)
+
+
+def test_host_lp_solver_reports_an_unbounded_problem():
+    from paper_2008_11778_gb300 import aafwi, build
+    build.build()
+    with pytest.raises(aafwi.AafwiError) as e:
+        aafwi.lp_min(np.array([[1.0, 0.0]]), np.array([1.0]), np.array([0.0, 1.0]))   # min x2, x2 free
+    assert e.value.code == 8
