@@ -161,20 +161,27 @@ def traffic_record(kernel, shots_per_launch=None):
 # workloads
 # ---------------------------------------------------------------------------
 
-def make_problem(name, shots=0):
+def make_problem(name, shots=0, nt=0):
     """The workload's problem; shots > 0 keeps only its first `shots` shots
-    (profiling runs: the launch list of a smaller command with the same
-    batches and kernels)."""
+    and nt > 0 cuts the records to nt steps (profiling runs: the launch list
+    of a smaller command with the same batches and kernels, whose per-step
+    costs do not depend on the record length)."""
     from paper_2008_11778_gb300 import synth
     prob = synth.large() if name == "large" else synth.batched()
     if shots:
         prob.geom = prob.geom.subset(range(min(shots, prob.geom.S)))
+    if nt:
+        prob.geom = prob.geom.with_nt(nt)
     return prob
 
 
 def workload_name(args):
     w = WORKLOADS[args.workload]
-    return w if not args.shots else w + "-first%dshots" % args.shots
+    if args.shots:
+        w += "-first%dshots" % args.shots
+    if args.nt:
+        w += "-cut%dsteps" % args.nt
+    return w
 
 
 def host_mem_available():
@@ -229,7 +236,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    prob = make_problem(args.workload, args.shots)
+    prob = make_problem(args.workload, args.shots, args.nt)
     import oracle
     cores = oracle.num_threads()
     # a few seconds per step on the host cores (the oracle stores every step
@@ -394,7 +401,7 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prob = make_problem(args.workload, args.shots)
+    prob = make_problem(args.workload, args.shots, args.nt)
     g = prob.geom
     m_start = torch.as_tensor(prob.m_start.astype(np.float32), device=dev)
     plan = make_plan(aafwi, prob, g, m_start, args)
@@ -723,6 +730,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--shots", type=int, default=0, help="keep only the first N shots (profiling runs)")
+    ap.add_argument("--nt", type=int, default=0, help="cut the records to N steps (profiling runs)")
     ap.add_argument("--kernel-reps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="end-to-end gradients through host buffers (default 1 large, 3 batched)")

@@ -61,6 +61,7 @@ struct aafwi_plan {
     CUtensorMap tm_f{}, tm_d{}, tm_z{}, tm_ck{};
     CUtensorMap tm_fi{}, tm_zi{}, tm_cki{}, tm_t{};
     CUtensorMap tm_w{};             // (Wh, Wl) as slots 0, 1 of a one-shot map
+    CUtensorMap tm_di{}, tm_rho{};  // interior boxes of dbuf; rho_pad as a one-shot, one-slot map
     CUtensorMap tm_f8{};            // fbuf with an 8-cell halo (two-step forward)
     float *dsyn = nullptr, *resid = nullptr;
     // device staging of aafwi_adjoint_gradient_host (allocated on first use)
@@ -349,9 +350,10 @@ int sweep_forward(aafwi_plan *p, const Geo &g, bool born, bool store, float *tra
         for (int l = 0; l < ln.L; ++l) {
             if (born) {
                 BornArgs a{p->W, p->rho_pad, cur, prev, next, n & 1,
-                           slot(p->dbuf, ps, (n + 1) & 1), slot(p->dbuf, ps, (n + 1) & 1), ckc, ckp,
-                           traces, tout, n};
-                launch_born(ln.g[l], a, p->tm_f, p->tm_d, ln.st[l], p->pdl && n > 0);
+                           slot(p->dbuf, ps, (n + 1) & 1), slot(p->dbuf, ps, (n + 1) & 1), prv, (n + 1) & 1,
+                           ckc, ckp, traces, tout, n};
+                launch_born(ln.g[l], a, p->tm_f, p->tm_d, p->tm_fi, p->tm_di, p->tm_w, p->tm_rho, ln.st[l],
+                            p->pdl && n > 0);
             } else {
                 FwdArgs a{p->W, cur, prv, next, ckc, ckp, traces, tout, n};
                 launch_fwd(ln.g[l], a, p->tm_f, p->tm_fi, p->tm_w, ln.st[l], p->pdl && n > 0);
@@ -847,7 +849,9 @@ int aafwi_plan_create(const aafwi_grid *g, const aafwi_shots *sh, const double *
         bool mk = map(&p->tm_f, p->fbuf, 4, true) && map(&p->tm_fi, p->fbuf, 4, false) &&
                   encode_tile_map(&p->tm_f8, p->fbuf, p->NX, p->NZ, p->pitch, p->field, p->Sb, 4, TZ, 2 * HALO,
                                   &why) &&
-                  map(&p->tm_d, p->dbuf, 2, true) && map(&p->tm_z, p->zbuf, 2, true) &&
+                  map(&p->tm_d, p->dbuf, 2, true) && map(&p->tm_di, p->dbuf, 2, false) &&
+                  encode_tile_map(&p->tm_rho, p->rho_pad, p->NX, p->NZ, p->pitch, p->field, 1, 1, TZ, 0, &why) &&
+                  map(&p->tm_z, p->zbuf, 2, true) &&
                   map(&p->tm_zi, p->zbuf, 2, false) &&
                   encode_tile_map(&p->tm_w, p->W, p->NX, p->NZ, p->pitch, p->field, 1, 2, TZ, 0, &why);
         if (mk && p->full) mk = map(&p->tm_t, p->hist, p->nt_max + 1, false);

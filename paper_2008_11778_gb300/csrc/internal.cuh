@@ -100,6 +100,7 @@ struct BornArgs {
     int d_slot;                    // slot of du^n in the du tile map
     const float *d_prev;
     float *d_next;
+    int u_prev_slot, d_prev_slot;  // slots of u^{n-1}, du^{n-1} in the interior maps
     float *ck_cur, *ck_prev;
     float *traces;                 // scattered-field gather
     float *t_out;                  // T^n of the background field (slot base) or null
@@ -163,7 +164,8 @@ void launch_fwd(const Geo &g, const FwdArgs &a, const CUtensorMap &tm_u, const C
 void launch_fwd2(const Geo &g, const Fwd2Args &a, const CUtensorMap &tm_u8, const CUtensorMap &tm_u4, cudaStream_t st,
                  bool pdl = false);
 void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d,
-                 cudaStream_t st, bool pdl = false);
+                 const CUtensorMap &tm_ui, const CUtensorMap &tm_di, const CUtensorMap &tm_w, const CUtensorMap &tm_r,
+                 cudaStream_t st, bool pdl);
 void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, const CUtensorMap &tm_z2,
                 const CUtensorMap &tm_t, const CUtensorMap &tm_w, cudaStream_t st, bool pdl = false);
 // Shot sum and E^T of the batch's images: rowsum (FP64 [NZ][nx]) = or +=

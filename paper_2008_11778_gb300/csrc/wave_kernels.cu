@@ -373,10 +373,28 @@ __global__ void __launch_bounds__(BX *BY, 5) k_fwd2(const Geo g, const Fwd2Args 
     if (a.traces) gather(g, sg, r0, r1, a.n + 1, a.u2 + base, a.traces);
 }
 
+// Born step n (eq. Born): the background u and the scattered du together.
+// With 16-row tiles (BornStaged) the CTA stages everything by TMA: W (Wh, Wl) and rho before the grid-dependency wait (written only
+// before a sweep), u^n and du^n with their 4-cell halos and u^{n-1}, du^{n-1}
+// after it; a thread owns RZ adjacent rows of its float4 column group and
+// keeps the z window of each pair of them (10 rows, for u, then for du) in
+// registers.  Taller tiles would hold one or no CTA per SM that way and
+// load the interior fields from global memory.  Every cell gets the operations of
+// the one-field forward step, in the same order.
 template <int RZ>
-__global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, const __grid_constant__ CUtensorMap tm_u,
-                                                 const __grid_constant__ CUtensorMap tm_d)
+struct BornStaged {   // 16-row tiles: 65.5 KB of shared memory, 3 CTAs per SM
+    static constexpr bool value = RZ == 2;
+};
+
+template <int RZ>
+__global__ void __launch_bounds__(BX *BY, 3) k_born(const Geo g, const BornArgs a, const __grid_constant__ CUtensorMap tm_u,
+                                                    const __grid_constant__ CUtensorMap tm_d,
+                                                    const __grid_constant__ CUtensorMap tm_ui,
+                                                    const __grid_constant__ CUtensorMap tm_di,
+                                                    const __grid_constant__ CUtensorMap tm_w,
+                                                    const __grid_constant__ CUtensorMap tm_r)
 {
+    constexpr bool STAGED = BornStaged<RZ>::value;
     constexpr int TZ = RZ * BY, SH = TZ + 2 * HALO;
     const int s = g.s_off + blockIdx.z, sg = g.shot0 + s;   // batch-local, global shot
     if (shot_done(g, sg, a.n)) {
@@ -389,40 +407,96 @@ __global__ void __launch_bounds__(BX *BY) k_born(const Geo g, const BornArgs a, 
     __shared__ unsigned long long bar;
     Tile *su = reinterpret_cast<Tile *>(smem);
     Tile *sd = su + SH;      // SH * SW * 4 bytes on: a multiple of 128
+    float(*sp)[TX] = reinterpret_cast<float(*)[TX]>(smem + 2 * SH * SW);   // u^{n-1}
+    float(*sdp)[TX] = sp + TZ;                                           // du^{n-1}
+    float(*swh)[TX] = sdp + TZ;                                          // Wh
+    float(*swl)[TX] = swh + TZ;                                          // Wl
+    float(*srho)[TX] = swl + TZ;                                         // rho
     const long long base = (long long)s * g.field;
-    const Copy4 cp[2] = {{su, &tm_u, x0 - HALO, z0 - HALO, s, a.u_slot}, {sd, &tm_d, x0 - HALO, z0 - HALO, s, a.d_slot}};
-    stage_issue(&bar, cp, (unsigned)(2 * SH * SW * sizeof(float)));
+    if constexpr (STAGED) {
+        const Copy4 cp[7] = {{swh, &tm_w, x0, z0, 0, 0}, {swl, &tm_w, x0, z0, 0, 1}, {srho, &tm_r, x0, z0, 0, 0},
+                             {su, &tm_u, x0 - HALO, z0 - HALO, s, a.u_slot},
+                             {sd, &tm_d, x0 - HALO, z0 - HALO, s, a.d_slot},
+                             {sp, &tm_ui, x0, z0, s, a.u_prev_slot}, {sdp, &tm_di, x0, z0, s, a.d_prev_slot}};
+        stage_issue(&bar, cp, (unsigned)((2 * SH * SW + 5 * TZ * TX) * sizeof(float)), 3);
+    } else {
+        const Copy4 cp[2] = {{su, &tm_u, x0 - HALO, z0 - HALO, s, a.u_slot},
+                             {sd, &tm_d, x0 - HALO, z0 - HALO, s, a.d_slot}};
+        stage_issue(&bar, cp, (unsigned)(2 * SH * SW * sizeof(float)));
+    }
     const int xl = threadIdx.x * 4, x = x0 + xl;
-    const Sponge<RZ> sp_ = load_sponge<RZ>(g, z0, x);
+    const int zb = threadIdx.y * RZ;   // this thread's RZ adjacent rows zb .. zb+RZ-1 of the tile
+    Sponge<RZ> sp_;
+    sp_.dgx = x < g.pitch ? ld4g(g.dGx + x) : make_float4(0.f, 0.f, 0.f, 0.f);
+    sp_.ndgx = neg4(sp_.dgx);
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) sp_.dz[r] = z0 + zb + r < g.NZ ? g.dGz[z0 + zb + r] : 0.f;
     const int src = g.src_pt[sg];
     const float wsn = g.ws[a.n];
     const int t = sg * g.ntiles + tile;
     const int r0 = g.trec_off[t], r1 = g.trec_off[t + 1];
     if (!stage_wait(&bar, g.err)) return;
     if (x < g.pitch) {
+        constexpr int RC = RZ < 2 ? RZ : 2;   // rows per register window
+        auto ld_tile = [&](float (*t)[TX], const float *gsrc, int zl, int cell) {
+            if constexpr (STAGED) return *reinterpret_cast<const float4 *>(&t[zl][xl]);
+            else return ld4g(gsrc + cell);
+        };
 #pragma unroll
-        for (int r = 0; r < RZ; ++r) {
-            const int zl = threadIdx.y + r * BY, z = z0 + zl;
-            if (z >= g.NZ) break;
-            const int cell = z * g.pitch + x;
-            float4 T = stencil4(su, zl + HALO, xl + HALO, g.rz);
-            add_source(T, src, (int)cell, wsn);
-            if (a.t_out) __stcs(reinterpret_cast<float4 *>(a.t_out + base + cell), T);
-            float4 Td = stencil4(sd, zl + HALO, xl + HALO, g.rz);
-            const float4 rho = ld4g(a.rho + cell);
-            // scattered source: W L du - W rho (L u + s)  ->  Wt (T_d - rho T)
-            Td = born_src(Td, rho, T);
-            const float4 ndG = neg_sponge4(sp_.dz[r], sp_.dgx, sp_.ndgx);
-            const float4 wh = ld4g(a.W + cell), wl = ld4g(a.W + g.field + cell);
-            const float4 uc = ld4s(su, zl + HALO, xl + HALO);
-            const float4 up = ld4g(a.u_prev + base + cell);
-            const float4 dc = ld4s(sd, zl + HALO, xl + HALO);
-            const float4 dp = ld4g(a.d_prev + base + cell);
-            st4g(a.u_next + base + cell, leapfrog(ndG, uc, up, T, wh, wl));
-            st4g(a.d_next + base + cell, leapfrog(ndG, dc, dp, Td, wh, wl));
-            if (a.ck_cur) {
-                st4g(a.ck_cur + base + cell, uc);
-                st4g(a.ck_prev + base + cell, up);
+        for (int c = 0; c < RZ; c += RC) {
+            float4 wz[RC + 8];
+            float4 T[RC];
+            // background: the window of u^n, its stencil and source, then u^{n+1}
+#pragma unroll
+            for (int k = 0; k < RC + 8; ++k) wz[k] = ld4s(su, zb + c + k, xl + HALO);
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                float4 up[4], dn[4];
+#pragma unroll
+                for (int k = 1; k <= 4; ++k) {
+                    up[k - 1] = wz[r + 4 - k];
+                    dn[k - 1] = wz[r + 4 + k];
+                }
+                T[r] = stencil_T(ld4s(su, zb + c + r + HALO, xl), wz[r + 4], ld4s(su, zb + c + r + HALO, xl + 2 * HALO),
+                                 up, dn, g.rz);
+                add_source(T[r], src, (int)((z0 + zb + c + r) * g.pitch + x), wsn);
+            }
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const int zl = zb + c + r, z = z0 + zl;
+                if (z >= g.NZ) break;
+                const int cell = z * g.pitch + x;
+                if (a.t_out) __stcs(reinterpret_cast<float4 *>(a.t_out + base + cell), T[r]);
+                const float4 ndG = neg_sponge4(sp_.dz[c + r], sp_.dgx, sp_.ndgx);
+                const float4 up = ld_tile(sp, a.u_prev + base, zl, cell);
+                st4g(a.u_next + base + cell, leapfrog(ndG, wz[r + 4], up, T[r], ld_tile(swh, a.W, zl, cell),
+                                                      ld_tile(swl, a.W + g.field, zl, cell)));
+                if (a.ck_cur) {
+                    st4g(a.ck_cur + base + cell, wz[r + 4]);
+                    st4g(a.ck_prev + base + cell, up);
+                }
+            }
+            // scattered field: the window of du^n, its stencil, the scattered
+            // source W L du - W rho (L u + s) -> Wt (T_d - rho T), du^{n+1}
+#pragma unroll
+            for (int k = 0; k < RC + 8; ++k) wz[k] = ld4s(sd, zb + c + k, xl + HALO);
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const int zl = zb + c + r, z = z0 + zl;
+                if (z >= g.NZ) break;
+                const int cell = z * g.pitch + x;
+                float4 up[4], dn[4];
+#pragma unroll
+                for (int k = 1; k <= 4; ++k) {
+                    up[k - 1] = wz[r + 4 - k];
+                    dn[k - 1] = wz[r + 4 + k];
+                }
+                const float4 Td = stencil_T(ld4s(sd, zb + c + r + HALO, xl), wz[r + 4],
+                                            ld4s(sd, zb + c + r + HALO, xl + 2 * HALO), up, dn, g.rz);
+                const float4 Ts = born_src(Td, ld_tile(srho, a.rho, zl, cell), T[r]);
+                const float4 ndG = neg_sponge4(sp_.dz[c + r], sp_.dgx, sp_.ndgx);
+                st4g(a.d_next + base + cell, leapfrog(ndG, wz[r + 4], ld_tile(sdp, a.d_prev + base, zl, cell), Ts,
+                                                      ld_tile(swh, a.W, zl, cell), ld_tile(swl, a.W + g.field, zl, cell)));
             }
         }
     }
@@ -584,7 +658,10 @@ static size_t fwd_smem() { return ((RZ * BY + 2 * HALO) * SW + 3 * RZ * BY * TX)
 template <int RZ>
 static size_t fwd2_smem() { return ((RZ * BY + 4 * HALO) * SW8 + (RZ * BY + 2 * HALO) * SW) * sizeof(float); }
 template <int RZ>
-static size_t born_smem() { return 2 * (RZ * BY + 2 * HALO) * SW * sizeof(float); }
+static size_t born_smem()
+{
+    return (2 * (RZ * BY + 2 * HALO) * SW + (BornStaged<RZ>::value ? 5 * RZ * BY * TX : 0)) * sizeof(float);
+}
 template <int RZ>
 static size_t adj_smem() { return ((RZ * BY + 2 * HALO) * SW + 5 * RZ * BY * TX) * sizeof(float); }
 
@@ -679,12 +756,13 @@ void launch_fwd2(const Geo &g, const Fwd2Args &a, const CUtensorMap &tm_u8, cons
     else launch_step(k_fwd2<4>, fwd2_smem<4>(), g, st, pdl, g, a, tm_u8, tm_u4);
 }
 
-void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d, cudaStream_t st,
-                 bool pdl)
+void launch_born(const Geo &g, const BornArgs &a, const CUtensorMap &tm_u, const CUtensorMap &tm_d,
+                 const CUtensorMap &tm_ui, const CUtensorMap &tm_di, const CUtensorMap &tm_w, const CUtensorMap &tm_r,
+                 cudaStream_t st, bool pdl)
 {
-    if (g.tz == 16) launch_step(k_born<2>, born_smem<2>(), g, st, pdl, g, a, tm_u, tm_d);
-    else if (g.tz == 64) launch_step(k_born<8>, born_smem<8>(), g, st, pdl, g, a, tm_u, tm_d);
-    else launch_step(k_born<4>, born_smem<4>(), g, st, pdl, g, a, tm_u, tm_d);
+    if (g.tz == 16) launch_step(k_born<2>, born_smem<2>(), g, st, pdl, g, a, tm_u, tm_d, tm_ui, tm_di, tm_w, tm_r);
+    else if (g.tz == 64) launch_step(k_born<8>, born_smem<8>(), g, st, pdl, g, a, tm_u, tm_d, tm_ui, tm_di, tm_w, tm_r);
+    else launch_step(k_born<4>, born_smem<4>(), g, st, pdl, g, a, tm_u, tm_d, tm_ui, tm_di, tm_w, tm_r);
 }
 
 void launch_adj(const Geo &g, const AdjArgs &a, const CUtensorMap &tm_z, const CUtensorMap &tm_z2,
