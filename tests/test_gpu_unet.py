@@ -86,8 +86,13 @@ def test_unet_training_reduces_loss(A):
 def production_case():
     """The production network (C = 32) on a batch of the training shape
     (2 x 96 x 256): split-K weight gradients and 16-byte channel gathers run
-    as in training.  Reference: the oracle in its BF16-rounding mode and in
-    FP64."""
+    as in training.  References: the oracle in FP64 and in its BF16-rounding
+    mode.  At this depth and size the BF16 network is chaotic in its rounding
+    points (FP32-level noise before each BF16 rounding moves the output by
+    most of the BF16 quantisation error: tests/test_oracle_unet.py), so the
+    runtime, which accumulates in FP32, is held to the accuracy of the BF16
+    reference itself against FP64: a wrong operand, gather or split would
+    show as an O(1) error."""
     from oracle import unet as U
     C = 32
     rng = np.random.default_rng(17)
@@ -98,9 +103,9 @@ def production_case():
 
 
 def test_unet_production_shape_forward(A, production_case):
-    """Forward of the C = 32 network on a 2 x 96 x 256 batch: the runtime sits
-    within a quarter of the BF16 quantisation error (the BF16 reference
-    against FP64) of the BF16 reference."""
+    """Forward of the C = 32 network on a 2 x 96 x 256 batch: as close to the
+    FP64 network as the BF16 reference is (within 1.5x), and within the
+    BF16 quantisation error of the BF16 reference."""
     import torch
     from oracle import unet as U
     C, p, x, _, _, _ = production_case
@@ -109,17 +114,15 @@ def test_unet_production_shape_forward(A, production_case):
     y = net.forward(torch.as_tensor(x, device="cuda")).cpu().numpy()
     ref, exact = U.forward(p, x, C), U.forward(p, x, C, exact=True)
     q = rel(ref, exact)                  # what BF16 activations cost
-    assert rel(y, ref) < 0.25 * q
+    assert rel(y, exact) < 1.5 * q, (rel(y, exact), q)
+    assert rel(y, ref) < 1.2 * q, (rel(y, ref), q)
     net.close()
 
 
 def test_unet_production_shape_gradient_per_layer(A, production_case):
     """Loss gradient of the C = 32 network on a 2 x 96 x 256 batch, layer by
-    layer: each weight and bias slice of the runtime lies within half of that
-    slice's BF16 quantisation error (BF16 reference against FP64) of the BF16
-    reference (the runtime accumulates in FP32 where the reference uses FP64,
-    so a BF16 rounding or a ReLU mask can flip where a value sits on the
-    boundary)."""
+    layer: each weight and bias slice (and the head) is as close to the FP64
+    gradient as the BF16 reference's slice is, within 1.5x."""
     import torch
     from oracle import unet as U
     C, p, x, t, (Lr, gr), (Le, ge) = production_case
@@ -128,13 +131,13 @@ def test_unet_production_shape_gradient_per_layer(A, production_case):
     g = torch.empty(net.nparam, device="cuda")
     L = net.loss_grad(torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda"), g)
     g = g.cpu().numpy()
-    assert abs(L - Lr) <= 0.25 * abs(Lr - Le) + 1e-6 * abs(Lr)
+    assert abs(L - Le) <= 1.5 * abs(Lr - Le) + 1e-6 * abs(Le)
     o = 0
     for kind, ci, co in U.layers(C):
         nw = (9 if kind == "c3" else 4) * ci * co
         for a, b in ((o, o + nw), (o + nw, o + nw + co)):
             q = rel(gr[a:b], ge[a:b])
-            assert rel(g[a:b], gr[a:b]) < 0.5 * q, (kind, ci, co, a == o, rel(g[a:b], gr[a:b]), q)
+            assert rel(g[a:b], ge[a:b]) < 1.5 * q, (kind, ci, co, a == o, rel(g[a:b], ge[a:b]), q)
         o += nw + co
-    assert rel(g[o:], gr[o:]) < 0.5 * rel(gr[o:], ge[o:])      # the 1x1 head
+    assert rel(g[o:], ge[o:]) < 1.5 * rel(gr[o:], ge[o:])      # the 1x1 head
     net.close()

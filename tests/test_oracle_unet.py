@@ -104,3 +104,26 @@ def test_network_gradient_central_differences():
         Lp, _ = U.loss_grad(p + e, x, t, C, exact=True)
         Lm, _ = U.loss_grad(p - e, x, t, C, exact=True)
         assert (Lp - Lm) / 2e-5 == pytest.approx(g[k], rel=1e-5, abs=1e-10)
+
+
+def test_bf16_network_is_chaotic_in_its_rounding_points():
+    """Why the production-shape GPU tests compare with FP64 rather than with
+    the BF16 reference: relative noise of 3e-7 (the size of an FP32
+    accumulation's rounding) added before each BF16 rounding of the BF16
+    reference moves its output by more than half the BF16 quantisation
+    error (BF16 reference against FP64), even on a small network."""
+    from oracle import unet as U
+    C, B, H, W = 16, 2, 16, 32
+    rng = np.random.default_rng(17)
+    p = U.init_params(C, 17)
+    x = rng.standard_normal((B, 2, H, W)).astype(np.float32)
+    ref, exact = U.forward(p, x, C), U.forward(p, x, C, exact=True)
+    q = np.linalg.norm(ref - exact) / np.linalg.norm(exact)
+    orig = U.bf16
+    nrng = np.random.default_rng(1)
+    try:
+        U.bf16 = lambda a: orig(np.asarray(a, dtype=np.float64) * (1.0 + 3e-7 * nrng.standard_normal(np.shape(a))))
+        y = U.forward(p, x, C)
+    finally:
+        U.bf16 = orig
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) > 0.5 * q
