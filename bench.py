@@ -138,23 +138,20 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_record(kernel, shots_per_launch=None):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None if absent or taken on a different kernel source.  Per-step kernels'
-    records hold one launch of `shots_per_launch` shots; the bytes scale with
-    the shots of the benchmark's launches (a lane of the batch)."""
+def traffic_record(workload, kernel, updates_per_launch):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload`, from
+    the committed ncu record (bytes per grid-point update over the captured
+    launches, scaled to the updates of the benchmark's launch), or None if
+    absent or taken on different kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    rec = d.get(kernel)
+    rec = d.get(workload, {}).get(kernel)
     if not rec or rec.get("source_hash") != kernel_source_hash():
         return None
-    b = rec.get("bytes_per_launch_full")
-    if b is not None and shots_per_launch and rec.get("shots_per_launch"):
-        b = b * shots_per_launch / rec["shots_per_launch"]
-    return b
+    return rec["dram_bytes_per_update"] * updates_per_launch
 
 
 # ---------------------------------------------------------------------------
@@ -279,7 +276,7 @@ def make_plan(aafwi, prob, g, m_tune, args, lanes=None):
     (timed on short sweeps of this geometry before the timed region), or the
     engine / tile height given on the command line."""
     kw = dict(pdl=not args.no_pdl, steps_per_launch=args.steps_per_launch,
-              lanes=args.lanes if lanes is None else lanes)
+              lanes=args.lanes if lanes is None else lanes, shots_per_batch=args.shots_per_batch)
     if args.engine == "tuned":
         return aafwi.Plan(g, c_max=prob.c_bounds[1], tune_model=m_tune, tune_cache=args.tune_cache, **kw)
     return aafwi.Plan(g, c_max=prob.c_bounds[1], engine=ENGINES[args.engine], tile_z=args.tile_z, **kw)
@@ -330,18 +327,24 @@ def sweep_launches(plan, info, nt, forward=True):
     return total
 
 
-def kernel_roof(name, what, bpu, points, launches, sweep_ms, share, peak, peak_kind, nt, shots_per_launch):
+def kernel_roof(name, what, bpu, points, launches, sweep_ms, share, peak, peak_kind, nt, traffic_key):
     """Algorithmic bytes of the sweep / launches over the sweep's CUDA-event
     time / launches (lanes overlap, so this is the time per launch of the
-    launch chains together)."""
+    launch chains together); beside it the DRAM bytes per launch of the
+    committed ncu record (traffic_key = (workload, record name)) over the
+    same time, as a fraction of the same peak."""
     b = bpu * points / launches
     ms = sweep_ms / launches
     gbs = b / (ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": name + " (" + what + ")", "achieved": gbs, "peak": peak,
-            "unit": "GB/s", "frac": gbs / peak, "peak_kind": peak_kind,
-            "traffic": traffic_record(name, shots_per_launch),
-            "bytes_per_launch": b, "ms_per_launch": ms, "launches_per_sweep": launches,
-            "us_per_time_step": 1e3 * sweep_ms / nt, "share_of_step": share}
+    traffic = traffic_record(traffic_key[0], traffic_key[1], points / launches) if traffic_key else None
+    out = {"bound": "hbm", "kernel": name + " (" + what + ")", "achieved": gbs, "peak": peak,
+           "unit": "GB/s", "frac": gbs / peak, "peak_kind": peak_kind, "traffic": traffic,
+           "bytes_per_launch": b, "ms_per_launch": ms, "launches_per_sweep": launches,
+           "us_per_time_step": 1e3 * sweep_ms / nt, "share_of_step": share}
+    if traffic:
+        out["dram_achieved"] = traffic / (ms * 1e-3) / 1e9
+        out["dram_frac"] = out["dram_achieved"] / peak
+    return out
 
 
 def alg2_run(aafwi, solve, prob, plan, dev, warmup, steps, ws, clocks=None):
@@ -415,7 +418,7 @@ def run_ours(args):
     run, rec = alg2_run(aafwi, solve, prob, plan, dev, args.warmup, args.steps, ws, clocks)
     ms_total = rec["ms_total"]
     value = job_value(rec["updates"], ws, ms_total)
-    J_ratio = run.J / run.J0
+    J_ratio = run.J / run.J0 if run.J0 > 0 else None
     run.close()
 
     # Dominant kernel, timed live over the timed region: the line search's
@@ -429,13 +432,15 @@ def run_ours(args):
     trial_ms = rec["trial_ms"]
     t_trials = float(np.sum(trial_ms)) if trial_ms else 0.0
     t_grads = float(np.sum(rec["grad_ms"])) if rec["grad_ms"] else 0.0
-    shots_per_launch = info.shots_per_batch / max(1, lanes)
+    # DRAM records: the line-search sweeps of a batched plan store no history
+    trial_rec = (args.workload, "k_fwd_traces" if info.n_batches > 1 else "k_fwd_history")
     fwd_roof = None
     if trial_ms:
         fwd_roof = kernel_roof(fwd_name, "line-search forward sweeps, timed live over the timed region, "
                                "%d step(s) per launch" % (2 if spl == 2 else 1),
                                BYTES_FWD, pts_sweep, fwd_launches, float(np.median(trial_ms)),
-                               t_trials / ms_total, peak, peak_kind, nt, shots_per_launch)
+                               t_trials / ms_total, peak, peak_kind, nt,
+                               trial_rec if fwd_name == "k_fwd" else None)
         fwd_roof["sweeps_timed"] = len(trial_ms)
 
     e2e = run_e2e(plan, prob, dev, args.e2e_steps) if args.e2e_steps > 0 else None
@@ -498,11 +503,12 @@ def batch_kernel_roofs(aafwi, prob, m_start, info, args, fwd_roof, fwd_name, t_g
     adj_roof = kernel_roof("k_adj_persist" if kt["adj_launches"] == 1 else "k_adj",
                            "adjoint sweep + imaging, one batch of %d shots, timed alone" % kt["shots"],
                            BYTES_ADJ, kt["points"], kt["adj_launches"], kt["adj_ms"],
-                           None, peak, peak_kind, nt, kt["shots"] / max(1, kt["lanes"]))
+                           None, peak, peak_kind, nt, (args.workload, "k_adj") if kt["adj_launches"] > 1 else None)
     adj_roof["share_of_step"] = (t_grads / ms_total) * kt["adj_ms"] / (kt["adj_ms"] + kt["fwd_ms"])
     fwdT_roof = kernel_roof(fwd_name, "forward sweep storing T^n for the adjoint, one batch of %d shots, "
                             "timed alone" % kt["shots"], BYTES_FWD, kt["points"], kt["fwd_launches"],
-                            kt["fwd_ms"], None, peak, peak_kind, nt, kt["shots"] / max(1, kt["lanes"]))
+                            kt["fwd_ms"], None, peak, peak_kind, nt,
+                            (args.workload, "k_fwd_history") if fwd_name == "k_fwd" else None)
     fwdT_roof["share_of_step"] = (t_grads / ms_total) * kt["fwd_ms"] / (kt["adj_ms"] + kt["fwd_ms"])
     # k_fwd runs both in the line-search sweeps and, storing T^n, in the
     # gradient: the kernel's share of the step is the sum of the two
@@ -562,14 +568,15 @@ def run_secondary(aafwi, solve, dev, args, peak, peak_kind):
     out = {"workload": WORKLOADS["batched"], "value": rec["updates"] / (rec["ms_total"] / 1e3), "unit": UNIT,
            "steps": args.secondary_steps, "warmup": 3, "ms_per_step": rec["ms_total"] / args.secondary_steps,
            "passes": {"forward": rec["nf"], "adjoint": rec["na"]},
-           "fwi_iterations_per_s": args.secondary_steps / (rec["ms_total"] / 1e3), "J_over_J0": run.J / run.J0,
+           "fwi_iterations_per_s": args.secondary_steps / (rec["ms_total"] / 1e3),
+           "J_over_J0": run.J / run.J0 if run.J0 > 0 else None,
            "engine": ENGINE_NAMES.get(info.engine, info.engine), "tile_z": info.tile_z, "lanes": info.lanes,
            "gpu_launches": rec["launches"]}
     if rec["trial_ms"]:
         out["k_fwd"] = kernel_roof("k_fwd", "line-search forward sweeps (L2-resident fields)", BYTES_FWD, pts,
                                    sweep_launches(plan, info, nt, True), float(np.median(rec["trial_ms"])),
                                    float(np.sum(rec["trial_ms"])) / rec["ms_total"], peak, peak_kind, nt,
-                                   info.shots_per_batch / max(1, info.lanes))
+                                   ("batched", "k_fwd_history"))
     run.close()
     plan.close()
     torch.cuda.empty_cache()
@@ -731,6 +738,8 @@ def main():
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--shots", type=int, default=0, help="keep only the first N shots (profiling runs)")
     ap.add_argument("--nt", type=int, default=0, help="cut the records to N steps (profiling runs)")
+    ap.add_argument("--shots-per-batch", type=int, default=0,
+                    help="fix the plan's shot batch (profiling runs of a cut workload: the batches of the full one)")
     ap.add_argument("--kernel-reps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="end-to-end gradients through host buffers (default 1 large, 3 batched)")
@@ -738,7 +747,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="small case for ncu captures")
-    ap.add_argument("--ncu-batch", type=int, default=7, help="shots per batch of the large ncu case")
+    ap.add_argument("--ncu-batch", type=int, default=3,
+                    help="shots per batch of the large ncu case (the planner takes 3 on a GB300)")
     ap.add_argument("--ncu-unet-case", action="store_true", help="small U-Net case for ncu captures")
     ap.add_argument("--ncu-lsrtm-case", action="store_true", help="small LSRTM case for ncu captures")
     ap.add_argument("--engine", default="tuned", choices=["tuned"] + list(ENGINES),

@@ -1,6 +1,6 @@
 """Host logic of the benchmark's DRAM-traffic field (no GPU): a record is
-used only when it was taken on the current kernel sources, and a per-step
-record scales with the shots of the benchmark's launches."""
+used only when it was taken on the current kernel sources, and it scales
+with the grid-point updates of the benchmark's launches."""
 import json
 import os
 import sys
@@ -16,22 +16,20 @@ def _write(tmp_path, rec):
         json.dump(rec, f)
 
 
-def test_record_matches_sources_and_scales_with_launch_shots(tmp_path, monkeypatch):
+def test_record_matches_sources_and_scales_with_launch_updates(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc")
-    _write(tmp_path, {"k_fwd": {"source_hash": "abc", "bytes_per_launch_full": 800, "shots_per_launch": 8},
-                      "k_adj": {"source_hash": "old", "bytes_per_launch_full": 900, "shots_per_launch": 8},
-                      "k_fwd_persist": {"source_hash": "abc", "bytes_per_launch_full": 5000}})
-    assert bench.traffic_record("k_fwd") == 800
-    assert bench.traffic_record("k_fwd", 16) == 1600          # two lanes of 32 shots: 16 per launch
-    assert bench.traffic_record("k_fwd", 8) == 800
-    assert bench.traffic_record("k_adj", 8) is None           # taken on other sources
-    assert bench.traffic_record("k_fwd_persist", None) == 5000
-    assert bench.traffic_record("k_born") is None
+    _write(tmp_path, {"large": {"k_fwd_traces": {"source_hash": "abc", "dram_bytes_per_update": 5.5},
+                                "k_adj": {"source_hash": "old", "dram_bytes_per_update": 20.0}}})
+    assert bench.traffic_record("large", "k_fwd_traces", 1000) == 5500.0
+    assert bench.traffic_record("large", "k_adj", 1000) is None          # taken on other sources
+    assert bench.traffic_record("batched", "k_fwd_traces", 1000) is None  # no record for that workload
+    assert bench.traffic_record("large", "k_born", 1000) is None
 
 
-def test_committed_record_names_the_per_step_kernels():
+def test_committed_record_names_the_headline_kernels():
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
         d = json.load(f)
-    for k in ("k_fwd", "k_adj"):
-        assert d[k]["bytes_per_launch_full"] > 0 and d[k]["shots_per_launch"] > 0 and d[k]["source_hash"]
+    for k in ("k_fwd_traces", "k_fwd_history", "k_adj"):
+        r = d["large"][k]
+        assert r["dram_bytes_per_update"] > 0 and r["source_hash"] and r["launches"] > 0
