@@ -143,7 +143,7 @@ def large_aa(iters=3, M=10, log=None):
     return out
 
 
-def lsrtm_gradient_rate(reps=3, log=None):
+def lsrtm_gradient_rate(reps=3, log=None, shots_per_batch=0):
     """Wall time of one LSRTM gradient on the LSRTM workload (737 x 240,
     64 shots, 4000 steps): Born pair forward + adjoint with the background
     replayed from the stored history, timed with CUDA events on the launching
@@ -151,7 +151,7 @@ def lsrtm_gradient_rate(reps=3, log=None):
     log = log or _log
     p = synth.lsrtm()
     g = p.geom
-    plan = aafwi.Plan(g, 4700.0)
+    plan = aafwi.Plan(g, 4700.0, shots_per_batch=shots_per_batch)
     m0 = _dev(p.m_true)
     rho = _dev(p.extra["rho_true"])
     d = torch.empty(plan.trace_count, device="cuda")
@@ -170,7 +170,7 @@ def lsrtm_gradient_rate(reps=3, log=None):
     upd = 4 * g.updates_per_pass()
     out = {"workload": "lsrtm-737x240-64shots-4000steps", "ms_per_gradient": min(ms),
            "updates_per_s": upd / (min(ms) * 1e-3), "lanes": plan.info.lanes,
-           "checkpoint_every": plan.info.checkpoint_every}
+           "checkpoint_every": plan.info.checkpoint_every, "shots_per_batch": plan.info.shots_per_batch}
     log("lsrtm gradient", out["ms_per_gradient"], "ms")
     plan.close()
     return out
@@ -184,10 +184,11 @@ if __name__ == "__main__":
     ap.add_argument("--large-iters", type=int, default=0, help="AA iterations on the large workload (0: skip)")
     ap.add_argument("--only-large", action="store_true")
     ap.add_argument("--lsrtm-rate", action="store_true", help="time one LSRTM gradient and stop")
+    ap.add_argument("--lsrtm-batch", type=int, default=0, help="shots per batch of the LSRTM plan (0: planner)")
     a = ap.parse_args()
     res = {}
     if a.lsrtm_rate:
-        print(json.dumps({"lsrtm_gradient": lsrtm_gradient_rate()}))
+        print(json.dumps({"lsrtm_gradient": lsrtm_gradient_rate(shots_per_batch=a.lsrtm_batch)}))
         raise SystemExit(0)
     if not a.only_large:
         res = {"lsrtm": lsrtm(a.lsrtm_iters), "fwi": fwi(a.fwi_grads), "fwi_noisy": fwi(a.fwi_grads, snr_db=a.snr_db)}
