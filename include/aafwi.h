@@ -408,6 +408,12 @@ int aafwi_dot(const float *x, const float *y, size_t n, double *host_out, aafwi_
  * Errors: ARG, CUDA (launch). */
 int aafwi_axpby(double a, const float *x, double b, float *y, size_t n, aafwi_stream stream);
 
+/* y = clip(a x + b y) to [lo, hi] (no clip when lo >= hi): the bound
+ * constraint applied to a trial point of a line search.  Asynchronous.
+ * Errors: ARG, CUDA (launch). */
+int aafwi_axpby_clip(double a, const float *x, double b, float *y, size_t n, float lo, float hi,
+                     aafwi_stream stream);
+
 /* ---- autotuner (launch configuration of the sweeps; the paper has no
  * counterpart) ------------------------------------------------------------ */
 

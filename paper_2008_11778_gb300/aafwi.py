@@ -32,7 +32,7 @@ EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aa
            "aafwi_unet_param_count", "aafwi_unet_set_params", "aafwi_unet_get_params", "aafwi_unet_forward",
            "aafwi_unet_loss_grad", "aafwi_unet_train_step", "aafwi_learned_features", "aafwi_learned_apply",
            "aafwi_autotune", "aafwi_dot", "aafwi_axpby", "aafwi_aa_set_norm", "aafwi_aa_get_lp_info",
-           "aafwi_lp_min")
+           "aafwi_lp_min", "aafwi_axpby_clip")
 
 NORM_L2, NORM_L1, NORM_LINF = 0, 1, 2
 
@@ -132,6 +132,7 @@ def load(path=LIB_PATH):
         "aafwi_aa_set_norm": ([P, I], I),
         "aafwi_aa_get_lp_info": ([P, P], I),
         "aafwi_lp_min": ([I, I, P, P, P, P, P], I),
+        "aafwi_axpby_clip": ([D, P, D, P, Z, ctypes.c_float, ctypes.c_float, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -377,6 +378,13 @@ def dot(x, y, stream=None):
 def axpby(a, x, b, y, stream=None):
     """y <- a x + b y in place (device float32)."""
     _check(load().aafwi_axpby(float(a), _f32(x), float(b), _f32(y), y.numel(), _stream(stream)))
+    return y
+
+
+def axpby_clip(a, x, b, y, lo, hi, stream=None):
+    """y <- clip(a x + b y, lo, hi) in place (device float32; no clip when lo >= hi)."""
+    _check(load().aafwi_axpby_clip(float(a), _f32(x), float(b), _f32(y), y.numel(), float(lo), float(hi),
+                                   _stream(stream)))
     return y
 
 

@@ -1313,6 +1313,15 @@ int aafwi_axpby(double a, const float *x, double b, float *y, size_t n, aafwi_st
     return AAFWI_OK;
 }
 
+int aafwi_axpby_clip(double a, const float *x, double b, float *y, size_t n, float lo, float hi, aafwi_stream stream)
+{
+    if (!x || !y || n == 0) return fail(nullptr, AAFWI_ERR_ARG, "NULL argument");
+    launch_axpby((float)a, x, (float)b, y, (long long)n, (cudaStream_t)stream, lo, hi);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "axpby_clip");
+    return AAFWI_OK;
+}
+
 unsigned long long aafwi_launch_count(void)
 {
     return g_launch_count.load(std::memory_order_relaxed);

@@ -221,7 +221,8 @@ void launch_misfit(const float *d_syn, const float *d_obs, float *resid, long lo
                    double *partials, double *J_dev, cudaStream_t st);
 void launch_absmax(const float *x, long long n, double *partials, double *out_dev, cudaStream_t st);
 void launch_dot(const float *x, const float *y, long long n, double *partials, double *out_dev, cudaStream_t st);
-void launch_axpby(float a, const float *x, float b, float *y, long long n, cudaStream_t st);
+void launch_axpby(float a, const float *x, float b, float *y, long long n, cudaStream_t st, float lo = 0.f,
+                  float hi = 0.f);
 
 // Anderson acceleration.
 constexpr int AA_MAXM = 20;

@@ -78,16 +78,22 @@ void launch_dot(const float *x, const float *y, long long n, double *partials, d
 }
 
 // y = a x + b y
-__global__ void __launch_bounds__(RT) k_axpby(float a, const float *x, float b, float *y, long long n)
+// y = a x + b y, then clipped to [lo, hi] when lo < hi
+__global__ void __launch_bounds__(RT) k_axpby(float a, const float *x, float b, float *y, long long n, float lo,
+                                              float hi)
 {
-    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
-        y[i] = fmaf(a, x[i], b * y[i]);
+    const bool clip = lo < hi;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
+        float v = fmaf(a, x[i], b * y[i]);
+        if (clip) v = fminf(fmaxf(v, lo), hi);
+        y[i] = v;
+    }
 }
 
-void launch_axpby(float a, const float *x, float b, float *y, long long n, cudaStream_t st)
+void launch_axpby(float a, const float *x, float b, float *y, long long n, cudaStream_t st, float lo, float hi)
 {
     count_launch();
-    k_axpby<<<RED_BLOCKS, RT, 0, st>>>(a, x, b, y, n);
+    k_axpby<<<RED_BLOCKS, RT, 0, st>>>(a, x, b, y, n, lo, hi);
 }
 
 __global__ void __launch_bounds__(RT) k_absmax(const float *x, long long n, double *partials)

@@ -222,11 +222,9 @@ class LBFGSInversion(AAInversion):
         """out = clip(p + lam d) (lam = 0: the plain gradient step)."""
         out.copy_(self.p)
         if lam > 0:
-            aafwi.axpby(lam, self.d, 1.0, out)
+            aafwi.axpby_clip(lam, self.d, 1.0, out, self.lo, self.hi)
         else:
-            aafwi.axpby(-self.eta, self.grad, 1.0, out)
-        if self.hi > self.lo:
-            out.clamp_(self.lo, self.hi)
+            aafwi.axpby_clip(-self.eta, self.grad, 1.0, out, self.lo, self.hi)
 
     def _armijo(self, Jc, cand):
         diff = self.p_tilde                  # scratch

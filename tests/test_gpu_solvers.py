@@ -52,6 +52,12 @@ def test_dot_and_axpby(gpu):
     assert abs(aafwi.dot(X, Y) - ref) <= 1e-12 * np.abs(x.astype(np.float64) * y).sum()
     aafwi.axpby(0.5, X, -2.0, Y)
     np.testing.assert_allclose(host(Y), 0.5 * x.astype(np.float64) - 2.0 * y, rtol=1e-6, atol=1e-6)
+    Z = dev(gpu, y)
+    aafwi.axpby_clip(0.5, X, -2.0, Z, -1.5, 2.0)          # the line-search bound constraint
+    np.testing.assert_allclose(host(Z), np.clip(0.5 * x.astype(np.float64) - 2.0 * y, -1.5, 2.0), rtol=1e-6, atol=1e-6)
+    W = dev(gpu, y)
+    aafwi.axpby_clip(0.5, X, -2.0, W, 1.0, 1.0)           # lo >= hi: no clip
+    assert gpu.equal(W, Y)
 
 
 @pytest.mark.parametrize("curvature", [False, True], ids=["armijo", "wolfe"])
