@@ -126,6 +126,13 @@ typedef struct {
                                     chains run on forked streams, so that one group's step
                                     boundary (grid drain, dependency wait, refill) overlaps the
                                     others' work; same results for any value */
+    int l2_batches;              /* shot batches sized for the L2: the most shots whose adjoint
+                                    working set (z^{n+1}, z^{n+2}, image) fits 40% of the L2,
+                                    split evenly.  0: only when the plan runs batches anyway
+                                    (memory); 1: always -- for workloads that reuse no stored
+                                    forward, such as LSRTM gradients (a one-batch FWI plan
+                                    would lose AAFWI_REUSE_FORWARD); -1: never.  Ignored when
+                                    shots_per_batch is set; same results for any value */
 } aafwi_plan_opts;
 
 /* plan engines */

@@ -62,7 +62,7 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("max_workspace_bytes", ctypes.c_size_t), ("checkpoint_every", ctypes.c_int),
                 ("tile_z", ctypes.c_int), ("tile_x", ctypes.c_int), ("engine", ctypes.c_int),
                 ("no_graphs", ctypes.c_int), ("shots_per_batch", ctypes.c_int), ("no_pdl", ctypes.c_int),
-                ("steps_per_launch", ctypes.c_int), ("lanes", ctypes.c_int)]
+                ("steps_per_launch", ctypes.c_int), ("lanes", ctypes.c_int), ("l2_batches", ctypes.c_int)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -278,7 +278,7 @@ class Plan:
 
     def __init__(self, geom, c_max, max_workspace_bytes=0, checkpoint_every=0, engine=ENGINE_AUTO,
                  graphs=True, tile_z=0, tune_model=None, tune_cache=None, shots_per_batch=0, pdl=True,
-                 steps_per_launch=0, lanes=0):
+                 steps_per_launch=0, lanes=0, l2_batches=0):
         """tune_model: a device model m [nz][nx]; when given, the engine and
         tile height (and the shot lanes, unless given) come from autotune() (cached in tune_cache, default
         $AAFWI_TUNE_CACHE or ~/.cache/aafwi/tune.json)."""
@@ -293,7 +293,7 @@ class Plan:
         g, s, self._keep = _geom_structs(geom, c_max)
         o = PlanOpts(int(max_workspace_bytes), int(checkpoint_every), int(tile_z), 0, int(engine),
                      0 if graphs else 1, int(shots_per_batch), 0 if pdl else 1, int(steps_per_launch),
-                     int(lanes))
+                     int(lanes), int(l2_batches))
         h = ctypes.c_void_p()
         _check(L.aafwi_plan_create(ctypes.byref(g), ctypes.byref(s), _np_ptr(self._keep[6]),
                                    ctypes.byref(o), ctypes.byref(h)))

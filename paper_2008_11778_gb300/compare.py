@@ -3,7 +3,8 @@
   * LSRTM (737 x 240, 64 shots, 4000 steps; start = the RTM image): steepest
     descent, AA(3), L-BFGS(3) and restarted GMRES(3) on the normal equations
     L^T L rho = L^T d (eq. LSRTM3), 20 iterations each;
-  * FWI (400 x 150, 32 shots, 2500 steps): steepest descent, AA(10) and
+  * FWI (400 x 150, 32 shots, 2500 steps): steepest descent, AA(10) with the
+    l2, l1 and l-infinity norms in its optimisation step (Sec. 2.1) and
     L-BFGS(10), with clean data and with mean-zero uniform noise at an SNR of
     0.55 dB, a fixed budget of gradient evaluations each.
 
@@ -43,7 +44,7 @@ def lsrtm(iters=20, M=3, log=None):
     log = log or _log
     p = synth.lsrtm()
     g = p.geom
-    plan = aafwi.Plan(g, 4700.0)
+    plan = aafwi.Plan(g, 4700.0, l2_batches=1)   # LSRTM reuses no stored forward: L2-sized batches
     m0 = _dev(p.m_true)
     rho_true = _dev(p.extra["rho_true"])
     d = torch.empty(plan.trace_count, device="cuda")
@@ -97,11 +98,13 @@ def fwi(grads=40, M=10, snr_db=None, log=None):
         d += _dev(synth.uniform_noise(d.cpu().numpy(), snr_db, seed=4 * 1000 + 2008))
     m0 = _dev(p.m_start)
     rows = {}
-    for name in ("steepest_descent", "aa", "lbfgs_wolfe", "lbfgs_armijo"):
+    norms = {"aa": aafwi.NORM_L2, "aa_l1": aafwi.NORM_L1, "aa_linf": aafwi.NORM_LINF}
+    for name in ("steepest_descent", "aa", "aa_l1", "aa_linf", "lbfgs_wolfe", "lbfgs_armijo"):
         if name.startswith("lbfgs"):
             run = solve.LBFGSInversion(plan, d, m0, M, bounds=(lo, hi), curvature=name == "lbfgs_wolfe")
         else:
-            run = solve.AAInversion(plan, d, m0, 0 if name == "steepest_descent" else M, bounds=(lo, hi))
+            run = solve.AAInversion(plan, d, m0, 0 if name == "steepest_descent" else M, bounds=(lo, hi),
+                                    norm=norms.get(name, aafwi.NORM_L2))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         while run.n_adjoint < grads:
@@ -151,7 +154,7 @@ def lsrtm_gradient_rate(reps=3, log=None, shots_per_batch=0):
     log = log or _log
     p = synth.lsrtm()
     g = p.geom
-    plan = aafwi.Plan(g, 4700.0, shots_per_batch=shots_per_batch)
+    plan = aafwi.Plan(g, 4700.0, shots_per_batch=shots_per_batch, l2_batches=1)
     m0 = _dev(p.m_true)
     rho = _dev(p.extra["rho_true"])
     d = torch.empty(plan.trace_count, device="cuda")
@@ -184,7 +187,8 @@ if __name__ == "__main__":
     ap.add_argument("--large-iters", type=int, default=0, help="AA iterations on the large workload (0: skip)")
     ap.add_argument("--only-large", action="store_true")
     ap.add_argument("--lsrtm-rate", action="store_true", help="time one LSRTM gradient and stop")
-    ap.add_argument("--lsrtm-batch", type=int, default=0, help="shots per batch of the LSRTM plan (0: planner)")
+    ap.add_argument("--lsrtm-batch", type=int, default=0,
+                    help="shots per batch of the LSRTM plan (0: the planner's L2-sized batches)")
     a = ap.parse_args()
     res = {}
     if a.lsrtm_rate:

@@ -660,12 +660,17 @@ PlanLayout aafwi::plan_layout(long long field, long long cells, int S, int nt_ma
     // batches, but its per-step working set must stay in L2: the adjoint step
     // keeps z^{n+1}, z^{n+2} and the image of every shot of the batch in
     // flight, so batches hold at most l2_shots shots (measured on the large
-    // workload, 2001 x 601: 2-3 shots per batch instead of 7 cut the
-    // gradient's time per update by a quarter).
+    // workload, 2001 x 601: 3 shots per batch instead of 7 cut the
+    // gradient's time per update by a quarter).  With opts.l2_batches = 1
+    // a plan that would fit in one batch is split too (LSRTM gradients, which
+    // reuse no stored forward: 4 batches of 16 shots instead of one of 64
+    // cut the 737 x 240 gradient from 472 to 393 ms).
     auto l2_cap = [&](PlanLayout l) {
-        if (o.shots_per_batch > 0 || l.nbatch == 1 || l.Sb <= l2_shots) return l;
-        const int Sb = l2_shots;
-        return take(Sb, l.full);
+        if (o.shots_per_batch > 0 || o.l2_batches < 0 || (o.l2_batches == 0 && l.nbatch == 1) ||
+            l.Sb <= l2_shots)
+            return l;
+        const int nb = (S + l2_shots - 1) / l2_shots;   // even split into the fewest batches that fit
+        return take((S + nb - 1) / nb, l.full);
     };
     if (o.checkpoint_every <= 1) {
         for (int Sb : sizes)

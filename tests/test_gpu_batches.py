@@ -96,3 +96,33 @@ def test_planner_checkpoints_then_batches_as_the_budget_shrinks(A):
     b2 = int(0.6 * ck.info.workspace_bytes)
     bat = A.Plan(g, 3000.0, max_workspace_bytes=b2)
     assert bat.info.checkpoint_every > 1 and bat.info.n_batches >= 2 and bat.info.workspace_bytes <= b2
+
+
+def test_l2_sized_batches_of_the_lsrtm_workload(A):
+    """l2_batches = 1 splits the LSRTM workload (64 shots of 280 x 777 padded
+    cells) into even batches whose adjoint working set fits 40% of the L2 --
+    4 batches of 16 on a GB300 -- and the LSRTM gradient stays bitwise that of
+    the one-batch plan (records cut to 64 steps)."""
+    import torch
+    p = synth.lsrtm()
+    g = p.geom.with_nt(64)
+    one = A.Plan(g, 4700.0)
+    split = A.Plan(g, 4700.0, l2_batches=1)
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    cap = max(1, int(0.4 * l2 / (3 * one.info.NZ * one.info.pitch * 4)))
+    nb = -(-64 // cap)
+    assert one.info.n_batches == 1
+    assert split.info.n_batches == nb and split.info.shots_per_batch == -(-64 // nb)
+    m0 = torch.as_tensor(p.m_true.astype(np.float32), device="cuda")
+    rho = torch.as_tensor(p.extra["rho_true"].astype(np.float32), device="cuda")
+    d = torch.empty(one.trace_count, device="cuda")
+    one.born_forward(m0, rho, d)
+    d2 = torch.empty_like(d)
+    split.born_forward(m0, rho, d2)
+    assert torch.equal(d, d2)
+    g1, g2 = torch.empty_like(m0), torch.empty_like(m0)
+    J1 = one.adjoint_gradient(A.MODE_LSRTM, m0, torch.zeros_like(rho), d, g1)
+    J2 = split.adjoint_gradient(A.MODE_LSRTM, m0, torch.zeros_like(rho), d, g2)
+    assert J1 == J2 and torch.equal(g1, g2)
+    one.close()
+    split.close()
