@@ -118,3 +118,25 @@ def test_large_all_shots_planner_and_batches(gpu):
     grad = torch.empty_like(m)
     J = plan.adjoint_gradient(0, m, None, d_obs, grad)
     assert J > 0 and torch.isfinite(grad).all() and grad.abs().max() > 0
+
+
+def test_large_gradient_in_the_benchmarks_launch_configuration(gpu, orc):
+    """The large grid in the launch configuration the benchmark times: the
+    planner's L2-sized batches (6 shots spread over the line -> 2 batches of
+    3 on a GB300), two lanes, 16-row tiles, records cut to 600 steps.  With
+    zero observed data the residual is the data itself (every receiver sees
+    the direct wave), so J and the FWI gradient meet the 1e-4 target against
+    the oracle."""
+    torch, A = gpu
+    p = synth.large()
+    g = p.geom.subset([0, 40, 80, 120, 160, 199]).with_nt(600)
+    plan = A.Plan(g, p.c_bounds[1], engine=A.ENGINE_PER_STEP, tile_z=16, lanes=2, l2_batches=1)
+    assert plan.info.n_batches == 2 and plan.info.shots_per_batch == 3 and plan.info.lanes == 2
+    m = p.m_start.astype(np.float32)
+    d_obs = np.zeros(g.trace_count(), dtype=np.float32)
+    J_ref, g_ref = orc.fwi_gradient(g, m, d_obs)
+    grad = torch.empty(m.shape, device="cuda")
+    J = plan.adjoint_gradient(0, dev(torch, m), None, dev(torch, d_obs), grad)
+    assert abs(J - J_ref) / J_ref < 1e-4
+    assert rel(host(grad), g_ref) < GRAD_TOL
+    plan.close()
