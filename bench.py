@@ -81,31 +81,6 @@ def read_peaks():
     return 6800.0, "fallback"
 
 
-def measure_l2_copy_gbs(dev):
-    """Copy bandwidth of buffers that stay in L2: torch's copy kernel over
-    buffers of 8, 16 and 24 MB (read + write bytes, best of 200 back-to-back
-    copies after warm-up, CUDA events).  The denominator for kernels whose
-    per-step working set is L2-resident, beside the HBM copy peak."""
-    import torch
-    best = 0.0
-    st = torch.cuda.current_stream()
-    for mb in (8, 16, 24):
-        n = mb * (1 << 20) // 4
-        a = torch.ones(n, device=dev)
-        b = torch.empty_like(a)
-        for _ in range(20):
-            b.copy_(a)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(200):
-            b.copy_(a)
-        e1.record(st)
-        torch.cuda.synchronize()
-        best = max(best, 2 * n * 4 * 200 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
-        del a, b
-    return best
-
-
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
@@ -467,12 +442,6 @@ def run_ours(args):
                                t_trials / ms_total, peak, peak_kind, nt,
                                trial_rec if fwd_name == "k_fwd" else None)
         fwd_roof["sweeps_timed"] = len(trial_ms)
-
-    if fwd_roof is not None and args.workload == "large":
-        l2_gbs = measure_l2_copy_gbs(dev)
-        fwd_roof["l2"] = {"achieved": fwd_roof["achieved"], "peak": l2_gbs, "unit": "GB/s",
-                          "frac": fwd_roof["achieved"] / l2_gbs,
-                          "peak_kind": "measured here: torch copy of 8-24 MB buffers (L2-resident)"}
 
     e2e = run_e2e(plan, prob, dev, args.e2e_steps) if args.e2e_steps > 0 else None
     plan.close()
