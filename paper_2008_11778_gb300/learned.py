@@ -17,7 +17,7 @@ import time
 import numpy as np
 import torch
 
-from . import aafwi, solve, synth
+from . import aafwi, solve
 
 
 def net_grid(nz, nx):

@@ -1,7 +1,6 @@
 """Host logic of the autotuner's cache (no GPU): keys distinguish what the
 launch configuration depends on, a stored tuning is reused, a different
 device or geometry is tuned afresh, and a damaged cache file is ignored."""
-import numpy as np
 
 from paper_2008_11778_gb300 import aafwi, synth
 
