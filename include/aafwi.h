@@ -359,6 +359,27 @@ int aafwi_unet_loss_grad(aafwi_unet *net, const float *x, const float *target, i
 int aafwi_unet_train_step(aafwi_unet *net, const float *x, const float *target, int B, float lr,
                           double *loss_host, aafwi_stream stream);
 
+/* One 3x3 convolution GEMM of the network (cross-correlation, zero padding
+ * 1) on BF16 operands with FP32 accumulation, as the forward and backward
+ * passes run it; device arrays, NHWC activations, raw BF16 bits.
+ *   AAFWI_CONV3_FWD   a = x [B][H][W][Cin], b = w [Cout][3][3][Cin]
+ *                     -> out [s][B H W][Cout]  (y = conv(x, w), no bias)
+ *   AAFWI_CONV3_DGRAD a = dz [B][H][W][Cout], b = wt [Cin][3][3][Cout] (w with
+ *                     its channel axes swapped) -> out [s][B H W][Cin] (dL/dx)
+ *   AAFWI_CONV3_WGRAD a = dz [B][H][W][Cout], b = x [B][H][W][Cin]
+ *                     -> out [s][Cout][3][3][Cin]  (dL/dw)
+ * The result is the sum of the s slices (split K); s is written to
+ * *splits_used (may be NULL).  splits: at most this many slices (<= 0: the
+ * network's own choice); out_cap: floats available at out, at least one
+ * result (the slices used never exceed it).  Synchronises the stream.
+ * Errors: AAFWI_ERR_ARG for bad sizes, AAFWI_ERR_TIMEOUT when a tensor-core
+ * wait ran out (the device context must then be reset). */
+#define AAFWI_CONV3_FWD 0
+#define AAFWI_CONV3_DGRAD 1
+#define AAFWI_CONV3_WGRAD 2
+int aafwi_unet_conv3x3(int op, const void *a, const void *b, int B, int H, int W, int Cin, int Cout, int splits,
+                       float *out, long long out_cap, int *splits_used, aafwi_stream stream);
+
 /* Network input of the learned step from a gradient and a model (device FP32
  * [nz][nx]): stats (device double[3]) = (max|grad|, mean m, std m) and
  * x[2][H][W] = (grad / max|grad|, (m - mean) / std) on the top-left nz x nx

@@ -32,9 +32,10 @@ EXPORTS = ("aafwi_plan_create", "aafwi_plan_destroy", "aafwi_plan_get_info", "aa
            "aafwi_unet_param_count", "aafwi_unet_set_params", "aafwi_unet_get_params", "aafwi_unet_forward",
            "aafwi_unet_loss_grad", "aafwi_unet_train_step", "aafwi_learned_features", "aafwi_learned_apply",
            "aafwi_autotune", "aafwi_dot", "aafwi_axpby", "aafwi_aa_set_norm", "aafwi_aa_get_lp_info",
-           "aafwi_lp_min", "aafwi_axpby_clip")
+           "aafwi_lp_min", "aafwi_axpby_clip", "aafwi_unet_conv3x3")
 
 NORM_L2, NORM_L1, NORM_LINF = 0, 1, 2
+CONV3_FWD, CONV3_DGRAD, CONV3_WGRAD = 0, 1, 2
 
 
 class AafwiError(RuntimeError):
@@ -124,6 +125,7 @@ def load(path=LIB_PATH):
         "aafwi_unet_forward": ([P, P, I, P, P], I),
         "aafwi_unet_loss_grad": ([P, P, P, I, P, P, P], I),
         "aafwi_unet_train_step": ([P, P, P, I, ctypes.c_float, P, P], I),
+        "aafwi_unet_conv3x3": ([I, P, P, I, I, I, I, I, I, P, ctypes.c_longlong, ctypes.POINTER(I), P], I),
         "aafwi_learned_features": ([P, P, I, I, I, I, P, P, P], I),
         "aafwi_learned_apply": ([P, P, I, I, I, P, ctypes.c_float, ctypes.c_float, P, P], I),
         "aafwi_autotune": ([P, P, P, P, I, I, P, P, I, P, P], I),
@@ -449,6 +451,26 @@ class AA:
 class AALpInfo(ctypes.Structure):
     _fields_ = [("objective", ctypes.c_double), ("lower_bound", ctypes.c_double),
                 ("rounds", ctypes.c_int), ("rows", ctypes.c_int)]
+
+
+def unet_conv3x3(op, a, b, B, H, W, Cin, Cout, splits=0, max_splits=8, stream=None):
+    """aafwi_unet_conv3x3: one 3x3 convolution GEMM of the U-Net on BF16 device
+    tensors (NHWC activations; weights [Cout][3][3][Cin], or [Cin][3][3][Cout]
+    for CONV3_DGRAD).  Returns the FP32 split slices [s][...] (their sum is the
+    result) and s."""
+    import torch
+    for t in (a, b):
+        if t.dtype != torch.bfloat16 or not t.is_cuda or not t.is_contiguous():
+            raise TypeError("expected contiguous CUDA bfloat16 tensors")
+    P = B * H * W
+    MN = 9 * Cin * Cout if op == CONV3_WGRAD else P * (Cout if op == CONV3_FWD else Cin)
+    cap = max(1, max_splits if splits <= 0 else min(splits, max_splits))
+    out = torch.empty(cap * MN, device=a.device, dtype=torch.float32)
+    s = ctypes.c_int(0)
+    _check(load().aafwi_unet_conv3x3(int(op), ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                     int(B), int(H), int(W), int(Cin), int(Cout), int(splits),
+                                     ctypes.c_void_p(out.data_ptr()), cap * MN, ctypes.byref(s), _stream(stream)))
+    return out[:s.value * MN].view(s.value, -1), s.value
 
 
 def lp_min(A, b, c):

@@ -14,6 +14,7 @@
 // FP32 masters with BF16 copies used by the kernels, Adam in FP32.
 #include <cuda_bf16.h>
 
+#include <climits>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -26,7 +27,7 @@ namespace aafwi {
 int unet_conv3_fwd(const __nv_bfloat16 *x, const __nv_bfloat16 *w, int B, int H, int W, int Cin, int Cout,
                    float *out, long long out_cap, cudaStream_t st);
 int unet_conv3_dgrad(const __nv_bfloat16 *dz, const __nv_bfloat16 *wt, int B, int H, int W, int Cin, int Cout,
-                     float *out, cudaStream_t st);
+                     float *out, long long out_cap, cudaStream_t st);
 int unet_conv3_wgrad(const __nv_bfloat16 *dz, const __nv_bfloat16 *x, int B, int H, int W, int Cin, int Cout,
                      int splits, float *out, cudaStream_t st);
 int unet_up_fwd(const __nv_bfloat16 *x, const __nv_bfloat16 *w, int B, int H, int W, int Cin, int Cout,
@@ -83,7 +84,7 @@ __global__ void k_relu_back(const float *g, int splits, long long n, const bf16 
     }
 }
 
-// FP32 weight gradient: dw = sum_splits parts  ([splits][n], fixed order)
+// FP32 sum of split slices: dw = sum_splits parts  ([splits][n], fixed order; dw may be parts)
 __global__ void k_sum_splits(const float *parts, int splits, long long n, float *dw)
 {
     GRID_LOOP(i, n) {
@@ -449,7 +450,7 @@ void up_fwd(aafwi_unet *u, const Conv &c, const bf16 *x, int B, int H, int W, bf
 int wgrad_splits(long long P) { return (int)std::max<long long>(1, std::min<long long>(64, P / 2048)); }
 
 // Backward of y = relu(conv3(x) + b): gy (FP32 [P][Cout]) -> dW, db (into u->G),
-// returns gx in FP32 (u->gemm, 1 split) when want_gx.
+// returns gx in FP32 (u->gemm, its split slices summed into the first) when want_gx.
 void conv_back(aafwi_unet *u, const Conv &c, const bf16 *x, const bf16 *y, const float *gy, int B, int H, int W,
                bool want_gx, cudaStream_t st)
 {
@@ -463,7 +464,11 @@ void conv_back(aafwi_unet *u, const Conv &c, const bf16 *x, const bf16 *y, const
         count_launch();
         bf16 *wt = u->Wt;
         k_transpose_w<<<nblk(c.nw()), ET, 0, st>>>(wb(u, c), c.Cout, c.Cin, wt);
-        unet_conv3_dgrad(u->gb1, wt, B, H, W, c.Cin, c.Cout, u->gemm, st);
+        const int sx = unet_conv3_dgrad(u->gb1, wt, B, H, W, c.Cin, c.Cout, u->gemm, u->gemm_size, st);
+        if (sx > 1) {   // sum the slices in place into the first
+            count_launch();
+            k_sum_splits<<<nblk(P * c.Cin), ET, 0, st>>>(u->gemm, sx, P * c.Cin, u->gemm);
+        }
     }
 }
 
@@ -757,5 +762,37 @@ int aafwi_unet_train_step(aafwi_unet *u, const float *x, const float *target, in
     return AAFWI_OK;
 }
 
+int aafwi_unet_conv3x3(int op, const void *a, const void *b, int B, int H, int W, int Cin, int Cout, int splits,
+                       float *out, long long out_cap, int *splits_used, aafwi_stream stream)
+{
+    if (!a || !b || !out || B < 1 || H < 1 || W < 1 || Cin < 1 || Cout < 1 || op < AAFWI_CONV3_FWD ||
+        op > AAFWI_CONV3_WGRAD || (long long)B * H * W > INT_MAX / 9)
+        return uerr(nullptr, AAFWI_ERR_ARG, "unet_conv3x3: bad arguments");
+    const long long P = (long long)B * H * W;
+    const long long MN = op == AAFWI_CONV3_WGRAD ? 9LL * Cin * Cout : P * (op == AAFWI_CONV3_FWD ? Cout : Cin);
+    if (out_cap < MN) return uerr(nullptr, AAFWI_ERR_ARG, "unet_conv3x3: out_cap below one result");
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto *x = static_cast<const bf16 *>(a), *y = static_cast<const bf16 *>(b);
+    int s = 1;
+    if (op == AAFWI_CONV3_FWD) {
+        const long long cap = splits > 0 ? std::min(out_cap, splits * MN) : out_cap;
+        s = unet_conv3_fwd(x, y, B, H, W, Cin, Cout, out, cap, st);
+    } else if (op == AAFWI_CONV3_DGRAD) {
+        const long long cap = splits > 0 ? std::min(out_cap, splits * MN) : out_cap;
+        s = unet_conv3_dgrad(x, y, B, H, W, Cin, Cout, out, cap, st);
+    } else {
+        const long long want = splits > 0 ? splits : wgrad_splits(P);
+        s = unet_conv3_wgrad(x, y, B, H, W, Cin, Cout, (int)std::max(1LL, std::min(want, out_cap / MN)), out, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return uerr(nullptr, AAFWI_ERR_CUDA, std::string("unet_conv3x3: ") + cudaGetErrorString(e));
+    if (unet_take_error())
+        return uerr(nullptr, AAFWI_ERR_TIMEOUT,
+                    "unet_conv3x3: a tensor-core wait ran out; reset the device context (cudaDeviceReset) before "
+                    "continuing");
+    if (splits_used) *splits_used = s;
+    return AAFWI_OK;
+}
 
 }  // extern "C"

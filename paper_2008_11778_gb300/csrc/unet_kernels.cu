@@ -198,12 +198,14 @@ __device__ __forceinline__ unsigned tc_off(int r, int k)
 __device__ __forceinline__ unsigned tc_smem(const void *p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
 
 // Shared-memory matrix descriptor: start address, leading (K) and stride
-// (8-row group) byte offsets, descriptor version 1, no swizzle.
-__device__ __forceinline__ unsigned long long tc_desc(unsigned addr)
+// (8-row group) byte offsets, descriptor version 1, no swizzle.  Every field
+// is in 16-byte units (14 bits: addresses and offsets below 256 KB).
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo)
 {
-    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((T_LBO >> 4) & 0x3FFF) << 16) |
-           ((unsigned long long)((T_SBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr) { return tc_desc(addr, T_LBO, T_SBO); }
 
 // Instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N = TN, M = TM.
 constexpr unsigned TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TN >> 3) << 17) |
@@ -423,6 +425,330 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const Op<MODE> o, float *out, i
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Windowed implicit GEMM of the 3x3 convolutions whose operand channels C
+// (forward: C = Cin; data gradient: C = Cout, taps mirrored) are 16 times a
+// power of two.  M rows are positions q of the zero-padded pixel grid
+// [B][H+2][W+2], flattened; output q of tap (ky, kx) reads the input at
+// q + s ((ky-1)(W+2) + (kx-1)), s = +1 / -1, which for an interior q stays
+// inside the same image's padded grid.  A CTA computes T consecutive 128-row
+// tiles, [q0, q0 + 128 T), so the A operand of every tap and tile is one
+// window of the padded input, positions [q0 - (W+2) - 1, q0 + 128 T + (W+2) + 1),
+// read at a row offset: no im2col gather.  Window layout: channel group g
+// (8 channels = 16 bytes) of window position p at g GS + 16 p, the K-major
+// core-matrix layout with adjacent 8-row groups (SBO 128) and K groups GS
+// apart (LBO GS); a tap's operand starts 16 bytes per position further on.
+// Output rows at padding positions are computed and dropped.
+//
+// K runs over stages of cs channels (all 9 taps each): a stage is the window
+// of its channels and the weights [tn][9][cs] (K-major, 8-row groups 9 cs 2
+// bytes apart), copied by cp.async (16 bytes each, zero-filled at the
+// padding) into one of two buffers, so the copies of stage j+1 run under the
+// MMAs of stage j; one thread issues T x 9 x cs/16 MMAs (128 x tn x 16) per
+// stage into T accumulators in tensor memory and commits them to the
+// buffer's mbarrier.  Large layers split their stages over blockIdx.z (FP32
+// slices, summed by the consumer).
+// ---------------------------------------------------------------------------
+struct WinOp {
+    const unsigned short *t, *w;   // input [B][H][W][C], weights [N][9][C] (raw BF16 bits)
+    int B, H, W, C, N;
+    int sign;                      // +1 forward, -1 data gradient
+    int T;                         // 128-row tiles per CTA
+    int tn, tstride;               // N tile (multiple of 16, <= 256); tensor-memory columns per tile
+    int cs, lg_g, spz;             // channels per stage; log2(cs / 8); stages per CTA
+    int nw, gs;                    // window positions; bytes between the window's channel groups
+    int wbytes, stage_bytes, nbuf; // window bytes; window + weight bytes of a stage; buffers (1 or 2)
+};
+
+constexpr int WIN_TN_MAX = 256;
+
+__host__ __device__ inline int win_tmem_cols(int cols)
+{
+    int c = 32;
+    while (c < cols) c *= 2;
+    return c;
+}
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(__cvta_generic_to_global(src)),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+// Copies of stage s (channels [s cs, (s+1) cs)) into the buffer at `base`.
+__device__ __forceinline__ void win_load_stage(const WinOp &o, int q0, int n0, int s, unsigned base)
+{
+    const int tid = threadIdx.x, Wp = o.W + 2, Hp = o.H + 2, G = 1 << o.lg_g, KG = 9 * G;
+    const int c0 = s * o.cs;
+    {   // window: thread -> channel group g, positions p = tid / G, + 128 / G, ...
+        const int g = tid & (G - 1), pstep = 128 >> o.lg_g;
+        int p = tid >> o.lg_g;
+        // q = q0 - Wp - 1 + p, decoded from q + Hp Wp >= 0: padded row ra over
+        // the batch (image bi - 1, row py), column px
+        const int qq = q0 - Wp - 1 + p + Hp * Wp;
+        const int ra = qq / Wp;
+        int px = qq - ra * Wp;
+        int bi = ra / Hp, py = ra - bi * Hp;
+        for (; p < o.nw; p += pstep) {
+            const bool valid = bi >= 1 && bi <= o.B && py >= 1 && py <= o.H && px >= 1 && px <= o.W;
+            const unsigned short *src =
+                valid ? o.t + ((long long)((bi - 1) * o.H + py - 1) * o.W + px - 1) * o.C + c0 + 8 * g : o.t;
+            cp_async16(base + g * o.gs + p * 16, src, valid);
+            px += pstep;
+            while (px >= Wp) {
+                px -= Wp;
+                if (++py == Hp) {
+                    py = 0;
+                    ++bi;
+                }
+            }
+        }
+    }
+    {   // weights: piece (row r, K group kg = tap G + cg) <- w[n0 + r][tap][c0 + 8 cg ...]
+        const unsigned wb = base + o.wbytes;
+        const int K = 9 * o.C, dr = 128 / KG, dk = 128 - dr * KG;
+        int r = tid / KG, kg = tid - r * KG;
+        for (int i = tid; i < o.tn * KG; i += 128) {
+            const int tap = kg >> o.lg_g, cg = kg & (G - 1), n = n0 + r;
+            const bool valid = n < o.N;
+            const unsigned short *src = valid ? o.w + (long long)n * K + tap * o.C + c0 + 8 * cg : o.w;
+            cp_async16(wb + (r >> 3) * (KG * 128) + kg * 128 + (r & 7) * 16, src, valid);
+            r += dr;
+            kg += dk;
+            if (kg >= KG) {
+                kg -= KG;
+                ++r;
+            }
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128) k_conv_win(const WinOp o, float *out, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    __shared__ unsigned long long bars[2];
+    __shared__ unsigned tmem_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Wp = o.W + 2, Hp = o.H + 2, G = 1 << o.lg_g, KG = 9 * G;
+    const int q0 = blockIdx.x * (o.T * TM), n0 = blockIdx.y * o.tn, s0 = blockIdx.z * o.spz;
+    const int ns = min(o.spz, o.C / o.cs - s0);   // stages of this CTA
+    const int tcols = win_tmem_cols(o.T * o.tstride);
+    const unsigned sm0 = tc_smem(dsm);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&tmem_sh)),
+                     "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&bars[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    win_load_stage(o, q0, n0, s0, sm0);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_sh;
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(o.tn >> 3) << 17) |
+                           ((unsigned)(TM >> 4) << 24);
+    bool ok = true;
+    int issued = 0;   // stages whose MMAs were issued (stage j commits to bars[j % nbuf])
+    for (int s = 0; s < ns && ok; ++s) {
+        const int b = s % o.nbuf;
+        if (o.nbuf == 2 && s + 1 < ns) {
+            if (s >= 1)   // the MMAs of stage s - 1 have read the other buffer
+                ok = __syncthreads_and(tc_wait(tc_smem(&bars[(s - 1) & 1]), ((s - 1) >> 1) & 1)) != 0;
+            if (!ok) break;
+            win_load_stage(o, q0, n0, s0 + s + 1, sm0 + ((s + 1) & 1) * o.stage_bytes);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the copies visible to the tensor cores
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned base = sm0 + b * o.stage_bytes;
+            for (int t = 0; t < o.T; ++t) {
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap - 3 * ky;
+                    const int r0 = o.sign * ((ky - 1) * Wp + (kx - 1)) + Wp + 1 + t * TM;   // window row of tile row 0
+                    for (int j = 0; j < o.cs / 16; ++j) {
+                        const unsigned long long ad = tc_desc(base + 2 * j * o.gs + r0 * 16, o.gs, 128);
+                        const unsigned long long bd =
+                            tc_desc(base + o.wbytes + (tap * G + 2 * j) * 128, 128, KG * 128);
+                        const unsigned accum = (s > 0 || tap > 0 || j > 0) ? 1u : 0u;
+                        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                                         tmem + (unsigned)(t * o.tstride)),
+                                     "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                                     : "memory");
+                    }
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tc_smem(&bars[b]))
+                         : "memory");
+        }
+        issued = s + 1;
+        if (o.nbuf == 1 && s + 1 < ns) {   // one buffer: the MMAs of stage s read it before the next copies
+            ok = __syncthreads_and(tc_wait(tc_smem(&bars[0]), s & 1)) != 0;
+            if (ok) win_load_stage(o, q0, n0, s0 + s + 1, sm0);
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (issued > 0) {   // the last issued stage's commit covers every earlier MMA
+        const int l = issued - 1;
+        const bool done = tc_wait(tc_smem(&bars[l % o.nbuf]), (l / o.nbuf) & 1);
+        ok = __syncthreads_and(ok && done) != 0;
+    }
+    if (!ok) {
+        if (tid == 0) atomicOr(err, 1);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float *dst = out + (long long)blockIdx.z * o.B * o.H * o.W * o.N;
+        for (int t = 0; t < o.T; ++t) {
+            const int q = q0 + t * TM + warp * 32 + lane;
+            const int ra = q / Wp, px = q - ra * Wp, bi = ra / Hp, py = ra - bi * Hp;
+            const long long pixel = (bi < o.B && py >= 1 && py <= o.H && px >= 1 && px <= o.W)
+                                        ? ((long long)bi * o.H + py - 1) * o.W + px - 1
+                                        : -1;
+            for (int c = 0; c < o.tn; c += 16) {
+                unsigned v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                    "%12, %13, %14, %15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(t * o.tstride + c)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (pixel >= 0) {
+                    float *rp = dst + pixel * o.N + n0 + c;
+                    if (n0 + c + 16 <= o.N && (o.N & 3) == 0) {   // 16-byte stores
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4)
+                            *reinterpret_cast<float4 *>(rp + j) =
+                                make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                            __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (n0 + c + j < o.N) rp[j] = __uint_as_float(v[j]);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+}
+
+// Launch geometry of the windowed kernel for C operand channels and N
+// outputs; false when it does not apply (C not 16 times a power of two, an
+// unaligned input, or sizes beyond its limits).
+struct WinPlan {
+    WinOp o;
+    dim3 grid;
+    size_t smem;
+};
+
+int win_smem_limit()
+{
+    static int lim = -1;
+    if (lim < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) lim = 0;
+        lim -= 2048;   // the kernel's static shared memory and the alignment of the dynamic block
+        if (lim > 0 && cudaFuncSetAttribute(k_conv_win, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess)
+            lim = 0;
+    }
+    return lim;
+}
+
+int win_sm_count()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    }
+    return sms;
+}
+
+// Stage geometry for T tiles and cs channels: window positions, group
+// stride (padded so that the 8 threads of a 16-byte copy phase, consecutive
+// groups then positions, fall on distinct bank quads) and bytes.
+void win_stage(WinOp &o, int T, int cs)
+{
+    const int Wp = o.W + 2, G = cs / 8;
+    o.T = T;
+    o.cs = cs;
+    o.lg_g = 0;
+    while ((1 << o.lg_g) < G) ++o.lg_g;
+    o.nw = T * TM + 2 * Wp + 2;
+    const int step = G >= 8 ? 1 : 8 / G;
+    o.gs = ((o.nw + 7) / 8 * 8 + step) * 16;
+    o.wbytes = G * o.gs;
+    o.stage_bytes = o.wbytes + o.tn * 9 * cs * 2;
+}
+
+// max_splits bounds blockIdx.z (the FP32 slices the caller can hold).
+bool win_plan(const __nv_bfloat16 *t, const __nv_bfloat16 *w, ConvGeom g, int C, int N, int sign, int max_splits,
+              WinPlan &wp)
+{
+    if (C < 16 || C % 16 != 0 || ((C / 16) & (C / 16 - 1)) != 0 || N < 1 || C > 1024 ||
+        (reinterpret_cast<uintptr_t>(t) & 15) != 0 || (reinterpret_cast<uintptr_t>(w) & 15) != 0 ||
+        (long long)g.B * (g.H + 2) * (g.W + 2) + 8LL * TM > INT_MAX / 2)
+        return false;
+    const int lim = win_smem_limit(), sms = win_sm_count();
+    constexpr int kStageCap = 100 * 1024;   // one stage; two buffers stay below the shared-memory limit
+    WinOp &o = wp.o;
+    o.t = reinterpret_cast<const unsigned short *>(t);
+    o.w = reinterpret_cast<const unsigned short *>(w);
+    o.B = g.B, o.H = g.H, o.W = g.W, o.C = C, o.N = N, o.sign = sign;
+    o.tn = std::min(WIN_TN_MAX, (N + 15) / 16 * 16);
+    o.tstride = win_tmem_cols(o.tn);
+    const int ntn = (N + o.tn - 1) / o.tn;
+    const long long Q = (long long)g.B * (g.H + 2) * (g.W + 2);
+    int cs = C;
+    for (win_stage(o, 1, cs); cs > 16 && o.stage_bytes > kStageCap; win_stage(o, 1, cs)) cs /= 2;
+    const int nstages = C / cs;
+    o.nbuf = nstages > 1 ? 2 : 1;
+    int T = 1;
+    for (int cand : {4, 2}) {   // more tiles per CTA share the window and the weights
+        win_stage(o, cand, cs);
+        if (cand * o.tstride <= 512 && o.nbuf * o.stage_bytes <= lim && (Q + cand * TM - 1) / (cand * TM) * ntn >= sms) {
+            T = cand;
+            break;
+        }
+    }
+    win_stage(o, T, cs);
+    if (o.nbuf * o.stage_bytes > lim || o.wbytes >= (1 << 18) || o.gs >= (1 << 18)) return false;
+    const long long xt = (Q + T * TM - 1) / (T * TM);
+    int z = 1;   // split the stages over CTAs while the grid leaves SMs idle
+    while (xt * ntn * z < 2LL * sms && z * 2 <= nstages && z * 2 <= max_splits) z *= 2;
+    o.spz = nstages / z;
+    wp.grid = dim3((unsigned)xt, (unsigned)ntn, (unsigned)z);
+    wp.smem = (size_t)o.nbuf * o.stage_bytes;
+    return true;
+}
+
+// Returns the FP32 slices written (blockIdx.z extent).
+int win_launch(const WinPlan &wp, float *out, cudaStream_t st)
+{
+    count_launch();
+    k_conv_win<<<wp.grid, 128, wp.smem, st>>>(wp.o, out, unet_error_word());
+    return (int)wp.grid.z;
+}
+
 template <int MODE>
 int gemm(const __nv_bfloat16 *a, const __nv_bfloat16 *b, ConvGeom g, int M, int N, int K, int splits,
          float *out, cudaStream_t st)
@@ -453,24 +779,25 @@ int unet_conv3_fwd(const __nv_bfloat16 *x, const __nv_bfloat16 *w, int B, int H,
                     float *out, long long out_cap, cudaStream_t st)
 {
     ConvGeom g{B, H, W, Cin, Cout};
-    // split K when the output tiles alone leave SMs idle (deep levels, small batches)
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    const int sms = win_sm_count();
     const long long M = (long long)B * H * W, N = Cout;
+    const long long cap = std::max(1LL, out_cap / (M * N));
+    WinPlan wp;
+    if (win_plan(x, w, g, Cin, Cout, 1, (int)std::min<long long>(cap, 64), wp)) return win_launch(wp, out, st);
+    // split K when the output tiles alone leave SMs idle (deep levels, small batches)
     const long long tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
     long long splits = (2LL * sms + tiles - 1) / tiles;
-    splits = std::max(1LL, std::min(splits, out_cap / (M * N)));
+    splits = std::max(1LL, std::min(splits, cap));
     return gemm<CONV_FWD>(x, w, g, (int)M, Cout, 9 * Cin, (int)splits, out, st);
 }
 
 int unet_conv3_dgrad(const __nv_bfloat16 *dz, const __nv_bfloat16 *wt, int B, int H, int W, int Cin, int Cout,
-                      float *out, cudaStream_t st)
+                      float *out, long long out_cap, cudaStream_t st)
 {
     ConvGeom g{B, H, W, Cin, Cout};
+    const long long cap = std::max(1LL, out_cap / ((long long)B * H * W * Cin));
+    WinPlan wp;
+    if (win_plan(dz, wt, g, Cout, Cin, -1, (int)std::min<long long>(cap, 64), wp)) return win_launch(wp, out, st);
     return gemm<CONV_DGRAD>(dz, wt, g, B * H * W, Cin, 9 * Cout, 1, out, st);
 }
 

@@ -327,6 +327,37 @@ def load_eval_record(path=EVAL_RECORD):
     return out
 
 
+def network_rate(C=32, reps=20):
+    """CUDA-event times (best of `reps`) of the network (seeded He weights):
+    forward and training step (forward, backward, Adam) on a 16 x 96 x 256
+    training batch, and the forward on one 152 x 400 evaluation input."""
+    out = {"C": C, "gpu": torch.cuda.get_device_name(0)}
+    for key, (B, H, W), train_too in (("train_16x96x256", (16, 96, 256), True), ("eval_1x152x400", (1, 152, 400), False)):
+        net = aafwi.UNet(B, H, W, C)
+        net.set_params(he_init(net.nparam, C, 0))
+        g = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.randn((B, 2, H, W), device="cuda", generator=g)
+        t = 0.1 * torch.randn((B, H, W), device="cuda", generator=g)
+        y = torch.empty((B, H, W), device="cuda")
+        calls = [("forward_ms", lambda: net.forward(x, y))]
+        if train_too:
+            calls.append(("train_step_ms", lambda: net.train_step(x, t, 1e-6)))
+        for name, f in calls:
+            for _ in range(3):
+                f()
+            ms = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                f()
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            out.setdefault(key, {})[name] = min(ms)
+        net.close()
+    return out
+
+
 if __name__ == "__main__":
     import argparse
     import json
@@ -342,7 +373,11 @@ if __name__ == "__main__":
     ap.add_argument("--eval-only", action="store_true")
     ap.add_argument("--record", nargs="?", const=EVAL_RECORD, default=None,
                     help="write the evaluation record (default path: the committed record)")
+    ap.add_argument("--rate", action="store_true", help="time the network's forward and training step and stop")
     a = ap.parse_args()
+    if a.rate:
+        print(json.dumps({"unet_rate": network_rate()}))
+        raise SystemExit(0)
     if a.eval_only:
         params, meta = load_weights(a.out)
     else:
