@@ -453,7 +453,7 @@ class AALpInfo(ctypes.Structure):
                 ("rounds", ctypes.c_int), ("rows", ctypes.c_int)]
 
 
-def unet_conv3x3(op, a, b, B, H, W, Cin, Cout, splits=0, max_splits=8, stream=None):
+def unet_conv3x3(op, a, b, B, H, W, Cin, Cout, splits=0, max_splits=None, stream=None):
     """aafwi_unet_conv3x3: one 3x3 convolution GEMM of the U-Net on BF16 device
     tensors (NHWC activations; weights [Cout][3][3][Cin], or [Cin][3][3][Cout]
     for CONV3_DGRAD).  Returns the FP32 split slices [s][...] (their sum is the
@@ -464,6 +464,8 @@ def unet_conv3x3(op, a, b, B, H, W, Cin, Cout, splits=0, max_splits=8, stream=No
             raise TypeError("expected contiguous CUDA bfloat16 tensors")
     P = B * H * W
     MN = 9 * Cin * Cout if op == CONV3_WGRAD else P * (Cout if op == CONV3_FWD else Cin)
+    if max_splits is None:
+        max_splits = 256 if op == CONV3_WGRAD else 8
     cap = max(1, max_splits if splits <= 0 else min(splits, max_splits))
     out = torch.empty(cap * MN, device=a.device, dtype=torch.float32)
     s = ctypes.c_int(0)

@@ -25,17 +25,17 @@
 namespace aafwi {
 
 int unet_conv3_fwd(const __nv_bfloat16 *x, const __nv_bfloat16 *w, int B, int H, int W, int Cin, int Cout,
-                   float *out, long long out_cap, cudaStream_t st);
+                   const float *bias, __nv_bfloat16 *y, float *out, long long out_cap, cudaStream_t st);
 int unet_conv3_dgrad(const __nv_bfloat16 *dz, const __nv_bfloat16 *wt, int B, int H, int W, int Cin, int Cout,
                      float *out, long long out_cap, cudaStream_t st);
 int unet_conv3_wgrad(const __nv_bfloat16 *dz, const __nv_bfloat16 *x, int B, int H, int W, int Cin, int Cout,
-                     int splits, float *out, cudaStream_t st);
+                     int max_splits, float *out, cudaStream_t st);
 int unet_up_fwd(const __nv_bfloat16 *x, const __nv_bfloat16 *w, int B, int H, int W, int Cin, int Cout,
                 float *out, cudaStream_t st);
 int unet_up_dgrad(const __nv_bfloat16 *dy, const __nv_bfloat16 *w, int B, int H, int W, int Cin, int Cout,
                   float *out, cudaStream_t st);
 int unet_up_wgrad(const __nv_bfloat16 *x, const __nv_bfloat16 *dy, int B, int H, int W, int Cin, int Cout,
-                  int splits, float *out, cudaStream_t st);
+                  int max_splits, float *out, cudaStream_t st);
 
 namespace {
 
@@ -46,41 +46,83 @@ inline int nblk(long long n) { return (int)std::min<long long>((n + ET - 1) / ET
 
 #define GRID_LOOP(i, n) for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
-// y = bf16(act(sum_splits out + bias)) for an [M][N] GEMM result
-__global__ void k_epi(const float *out, int splits, long long MN, int N, const float *bias, int relu, bf16 *y)
+// The elementwise kernels work in chunks of 8 channels (every channel count of
+// the network is a multiple of 8): a thread moves 16 bytes of BF16 or 32 bytes
+// of FP32, with 32-bit index arithmetic (element counts below 2^31).  Each
+// element's arithmetic is the same as element by element.
+__device__ __forceinline__ void load8(const float *p, float (&v)[8])
 {
-    GRID_LOOP(i, MN) {
-        float v = 0.f;
-        for (int s = 0; s < splits; ++s) v += out[s * MN + i];
-        v += bias[i % N];
-        if (relu) v = fmaxf(v, 0.f);
-        y[i] = __float2bfloat16_rn(v);
+    const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+}
+
+__device__ __forceinline__ uint4 bf16x8(const float (&v)[8])
+{
+    unsigned h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) h[j] = __bfloat16_as_ushort(__float2bfloat16_rn(v[j]));
+    return make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+}
+
+// y = bf16(act(sum_splits out + bias)) over [MN] = [M][N], MN = 8 n8
+__global__ void k_epi(const float *out, int splits, int n8, int N, const float *bias, int relu, bf16 *y)
+{
+    const long long MN = 8LL * n8;
+    GRID_LOOP(i, n8) {
+        const int e = 8 * (int)i, c = e % N;
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int s = 0; s < splits; ++s) {
+            float u[8];
+            load8(out + s * MN + e, u);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] += u[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            v[j] += bias[c + j];
+            if (relu) v[j] = fmaxf(v[j], 0.f);
+        }
+        *reinterpret_cast<uint4 *>(y + e) = bf16x8(v);
     }
 }
 
-// upconv epilogue: out [Pin][4][C] -> y [B][2H][2W][C] with bias
+// upconv epilogue: out [Pin][4][C] (child q = 2 i + j of input pixel (y, x)) -> y [B][2H][2W][C] + bias
 __global__ void k_epi_up(const float *out, int B, int H, int W, int C, const float *bias, bf16 *y)
 {
-    const long long n = (long long)B * H * W * 4 * C;
-    GRID_LOOP(i, n) {
-        const int c = (int)(i % C);
-        const long long t = i / C;
-        const int q = (int)(t % 4);
-        const long long p = t / 4;
-        const int x = (int)(p % W), yy = (int)((p / W) % H), b = (int)(p / ((long long)W * H));
+    const int n8 = B * H * W * 4 * C / 8;
+    GRID_LOOP(i, n8) {
+        const int e = 8 * (int)i, c = e % C, t = e / C, q = t & 3, p = t >> 2;
+        const int x = p % W, yy = (p / W) % H, b = p / (W * H);
+        float v[8];
+        load8(out + e, v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] += bias[c + j];
         const long long dst = (((long long)b * 2 * H + 2 * yy + q / 2) * 2 * W + 2 * x + (q & 1)) * C + c;
-        y[dst] = __float2bfloat16_rn(out[i] + bias[c]);
+        *reinterpret_cast<uint4 *>(y + dst) = bf16x8(v);
     }
 }
 
-// dz = bf16(sum_splits g) * (y > 0)   (ReLU backward on the post-activation y)
-__global__ void k_relu_back(const float *g, int splits, long long n, const bf16 *y, bf16 *dz)
+// dz = bf16(sum_splits g) * (y > 0)   (ReLU backward on the post-activation y), n = 8 n8 elements
+__global__ void k_relu_back(const float *g, int splits, int n8, const bf16 *y, bf16 *dz)
 {
-    GRID_LOOP(i, n) {
-        float v = 0.f;
-        for (int s = 0; s < splits; ++s) v += g[s * n + i];
-        const bf16 vb = __float2bfloat16_rn(v);
-        dz[i] = __bfloat162float(y[i]) > 0.f ? vb : __float2bfloat16_rn(0.f);
+    const long long n = 8LL * n8;
+    GRID_LOOP(i, n8) {
+        const int e = 8 * (int)i;
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int s = 0; s < splits; ++s) {
+            float u[8];
+            load8(g + s * n + e, u);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] += u[j];
+        }
+        const uint4 yb = *reinterpret_cast<const uint4 *>(y + e);
+        const unsigned yw[4] = {yb.x, yb.y, yb.z, yb.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float yv = __uint_as_float(j & 1 ? yw[j / 2] & 0xFFFF0000u : yw[j / 2] << 16);
+            v[j] = yv > 0.f ? v[j] : 0.f;   // bf16 of 0 is +0, as the rounded sum masked to zero
+        }
+        *reinterpret_cast<uint4 *>(dz + e) = bf16x8(v);
     }
 }
 
@@ -94,20 +136,67 @@ __global__ void k_sum_splits(const float *parts, int splits, long long n, float 
     }
 }
 
-// bias gradient db[c] = sum_p dz[p][c]: one block per channel, fixed order
-__global__ void k_bias_grad(const bf16 *dz, long long P, int C, float *db)
+// The same for many slices: 8 lanes per output sum contiguous slice ranges,
+// then the lane sums are added in lane order (fixed order; out may be parts).
+__global__ void k_sum_splits_wide(const float *parts, int splits, long long n, float *out)
 {
-    __shared__ float sh[ET];
-    const int c = blockIdx.x;
-    float acc = 0.f;
-    for (long long p = threadIdx.x; p < P; p += ET) acc += __bfloat162float(dz[p * C + c]);
-    sh[threadIdx.x] = acc;
+    __shared__ float sh[8][32];
+    const int o = threadIdx.x & 31, l = threadIdx.x >> 5;
+    const long long i = blockIdx.x * 32LL + o;
+    const int per = (splits + 7) / 8, s0 = l * per, s1 = min(splits, s0 + per);
+    float v = 0.f;
+    if (i < n)
+        for (int s = s0; s < s1; ++s) v += parts[(long long)s * n + i];
+    sh[l][o] = v;
     __syncthreads();
-    for (int o = ET / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
+    if (l == 0 && i < n) {
+        float t = sh[0][o];
+        for (int j = 1; j < 8; ++j) t += sh[j][o];
+        out[i] = t;
     }
-    if (threadIdx.x == 0) db[c] = sh[0];
+}
+
+// Column sums of x [P][C] (BF16, C a multiple of 8, C / 8 <= ET), each row r
+// weighted by wrow[r] when wrow is given, over the row block [b R, (b+1) R):
+// part[b][c] = sum_r wrow[r] x[r][c], and part[b][C] = sum_r wrow[r] when
+// ones.  Thread t reads 16 bytes (channels 8 (t % (C/8)) ..) of rows
+// t / (C/8), + ET / (C/8), ...; the row lanes are added in a fixed order.
+// sum_slices then adds the blocks: a deterministic reduction over P.
+constexpr int COLSUM_BLOCKS = 512;
+__global__ void k_colsum_partial(const bf16 *x, const float *wrow, long long P, int C, long long R, int ones,
+                                 float *part)
+{
+    __shared__ float sh[ET * 8];
+    __shared__ float shw[ET];
+    const int t = threadIdx.x, q = C / 8, per = ET / q, cg = t % q, rl = t / q;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, accw = 0.f;
+    if (rl < per) {
+        const long long r1 = std::min(P, (blockIdx.x + 1) * R);
+        for (long long r = blockIdx.x * R + rl; r < r1; r += per) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(x + r * C) + cg);
+            const float w = wrow ? wrow[r] : 1.f;
+            const unsigned u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                acc[2 * j] += w * __uint_as_float(u[j] << 16);
+                acc[2 * j + 1] += w * __uint_as_float(u[j] & 0xFFFF0000u);
+            }
+            accw += w;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sh[t * 8 + j] = acc[j];
+    shw[t] = accw;
+    __syncthreads();
+    if (t < C) {   // channel t = 8 cg + j
+        float v = 0.f;
+        for (int l = 0; l < per; ++l) v += sh[(l * q + t / 8) * 8 + (t & 7)];
+        part[(long long)blockIdx.x * (C + ones) + t] = v;
+    } else if (ones && t == C) {
+        float v = 0.f;
+        for (int l = 0; l < per; ++l) v += shw[l * q];
+        part[(long long)blockIdx.x * (C + 1) + C] = v;
+    }
 }
 
 // bias gradient of an upconv from its fine-grid output gradient dy [Pfine][C]
@@ -147,26 +236,34 @@ __global__ void k_maxpool_back(const float *dy, const unsigned char *arg, int B,
     }
 }
 
-// concat [P][Ca] ++ [P][Cb] -> [P][Ca+Cb]
-__global__ void k_concat(const bf16 *a, int Ca, const bf16 *b, int Cb, long long P, bf16 *y)
+// concat [P][Ca] ++ [P][Cb] -> [P][Ca+Cb]  (8-channel chunks)
+__global__ void k_concat(const bf16 *a, int Ca, const bf16 *b, int Cb, int P, bf16 *y)
 {
-    const int C = Ca + Cb;
-    GRID_LOOP(i, P * C) {
-        const long long p = i / C;
-        const int c = (int)(i % C);
-        y[i] = c < Ca ? a[p * Ca + c] : b[p * Cb + c - Ca];
+    const int C = Ca + Cb, n8 = P * (C / 8);
+    GRID_LOOP(i, n8) {
+        const int e = 8 * (int)i, p = e / C, c = e - p * C;
+        *reinterpret_cast<uint4 *>(y + e) = c < Ca ? *reinterpret_cast<const uint4 *>(a + (long long)p * Ca + c)
+                                                   : *reinterpret_cast<const uint4 *>(b + (long long)p * Cb + c - Ca);
     }
 }
 
 // split the FP32 gradient of a concat: first Ca channels -> ga (bf16), the rest added to gb (FP32)
-__global__ void k_concat_back(const float *g, int Ca, int Cb, long long P, bf16 *ga, float *gb)
+__global__ void k_concat_back(const float *g, int Ca, int Cb, int P, bf16 *ga, float *gb)
 {
-    const int C = Ca + Cb;
-    GRID_LOOP(i, P * C) {
-        const long long p = i / C;
-        const int c = (int)(i % C);
-        if (c < Ca) ga[p * Ca + c] = __float2bfloat16_rn(g[i]);
-        else gb[p * Cb + c - Ca] += g[i];
+    const int C = Ca + Cb, n8 = P * (C / 8);
+    GRID_LOOP(i, n8) {
+        const int e = 8 * (int)i, p = e / C, c = e - p * C;
+        float v[8];
+        load8(g + e, v);
+        if (c < Ca) {
+            *reinterpret_cast<uint4 *>(ga + (long long)p * Ca + c) = bf16x8(v);
+        } else {
+            float *d = gb + (long long)p * Cb + c - Ca;
+            float u[8];
+            load8(d, u);
+            *reinterpret_cast<float4 *>(d) = make_float4(u[0] + v[0], u[1] + v[1], u[2] + v[2], u[3] + v[3]);
+            *reinterpret_cast<float4 *>(d + 4) = make_float4(u[4] + v[4], u[5] + v[5], u[6] + v[6], u[7] + v[7]);
+        }
     }
 }
 
@@ -225,39 +322,33 @@ __global__ void k_mse(const float *out, const float *t, long long P, float *dout
 
 __global__ void k_mse_finish(const double *part, int nb, long long P, double *loss)
 {
-    if (threadIdx.x == 0) {
-        double a = 0.0;
-        for (int i = 0; i < nb; ++i) a += part[i];
-        *loss = 0.5 * a / (double)P;
-    }
-}
-
-// head backward: gx[p][c] = dout[p] w[c] (FP32), dw[c] = sum_p dout[p] x[p][c], db = sum dout
-__global__ void k_head_back_x(const float *dout, long long P, int C, const bf16 *w, float *gx)
-{
-    GRID_LOOP(i, P * C) {
-        const long long p = i / C;
-        const int c = (int)(i % C);
-        gx[i] = dout[p] * __bfloat162float(w[c]);
-    }
-}
-
-__global__ void k_head_back_w(const float *dout, const bf16 *x, long long P, int C, float *dw, float *db)
-{
-    __shared__ float sh[ET];
-    const int c = blockIdx.x;   // c == C: bias
-    float acc = 0.f;
-    for (long long p = threadIdx.x; p < P; p += ET)
-        acc += c < C ? dout[p] * __bfloat162float(x[p * C + c]) : dout[p];
-    sh[threadIdx.x] = acc;
+    __shared__ double sh[ET];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nb; i += ET) a += part[i];
+    sh[threadIdx.x] = a;
     __syncthreads();
     for (int o = ET / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        if (c < C) dw[c] = sh[0];
-        else db[0] = sh[0];
+    if (threadIdx.x == 0) *loss = 0.5 * sh[0] / (double)P;
+}
+
+// head backward: gx[p][c] = dout[p] w[c] (FP32); dw[c] = sum_p dout[p] x[p][c] and db = sum dout by
+// k_colsum_partial (rows weighted by dout, a ones column)
+__global__ void k_head_back_x(const float *dout, int P, int C, const bf16 *w, float *gx)
+{
+    const int n8 = P * (C / 8);
+    GRID_LOOP(i, n8) {
+        const int e = 8 * (int)i, p = e / C, c = e - p * C;
+        const float d = dout[p];
+        float4 lo, hi;
+        lo.x = d * __bfloat162float(w[c]), lo.y = d * __bfloat162float(w[c + 1]);
+        lo.z = d * __bfloat162float(w[c + 2]), lo.w = d * __bfloat162float(w[c + 3]);
+        hi.x = d * __bfloat162float(w[c + 4]), hi.y = d * __bfloat162float(w[c + 5]);
+        hi.z = d * __bfloat162float(w[c + 6]), hi.w = d * __bfloat162float(w[c + 7]);
+        *reinterpret_cast<float4 *>(gx + e) = lo;
+        *reinterpret_cast<float4 *>(gx + e + 4) = hi;
     }
 }
 
@@ -379,6 +470,7 @@ struct aafwi_unet {
     float *gacc = nullptr, *gacc2 = nullptr;   // FP32 activation-gradient accumulators
     bf16 *gb1 = nullptr, *gb2 = nullptr;       // BF16 activation gradients
     double *lpart = nullptr, *loss = nullptr;
+    float *bpart = nullptr;   // column-sum block partials [COLSUM_BLOCKS][8 C + 1]
     bool retired = false;   // a tensor-core wait ran out: every later call is refused
     std::string msg;
 };
@@ -434,20 +526,48 @@ const bf16 *wb(const aafwi_unet *u, const Conv &c) { return u->Pb + c.w; }
 // forward of one 3x3 conv + bias + ReLU into y
 void conv_fwd(aafwi_unet *u, const Conv &c, const bf16 *x, int B, int H, int W, bf16 *y, cudaStream_t st)
 {
-    const int s = unet_conv3_fwd(x, wb(u, c), B, H, W, c.Cin, c.Cout, u->gemm, u->gemm_size, st);
-    const long long MN = (long long)B * H * W * c.Cout;
-    count_launch();
-    k_epi<<<nblk(MN), ET, 0, st>>>(u->gemm, s, MN, c.Cout, u->P + c.b, 1, y);
+    const int s = unet_conv3_fwd(x, wb(u, c), B, H, W, c.Cin, c.Cout, u->P + c.b, y, u->gemm, u->gemm_size, st);
+    if (s > 0) {   // split slices: sum, bias, ReLU, BF16
+        const long long MN = (long long)B * H * W * c.Cout;
+        count_launch();
+        k_epi<<<nblk(MN / 8), ET, 0, st>>>(u->gemm, s, (int)(MN / 8), c.Cout, u->P + c.b, 1, y);
+    }
 }
 
 void up_fwd(aafwi_unet *u, const Conv &c, const bf16 *x, int B, int H, int W, bf16 *y, cudaStream_t st)
 {
     unet_up_fwd(x, wb(u, c), B, H, W, c.Cin, c.Cout, u->gemm, st);
     count_launch();
-    k_epi_up<<<nblk((long long)B * H * W * 4 * c.Cout), ET, 0, st>>>(u->gemm, B, H, W, c.Cout, u->P + c.b, y);
+    k_epi_up<<<nblk((long long)B * H * W * c.Cout / 2), ET, 0, st>>>(u->gemm, B, H, W, c.Cout, u->P + c.b, y);
 }
 
-int wgrad_splits(long long P) { return (int)std::max<long long>(1, std::min<long long>(64, P / 2048)); }
+// out[i] = sum over the split slices of parts [splits][n] (out may be parts)
+void sum_slices(const float *parts, int splits, long long n, float *out, cudaStream_t st)
+{
+    count_launch();
+    if (splits <= 8) k_sum_splits<<<nblk(n), ET, 0, st>>>(parts, splits, n, out);
+    else k_sum_splits_wide<<<(unsigned)((n + 31) / 32), ET, 0, st>>>(parts, splits, n, out);
+}
+
+// out[c] = sum_r wrow[r] x[r][c] over the P rows of x [P][C] (wrow NULL: 1),
+// and out[C] = sum_r wrow[r] when ones
+void colsum(aafwi_unet *u, const bf16 *x, const float *wrow, long long P, int C, int ones, float *out, cudaStream_t st)
+{
+    const long long nb = std::max(1LL, std::min<long long>(COLSUM_BLOCKS, P / 512));
+    const long long R = (P + nb - 1) / nb;
+    count_launch();
+    k_colsum_partial<<<(unsigned)nb, ET, 0, st>>>(x, wrow, P, C, R, ones, u->bpart);
+    sum_slices(u->bpart, (int)nb, C + ones, out, st);
+}
+
+// db = sum over the P rows of dz [P][C]
+void bias_grad(aafwi_unet *u, const bf16 *dz, long long P, int C, float *db, cudaStream_t st)
+{
+    colsum(u, dz, nullptr, P, C, 0, db, st);
+}
+
+// K splits a weight gradient may write into u->gemm
+int wgrad_cap(const aafwi_unet *u, const Conv &c) { return (int)std::max(1LL, std::min(1024LL, u->gemm_size / c.nw())); }
 
 // Backward of y = relu(conv3(x) + b): gy (FP32 [P][Cout]) -> dW, db (into u->G),
 // returns gx in FP32 (u->gemm, its split slices summed into the first) when want_gx.
@@ -455,20 +575,17 @@ void conv_back(aafwi_unet *u, const Conv &c, const bf16 *x, const bf16 *y, const
                bool want_gx, cudaStream_t st)
 {
     const long long P = (long long)B * H * W;
-    count_launch(3);
-    k_relu_back<<<nblk(P * c.Cout), ET, 0, st>>>(gy, 1, P * c.Cout, y, u->gb1);
-    k_bias_grad<<<c.Cout, ET, 0, st>>>(u->gb1, P, c.Cout, u->G + c.b);
-    const int s = unet_conv3_wgrad(u->gb1, x, B, H, W, c.Cin, c.Cout, wgrad_splits(P), u->gemm, st);
-    k_sum_splits<<<nblk(c.nw()), ET, 0, st>>>(u->gemm, s, c.nw(), u->G + c.w);
+    count_launch();
+    k_relu_back<<<nblk(P * c.Cout / 8), ET, 0, st>>>(gy, 1, (int)(P * c.Cout / 8), y, u->gb1);
+    bias_grad(u, u->gb1, P, c.Cout, u->G + c.b, st);
+    const int s = unet_conv3_wgrad(u->gb1, x, B, H, W, c.Cin, c.Cout, wgrad_cap(u, c), u->gemm, st);
+    sum_slices(u->gemm, s, c.nw(), u->G + c.w, st);
     if (want_gx) {
         count_launch();
         bf16 *wt = u->Wt;
         k_transpose_w<<<nblk(c.nw()), ET, 0, st>>>(wb(u, c), c.Cout, c.Cin, wt);
         const int sx = unet_conv3_dgrad(u->gb1, wt, B, H, W, c.Cin, c.Cout, u->gemm, u->gemm_size, st);
-        if (sx > 1) {   // sum the slices in place into the first
-            count_launch();
-            k_sum_splits<<<nblk(P * c.Cin), ET, 0, st>>>(u->gemm, sx, P * c.Cin, u->gemm);
-        }
+        if (sx > 1) sum_slices(u->gemm, sx, P * c.Cin, u->gemm, st);   // the slices, in place into the first
     }
 }
 
@@ -476,10 +593,9 @@ void conv_back(aafwi_unet *u, const Conv &c, const bf16 *x, const bf16 *y, const
 void up_back(aafwi_unet *u, const Conv &c, const bf16 *x, const bf16 *gy, int B, int H, int W, cudaStream_t st)
 {
     const long long Pin = (long long)B * H * W;
-    count_launch(2);
-    k_bias_grad<<<c.Cout, ET, 0, st>>>(gy, 4 * Pin, c.Cout, u->G + c.b);
-    const int s = unet_up_wgrad(x, gy, B, H, W, c.Cin, c.Cout, wgrad_splits(Pin), u->gemm, st);
-    k_sum_splits<<<nblk(c.nw()), ET, 0, st>>>(u->gemm, s, c.nw(), u->G + c.w);
+    bias_grad(u, gy, 4 * Pin, c.Cout, u->G + c.b, st);
+    const int s = unet_up_wgrad(x, gy, B, H, W, c.Cin, c.Cout, wgrad_cap(u, c), u->gemm, st);
+    sum_slices(u->gemm, s, c.nw(), u->G + c.w, st);
     unet_up_dgrad(gy, wb(u, c), B, H, W, c.Cin, c.Cout, u->gemm, st);
 }
 
@@ -505,7 +621,7 @@ void forward(aafwi_unet *u, const float *xin, int B, cudaStream_t st)
         up_fwd(u, u->L[li++], x, B, H / 2, W / 2, u->up[l], st);
         const long long P = (long long)B * H * W;
         count_launch();
-        k_concat<<<nblk(P * 2 * Cl(u, l)), ET, 0, st>>>(u->up[l], Cl(u, l), u->eb[l], Cl(u, l), P, u->cat[l]);
+        k_concat<<<nblk(P * 2 * Cl(u, l) / 8), ET, 0, st>>>(u->up[l], Cl(u, l), u->eb[l], Cl(u, l), (int)P, u->cat[l]);
         conv_fwd(u, u->L[li++], u->cat[l], B, H, W, u->da[l], st);
         conv_fwd(u, u->L[li++], u->da[l], B, H, W, u->db[l], st);
         x = u->db[l];
@@ -522,9 +638,9 @@ void backward(aafwi_unet *u, int B, cudaStream_t st)
 {
     const long long P0 = (long long)B * u->H * u->W;
     const int C = u->C;
-    count_launch(2);
-    k_head_back_w<<<C + 1, ET, 0, st>>>(u->dout, u->db[0], P0, C, u->G + u->head_w, u->G + u->head_b);
-    k_head_back_x<<<nblk(P0 * C), ET, 0, st>>>(u->dout, P0, C, u->Pb + u->head_w, u->gacc);
+    colsum(u, u->db[0], u->dout, P0, C, 1, u->G + u->head_w, st);   // head weights, then its bias (head_b = head_w + C)
+    count_launch();
+    k_head_back_x<<<nblk(P0 * C / 8), ET, 0, st>>>(u->dout, (int)P0, C, u->Pb + u->head_w, u->gacc);
     float *gskip[3];
     {
         long long off = 0;
@@ -542,7 +658,7 @@ void backward(aafwi_unet *u, int B, cudaStream_t st)
         conv_back(u, u->L[li--], u->cat[l], u->da[l], u->gemm, B, H, W, true, st);   // dec a
         cudaMemsetAsync(gskip[l], 0, P * Cv * sizeof(float), st);
         count_launch();
-        k_concat_back<<<nblk(P * 2 * Cv), ET, 0, st>>>(u->gemm, Cv, Cv, P, u->gb2, gskip[l]);
+        k_concat_back<<<nblk(P * 2 * Cv / 8), ET, 0, st>>>(u->gemm, Cv, Cv, (int)P, u->gb2, gskip[l]);
         const bf16 *xin = l == 2 ? u->bb : u->db[l + 1];
         up_back(u, u->L[li--], xin, u->gb2, B, H / 2, W / 2, st);               // upconv
         g = u->gemm;                   // gradient of the coarser level's output
@@ -568,7 +684,7 @@ void loss_and_grad(aafwi_unet *u, const float *xin, const float *target, int B, 
     const int nb = (int)std::min<long long>(4096, (P + ET - 1) / ET);
     count_launch(2);
     k_mse<<<nb, ET, 0, st>>>(u->out, target, P, u->dout, u->lpart);
-    k_mse_finish<<<1, 32, 0, st>>>(u->lpart, nb, P, u->loss);
+    k_mse_finish<<<1, ET, 0, st>>>(u->lpart, nb, P, u->loss);
     backward(u, B, st);
 }
 
@@ -578,8 +694,11 @@ extern "C" {
 
 int aafwi_unet_create(int Bmax, int H, int W, int C, aafwi_unet **out)
 {
-    if (!out || Bmax < 1 || H < 8 || W < 8 || H % 8 || W % 8 || C < 8 || C % 8)
-        return uerr(nullptr, AAFWI_ERR_ARG, "unet_create: need Bmax >= 1, H, W multiples of 8, C multiple of 8");
+    if (!out || Bmax < 1 || H < 8 || W < 8 || H % 8 || W % 8 || C < 8 || C % 8 || C > 1024 ||
+        (long long)Bmax * H * W * 16 * C >= INT_MAX)
+        return uerr(nullptr, AAFWI_ERR_ARG,
+                    "unet_create: need Bmax >= 1, H, W multiples of 8, C multiple of 8 (at most 1024), "
+                    "Bmax H W 16 C below 2^31");
     *out = nullptr;
     auto *u = new aafwi_unet();
     u->Bmax = Bmax;
@@ -617,19 +736,19 @@ int aafwi_unet_create(int Bmax, int H, int W, int C, aafwi_unet **out)
     for (auto &c : u->L) maxw = std::max(maxw, c.nw());
     u->wt_size = maxw;
     const long long P0 = (long long)Bmax * H * W;
-    // largest GEMM output: max over layers of M*N*splits
+    // largest GEMM output (the split slices of the weight gradients are bounded by this size)
     long long gs = 0;
     for (int l = 0; l < 4; ++l) {
         const long long P = P0 >> (2 * l);
         gs = std::max(gs, P * (8LL * C) * 2);        // activations x widest channels (concat)
-        gs = std::max(gs, (long long)wgrad_splits(P) * maxw);
     }
     u->gemm_size = gs;
     bool ok = ualloc(u, &u->P, off) && ualloc(u, &u->G, off) && ualloc(u, &u->Mm, off) && ualloc(u, &u->Vv, off) &&
               ualloc(u, &u->Pb, off) && ualloc(u, &u->Wt, maxw) && ualloc(u, &u->xin, P0 * 2) &&
               ualloc(u, &u->gemm, gs) && ualloc(u, &u->gacc, P0 * 8 * C) && ualloc(u, &u->gacc2, P0 * 2 * C) &&
               ualloc(u, &u->gb1, P0 * 8 * C) && ualloc(u, &u->gb2, P0 * 8 * C) && ualloc(u, &u->out, P0) &&
-              ualloc(u, &u->dout, P0) && ualloc(u, &u->lpart, 4096) && ualloc(u, &u->loss, 1);
+              ualloc(u, &u->dout, P0) && ualloc(u, &u->lpart, 4096) && ualloc(u, &u->loss, 1) &&
+              ualloc(u, &u->bpart, (size_t)COLSUM_BLOCKS * (8 * C + 1));
     for (int l = 0; l < 3 && ok; ++l) {
         const long long P = P0 >> (2 * l);
         const int Cv = C << l;
@@ -776,13 +895,14 @@ int aafwi_unet_conv3x3(int op, const void *a, const void *b, int B, int H, int W
     int s = 1;
     if (op == AAFWI_CONV3_FWD) {
         const long long cap = splits > 0 ? std::min(out_cap, splits * MN) : out_cap;
-        s = unet_conv3_fwd(x, y, B, H, W, Cin, Cout, out, cap, st);
+        s = unet_conv3_fwd(x, y, B, H, W, Cin, Cout, nullptr, nullptr, out, cap, st);
     } else if (op == AAFWI_CONV3_DGRAD) {
         const long long cap = splits > 0 ? std::min(out_cap, splits * MN) : out_cap;
         s = unet_conv3_dgrad(x, y, B, H, W, Cin, Cout, out, cap, st);
     } else {
-        const long long want = splits > 0 ? splits : wgrad_splits(P);
-        s = unet_conv3_wgrad(x, y, B, H, W, Cin, Cout, (int)std::max(1LL, std::min(want, out_cap / MN)), out, st);
+        const long long cap = std::min(1024LL, out_cap / MN);
+        s = unet_conv3_wgrad(x, y, B, H, W, Cin, Cout, (int)(splits > 0 ? std::min<long long>(splits, cap) : cap), out,
+                             st);
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -86,7 +86,7 @@ def test_conv3_data_gradient_matches_oracle(A, shape):
     assert (err <= bound(9 * Cout, S)).all(), (s, float((err / (S + 1e-30)).max()))
 
 
-@pytest.mark.parametrize("shape", SHAPES[:2] + SHAPES[5:], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
 def test_conv3_weight_gradient_matches_oracle(A, shape):
     from oracle import unet as U
     B, H, W, Cin, Cout = shape
@@ -115,6 +115,20 @@ def test_conv3_forward_split_slices_sum_to_one_result(A):
     assert (s1, s4) == (1, 4)
     y1, y4 = o1.double().sum(0), o4.double().sum(0)
     assert float((y1 - y4).abs().max()) <= 1e-5 * float(y1.abs().max())
+
+
+def test_conv3_weight_gradient_one_span_equals_many(A):
+    """The windowed weight gradient with one position span (all stages in
+    one CTA, two buffers in turn) and with its own split: the same result."""
+    B, H, W, Cin, Cout = 2, 24, 64, 64, 64
+    rng = np.random.default_rng(9)
+    x, _ = bf16_pair(rng, (B, H, W, Cin))
+    dz, _ = bf16_pair(rng, (B, H, W, Cout))
+    o1, s1 = A.unet_conv3x3(A.CONV3_WGRAD, dz, x, B, H, W, Cin, Cout, splits=1)
+    on, sn = A.unet_conv3x3(A.CONV3_WGRAD, dz, x, B, H, W, Cin, Cout)
+    assert s1 == 1 and sn > 1
+    y1, yn = o1.double().sum(0), on.double().sum(0)
+    assert float((y1 - yn).abs().max()) <= 1e-5 * float(y1.abs().max())
 
 
 def test_conv3_rejects_bad_arguments(A):
