@@ -30,7 +30,7 @@ int unet_conv3_dgrad(const __nv_bfloat16 *dz, const __nv_bfloat16 *wt, int B, in
                      float *out, long long out_cap, cudaStream_t st);
 int unet_conv3_wgrad(const __nv_bfloat16 *dz, const __nv_bfloat16 *x, int B, int H, int W, int Cin, int Cout,
                      int max_splits, float *out, cudaStream_t st);
-int unet_up_fwd(const __nv_bfloat16 *x, const __nv_bfloat16 *w, int B, int H, int W, int Cin, int Cout,
+int unet_up_fwd(const __nv_bfloat16 *x, const __nv_bfloat16 *wt, int B, int H, int W, int Cin, int Cout,
                 float *out, cudaStream_t st);
 int unet_up_dgrad(const __nv_bfloat16 *dy, const __nv_bfloat16 *w, int B, int H, int W, int Cin, int Cout,
                   float *out, cudaStream_t st);
@@ -275,6 +275,15 @@ __global__ void k_transpose_w(const bf16 *w, int Cout, int Cin, bf16 *wt)
         const int tap = (int)((i / Cin) % 9);
         const int co = (int)(i / (9LL * Cin));
         wt[((long long)ci * 9 + tap) * Cout + co] = w[i];
+    }
+}
+
+// upconv weights w [Cin][4 Cout] -> wt [4 Cout][Cin]
+__global__ void k_transpose_up(const bf16 *w, int Cin, int N4, bf16 *wt)
+{
+    GRID_LOOP(i, (long long)Cin * N4) {
+        const int n = (int)(i % N4), ci = (int)(i / N4);
+        wt[(long long)n * Cin + ci] = w[i];
     }
 }
 
@@ -536,7 +545,9 @@ void conv_fwd(aafwi_unet *u, const Conv &c, const bf16 *x, int B, int H, int W, 
 
 void up_fwd(aafwi_unet *u, const Conv &c, const bf16 *x, int B, int H, int W, bf16 *y, cudaStream_t st)
 {
-    unet_up_fwd(x, wb(u, c), B, H, W, c.Cin, c.Cout, u->gemm, st);
+    count_launch();
+    k_transpose_up<<<nblk(c.nw()), ET, 0, st>>>(wb(u, c), c.Cin, 4 * c.Cout, u->Wt);
+    unet_up_fwd(x, u->Wt, B, H, W, c.Cin, c.Cout, u->gemm, st);
     count_launch();
     k_epi_up<<<nblk((long long)B * H * W * c.Cout / 2), ET, 0, st>>>(u->gemm, B, H, W, c.Cout, u->P + c.b, y);
 }

@@ -119,6 +119,11 @@ __device__ __forceinline__ void fillA(const Op<MODE> &o, int m, int k0, int ke, 
     } else {  // UP_DGRAD: m = coarse pixel, k = q * Cout + co; dy [B][2H][2W][Cout]
         const Pix q0 = pix(g, m);
         int q = k0 / g.Cout, co = k0 - q * g.Cout;
+        if ((g.Cout & 15) == 0 && k0 + 16 <= ke) {   // 16 channels of one child pixel
+            const int Y = 2 * q0.y + q / 2, X = 2 * q0.x + (q & 1);
+            load16(o.a + (((long long)q0.b * 2 * g.H + Y) * 2 * g.W + X) * g.Cout + co, dst);
+            return;
+        }
         for (int i = 0; i < 16; ++i) {
             unsigned short v = 0;
             if (k0 + i < ke) {
@@ -138,13 +143,11 @@ template <int MODE>
 __device__ __forceinline__ void fillB(const Op<MODE> &o, int n, int k0, int ke, unsigned short *dst)
 {
     const ConvGeom &g = o.g;
-    if (MODE == CONV_FWD || MODE == CONV_DGRAD || MODE == UP_DGRAD) {
-        // weights stored N-major with K contiguous: w[n][k]
+    if (MODE == CONV_FWD || MODE == CONV_DGRAD || MODE == UP_DGRAD || MODE == UP_FWD) {
+        // weights stored N-major with K contiguous: w[n][k] (the upconv forward takes w^T [4 Cout][Cin])
         if ((o.K & 15) == 0 && k0 + 16 <= ke) load16(o.b + (long long)n * o.K + k0, dst);
         else
             for (int i = 0; i < 16; ++i) dst[i] = k0 + i < ke ? o.b[(long long)n * o.K + k0 + i] : 0;
-    } else if (MODE == UP_FWD) {  // w [Cin][4 Cout]: B(k = cin, n)
-        for (int i = 0; i < 16; ++i) dst[i] = k0 + i < ke ? o.b[(long long)(k0 + i) * o.N + n] : 0;
     }
 }
 
@@ -1165,11 +1168,12 @@ int unet_conv3_wgrad(const __nv_bfloat16 *dz, const __nv_bfloat16 *x, int B, int
     return gemm<CONV_WGRAD>(dz, x, g, Cout, 9 * Cin, P, std::min(max_splits, std::max(1, P / 512)), out, st);
 }
 
-int unet_up_fwd(const __nv_bfloat16 *x, const __nv_bfloat16 *w, int B, int H, int W, int Cin, int Cout,
+// wt: the upconv weights transposed, [4 Cout][Cin]
+int unet_up_fwd(const __nv_bfloat16 *x, const __nv_bfloat16 *wt, int B, int H, int W, int Cin, int Cout,
                  float *out, cudaStream_t st)
 {
     ConvGeom g{B, H, W, Cin, Cout};
-    return gemm<UP_FWD>(x, w, g, B * H * W, 4 * Cout, Cin, 1, out, st);
+    return gemm<UP_FWD>(x, wt, g, B * H * W, 4 * Cout, Cin, 1, out, st);
 }
 
 int unet_up_dgrad(const __nv_bfloat16 *dy, const __nv_bfloat16 *w, int B, int H, int W, int Cin, int Cout,
