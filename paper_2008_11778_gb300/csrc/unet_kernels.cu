@@ -817,23 +817,31 @@ bool win_plan(const __nv_bfloat16 *t, const __nv_bfloat16 *w, ConvGeom g, int C,
     o.tn = std::min(WIN_TN_MAX, (N + 15) / 16 * 16);
     o.tstride = win_tmem_cols(o.tn);
     const int ntn = (N + o.tn - 1) / o.tn;
-    int cs = C;
-    for (win_stage(o, 1, cs); cs > 16 && o.stage_bytes > kStageCap; win_stage(o, 1, cs)) cs /= 2;
-    const int nstages = C / cs;
-    o.nbuf = nstages > 1 ? 2 : 1;
-    int T = 1;
-    for (int cand : {4, 2}) {   // more tiles per CTA share the window and the weights
-        win_stage(o, cand, cs);
-        if (cand * o.tstride <= 512 && o.nbuf * o.stage_bytes <= lim && (Q + cand * TM - 1) / (cand * TM) * ntn >= sms) {
+    // Four tiles per CTA where the tensor memory allows: an MMA costs the same for
+    // any N, so the tiles share each stage's weights (the deep layers' copies are
+    // mostly weights); the channel stage shrinks until two buffers fit, and the
+    // stages split over CTAs (blockIdx.z) while the grid has fewer CTAs than SMs.
+    int T = 0, cs = C;
+    for (int cand : {4, 2, 1}) {
+        if (cand * o.tstride > 512) continue;
+        int c = C;
+        for (win_stage(o, cand, c); c > 16 && (o.stage_bytes > kStageCap || (C / c > 1 && 2 * o.stage_bytes > lim));
+             win_stage(o, cand, c))
+            c /= 2;
+        if ((C / c > 1 ? 2 : 1) * o.stage_bytes <= lim) {
             T = cand;
+            cs = c;
             break;
         }
     }
+    if (T == 0) return false;
+    const int nstages = C / cs;
+    o.nbuf = nstages > 1 ? 2 : 1;
     win_stage(o, T, cs);
     if (o.nbuf * o.stage_bytes > lim || o.gs >= (1 << 18)) return false;
     const long long xt = (Q + T * TM - 1) / (T * TM);
-    int z = 1;   // split the stages over CTAs while the grid leaves SMs idle
-    while (xt * ntn * z < 2LL * sms && z * 2 <= nstages && z * 2 <= max_splits) z *= 2;
+    int z = 1;
+    while (xt * ntn * z < sms && z * 2 <= nstages && z * 2 <= max_splits) z *= 2;
     o.spz = nstages / z;
     wp.grid = dim3((unsigned)xt, (unsigned)ntn, (unsigned)z);
     wp.smem = (size_t)o.nbuf * o.stage_bytes;
