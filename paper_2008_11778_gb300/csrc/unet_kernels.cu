@@ -590,7 +590,31 @@ __device__ __forceinline__ void win_copy_stage(const WinOp &o, const unsigned sh
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(WT) k_conv_win(const WinOp o, const unsigned short *t, const unsigned short *w,
+// One 128 x N x 16 MMA into tensor memory; the accumulate flag is an immediate
+// (ACC 0: D = A B, 1: D += A B), so the issue loop spends no predicate set-up.
+template <int ACC>
+__device__ __forceinline__ void mma_f16(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc)
+{
+    if (ACC)
+        asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;" ::"r"(d), "l"(a), "l"(b), "r"(idesc)
+                     : "memory");
+    else
+        asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 0;" ::"r"(d), "l"(a), "l"(b), "r"(idesc)
+                     : "memory");
+}
+
+// The T tiles of one (tap, 16-channel) step: tile t's A starts 128 rows (128 in
+// 16-byte units) further on, its accumulator T_STRIDE columns further on.
+template <int T, int ACC>
+__device__ __forceinline__ void mma_tiles(unsigned tmem, int tstride, unsigned long long ad, unsigned long long bd,
+                                          unsigned idesc)
+{
+#pragma unroll
+    for (int tt = 0; tt < T; ++tt) mma_f16<ACC>(tmem + (unsigned)(tt * tstride), ad + (unsigned long long)(tt * 128), bd, idesc);
+}
+
+template <int T>
+__global__ void __launch_bounds__(WT, 2) k_conv_win(const WinOp o, const unsigned short *t, const unsigned short *w,
                                                  float *out, int *err)
 {
     extern __shared__ __align__(1024) unsigned char dsm[];
@@ -600,9 +624,9 @@ __global__ void __launch_bounds__(WT) k_conv_win(const WinOp o, const unsigned s
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, half = warp >> 2;   // tensor-memory lane quadrant; column-chunk parity
     const int Wps = o.wps, Hp = o.H + 2, G = 1 << o.lg_g;
-    const int q0 = blockIdx.x * (o.T * TM), n0 = blockIdx.y * o.tn, s0 = blockIdx.z * o.spz;
+    const int q0 = blockIdx.x * (T * TM), n0 = blockIdx.y * o.tn, s0 = blockIdx.z * o.spz;
     const int ns = min(o.spz, o.C / o.cs - s0);   // stages of this CTA
-    const int tcols = win_tmem_cols(o.T * o.tstride);
+    const int tcols = win_tmem_cols(T * o.tstride);
     const unsigned sm0 = tc_smem(dsm);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&tmem_sh)),
@@ -654,17 +678,18 @@ __global__ void __launch_bounds__(WT) k_conv_win(const WinOp o, const unsigned s
                 // the innermost loop, so consecutive MMAs feed different accumulators.
                 unsigned long long ad = tc_desc(base + r0 * 16, o.gs, 128);
                 unsigned long long bd = tc_desc(base + o.wbytes + tap * G * o.tn * 16, o.tn * 16, 128);
-                for (int j = 0; j < o.cs / 16; ++j) {
-                    const unsigned accum = (s > 0 || tap > 0 || j > 0) ? 1u : 0u;
-                    for (int tt = 0; tt < o.T; ++tt)
-                        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-                                         tmem + (unsigned)(tt * o.tstride)),
-                                     "l"(ad + (unsigned long long)(tt * (TM * 16 >> 4))), "l"(bd), "r"(idesc),
-                                     "r"(accum)
-                                     : "memory");
+                const unsigned long long dB = (unsigned long long)((2 * o.tn * 16) >> 4);
+                int j = 0;
+                if (s == 0 && tap == 0) {   // the first step of each accumulator overwrites it
+                    mma_tiles<T, 0>(tmem, o.tstride, ad, bd, idesc);
                     ad += dA;
-                    bd += (unsigned long long)((2 * o.tn * 16) >> 4);
+                    bd += dB;
+                    j = 1;
+                }
+                for (; j < o.cs / 16; ++j) {
+                    mma_tiles<T, 1>(tmem, o.tstride, ad, bd, idesc);
+                    ad += dA;
+                    bd += dB;
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -688,7 +713,7 @@ __global__ void __launch_bounds__(WT) k_conv_win(const WinOp o, const unsigned s
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float *dst = out + (long long)blockIdx.z * o.B * o.H * o.W * o.N;
-        for (int t = 0; t < o.T; ++t) {
+        for (int t = 0; t < T; ++t) {
             const int q = q0 + t * TM + quad * 32 + lane;
             const int ra = q / Wps, px = q - ra * Wps, bi = ra / Hp, py = ra - bi * Hp;
             const long long pixel = (bi < o.B && py >= 1 && py <= o.H && px >= 1 && px <= o.W)
@@ -763,7 +788,9 @@ int win_smem_limit()
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) lim = 0;
         lim -= 4096;   // the kernel's static shared memory and the alignment of the dynamic block
-        if (lim > 0 && cudaFuncSetAttribute(k_conv_win, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess)
+        if (lim > 0 && (cudaFuncSetAttribute(k_conv_win<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+                        cudaFuncSetAttribute(k_conv_win<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+                        cudaFuncSetAttribute(k_conv_win<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess))
             lim = 0;
     }
     return lim;
@@ -854,7 +881,8 @@ bool win_plan(const __nv_bfloat16 *t, const __nv_bfloat16 *w, ConvGeom g, int C,
 int win_launch(const WinPlan &wp, float *out, cudaStream_t st)
 {
     count_launch();
-    k_conv_win<<<wp.grid, WT, wp.smem, st>>>(wp.o, wp.t, wp.w, out, unet_error_word());
+    auto kern = wp.o.T == 4 ? k_conv_win<4> : wp.o.T == 2 ? k_conv_win<2> : k_conv_win<1>;
+    kern<<<wp.grid, WT, wp.smem, st>>>(wp.o, wp.t, wp.w, out, unet_error_word());
     return (int)wp.grid.z;
 }
 
@@ -924,7 +952,7 @@ __device__ __forceinline__ void wg_load_stage(const WgOp &o, int p0, int m0, int
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(WT) k_wgrad_win(const WgOp o, float *out, int *err)
+__global__ void __launch_bounds__(WT, 1) k_wgrad_win(const WgOp o, float *out, int *err)
 {
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ unsigned long long bars[2];
@@ -981,15 +1009,20 @@ __global__ void __launch_bounds__(WT) k_wgrad_win(const WgOp o, float *out, int 
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) bd[tap] = tc_desc(xbase + ((tap / 3) * Wp + tap % 3) * 16, 128, o.gs);
             const unsigned long long dA = (unsigned long long)((2 * lbo_a) >> 4);
-            for (int kk = 0; kk < o.pb / 16; ++kk) {
-                const unsigned accum = (s > 0 || kk > 0) ? 1u : 0u;
+            int kk = 0;
+            if (s == 0) {   // the first K step overwrites the nine accumulators
 #pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
-                    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-                                     tmem + (unsigned)(tap * o.tstride)),
-                                 "l"(ad), "l"(bd[tap]), "r"(idesc), "r"(accum)
-                                 : "memory");
+                    mma_f16<0>(tmem + (unsigned)(tap * o.tstride), ad, bd[tap], idesc);
+                    bd[tap] += 16;
+                }
+                ad += dA;
+                kk = 1;
+            }
+            for (; kk < o.pb / 16; ++kk) {
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    mma_f16<1>(tmem + (unsigned)(tap * o.tstride), ad, bd[tap], idesc);
                     bd[tap] += 16;
                 }
                 ad += dA;
