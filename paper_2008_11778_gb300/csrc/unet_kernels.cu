@@ -11,7 +11,12 @@
 //   upconv2x2 forward M = pixels_in, N = 4 Cout, K = Cin      (output scattered to the 2x2 children)
 //   upconv2x2 dgrad   M = pixels_in, N = Cin,    K = 4 Cout   (gathers the 2x2 children)
 //   upconv2x2 wgrad   M = Cin,       N = 4 Cout, K = pixels_in
-// CTA tile 128 x 64, K chunks of 32; see k_gemm_tc.
+// Two forms:
+//   * k_conv_win / k_wgrad_win: the 3x3 layers whose channels are 16 times a
+//     power of two, as windowed GEMMs -- the padded input is staged once per
+//     CTA and every tap reads it at a row offset (no im2col); see k_conv_win;
+//   * k_gemm_tc: the first layer (2 input channels) and the upconvs, with the
+//     operands gathered per K chunk of 32 (CTA tile 128 x 64).
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
