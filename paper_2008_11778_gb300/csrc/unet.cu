@@ -204,35 +204,49 @@ __global__ void k_colsum_partial(const bf16 *x, const float *wrow, long long P, 
 
 __global__ void k_maxpool(const bf16 *x, int B, int H, int W, int C, bf16 *y, unsigned char *arg)
 {
-    const long long n = (long long)B * (H / 2) * (W / 2) * C;
-    GRID_LOOP(i, n) {
-        const int c = (int)(i % C);
-        const long long p = i / C;
-        const int xo = (int)(p % (W / 2)), yo = (int)((p / (W / 2)) % (H / 2)), b = (int)(p / ((long long)(W / 2) * (H / 2)));
-        float best = -INFINITY;
-        int bi = 0;
-        for (int q = 0; q < 4; ++q) {
-            const float v = __bfloat162float(x[(((long long)b * H + 2 * yo + q / 2) * W + 2 * xo + (q & 1)) * C + c]);
-            if (v > best) {
-                best = v;
-                bi = q;
+    const int Ho = H / 2, Wo = W / 2, n8 = B * Ho * Wo * (C / 8);
+    GRID_LOOP(i, n8) {   // 8 channels of one output pixel
+        const int e = 8 * (int)i, p = e / C, c = e - p * C;
+        const int xo = p % Wo, yo = (p / Wo) % Ho, b = p / (Wo * Ho);
+        float best[8];
+        unsigned bi[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) best[j] = -INFINITY, bi[j] = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {   // (0,0), (0,1), (1,0), (1,1): the first maximum wins
+            const uint4 u = *reinterpret_cast<const uint4 *>(
+                x + (((long long)b * H + 2 * yo + q / 2) * W + 2 * xo + (q & 1)) * C + c);
+            const unsigned wv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float v = __uint_as_float(j & 1 ? wv[j / 2] & 0xFFFF0000u : wv[j / 2] << 16);
+                if (v > best[j]) {
+                    best[j] = v;
+                    bi[j] = q;
+                }
             }
         }
-        y[i] = __float2bfloat16_rn(best);
-        arg[i] = (unsigned char)bi;
+        *reinterpret_cast<uint4 *>(y + e) = bf16x8(best);
+        *reinterpret_cast<uint2 *>(arg + e) = make_uint2(bi[0] | (bi[1] << 8) | (bi[2] << 16) | (bi[3] << 24),
+                                                         bi[4] | (bi[5] << 8) | (bi[6] << 16) | (bi[7] << 24));
     }
 }
 
 // g_fine (FP32 accumulator, [B][H][W][C]) += scatter of dy (FP32) at the argmax
 __global__ void k_maxpool_back(const float *dy, const unsigned char *arg, int B, int H, int W, int C, float *gx)
 {
-    const long long n = (long long)B * (H / 2) * (W / 2) * C;
-    GRID_LOOP(i, n) {
-        const int c = (int)(i % C);
-        const long long p = i / C;
-        const int xo = (int)(p % (W / 2)), yo = (int)((p / (W / 2)) % (H / 2)), b = (int)(p / ((long long)(W / 2) * (H / 2)));
-        const int q = arg[i];
-        gx[(((long long)b * H + 2 * yo + q / 2) * W + 2 * xo + (q & 1)) * C + c] += dy[i];
+    const int Ho = H / 2, Wo = W / 2, n8 = B * Ho * Wo * (C / 8);
+    GRID_LOOP(i, n8) {   // 8 channels of one coarse pixel; each goes to its own fine cell
+        const int e = 8 * (int)i, p = e / C, c = e - p * C;
+        const int xo = p % Wo, yo = (p / Wo) % Ho, b = p / (Wo * Ho);
+        float d[8];
+        load8(dy + e, d);
+        const uint2 a = *reinterpret_cast<const uint2 *>(arg + e);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int q = (int)(((j < 4 ? a.x : a.y) >> (8 * (j & 3))) & 0xFFu);
+            gx[(((long long)b * H + 2 * yo + q / 2) * W + 2 * xo + (q & 1)) * C + c + j] += d[j];
+        }
     }
 }
 
@@ -621,7 +635,7 @@ void forward(aafwi_unet *u, const float *xin, int B, cudaStream_t st)
         conv_fwd(u, u->L[li++], x, B, H, W, u->ea[l], st);
         conv_fwd(u, u->L[li++], u->ea[l], B, H, W, u->eb[l], st);
         count_launch();
-        k_maxpool<<<nblk((long long)B * H / 2 * W / 2 * Cl(u, l)), ET, 0, st>>>(u->eb[l], B, H, W, Cl(u, l), u->pool[l], u->arg[l]);
+        k_maxpool<<<nblk((long long)B * H / 2 * W / 2 * Cl(u, l) / 8), ET, 0, st>>>(u->eb[l], B, H, W, Cl(u, l), u->pool[l], u->arg[l]);
         x = u->pool[l];
     }
     conv_fwd(u, u->L[li++], x, B, Hl(u, 3), Wl(u, 3), u->ba, st);
@@ -680,7 +694,7 @@ void backward(aafwi_unet *u, int B, cudaStream_t st)
     for (int l = 2; l >= 0; --l) {     // encoder levels, coarsest first
         const int H = Hl(u, l), W = Wl(u, l), Cv = Cl(u, l);
         count_launch();
-        k_maxpool_back<<<nblk((long long)B * H / 2 * W / 2 * Cv), ET, 0, st>>>(u->gemm, u->arg[l], B, H, W, Cv,
+        k_maxpool_back<<<nblk((long long)B * H / 2 * W / 2 * Cv / 8), ET, 0, st>>>(u->gemm, u->arg[l], B, H, W, Cv,
                                                                                 gskip[l]);
         conv_back(u, u->L[li--], u->ea[l], u->eb[l], gskip[l], B, H, W, true, st);          // enc b
         const bf16 *xin = l == 0 ? u->xin : u->pool[l - 1];
