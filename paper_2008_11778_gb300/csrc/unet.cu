@@ -41,6 +41,9 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 constexpr int ET = 256;
+// The 2-channel network input is stored with XIN_C channels (the rest zero),
+// so that the first 3x3 layer runs the windowed tensor-core GEMMs too.
+constexpr int XIN_C = 16;
 
 inline int nblk(long long n) { return (int)std::min<long long>((n + ET - 1) / ET, 65535LL * 8); }
 
@@ -304,14 +307,30 @@ __global__ void k_transpose_up(const bf16 *w, int Cin, int N4, bf16 *wt)
 // input [B][2][H][W] FP32 (NCHW) -> [B][H][W][2] BF16
 __global__ void k_pack_input(const float *x, int B, int H, int W, bf16 *y)
 {
-    const long long n = (long long)B * H * W;
-    GRID_LOOP(i, n * 2) {
-        const int c = (int)(i % 2);
-        const long long p = i / 2;
-        const long long hw = (long long)H * W;
+    const long long hw = (long long)H * W, n = B * hw;
+    GRID_LOOP(p, n) {   // pixel p: channels 0, 1 from the two input planes, 2 .. XIN_C - 1 zero
         const long long b = p / hw, r = p - b * hw;
-        y[i] = __float2bfloat16_rn(x[(b * 2 + c) * hw + r]);
+        const unsigned c0 = __bfloat16_as_ushort(__float2bfloat16_rn(x[(b * 2) * hw + r]));
+        const unsigned c1 = __bfloat16_as_ushort(__float2bfloat16_rn(x[(b * 2 + 1) * hw + r]));
+        uint4 *d = reinterpret_cast<uint4 *>(y + p * XIN_C);
+        d[0] = make_uint4(c0 | (c1 << 16), 0, 0, 0);
+        d[1] = make_uint4(0, 0, 0, 0);
     }
+}
+
+// first-layer weights w [Cout][9][2] -> wp [Cout][9][XIN_C] (zero beyond channel 1)
+__global__ void k_pad_w0(const bf16 *w, int Cout, bf16 *wp)
+{
+    GRID_LOOP(i, (long long)Cout * 9 * XIN_C) {
+        const int c = (int)(i % XIN_C);
+        wp[i] = c < 2 ? w[(i / XIN_C) * 2 + c] : __float2bfloat16_rn(0.f);
+    }
+}
+
+// first-layer weight gradient: g [Cout][9][2] <- gp [Cout][9][XIN_C], channels 0, 1
+__global__ void k_unpad_w0(const float *gp, int Cout, float *g)
+{
+    GRID_LOOP(i, (long long)Cout * 9 * 2) g[i] = gp[(i / 2) * XIN_C + (i % 2)];
 }
 
 // head: out[p] = sum_c x[p][c] w[c] + b   (FP32)
@@ -494,6 +513,7 @@ struct aafwi_unet {
     bf16 *gb1 = nullptr, *gb2 = nullptr;       // BF16 activation gradients
     double *lpart = nullptr, *loss = nullptr;
     float *bpart = nullptr;   // column-sum block partials [COLSUM_BLOCKS][8 C + 1]
+    bf16 *w0p = nullptr;      // first-layer weights padded to XIN_C input channels
     bool retired = false;   // a tensor-core wait ran out: every later call is refused
     std::string msg;
 };
@@ -547,9 +567,12 @@ inline int Cl(const aafwi_unet *u, int l) { return u->C << l; }
 const bf16 *wb(const aafwi_unet *u, const Conv &c) { return u->Pb + c.w; }
 
 // forward of one 3x3 conv + bias + ReLU into y
-void conv_fwd(aafwi_unet *u, const Conv &c, const bf16 *x, int B, int H, int W, bf16 *y, cudaStream_t st)
+// (w, cin: the first layer's padded weights and input channels; NULL / 0: the layer's own)
+void conv_fwd(aafwi_unet *u, const Conv &c, const bf16 *x, int B, int H, int W, bf16 *y, cudaStream_t st,
+              const bf16 *w = nullptr, int cin = 0)
 {
-    const int s = unet_conv3_fwd(x, wb(u, c), B, H, W, c.Cin, c.Cout, u->P + c.b, y, u->gemm, u->gemm_size, st);
+    const int s = unet_conv3_fwd(x, w ? w : wb(u, c), B, H, W, cin ? cin : c.Cin, c.Cout, u->P + c.b, y, u->gemm,
+                                 u->gemm_size, st);
     if (s > 0) {   // split slices: sum, bias, ReLU, BF16
         const long long MN = (long long)B * H * W * c.Cout;
         count_launch();
@@ -596,15 +619,25 @@ int wgrad_cap(const aafwi_unet *u, const Conv &c) { return (int)std::max(1LL, st
 
 // Backward of y = relu(conv3(x) + b): gy (FP32 [P][Cout]) -> dW, db (into u->G),
 // returns gx in FP32 (u->gemm, its split slices summed into the first) when want_gx.
+// xc: channels of x as stored (the first layer's padded input), 0: c.Cin
 void conv_back(aafwi_unet *u, const Conv &c, const bf16 *x, const bf16 *y, const float *gy, int B, int H, int W,
-               bool want_gx, cudaStream_t st)
+               bool want_gx, cudaStream_t st, int xc = 0)
 {
     const long long P = (long long)B * H * W;
     count_launch();
     k_relu_back<<<nblk(P * c.Cout / 8), ET, 0, st>>>(gy, 1, (int)(P * c.Cout / 8), y, u->gb1);
     bias_grad(u, u->gb1, P, c.Cout, u->G + c.b, st);
-    const int s = unet_conv3_wgrad(u->gb1, x, B, H, W, c.Cin, c.Cout, wgrad_cap(u, c), u->gemm, st);
-    sum_slices(u->gemm, s, c.nw(), u->G + c.w, st);
+    if (xc && xc != c.Cin) {   // weight gradient at xc input channels, then the first c.Cin of them
+        const long long nwp = 9LL * xc * c.Cout;
+        const int cap = (int)std::max(1LL, std::min(1024LL, u->gemm_size / nwp));
+        const int s = unet_conv3_wgrad(u->gb1, x, B, H, W, xc, c.Cout, cap, u->gemm, st);
+        sum_slices(u->gemm, s, nwp, u->bpart, st);
+        count_launch();
+        k_unpad_w0<<<nblk(c.nw()), ET, 0, st>>>(u->bpart, c.Cout, u->G + c.w);
+    } else {
+        const int s = unet_conv3_wgrad(u->gb1, x, B, H, W, c.Cin, c.Cout, wgrad_cap(u, c), u->gemm, st);
+        sum_slices(u->gemm, s, c.nw(), u->G + c.w, st);
+    }
     if (want_gx) {
         count_launch();
         bf16 *wt = u->Wt;
@@ -627,12 +660,15 @@ void up_back(aafwi_unet *u, const Conv &c, const bf16 *x, const bf16 *gy, int B,
 void forward(aafwi_unet *u, const float *xin, int B, cudaStream_t st)
 {
     count_launch();
-    k_pack_input<<<nblk((long long)B * u->H * u->W * 2), ET, 0, st>>>(xin, B, u->H, u->W, u->xin);
+    k_pack_input<<<nblk((long long)B * u->H * u->W), ET, 0, st>>>(xin, B, u->H, u->W, u->xin);
+    count_launch();
+    k_pad_w0<<<nblk(9LL * XIN_C * u->C), ET, 0, st>>>(wb(u, u->L[0]), u->C, u->w0p);
     const bf16 *x = u->xin;
     int li = 0;
     for (int l = 0; l < 3; ++l) {
         const int H = Hl(u, l), W = Wl(u, l);
-        conv_fwd(u, u->L[li++], x, B, H, W, u->ea[l], st);
+        if (l == 0) conv_fwd(u, u->L[li++], x, B, H, W, u->ea[l], st, u->w0p, XIN_C);
+        else conv_fwd(u, u->L[li++], x, B, H, W, u->ea[l], st);
         conv_fwd(u, u->L[li++], u->ea[l], B, H, W, u->eb[l], st);
         count_launch();
         k_maxpool<<<nblk((long long)B * H / 2 * W / 2 * Cl(u, l) / 8), ET, 0, st>>>(u->eb[l], B, H, W, Cl(u, l), u->pool[l], u->arg[l]);
@@ -698,7 +734,7 @@ void backward(aafwi_unet *u, int B, cudaStream_t st)
                                                                                 gskip[l]);
         conv_back(u, u->L[li--], u->ea[l], u->eb[l], gskip[l], B, H, W, true, st);          // enc b
         const bf16 *xin = l == 0 ? u->xin : u->pool[l - 1];
-        conv_back(u, u->L[li--], xin, u->ea[l], u->gemm, B, H, W, l > 0, st);             // enc a
+        conv_back(u, u->L[li--], xin, u->ea[l], u->gemm, B, H, W, l > 0, st, l == 0 ? XIN_C : 0);   // enc a
     }
 }
 
@@ -769,7 +805,7 @@ int aafwi_unet_create(int Bmax, int H, int W, int C, aafwi_unet **out)
     }
     u->gemm_size = gs;
     bool ok = ualloc(u, &u->P, off) && ualloc(u, &u->G, off) && ualloc(u, &u->Mm, off) && ualloc(u, &u->Vv, off) &&
-              ualloc(u, &u->Pb, off) && ualloc(u, &u->Wt, maxw) && ualloc(u, &u->xin, P0 * 2) &&
+              ualloc(u, &u->Pb, off) && ualloc(u, &u->Wt, maxw) && ualloc(u, &u->xin, P0 * XIN_C) && ualloc(u, &u->w0p, 9LL * XIN_C * C) &&
               ualloc(u, &u->gemm, gs) && ualloc(u, &u->gacc, P0 * 8 * C) && ualloc(u, &u->gacc2, P0 * 2 * C) &&
               ualloc(u, &u->gb1, P0 * 8 * C) && ualloc(u, &u->gb2, P0 * 8 * C) && ualloc(u, &u->out, P0) &&
               ualloc(u, &u->dout, P0) && ualloc(u, &u->lpart, 4096) && ualloc(u, &u->loss, 1) &&
