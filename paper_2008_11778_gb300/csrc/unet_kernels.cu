@@ -15,8 +15,8 @@
 //   * k_conv_win / k_wgrad_win: the 3x3 layers whose channels are 16 times a
 //     power of two, as windowed GEMMs -- the padded input is staged once per
 //     CTA and every tap reads it at a row offset (no im2col); see k_conv_win;
-//   * k_gemm_tc: the first layer (2 input channels) and the upconvs, with the
-//     operands gathered per K chunk of 32 (CTA tile 128 x 64).
+//   * k_gemm_tc: the upconvs and any 3x3 layer with other channel counts, with
+//     the operands gathered per K chunk of 32 (CTA tile 128 x 64).
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
